@@ -1,0 +1,112 @@
+/*
+ * cq_oracle.h -- plain, slow CPU oracle for filter / group-by / aggregate
+ * queries over lightweight-compressed columns.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA library: it decompresses every
+ * referenced column to flat int64 rows with its own decoders and evaluates
+ * the query row by row, which is the plain definition of what the
+ * compressed-domain method computes exactly (Sections 6-7 of the paper:
+ * selection, grouping, aggregation; Appendix A.2 worked example).
+ *
+ * Column encodings (Section 3, "Basic Encodings"):
+ *   RLE    run values + exclusive run ends (row r is in run i iff
+ *          ends[i-1] <= r < ends[i]); ends strictly increasing, last == n_rows.
+ *   INDEX  sorted unique positions + values; unlisted rows hold a default.
+ *   DICT   bytewise-sorted unique strings; per-row codes bit-packed LSB-first.
+ *   PACKED per-row unsigned offsets bit-packed LSB-first; value = base + offset.
+ *   PLAIN  one value per row.
+ * All integer inputs are passed as int64 (the test wrapper widens them).
+ */
+#ifndef CQ_ORACLE_H
+#define CQ_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_RLE = 1, ORC_DICT = 2, ORC_INDEX = 3, ORC_PACKED = 4, ORC_PLAIN = 5 };
+enum { ORC_LT = 0, ORC_LE, ORC_GT, ORC_GE, ORC_EQ, ORC_NE, ORC_BETWEEN, ORC_IN };
+enum { ORC_SUM = 0, ORC_COUNT, ORC_MIN, ORC_MAX, ORC_AVG };
+enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_OVERFLOW = -6 };
+
+typedef struct {
+  int32_t enc;
+  uint64_t n_rows;
+  /* RLE */
+  const int64_t* run_values;
+  const int64_t* run_ends;
+  uint64_t n_runs;
+  /* PACKED and DICT codes */
+  const uint32_t* words;
+  uint64_t n_words;
+  uint32_t bit_width;
+  int64_t base;
+  /* INDEX */
+  const int64_t* idx_values;
+  const int64_t* positions;
+  uint64_t nnz;
+  int64_t default_value;
+  /* PLAIN */
+  const int64_t* values;
+  /* DICT strings: entry i is dict_bytes[dict_offsets[i] .. dict_offsets[i+1]) */
+  const uint8_t* dict_bytes;
+  const uint64_t* dict_offsets;
+  uint32_t n_entries;
+} orc_column;
+
+typedef struct {
+  uint32_t col;
+  int32_t op;
+  int64_t lo, hi;                 /* integer literals; BETWEEN is inclusive */
+  const int64_t* in_ints;         /* IN list on an integer column */
+  uint32_t n_in;
+  const uint8_t* const* strs;     /* string literals on a DICT column */
+  const uint32_t* str_lens;
+  uint32_t n_strs;
+} orc_pred;
+
+typedef struct {
+  int32_t op;
+  uint32_t col;                   /* ignored for COUNT(*) */
+} orc_agg;
+
+typedef struct orc_result orc_result;
+
+/* Decode rows [row_begin, row_end) of one column to int64 (DICT: codes). */
+int orc_decode(const orc_column* c, uint64_t row_begin, uint64_t row_end, int64_t* out);
+
+/* Evaluate the query.  row_ranges (optional, n_ranges pairs [b,e) in row
+ * order) restricts the scan to those rows; n_threads >= 1 splits the scan
+ * into fixed 1M-row chunks whose per-chunk maps are merged exactly. */
+int orc_query(const orc_column* cols, uint32_t n_cols, uint64_t n_rows,
+              const orc_pred* preds, uint32_t n_preds,
+              const uint32_t* group_by, uint32_t n_group_by,
+              const orc_agg* aggs, uint32_t n_aggs,
+              const uint64_t* row_ranges, uint32_t n_ranges,
+              uint32_t n_threads, orc_result** out);
+
+int orc_result_status(const orc_result* r);
+uint64_t orc_result_num_groups(const orc_result* r);
+/* key column k of every group, groups in ascending lexicographic key order */
+void orc_result_keys(const orc_result* r, uint32_t k, int64_t* out);
+/* aggregate a: SUM/MIN/MAX as int64, COUNT as uint64 bits, AVG as double */
+void orc_result_agg(const orc_result* r, uint32_t a, void* out);
+/* exact 128-bit SUM of aggregate a (lo, hi words) for every group */
+void orc_result_sum128(const orc_result* r, uint32_t a, uint64_t* lo, int64_t* hi);
+void orc_result_free(orc_result* r);
+
+/* Common refinement of k RLE columns' run boundaries (Section 6 Alignment):
+ * the sorted distinct union of all exclusive run ends, and for each segment
+ * and column the index of the run covering it.  Call once with seg_ends and
+ * ridx NULL to get the count, then again with buffers of that size
+ * (ridx is column-major: ridx[j * S + s]). */
+int orc_align(uint32_t k, const int64_t* const* run_ends, const uint64_t* n_runs,
+              uint64_t n_rows, uint64_t* n_segments, int64_t* seg_ends, int64_t* ridx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
