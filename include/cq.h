@@ -1,0 +1,313 @@
+/*
+ * cq.h -- C ABI of the compressed-column query library (GB300, sm_103a).
+ *
+ * The library runs SQL filter -> group-by -> aggregate queries directly on
+ * lightweight-compressed columns without decompressing them, the method of
+ * "GPU Acceleration of SQL Analytics on Compressed Data" (arXiv 2506.10092):
+ * encodings of Section 3, alignment of run boundaries of Section 6 (the
+ * common refinement of several RLE columns' runs), selection of Section 6
+ * and grouping / aggregation of Section 7 (SUM = value x run length,
+ * COUNT = run length, MIN / MAX on values, AVG = SUM / COUNT).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a cq_status; CQ_OK is 0, errors are negative.  A
+ *    human-readable message for the last error of the calling thread is
+ *    available from cq_last_error().  No C++ exception crosses the ABI.
+ *  - Handles are created by *_create / cq_table_bind / cq_query_run* and
+ *    released by the matching *_destroy; all handles belong to the caller.
+ *  - "Device" pointers are CUDA device addresses on the context's device;
+ *    "host" pointers are ordinary (pageable or pinned) host memory.
+ *  - Integer results are exact.  SUM is accumulated in 128 bits and
+ *    reported as int64; a group whose SUM does not fit int64 makes the query
+ *    fail with CQ_ERR_OVERFLOW.  AVG is the exact 128-bit SUM rounded once to
+ *    double (nearest even) divided by the COUNT converted to double.
+ *  - The library never falls back to the CPU: with no usable CUDA device the
+ *    context cannot be created (CQ_ERR_CUDA).
+ */
+#ifndef CQ_H
+#define CQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cq_ctx cq_ctx;
+typedef struct cq_column cq_column;
+typedef struct cq_table cq_table;
+typedef struct cq_result cq_result;
+
+typedef enum {
+  CQ_OK = 0,
+  CQ_ERR_INVALID_ARG = -1,   /* malformed argument, plan or column buffer */
+  CQ_ERR_UNSORTED = -2,      /* run ends / positions not strictly increasing */
+  CQ_ERR_SIZE_MISMATCH = -3, /* lengths disagree (run ends vs n_rows, table rows) */
+  CQ_ERR_OOM = -4,           /* device or host allocation failed */
+  CQ_ERR_CUDA = -5,          /* a CUDA runtime call failed */
+  CQ_ERR_OVERFLOW = -6,      /* a SUM result does not fit int64 */
+  CQ_ERR_UNSUPPORTED = -7,   /* valid request outside what this build supports */
+  CQ_ERR_TABLE_FULL = -8,    /* group table capacity exceeded (device flag) */
+  CQ_ERR_TIMEOUT = -9,       /* a bounded device wait gave up (device flag) */
+  CQ_ERR_NOT_READY = -10,    /* cq_result_wait: still running when the timeout expired */
+  CQ_ERR_BUSY = -11          /* serving loop: admission refused, over the memory budget */
+} cq_status;
+
+typedef enum { CQ_I32 = 1, CQ_I64 = 2 } cq_dtype;
+
+/* mem_flags of the column constructors */
+enum {
+  CQ_MEM_HOST_COPY = 0,      /* buffers are host memory; the library copies them to the device */
+  CQ_MEM_DEVICE_BORROW = 1   /* buffers are device memory the caller keeps alive and unmodified
+                                until cq_column_destroy; each must be 16-byte aligned and readable
+                                up to the next 16-byte multiple of its length */
+};
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` (a cudaStream_t,
+ * may be NULL for the legacy default stream) is the stream used by calls that
+ * are not given one.  The context owns a stream-ordered memory pool from which
+ * all per-query scratch and result buffers are taken. */
+int cq_ctx_create(int device, void* cuda_stream, cq_ctx** out);
+int cq_ctx_destroy(cq_ctx* ctx);
+
+/* Number of streaming multiprocessors of the context's device. */
+int cq_ctx_num_sms(cq_ctx* ctx, uint32_t* out);
+
+/* Message describing the last failed call of the calling thread ("" if none).
+ * The pointer stays valid until the thread's next cq_* call. */
+const char* cq_last_error(void);
+
+/* ------------------------------------------------------------------ columns
+ * Section 3 ("Basic Encodings") of the paper.  All constructors validate the
+ * buffers (on the device for borrowed buffers) and record the column's value
+ * range, which the planner uses for dense group keys and exactness bounds.
+ * Creation is synchronous.  A column may be bound into several tables; it is
+ * released when the last table holding it and the caller have destroyed it. */
+
+/* RLE (Section 3.1): run i holds run_values[i] on rows
+ * [run_ends[i-1], run_ends[i]) (run_ends[-1] = 0).  run_ends are EXCLUSIVE
+ * ends -- the paper's inclusive end is run_ends[i] - 1 -- strictly
+ * increasing, and the last equals n_rows (a base-table column has no gaps).
+ * Adjacent runs may hold equal values.  val_t / end_t: CQ_I32 or CQ_I64.
+ * Errors: CQ_ERR_UNSORTED (ends not strictly increasing),
+ * CQ_ERR_SIZE_MISMATCH (last end != n_rows, n_runs == 0 with n_rows > 0). */
+int cq_column_create_rle(cq_ctx* ctx, cq_dtype val_t, const void* run_values,
+                         cq_dtype end_t, const void* run_ends, uint64_t n_runs,
+                         uint64_t n_rows, uint32_t mem_flags, cq_column** out);
+
+/* Dictionary-encoded strings (Section 2.1: strings are value- and
+ * dictionary-encoded to numeric codes).  The dictionary -- always HOST memory
+ * -- holds n_entries strings, entry i being dict_bytes[dict_offsets[i] ..
+ * dict_offsets[i+1]); entries must be sorted bytewise (unsigned lexicographic,
+ * a proper prefix sorts first) and unique, so code order is string order.
+ * Row r's code is field r of the LSB-first bit stream in packed_codes
+ * (n_words little-endian uint32; field r occupies stream bits
+ * [r*bit_width, (r+1)*bit_width), stream bit b is bit b%32 of word b/32).
+ * 1 <= bit_width <= 32; n_words >= ceil(n_rows*bit_width/32) rounded up to a
+ * multiple of 4 (borrowed buffers; copies are padded by the library).
+ * Errors: CQ_ERR_INVALID_ARG (bit width, short buffer, a code >= n_entries,
+ * dictionary not sorted / not unique). */
+int cq_column_create_dict(cq_ctx* ctx, const char* dict_bytes, const uint64_t* dict_offsets,
+                          uint32_t n_entries, const uint32_t* packed_codes, uint64_t n_words,
+                          uint32_t bit_width, uint64_t n_rows, uint32_t mem_flags,
+                          cq_column** out);
+
+/* Index encoding for sparse data (Section 3.1 Index; unlisted rows hold
+ * default_value, which makes it the Plain + Index composite of Section 3.2
+ * with a constant plain part): row positions[k] holds values[k]; positions
+ * are sorted, unique and < n_rows.  nnz may be 0 or n_rows.
+ * Errors: CQ_ERR_UNSORTED, CQ_ERR_INVALID_ARG (position out of range). */
+int cq_column_create_index(cq_ctx* ctx, cq_dtype val_t, const void* values,
+                           cq_dtype pos_t, const void* positions, uint64_t nnz,
+                           int64_t default_value, uint64_t n_rows, uint32_t mem_flags,
+                           cq_column** out);
+
+/* Bit-width reduction (Section 3.2, "centering"; here frame of reference with
+ * base = the minimum): row r holds base + field r of the LSB-first bit stream
+ * in words (layout as for dictionary codes), computed modulo 2^64.
+ * 1 <= bit_width <= 64.  logical_t is the column's declared type.
+ * Errors: CQ_ERR_INVALID_ARG (bit width, short buffer). */
+int cq_column_create_bitpacked(cq_ctx* ctx, cq_dtype logical_t, const uint32_t* words,
+                               uint64_t n_words, uint32_t bit_width, int64_t base,
+                               uint64_t n_rows, uint32_t mem_flags, cq_column** out);
+
+/* Plain (Section 3.1): one value per row. */
+int cq_column_create_plain(cq_ctx* ctx, cq_dtype t, const void* values, uint64_t n_rows,
+                           uint32_t mem_flags, cq_column** out);
+
+int cq_column_destroy(cq_column* col);
+
+/* Encoding of a column: 1 RLE, 2 dictionary, 3 index, 4 bit-packed, 5 plain. */
+int cq_column_encoding(const cq_column* col, uint32_t* enc);
+
+/* Bytes of the column's compressed device representation (strings excluded). */
+int cq_column_device_bytes(const cq_column* col, uint64_t* bytes);
+
+/* ------------------------------------------------------------------ tables */
+
+/* Bind n_cols columns (all with the same n_rows) into a table; column i of
+ * the table is cols[i].  The table holds a reference to each column.
+ * Errors: CQ_ERR_SIZE_MISMATCH (row counts differ), CQ_ERR_INVALID_ARG. */
+int cq_table_bind(cq_ctx* ctx, cq_column* const* cols, uint32_t n_cols, cq_table** out);
+int cq_table_destroy(cq_table* table);
+int cq_table_num_rows(const cq_table* table, uint64_t* n_rows);
+
+/* ------------------------------------------------------------------ plans
+ * A plan is the conjunction (AND) of predicates, each on one column, then
+ * GROUP BY the listed columns and the listed aggregates (Sections 6-7).
+ * Predicates on a dictionary column take string literals (strs); predicates
+ * on every other column take integer literals compared with the row's
+ * logical value.  Literals absent from a dictionary simply match nothing. */
+typedef enum {
+  CQ_LT = 0, CQ_LE = 1, CQ_GT = 2, CQ_GE = 3, CQ_EQ = 4, CQ_NE = 5,
+  CQ_BETWEEN = 6,  /* lo <= v <= hi (strings: strs[0] <= s <= strs[1]) */
+  CQ_IN = 7        /* v in in_ints[0..n_in) (strings: s in strs[0..n_strs)) */
+} cq_pred_op;
+
+typedef struct {
+  uint32_t col;                 /* table column index */
+  int32_t op;                   /* cq_pred_op */
+  int64_t lo, hi;               /* integer literals: comparisons use lo; BETWEEN uses lo..hi */
+  const int64_t* in_ints;       /* IN list on an integer column (host) */
+  uint32_t n_in;
+  const char* const* strs;      /* string literals on a dictionary column (host) */
+  const uint32_t* str_lens;     /* byte length of each literal; NULL = NUL-terminated */
+  uint32_t n_strs;
+} cq_predicate;
+
+typedef enum { CQ_SUM = 0, CQ_COUNT = 1, CQ_MIN = 2, CQ_MAX = 3, CQ_AVG = 4 } cq_agg_op;
+
+typedef struct {
+  int32_t op;                   /* cq_agg_op; SUM / AVG are rejected on dictionary columns */
+  uint32_t col;                 /* ignored for COUNT(*) */
+} cq_aggregate;
+
+typedef struct {
+  const cq_predicate* preds;  uint32_t n_preds;     /* <= 16 */
+  const uint32_t* group_by;   uint32_t n_group_by;  /* <= 8 */
+  const cq_aggregate* aggs;   uint32_t n_aggs;      /* <= 16 */
+} cq_plan;
+
+/* Execution choices; zero-initialise for the defaults. */
+typedef enum {
+  CQ_EXEC_FUSED = 0,                 /* compressed-domain fused kernel (the method) */
+  CQ_EXEC_DECOMPRESS_THEN_SCAN = 1   /* comparison path: expand every referenced column to
+                                        flat device arrays, then a row-wise scan */
+} cq_exec_mode;
+
+typedef struct {
+  int32_t mode;          /* cq_exec_mode */
+  uint32_t tile_rows;    /* rows per tile (multiple of 1024, <= 16384); 0 = default */
+  uint32_t ctas_per_sm;  /* 0 = default */
+  uint32_t stages;       /* bulk-copy pipeline depth (2..8); 0 = default */
+  uint32_t table_slots;  /* shared-memory group-table slots per CTA (power of 2); 0 = default */
+  uint32_t reserved[3];
+} cq_exec_options;
+
+/* ------------------------------------------------------------------ queries */
+
+/* Plan the query on `table` and enqueue its kernels on `cuda_stream`
+ * (NULL: the context's stream).  Asynchronous: returns once the work is
+ * enqueued; the result handle owns every device buffer of the query.
+ * Output columns are the group keys in group_by order, then the aggregates
+ * in plan order.  Groups are the distinct key tuples of rows that pass every
+ * predicate, in ascending lexicographic key order (dictionary keys by code,
+ * i.e. by string); a plan without GROUP BY yields exactly one row (COUNT 0,
+ * SUM 0, MIN / MAX / AVG 0 when nothing passes).
+ * Errors (synchronous): CQ_ERR_INVALID_ARG for a malformed plan,
+ * CQ_ERR_UNSUPPORTED when the dense key domain exceeds 2^24 groups. */
+int cq_query_run(cq_table* table, const cq_plan* plan, void* cuda_stream, cq_result** out);
+int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_exec_options* opts,
+                    void* cuda_stream, cq_result** out);
+
+/* Run n independent queries (tables[i], plans[i]) as ONE persistent fused
+ * launch over a shared work list of (query, tile) items, replayed from a
+ * cached CUDA graph when the same batch shape recurs.  results[i] receives
+ * the handle of query i.  Same semantics per query as cq_query_run. */
+int cq_batch_run(uint32_t n, cq_table* const* tables, const cq_plan* plans,
+                 const cq_exec_options* opts, void* cuda_stream, cq_result** results);
+
+/* Wait up to timeout_us microseconds (UINT64_MAX = forever) for the query
+ * to finish.  Returns CQ_OK, CQ_ERR_NOT_READY, or the query's own error
+ * (CQ_ERR_OVERFLOW, CQ_ERR_TABLE_FULL, CQ_ERR_TIMEOUT, CQ_ERR_INVALID_ARG
+ * for out-of-domain data met on the device, CQ_ERR_CUDA). */
+int cq_result_wait(cq_result* res, uint64_t timeout_us);
+
+/* Number of result rows (waits for the query). */
+int cq_result_num_groups(cq_result* res, uint64_t* n);
+
+/* Number of output columns and the byte width / kind of column i:
+ * kind 0 int64 (keys, SUM, MIN, MAX), 1 uint64 (COUNT), 2 double (AVG). */
+int cq_result_num_columns(cq_result* res, uint32_t* n);
+int cq_result_column_kind(cq_result* res, uint32_t out_col, uint32_t* kind);
+
+/* Copy output column out_col (num_groups x 8 bytes) to host_dst (waits). */
+int cq_result_fetch(cq_result* res, uint32_t out_col, void* host_dst, uint64_t dst_bytes);
+
+/* Device address of output column out_col (valid until cq_result_destroy). */
+int cq_result_device_column(cq_result* res, uint32_t out_col, const void** dptr);
+
+/* The dictionary string of key column key_col (must be a dictionary column)
+ * in result row `row`; the pointer is into the column's host dictionary. */
+int cq_result_key_string(cq_result* res, uint32_t key_col, uint64_t row,
+                         const char** s, uint32_t* len);
+
+/* Microseconds between the query's first and last kernel on the device
+ * (CUDA events on the query's stream; waits for the query). */
+int cq_result_device_time_us(cq_result* res, double* us);
+
+int cq_result_destroy(cq_result* res);
+
+/* ------------------------------------------------------------------ alignment
+ * Materialising form of the run-boundary alignment (Section 6, Alignment;
+ * Algorithm 1 generalised from two to k RLE columns): the segments are the
+ * common refinement of the k columns' runs -- the distinct union of all run
+ * ends -- and for every segment and column the index of the run covering it.
+ * cols: k RLE columns of equal n_rows.  seg_ends (int64[capacity]) and ridx
+ * (int64[k * capacity], column-major: ridx[j * capacity + s]) are DEVICE
+ * buffers; n_segments (host) receives the segment count.  When capacity is
+ * smaller than the count nothing is written past it and CQ_ERR_SIZE_MISMATCH
+ * is returned with *n_segments set (call with capacity 0 to size buffers).
+ * Synchronous. */
+int cq_align_segments(cq_ctx* ctx, cq_column* const* cols, uint32_t k, void* cuda_stream,
+                      int64_t* seg_ends, int64_t* ridx, uint64_t capacity,
+                      uint64_t* n_segments);
+
+/* ------------------------------------------------------------------ serving
+ * A serving loop that keeps tables resident, admits queries by their device
+ * memory footprint and batches the queries that arrive while others run
+ * (continuous batching over several streams).  Submission is thread-safe. */
+typedef struct cq_server cq_server;
+
+typedef struct {
+  uint64_t memory_budget_bytes;  /* admission limit on in-flight query scratch; 0 = 1 GiB */
+  uint32_t max_batch;            /* most queries per launch; 0 = 256 */
+  uint32_t n_streams;            /* concurrent launches in flight; 0 = 2 */
+  uint32_t max_wait_us;          /* how long a partial batch may wait for company; 0 = 50 */
+  uint32_t reserved[3];
+} cq_server_options;
+
+int cq_server_create(cq_ctx* ctx, const cq_server_options* opts, cq_server** out);
+
+/* Submit a query; *ticket identifies it.  The plan and its literals are
+ * copied.  CQ_ERR_BUSY when its footprint alone exceeds the budget. */
+int cq_server_submit(cq_server* srv, cq_table* table, const cq_plan* plan, uint64_t* ticket);
+
+/* Wait up to timeout_us for query `ticket`; on success *res receives its
+ * result handle (owned by the caller) and *latency_us the time from
+ * submission to completion observed by the serving loop. */
+int cq_server_wait(cq_server* srv, uint64_t ticket, uint64_t timeout_us,
+                   cq_result** res, double* latency_us);
+
+/* Launches issued and queries completed so far. */
+int cq_server_stats(cq_server* srv, uint64_t* launches, uint64_t* completed);
+
+int cq_server_destroy(cq_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CQ_H */

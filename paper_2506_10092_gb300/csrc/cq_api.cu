@@ -1,0 +1,1161 @@
+// cq_api.cu -- the C ABI of include/cq.h: handles, validation, the query
+// planner and the launch sequence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "cq_internal.h"
+
+namespace cq {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+int set_error(int status, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return status;
+}
+
+void clear_error() { g_err.clear(); }
+
+#define CQ_CUDA(call)                                                                           \
+  do {                                                                                          \
+    cudaError_t _e = (call);                                                                    \
+    if (_e != cudaSuccess)                                                                      \
+      return set_error(CQ_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(_e));            \
+  } while (0)
+
+// kernels (cq_columns.cu / cq_query.cu)
+cudaError_t run_column_check(const cq_column* c, void* d_out, cudaStream_t s);
+cudaError_t align_segments(cq_column* const* cols, uint32_t k, cudaStream_t s, void* scratch_counts,
+                           unsigned long long n_tiles, unsigned long long n_rows, long long* seg_ends,
+                           long long* ridx, unsigned long long capacity, unsigned long long* host_counts,
+                           unsigned long long* n_segments);
+cudaError_t expand_column(const cq_column* c, long long* out, cudaStream_t s, int num_sms);
+
+// ------------------------------------------------------------------ helpers
+typedef __int128 i128;
+
+static int cmp_bytes(const char* a, size_t la, const char* b, size_t lb) {
+  const size_t m = la < lb ? la : lb;
+  const int c = m ? memcmp(a, b, m) : 0;
+  if (c) return c < 0 ? -1 : 1;
+  return la == lb ? 0 : (la < lb ? -1 : 1);
+}
+
+static bool dtype_ok(int t) { return t == CQ_I32 || t == CQ_I64; }
+static size_t dsize(int t) { return t == CQ_I64 ? 8 : 4; }
+
+static uint64_t pad16(uint64_t bytes) { return (bytes + 15) / 16 * 16; }
+
+// Allocate library-owned device memory (padded to 16 bytes plus 16 of slack)
+// and fill it from host or device memory.
+static int own_copy(cq_ctx* ctx, const void* src, uint64_t bytes, bool from_device, void** dst) {
+  const uint64_t alloc = pad16(bytes) + 16;
+  void* p = nullptr;
+  if (cudaMalloc(&p, alloc) != cudaSuccess) return set_error(CQ_ERR_OOM, "cudaMalloc of %llu bytes failed", (unsigned long long)alloc);
+  cudaMemsetAsync(p, 0, alloc, ctx->stream);
+  if (bytes) {
+    cudaError_t e = cudaMemcpyAsync(p, src, bytes, from_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e != cudaSuccess) {
+      cudaFree(p);
+      return set_error(CQ_ERR_CUDA, "copy of column buffer failed: %s", cudaGetErrorString(e));
+    }
+  }
+  *dst = p;
+  return CQ_OK;
+}
+
+static int check_borrow(const void* p, const char* what) {
+  if (p && (reinterpret_cast<uintptr_t>(p) & 15))
+    return set_error(CQ_ERR_INVALID_ARG, "borrowed %s buffer is not 16-byte aligned", what);
+  return CQ_OK;
+}
+
+// Validate on the device and record the column's raw / logical ranges.
+static int finish_column(cq_column* c) {
+  cq_ctx* ctx = c->ctx;
+  void* d = nullptr;
+  CQ_CUDA(cudaMalloc(&d, 64));
+  struct {
+    int err, pad;
+    long long mn, mx;
+  } h{};
+  cudaError_t e = run_column_check(c, d, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "column check failed: %s", cudaGetErrorString(e));
+  if (h.err) {
+    const char* why = h.err == CQ_ERR_UNSORTED ? "run ends / positions are not strictly increasing"
+                      : h.err == CQ_ERR_SIZE_MISMATCH ? "last run end differs from n_rows"
+                      : c->enc == ENC_DICT ? "a code is not below the dictionary size"
+                                           : "a position is out of range";
+    return set_error(h.err, "column rejected: %s", why);
+  }
+  ColumnStats& st = c->stats;
+  const bool empty = h.mx < h.mn;
+  st.min_raw = empty ? 0 : h.mn;
+  st.max_raw = empty ? -1 : h.mx;
+  i128 lo = st.min_raw, hi = st.max_raw;
+  if (c->enc == ENC_PACKED) {
+    lo += c->base;
+    hi += c->base;
+    if (c->bit_width == 64) {  // 64-bit fields: raw range is already the logical value's
+      lo = (i128)st.min_raw + (i128)c->base;
+      hi = (i128)st.max_raw + (i128)c->base;
+    }
+  }
+  if (c->enc == ENC_INDEX && c->n < c->n_rows) {
+    if (empty) { lo = hi = c->base; }
+    else { lo = std::min(lo, (i128)c->base); hi = std::max(hi, (i128)c->base); }
+  }
+  const bool fits = lo >= (i128)LLONG_MIN && hi <= (i128)LLONG_MAX;
+  st.min_val = fits ? (int64_t)lo : LLONG_MIN;
+  st.max_val = fits ? (int64_t)hi : LLONG_MAX;
+  const i128 a = std::max(lo < 0 ? -lo : lo, hi < 0 ? -hi : hi);
+  st.max_abs_val = a > (i128)ULLONG_MAX ? ULLONG_MAX : (uint64_t)a;
+  if (c->enc == ENC_INDEX && c->n == c->n_rows && empty) st.max_abs_val = 0;
+  return CQ_OK;
+}
+
+}  // namespace cq
+
+using namespace cq;
+
+// ====================================================================== context
+extern "C" const char* cq_last_error(void) { return g_err.c_str(); }
+
+extern "C" int cq_ctx_create(int device, void* cuda_stream, cq_ctx** out) {
+  clear_error();
+  if (!out) return set_error(CQ_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0)
+    return set_error(CQ_ERR_CUDA, "no CUDA device is available (this library has no CPU path)");
+  if (device < 0 || device >= n) return set_error(CQ_ERR_INVALID_ARG, "device %d out of range", device);
+  CQ_CUDA(cudaSetDevice(device));
+  std::unique_ptr<cq_ctx> c(new cq_ctx);
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  CQ_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  int smem = 0;
+  CQ_CUDA(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  c->smem_optin = (size_t)smem;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  CQ_CUDA(cudaMemPoolCreate(&c->pool, &props));
+  uint64_t thr = UINT64_MAX;
+  CQ_CUDA(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  CQ_CUDA(query_kernel_set_smem(c->smem_optin));
+  *out = c.release();
+  return CQ_OK;
+}
+
+extern "C" int cq_ctx_destroy(cq_ctx* ctx) {
+  clear_error();
+  if (!ctx) return CQ_OK;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  delete ctx;
+  return CQ_OK;
+}
+
+extern "C" int cq_ctx_num_sms(cq_ctx* ctx, uint32_t* out) {
+  if (!ctx || !out) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  *out = (uint32_t)ctx->num_sms;
+  return CQ_OK;
+}
+
+// ====================================================================== columns
+static int new_column(cq_ctx* ctx, uint8_t enc, uint64_t n_rows, cq_column** out, std::unique_ptr<cq_column>* c) {
+  if (!ctx || !out) return set_error(CQ_ERR_INVALID_ARG, "NULL context or out");
+  *out = nullptr;
+  c->reset(new cq_column);
+  (*c)->ctx = ctx;
+  (*c)->enc = enc;
+  (*c)->n_rows = n_rows;
+  CQ_CUDA(cudaSetDevice(ctx->device));
+  return CQ_OK;
+}
+
+static void release_buffers(cq_column* c) {
+  if (c->owned) {
+    if (c->vals) cudaFree(c->vals);
+    if (c->ends) cudaFree(c->ends);
+  }
+  c->vals = c->ends = nullptr;
+}
+
+static int finish_or_release(std::unique_ptr<cq_column>& c, cq_column** out) {
+  int rc = finish_column(c.get());
+  if (rc != CQ_OK) {
+    release_buffers(c.get());
+    return rc;
+  }
+  *out = c.release();
+  return CQ_OK;
+}
+
+extern "C" int cq_column_create_rle(cq_ctx* ctx, cq_dtype val_t, const void* run_values, cq_dtype end_t,
+                                    const void* run_ends, uint64_t n_runs, uint64_t n_rows, uint32_t mem_flags,
+                                    cq_column** out) {
+  clear_error();
+  std::unique_ptr<cq_column> c;
+  int rc = new_column(ctx, ENC_RLE, n_rows, out, &c);
+  if (rc) return rc;
+  if (!dtype_ok(val_t) || !dtype_ok(end_t)) return set_error(CQ_ERR_INVALID_ARG, "bad dtype");
+  if (n_rows > 0 && n_runs == 0) return set_error(CQ_ERR_SIZE_MISMATCH, "no runs for %llu rows", (unsigned long long)n_rows);
+  if (n_rows == 0 && n_runs != 0) return set_error(CQ_ERR_SIZE_MISMATCH, "runs given for an empty column");
+  if (end_t == CQ_I32 && n_rows > (uint64_t)INT_MAX) return set_error(CQ_ERR_INVALID_ARG, "int32 run ends cannot address n_rows");
+  if (n_runs && (!run_values || !run_ends)) return set_error(CQ_ERR_INVALID_ARG, "NULL buffer");
+  c->val_t = val_t;
+  c->end_t = end_t;
+  c->n = n_runs;
+  if (mem_flags == CQ_MEM_DEVICE_BORROW) {
+    if ((rc = check_borrow(run_values, "run_values")) || (rc = check_borrow(run_ends, "run_ends"))) return rc;
+    c->vals = const_cast<void*>(run_values);
+    c->ends = const_cast<void*>(run_ends);
+  } else {
+    c->owned = true;
+    if ((rc = own_copy(ctx, run_values, n_runs * dsize(val_t), false, &c->vals))) return rc;
+    if ((rc = own_copy(ctx, run_ends, n_runs * dsize(end_t), false, &c->ends))) { release_buffers(c.get()); return rc; }
+  }
+  c->device_bytes = n_runs * (dsize(val_t) + dsize(end_t));
+  return finish_or_release(c, out);
+}
+
+extern "C" int cq_column_create_dict(cq_ctx* ctx, const char* dict_bytes, const uint64_t* dict_offsets,
+                                     uint32_t n_entries, const uint32_t* packed_codes, uint64_t n_words,
+                                     uint32_t bit_width, uint64_t n_rows, uint32_t mem_flags, cq_column** out) {
+  clear_error();
+  std::unique_ptr<cq_column> c;
+  int rc = new_column(ctx, ENC_DICT, n_rows, out, &c);
+  if (rc) return rc;
+  if (bit_width < 1 || bit_width > 32) return set_error(CQ_ERR_INVALID_ARG, "dictionary code width %u not in 1..32", bit_width);
+  if (n_entries == 0 && n_rows > 0) return set_error(CQ_ERR_INVALID_ARG, "empty dictionary");
+  if (n_entries && (!dict_bytes || !dict_offsets)) return set_error(CQ_ERR_INVALID_ARG, "NULL dictionary");
+  const uint64_t need = (n_rows * bit_width + 31) / 32;
+  const uint64_t need_pad = (need + 3) / 4 * 4;
+  if (n_words < need) return set_error(CQ_ERR_INVALID_ARG, "%llu code words given, %llu needed", (unsigned long long)n_words, (unsigned long long)need);
+  if (mem_flags == CQ_MEM_DEVICE_BORROW && n_words < need_pad)
+    return set_error(CQ_ERR_INVALID_ARG, "borrowed code words must be padded to %llu words", (unsigned long long)need_pad);
+  c->n_entries = n_entries;
+  c->dict_offsets.assign(dict_offsets, dict_offsets + (n_entries ? n_entries + 1 : 0));
+  if (n_entries) {
+    if (dict_offsets[0] != 0) return set_error(CQ_ERR_INVALID_ARG, "dictionary offsets must start at 0");
+    for (uint32_t i = 0; i < n_entries; ++i)
+      if (dict_offsets[i + 1] < dict_offsets[i]) return set_error(CQ_ERR_INVALID_ARG, "dictionary offsets decrease");
+    c->dict_bytes.assign(dict_bytes, dict_bytes + dict_offsets[n_entries]);
+    for (uint32_t i = 0; i + 1 < n_entries; ++i) {
+      const char* a = c->dict_bytes.data() + dict_offsets[i];
+      const char* b = c->dict_bytes.data() + dict_offsets[i + 1];
+      if (cmp_bytes(a, dict_offsets[i + 1] - dict_offsets[i], b, dict_offsets[i + 2] - dict_offsets[i + 1]) >= 0)
+        return set_error(CQ_ERR_INVALID_ARG, "dictionary is not sorted and unique at entry %u", i);
+    }
+  }
+  c->bit_width = bit_width;
+  c->n = n_words;
+  if (mem_flags == CQ_MEM_DEVICE_BORROW) {
+    if ((rc = check_borrow(packed_codes, "packed_codes"))) return rc;
+    c->vals = const_cast<uint32_t*>(packed_codes);
+  } else {
+    c->owned = true;
+    if ((rc = own_copy(ctx, packed_codes, need * 4, false, &c->vals))) return rc;
+    c->n = (pad16(need * 4) + 16) / 4;
+  }
+  c->device_bytes = (n_rows * bit_width + 7) / 8;
+  return finish_or_release(c, out);
+}
+
+extern "C" int cq_column_create_index(cq_ctx* ctx, cq_dtype val_t, const void* values, cq_dtype pos_t,
+                                      const void* positions, uint64_t nnz, int64_t default_value, uint64_t n_rows,
+                                      uint32_t mem_flags, cq_column** out) {
+  clear_error();
+  std::unique_ptr<cq_column> c;
+  int rc = new_column(ctx, ENC_INDEX, n_rows, out, &c);
+  if (rc) return rc;
+  if (!dtype_ok(val_t) || !dtype_ok(pos_t)) return set_error(CQ_ERR_INVALID_ARG, "bad dtype");
+  if (nnz > n_rows) return set_error(CQ_ERR_INVALID_ARG, "more listed positions than rows");
+  if (nnz && (!values || !positions)) return set_error(CQ_ERR_INVALID_ARG, "NULL buffer");
+  c->val_t = val_t;
+  c->end_t = pos_t;
+  c->n = nnz;
+  c->base = default_value;
+  if (mem_flags == CQ_MEM_DEVICE_BORROW) {
+    if ((rc = check_borrow(values, "values")) || (rc = check_borrow(positions, "positions"))) return rc;
+    c->vals = const_cast<void*>(values);
+    c->ends = const_cast<void*>(positions);
+  } else {
+    c->owned = true;
+    if ((rc = own_copy(ctx, values, nnz * dsize(val_t), false, &c->vals))) return rc;
+    if ((rc = own_copy(ctx, positions, nnz * dsize(pos_t), false, &c->ends))) { release_buffers(c.get()); return rc; }
+  }
+  c->device_bytes = nnz * (dsize(val_t) + dsize(pos_t));
+  return finish_or_release(c, out);
+}
+
+extern "C" int cq_column_create_bitpacked(cq_ctx* ctx, cq_dtype logical_t, const uint32_t* words, uint64_t n_words,
+                                          uint32_t bit_width, int64_t base, uint64_t n_rows, uint32_t mem_flags,
+                                          cq_column** out) {
+  clear_error();
+  std::unique_ptr<cq_column> c;
+  int rc = new_column(ctx, ENC_PACKED, n_rows, out, &c);
+  if (rc) return rc;
+  if (!dtype_ok(logical_t)) return set_error(CQ_ERR_INVALID_ARG, "bad dtype");
+  if (bit_width < 1 || bit_width > 64) return set_error(CQ_ERR_INVALID_ARG, "bit width %u not in 1..64", bit_width);
+  const uint64_t need = (n_rows * bit_width + 31) / 32;
+  const uint64_t need_pad = (need + 3) / 4 * 4;
+  if (n_words < need) return set_error(CQ_ERR_INVALID_ARG, "%llu words given, %llu needed", (unsigned long long)n_words, (unsigned long long)need);
+  if (mem_flags == CQ_MEM_DEVICE_BORROW && n_words < need_pad)
+    return set_error(CQ_ERR_INVALID_ARG, "borrowed words must be padded to %llu words", (unsigned long long)need_pad);
+  c->logical_t = logical_t;
+  c->bit_width = bit_width;
+  c->base = base;
+  c->n = n_words;
+  if (mem_flags == CQ_MEM_DEVICE_BORROW) {
+    if ((rc = check_borrow(words, "words"))) return rc;
+    c->vals = const_cast<uint32_t*>(words);
+  } else {
+    c->owned = true;
+    if ((rc = own_copy(ctx, words, need * 4, false, &c->vals))) return rc;
+    c->n = (pad16(need * 4) + 16) / 4;
+  }
+  c->device_bytes = (n_rows * bit_width + 7) / 8;
+  return finish_or_release(c, out);
+}
+
+extern "C" int cq_column_create_plain(cq_ctx* ctx, cq_dtype t, const void* values, uint64_t n_rows,
+                                      uint32_t mem_flags, cq_column** out) {
+  clear_error();
+  std::unique_ptr<cq_column> c;
+  int rc = new_column(ctx, ENC_PLAIN, n_rows, out, &c);
+  if (rc) return rc;
+  if (!dtype_ok(t)) return set_error(CQ_ERR_INVALID_ARG, "bad dtype");
+  if (n_rows && !values) return set_error(CQ_ERR_INVALID_ARG, "NULL buffer");
+  c->val_t = t;
+  c->n = n_rows;
+  if (mem_flags == CQ_MEM_DEVICE_BORROW) {
+    if ((rc = check_borrow(values, "values"))) return rc;
+    c->vals = const_cast<void*>(values);
+  } else {
+    c->owned = true;
+    if ((rc = own_copy(ctx, values, n_rows * dsize(t), false, &c->vals))) return rc;
+  }
+  c->device_bytes = n_rows * dsize(t);
+  return finish_or_release(c, out);
+}
+
+extern "C" int cq_column_destroy(cq_column* col) {
+  clear_error();
+  if (!col) return CQ_OK;
+  if (--col->refs == 0) {
+    cudaSetDevice(col->ctx->device);
+    cudaStreamSynchronize(col->ctx->stream);
+    release_buffers(col);
+    delete col;
+  }
+  return CQ_OK;
+}
+
+extern "C" int cq_column_encoding(const cq_column* col, uint32_t* enc) {
+  if (!col || !enc) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  *enc = col->enc;
+  return CQ_OK;
+}
+
+extern "C" int cq_column_device_bytes(const cq_column* col, uint64_t* bytes) {
+  if (!col || !bytes) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  *bytes = col->device_bytes;
+  return CQ_OK;
+}
+
+// ====================================================================== tables
+extern "C" int cq_table_bind(cq_ctx* ctx, cq_column* const* cols, uint32_t n_cols, cq_table** out) {
+  clear_error();
+  if (!ctx || !out || (n_cols && !cols)) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (n_cols == 0) return set_error(CQ_ERR_INVALID_ARG, "a table needs at least one column");
+  for (uint32_t i = 0; i < n_cols; ++i) {
+    if (!cols[i]) return set_error(CQ_ERR_INVALID_ARG, "column %u is NULL", i);
+    if (cols[i]->ctx != ctx) return set_error(CQ_ERR_INVALID_ARG, "column %u belongs to another context", i);
+    if (cols[i]->n_rows != cols[0]->n_rows)
+      return set_error(CQ_ERR_SIZE_MISMATCH, "column %u has %llu rows, column 0 has %llu", i,
+                       (unsigned long long)cols[i]->n_rows, (unsigned long long)cols[0]->n_rows);
+  }
+  cq_table* t = new cq_table;
+  t->ctx = ctx;
+  t->n_rows = cols[0]->n_rows;
+  for (uint32_t i = 0; i < n_cols; ++i) {
+    cols[i]->refs++;
+    t->cols.push_back(cols[i]);
+  }
+  *out = t;
+  return CQ_OK;
+}
+
+extern "C" int cq_table_destroy(cq_table* table) {
+  clear_error();
+  if (!table) return CQ_OK;
+  for (cq_column* c : table->cols) cq_column_destroy(c);
+  delete table;
+  return CQ_OK;
+}
+
+extern "C" int cq_table_num_rows(const cq_table* table, uint64_t* n_rows) {
+  if (!table || !n_rows) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  *n_rows = table->n_rows;
+  return CQ_OK;
+}
+
+// ====================================================================== planner
+namespace cq {
+
+// A column as the planner sees it (a table column, or the flat int64 array
+// the decompress-then-scan path expanded it to).
+struct PlanCol {
+  uint8_t enc;
+  bool v64, e64;
+  uint32_t bw;
+  int64_t base;
+  const void* vals;
+  const void* ends;
+  uint64_t n;
+  ColumnStats stats;
+  const cq_column* src;   // dictionary and key-string lookups
+};
+
+static PlanCol view_of(const cq_column* c) {
+  PlanCol p;
+  p.enc = c->enc;
+  p.v64 = c->val_t == CQ_I64;
+  p.e64 = c->end_t == CQ_I64;
+  p.bw = c->bit_width;
+  p.base = c->base;
+  p.vals = c->vals;
+  p.ends = c->ends;
+  p.n = c->n;
+  p.stats = c->stats;
+  p.src = c;
+  return p;
+}
+
+struct Planned {
+  QueryDesc q;
+  std::vector<uint32_t> aux;
+  std::vector<uint32_t> out_kind;
+  std::vector<int> out_key_col;
+  int ctas_per_sm = 1;
+};
+
+static bool is_dict(const PlanCol& c) { return c.src && c.src->enc == ENC_DICT; }
+
+// lower / upper bound of a literal in the sorted dictionary
+static uint32_t dict_bound(const cq_column* d, const char* s, size_t ls, bool upper) {
+  uint32_t lo = 0, hi = d->n_entries;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) / 2;
+    const char* m = d->dict_bytes.data() + d->dict_offsets[mid];
+    const size_t lm = d->dict_offsets[mid + 1] - d->dict_offsets[mid];
+    const int c = cmp_bytes(m, lm, s, ls);
+    if (c < 0 || (upper && c == 0)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+static size_t lit_len(const cq_predicate& p, uint32_t i) {
+  return p.str_lens ? p.str_lens[i] : strlen(p.strs[i]);
+}
+
+// Raw-space transform of a logical integer interval for one column.
+struct RawMap {
+  bool offset;       // raw = logical - base (bit-packed, no wrap-around)
+  int64_t base;
+  i128 rmin, rmax;   // raw domain
+};
+
+static RawMap raw_map(const PlanCol& c, bool raw_is_offset) {
+  RawMap m;
+  m.offset = raw_is_offset;
+  m.base = raw_is_offset ? c.base : 0;
+  if (raw_is_offset) {
+    m.rmin = 0;
+    m.rmax = (((i128)1) << c.bw) - 1;
+  } else {
+    m.rmin = LLONG_MIN;
+    m.rmax = LLONG_MAX;
+  }
+  return m;
+}
+
+static void set_range(PredDesc& d, i128 lo, i128 hi, const RawMap& m) {
+  lo -= m.base;
+  hi -= m.base;
+  if (lo < m.rmin) lo = m.rmin;
+  if (hi > m.rmax) hi = m.rmax;
+  if (lo > hi) {
+    d.kind = PK_FALSE;
+    return;
+  }
+  d.kind = PK_RANGE;
+  d.lo = (int64_t)lo;
+  d.hi = (int64_t)hi;
+}
+
+// Bitmap (small span) or sorted list of raw values in aux.
+static void set_members(PredDesc& d, std::vector<int64_t> vals, std::vector<uint32_t>& aux) {
+  std::sort(vals.begin(), vals.end());
+  vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+  if (vals.empty()) {
+    d.kind = PK_FALSE;
+    return;
+  }
+  const i128 span = (i128)vals.back() - (i128)vals.front();
+  if (span < (1 << 20)) {
+    const uint32_t words = (uint32_t)(span / 32 + 1);
+    d.kind = PK_BITMAP;
+    d.lo = vals.front();
+    d.hi = vals.back();
+    d.aux_off = (uint32_t)aux.size();
+    d.aux_len = words;
+    aux.resize(aux.size() + words, 0u);
+    for (int64_t v : vals) {
+      const uint64_t o = (uint64_t)((i128)v - (i128)d.lo);
+      aux[d.aux_off + o / 32] |= 1u << (o % 32);
+    }
+  } else {
+    d.kind = PK_LIST;
+    if (aux.size() & 1) aux.push_back(0);  // 8-byte alignment of the list
+    d.aux_off = (uint32_t)aux.size();
+    d.aux_len = (uint32_t)vals.size();
+    for (int64_t v : vals) {
+      aux.push_back((uint32_t)(uint64_t)v);
+      aux.push_back((uint32_t)((uint64_t)v >> 32));
+    }
+  }
+}
+
+static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
+                      const cq_exec_options* opts, const cq_ctx* ctx, Planned* P) {
+  if (!plan) return set_error(CQ_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->n_preds > (uint32_t)kMaxPreds || plan->n_group_by > (uint32_t)kMaxKeys || plan->n_aggs > (uint32_t)kMaxAggs)
+    return set_error(CQ_ERR_INVALID_ARG, "plan exceeds 16 predicates / 8 group-by columns / 16 aggregates");
+  if ((plan->n_preds && !plan->preds) || (plan->n_group_by && !plan->group_by) || (plan->n_aggs && !plan->aggs))
+    return set_error(CQ_ERR_INVALID_ARG, "plan array is NULL");
+  QueryDesc& q = P->q;
+  memset(&q, 0, sizeof(q));
+  q.n_rows = n_rows;
+  std::vector<int> slot(tcols.size(), -1);
+  std::vector<int> order;
+  auto use = [&](uint32_t col) -> int {
+    if (col >= tcols.size()) return -1;
+    if (slot[col] < 0) {
+      if (order.size() >= (size_t)kMaxCols) return -2;
+      slot[col] = (int)order.size();
+      order.push_back((int)col);
+    }
+    return slot[col];
+  };
+  for (uint32_t i = 0; i < plan->n_preds; ++i)
+    if (use(plan->preds[i].col) < 0) return set_error(CQ_ERR_INVALID_ARG, "predicate %u: bad column %u", i, plan->preds[i].col);
+  for (uint32_t i = 0; i < plan->n_group_by; ++i)
+    if (use(plan->group_by[i]) < 0) return set_error(CQ_ERR_INVALID_ARG, "group-by %u: bad column %u", i, plan->group_by[i]);
+  for (uint32_t i = 0; i < plan->n_aggs; ++i) {
+    const cq_aggregate& a = plan->aggs[i];
+    if (a.op < CQ_SUM || a.op > CQ_AVG) return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: bad op %d", i, a.op);
+    if (a.op == CQ_COUNT) continue;
+    if (use(a.col) < 0) return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: bad column %u", i, a.col);
+    if ((a.op == CQ_SUM || a.op == CQ_AVG) && is_dict(tcols[a.col]))
+      return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: SUM/AVG of a dictionary column", i);
+  }
+  // ---- tile / pipeline shape
+  uint32_t tile = opts && opts->tile_rows ? opts->tile_rows : 4096;
+  if (tile < 1024 || tile > 8192 || (tile & (tile - 1)))
+    return set_error(CQ_ERR_INVALID_ARG, "tile_rows must be 1024, 2048, 4096 or 8192");
+  q.tile_rows = tile;
+  q.n_tiles = (n_rows + tile - 1) / tile;
+  q.n_cols = (uint8_t)order.size();
+  // ---- columns
+  int nb = 0, nrow = 0;
+  uint32_t stage_off = 0;
+  for (size_t i = 0; i < order.size(); ++i) {
+    const PlanCol& pc = tcols[order[i]];
+    ColDesc& d = q.cols[i];
+    d.enc = pc.enc;
+    d.v64 = pc.v64;
+    d.e64 = pc.e64;
+    d.bw = (uint8_t)pc.bw;
+    d.base = pc.base;
+    d.vals = pc.vals;
+    d.ends = pc.ends;
+    d.n = pc.n;
+    d.bslot = 0xFF;
+    d.raw_is_offset = 0;
+    if (pc.enc == ENC_DICT) d.raw_is_offset = 1;
+    if (pc.enc == ENC_PACKED && pc.bw < 64 && (i128)pc.base + ((((i128)1) << pc.bw) - 1) <= (i128)LLONG_MAX)
+      d.raw_is_offset = 1;
+    if (pc.enc == ENC_RLE || pc.enc == ENC_INDEX) {
+      if (nb >= kMaxBitmapCols) return set_error(CQ_ERR_UNSUPPORTED, "more than %d RLE / index columns in one query", kMaxBitmapCols);
+      d.bslot = (uint8_t)nb++;
+    } else {
+      const uint32_t bits = pc.enc == ENC_PLAIN ? (pc.v64 ? 64u : 32u) : pc.bw;
+      d.stage_off = stage_off;
+      d.stage_bytes = (uint32_t)(pad16((uint64_t)tile * bits / 8) + 16);
+      stage_off += d.stage_bytes;
+      q.row_cols[nrow++] = (uint8_t)i;
+    }
+  }
+  q.n_bitmaps = (uint8_t)nb;
+  q.n_row_cols = (uint8_t)nrow;
+  q.seg_mode = nrow == 0;
+  q.stage_bytes = stage_off;
+  q.stages = (uint8_t)(opts && opts->stages ? opts->stages : 4);
+  if (q.stages < 2 || q.stages > 8) return set_error(CQ_ERR_INVALID_ARG, "stages must be in 2..8");
+  auto& aux = P->aux;
+  // ---- predicates
+  q.n_preds = (uint8_t)plan->n_preds;
+  std::vector<int> in_pred_of_col(q.n_cols, -1);
+  std::vector<int> in_count(q.n_cols, 0);
+  for (uint32_t i = 0; i < plan->n_preds; ++i) {
+    const cq_predicate& p = plan->preds[i];
+    const int ci = slot[p.col];
+    const PlanCol& pc = tcols[p.col];
+    const ColDesc& cd = q.cols[ci];
+    PredDesc& d = q.preds[i];
+    d.col = (uint8_t)ci;
+    if (p.op < CQ_LT || p.op > CQ_IN) return set_error(CQ_ERR_INVALID_ARG, "predicate %u: bad op %d", i, p.op);
+    if (is_dict(pc)) {
+      const cq_column* dc = pc.src;
+      const uint32_t need = p.op == CQ_IN ? 0u : (p.op == CQ_BETWEEN ? 2u : 1u);
+      if (p.n_strs < need || (p.n_strs && !p.strs))
+        return set_error(CQ_ERR_INVALID_ARG, "predicate %u on a dictionary column needs string literals", i);
+      auto lb = [&](uint32_t k) { return dict_bound(dc, p.strs[k], lit_len(p, k), false); };
+      auto ub = [&](uint32_t k) { return dict_bound(dc, p.strs[k], lit_len(p, k), true); };
+      RawMap m{false, 0, 0, (i128)dc->n_entries - 1};
+      switch (p.op) {
+        case CQ_LT: set_range(d, 0, (i128)lb(0) - 1, m); break;
+        case CQ_LE: set_range(d, 0, (i128)ub(0) - 1, m); break;
+        case CQ_GT: set_range(d, ub(0), m.rmax, m); break;
+        case CQ_GE: set_range(d, lb(0), m.rmax, m); break;
+        case CQ_EQ: {
+          const uint32_t a = lb(0), b = ub(0);
+          if (a < b) set_range(d, a, a, m); else d.kind = PK_FALSE;
+          break;
+        }
+        case CQ_NE: {
+          const uint32_t a = lb(0), b = ub(0);
+          if (a < b) { d.kind = PK_NE; d.lo = a; } else d.kind = PK_TRUE;
+          break;
+        }
+        case CQ_BETWEEN: set_range(d, lb(0), (i128)ub(1) - 1, m); break;
+        case CQ_IN: {
+          std::vector<int64_t> codes;
+          for (uint32_t k = 0; k < p.n_strs; ++k) {
+            const uint32_t a = lb(k), b = ub(k);
+            if (a < b) codes.push_back(a);
+          }
+          set_members(d, codes, aux);
+          in_pred_of_col[ci] = (int)i;
+          in_count[ci]++;
+          break;
+        }
+      }
+      continue;
+    }
+    if (p.n_strs) return set_error(CQ_ERR_INVALID_ARG, "predicate %u: string literal on an integer column", i);
+    const RawMap m = raw_map(pc, cd.raw_is_offset);
+    switch (p.op) {
+      case CQ_LT: set_range(d, LLONG_MIN, (i128)p.lo - 1, m); break;
+      case CQ_LE: set_range(d, LLONG_MIN, p.lo, m); break;
+      case CQ_GT: set_range(d, (i128)p.lo + 1, LLONG_MAX, m); break;
+      case CQ_GE: set_range(d, p.lo, LLONG_MAX, m); break;
+      case CQ_EQ: set_range(d, p.lo, p.lo, m); break;
+      case CQ_BETWEEN: set_range(d, p.lo, p.hi, m); break;
+      case CQ_NE: {
+        const i128 r = (i128)p.lo - m.base;
+        if (r < m.rmin || r > m.rmax) d.kind = PK_TRUE;
+        else { d.kind = PK_NE; d.lo = (int64_t)r; }
+        break;
+      }
+      case CQ_IN: {
+        if (p.n_in && !p.in_ints) return set_error(CQ_ERR_INVALID_ARG, "predicate %u: NULL IN list", i);
+        std::vector<int64_t> vals;
+        for (uint32_t k = 0; k < p.n_in; ++k) {
+          const i128 r = (i128)p.in_ints[k] - m.base;
+          if (r >= m.rmin && r <= m.rmax) vals.push_back((int64_t)r);
+        }
+        set_members(d, vals, aux);
+        in_pred_of_col[ci] = (int)i;
+        in_count[ci]++;
+        break;
+      }
+    }
+  }
+  // ---- group keys (dense mixed radix, first key most significant)
+  q.n_keys = (uint8_t)plan->n_group_by;
+  i128 groups = 1;
+  for (uint32_t k = 0; k < plan->n_group_by; ++k) {
+    const int ci = slot[plan->group_by[k]];
+    const PlanCol& pc = tcols[plan->group_by[k]];
+    const ColDesc& cd = q.cols[ci];
+    KeyDesc& kd = q.keys[k];
+    kd.col = (uint8_t)ci;
+    const int ip = in_pred_of_col[ci];
+    if (ip >= 0 && in_count[ci] == 1 && q.preds[ip].kind == PK_BITMAP) {
+      // an IN list on the key: digits are ranks of the listed values
+      const PredDesc& pd = q.preds[ip];
+      kd.remap = 1;
+      kd.kmin = pd.lo;
+      kd.aux_off = pd.aux_off;
+      kd.aux_len = pd.aux_len;
+      kd.prefix_off = (uint32_t)aux.size();
+      uint32_t run = 0;
+      std::vector<int64_t> members;
+      for (uint32_t w = 0; w < pd.aux_len; ++w) {
+        aux.push_back(run);
+        const uint32_t bits = aux[pd.aux_off + w];
+        run += (uint32_t)__builtin_popcount(bits);
+        for (int b = 0; b < 32; ++b)
+          if ((bits >> b) & 1u) members.push_back(pd.lo + (int64_t)w * 32 + b);
+      }
+      kd.card = run;
+      if (aux.size() & 1) aux.push_back(0);
+      kd.list_off = (uint32_t)aux.size();
+      for (int64_t v : members) {
+        aux.push_back((uint32_t)(uint64_t)v);
+        aux.push_back((uint32_t)((uint64_t)v >> 32));
+      }
+    } else {
+      i128 lo, hi;
+      if (is_dict(pc)) {
+        lo = pc.stats.min_raw;
+        hi = pc.stats.max_raw;
+      } else if (cd.raw_is_offset) {
+        lo = pc.stats.min_raw;
+        hi = pc.stats.max_raw;
+      } else {
+        lo = pc.stats.min_val;
+        hi = pc.stats.max_val;
+      }
+      // a range predicate on the key column narrows its domain
+      for (uint32_t i = 0; i < plan->n_preds; ++i) {
+        const PredDesc& pd = q.preds[i];
+        if (pd.col != ci) continue;
+        if (pd.kind == PK_RANGE) { lo = std::max(lo, (i128)pd.lo); hi = std::min(hi, (i128)pd.hi); }
+        if (pd.kind == PK_BITMAP) { lo = std::max(lo, (i128)pd.lo); hi = std::min(hi, (i128)pd.hi); }
+      }
+      if (hi < lo) { lo = 0; hi = 0; }
+      const i128 card = hi - lo + 1;
+      if (card > (i128)kDenseMaxGroups)
+        return set_error(CQ_ERR_UNSUPPORTED, "group-by column %u spans %.3g values; dense key domains are limited to 2^24",
+                         plan->group_by[k], (double)card);
+      kd.kmin = (int64_t)lo;
+      kd.card = (uint32_t)card;
+    }
+    if (kd.card == 0) kd.card = 1;
+    groups *= kd.card;
+    if (groups > (i128)kDenseMaxGroups)
+      return set_error(CQ_ERR_UNSUPPORTED, "the group-by key domain exceeds 2^24 groups");
+  }
+  uint64_t stride = 1;
+  for (int k = (int)plan->n_group_by - 1; k >= 0; --k) {
+    q.keys[k].stride = stride;
+    stride *= q.keys[k].card;
+  }
+  q.n_groups = (uint64_t)groups;
+  // ---- table shape and flush period
+  q.flush_rows = 1u << 20;
+  if (q.flush_rows < tile) q.flush_rows = tile;
+  // ---- aggregates
+  q.n_aggs = (uint8_t)plan->n_aggs;
+  uint32_t sw = 1, gw = 1;
+  q.has_index_agg = 0;
+  for (uint32_t i = 0; i < plan->n_aggs; ++i) {
+    const cq_aggregate& a = plan->aggs[i];
+    AggDesc& d = q.aggs[i];
+    d.op = (uint8_t)a.op;
+    d.out_kind = a.op == CQ_COUNT ? 1 : (a.op == CQ_AVG ? 2 : 0);
+    if (a.op == CQ_COUNT) {
+      d.kind = AK_COUNT;
+      continue;
+    }
+    const int ci = slot[a.col];
+    const PlanCol& pc = tcols[a.col];
+    const ColDesc& cd = q.cols[ci];
+    d.col = (uint8_t)ci;
+    const bool idx = pc.enc == ENC_INDEX;
+    if (idx) q.has_index_agg = 1;
+    if (a.op == CQ_SUM || a.op == CQ_AVG) {
+      d.kind = idx ? AK_ISUM : AK_SUM;
+      i128 bound;
+      if (idx) {
+        bound = (i128)pc.stats.max_abs_val + (pc.base < 0 ? -(i128)pc.base : (i128)pc.base);
+        d.base = pc.base;
+      } else if (cd.raw_is_offset && pc.enc == ENC_PACKED) {
+        bound = (i128)std::max<int64_t>(pc.stats.max_raw, 0);
+        d.base = pc.base;
+      } else {
+        bound = pc.stats.max_abs_val;
+        d.base = 0;
+      }
+      d.wide = bound * (i128)q.flush_rows >= ((i128)1 << 62) ? 1 : 0;
+      d.sw = (uint8_t)sw;
+      sw += d.wide ? 2 : 1;
+      d.gw = gw;
+      gw += 3;
+    } else {  // MIN / MAX
+      if (idx) {
+        d.kind = a.op == CQ_MIN ? AK_IMIN : AK_IMAX;
+        d.base = pc.base;
+        d.sw = (uint8_t)sw;
+        sw += 2;
+        d.gw = gw;
+        gw += 2;
+      } else {
+        d.kind = a.op == CQ_MIN ? AK_MIN : AK_MAX;
+        d.base = (cd.raw_is_offset && pc.enc == ENC_PACKED) ? pc.base : 0;
+        d.sw = (uint8_t)sw;
+        sw += 1;
+        d.gw = gw;
+        gw += 1;
+      }
+    }
+  }
+  q.n_sw = (uint8_t)sw;
+  q.n_gw = (uint8_t)gw;
+  // ---- shared-memory group table: dense bins when the whole domain fits
+  uint32_t slots = opts && opts->table_slots ? opts->table_slots : 1024;
+  if (slots & (slots - 1)) return set_error(CQ_ERR_INVALID_ARG, "table_slots must be a power of two");
+  const uint64_t dense_cap = 4096;
+  if (q.n_groups <= dense_cap) {
+    q.table_dense = 1;
+    q.table_slots = (uint32_t)q.n_groups;
+  } else {
+    q.table_dense = 0;
+    q.table_slots = slots;
+  }
+  // ---- fit shared memory: fewer stages, then fewer slots
+  for (;;) {
+    q.smem_bytes = 0;
+    const size_t need = query_kernel_smem(q);
+    if (need <= ctx->smem_optin) {
+      q.smem_bytes = (uint32_t)need;
+      break;
+    }
+    if (!q.seg_mode && q.stages > 2) { q.stages--; continue; }
+    if (!q.table_dense && q.table_slots > 128) { q.table_slots /= 2; continue; }
+    return set_error(CQ_ERR_UNSUPPORTED, "query does not fit in %zu bytes of shared memory (tile_rows %u)",
+                     ctx->smem_optin, tile);
+  }
+  P->ctas_per_sm = opts && opts->ctas_per_sm ? (int)opts->ctas_per_sm : 1;
+  // ---- outputs
+  q.n_out = plan->n_group_by + plan->n_aggs;
+  P->out_kind.clear();
+  P->out_key_col.clear();
+  for (uint32_t k = 0; k < plan->n_group_by; ++k) {
+    q.out_is_key[k] = 1;
+    q.out_index[k] = (uint8_t)k;
+    P->out_kind.push_back(0);
+    P->out_key_col.push_back((int)plan->group_by[k]);
+  }
+  for (uint32_t i = 0; i < plan->n_aggs; ++i) {
+    q.out_is_key[plan->n_group_by + i] = 0;
+    q.out_index[plan->n_group_by + i] = (uint8_t)i;
+    P->out_kind.push_back(q.aggs[i].out_kind);
+    P->out_key_col.push_back(-1);
+  }
+  return CQ_OK;
+}
+
+// Carve one pool allocation into the query's device buffers and enqueue
+// init -> fused kernel -> finalize on `s`.
+static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r) {
+  QueryDesc& q = P.q;
+  const uint64_t G = q.n_groups;
+  const uint64_t nb = (G + 1023) / 1024;
+  auto al = [](uint64_t x) { return (x + 255) / 256 * 256; };
+  const uint64_t off_gacc = 0;
+  const uint64_t off_out = off_gacc + al(8ull * q.n_gw * G);
+  const uint64_t off_aux = off_out + al(8ull * q.n_out * G) * 1;
+  const uint64_t off_err = off_aux + al(4ull * (P.aux.size() + 2));
+  const uint64_t off_cnt = off_err + 256;
+  const uint64_t off_blk = off_cnt + 256;
+  const uint64_t total = off_blk + al(4ull * (nb + 1));
+  void* base = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&base, total, ctx->pool, s);
+  if (e != cudaSuccess) return set_error(CQ_ERR_OOM, "device pool allocation of %llu bytes failed: %s", (unsigned long long)total, cudaGetErrorString(e));
+  r->dev_block = base;
+  r->dev_bytes = total;
+  uint8_t* b = reinterpret_cast<uint8_t*>(base);
+  q.gacc = reinterpret_cast<unsigned long long*>(b + off_gacc);
+  for (uint32_t i = 0; i < q.n_out; ++i) q.out[i] = b + off_out + (uint64_t)i * 8 * G;
+  q.aux = reinterpret_cast<const uint32_t*>(b + off_aux);
+  q.aux_words = (uint32_t)P.aux.size();
+  q.err = reinterpret_cast<int*>(b + off_err);
+  q.out_count = reinterpret_cast<unsigned long long*>(b + off_cnt);
+  q.block_counts = reinterpret_cast<unsigned int*>(b + off_blk);
+  if (!P.aux.empty()) {
+    // the descriptor's aux words travel through the stream like the launch itself
+    e = cudaMemcpyAsync(b + off_aux, P.aux.data(), 4 * P.aux.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "aux upload failed: %s", cudaGetErrorString(e));
+  }
+  e = launch_init_global(q, s);
+  if (e == cudaSuccess) e = launch_query(q, s, ctx->num_sms, P.ctas_per_sm);
+  if (e == cudaSuccess) e = launch_finalize(q, s);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  r->desc = q;
+  r->err_dev = q.err;
+  r->count_dev = q.out_count;
+  r->n_out = q.n_out;
+  r->out_kind = P.out_kind;
+  r->out_key_col = P.out_key_col;
+  r->out_dev.assign(q.out, q.out + q.n_out);
+  return CQ_OK;
+}
+
+static cq_result* new_result(cq_ctx* ctx, cudaStream_t s) {
+  cq_result* r = new cq_result;
+  r->ctx = ctx;
+  r->stream = s;
+  cudaEventCreate(&r->ev_start);
+  cudaEventCreate(&r->ev_done);
+  return r;
+}
+
+static void free_result(cq_result* r) {
+  if (!r) return;
+  if (r->dev_block) cudaFreeAsync(r->dev_block, r->stream);
+  for (void* p : r->extra_dev) cudaFreeAsync(p, r->stream);
+  if (r->ev_start) cudaEventDestroy(r->ev_start);
+  if (r->ev_done) cudaEventDestroy(r->ev_done);
+  delete r;
+}
+
+}  // namespace cq
+
+// ====================================================================== queries
+extern "C" int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_exec_options* opts, void* cuda_stream,
+                               cq_result** out) {
+  clear_error();
+  if (!table || !out) return set_error(CQ_ERR_INVALID_ARG, "NULL table or out");
+  *out = nullptr;
+  cq_ctx* ctx = table->ctx;
+  CQ_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = cuda_stream ? reinterpret_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  const int mode = opts ? opts->mode : CQ_EXEC_FUSED;
+  if (mode != CQ_EXEC_FUSED && mode != CQ_EXEC_DECOMPRESS_THEN_SCAN)
+    return set_error(CQ_ERR_INVALID_ARG, "unknown execution mode %d", mode);
+  std::vector<PlanCol> cols;
+  for (cq_column* c : table->cols) cols.push_back(view_of(c));
+  cq_result* r = new_result(ctx, s);
+  cudaEventRecord(r->ev_start, s);
+  if (mode == CQ_EXEC_DECOMPRESS_THEN_SCAN) {
+    // expand every referenced column to a flat int64 array first
+    std::vector<bool> used(cols.size(), false);
+    if (plan) {
+      for (uint32_t i = 0; i < plan->n_preds && plan->preds; ++i) if (plan->preds[i].col < cols.size()) used[plan->preds[i].col] = true;
+      for (uint32_t i = 0; i < plan->n_group_by && plan->group_by; ++i) if (plan->group_by[i] < cols.size()) used[plan->group_by[i]] = true;
+      for (uint32_t i = 0; i < plan->n_aggs && plan->aggs; ++i)
+        if (plan->aggs[i].op != CQ_COUNT && plan->aggs[i].col < cols.size()) used[plan->aggs[i].col] = true;
+    }
+    for (size_t i = 0; i < cols.size(); ++i) {
+      if (!used[i]) continue;
+      void* flat = nullptr;
+      cudaError_t e = cudaMallocFromPoolAsync(&flat, pad16(table->n_rows * 8) + 16, ctx->pool, s);
+      if (e != cudaSuccess) {
+        free_result(r);
+        return set_error(CQ_ERR_OOM, "flat column allocation failed: %s", cudaGetErrorString(e));
+      }
+      r->extra_dev.push_back(flat);
+      e = expand_column(table->cols[i], reinterpret_cast<long long*>(flat), s, ctx->num_sms);
+      if (e != cudaSuccess) {
+        free_result(r);
+        return set_error(CQ_ERR_CUDA, "expansion failed: %s", cudaGetErrorString(e));
+      }
+      PlanCol& pc = cols[i];
+      pc.enc = ENC_PLAIN;
+      pc.v64 = true;
+      pc.vals = flat;
+      pc.n = table->n_rows;
+      pc.bw = 0;
+      // flat values are logical values (dictionary: codes)
+      if (table->cols[i]->enc == ENC_DICT) {
+        pc.stats.min_val = pc.stats.min_raw;
+        pc.stats.max_val = pc.stats.max_raw;
+      }
+    }
+  }
+  Planned P;
+  int rc = plan_query(cols, table->n_rows, plan, opts, ctx, &P);
+  if (rc == CQ_OK) rc = launch_planned(ctx, P, s, r);
+  if (rc != CQ_OK) {
+    free_result(r);
+    return rc;
+  }
+  for (int kc : P.out_key_col) r->key_cols.push_back(kc >= 0 ? table->cols[kc] : nullptr);
+  for (cq_column* c : table->cols) c->refs++;   // results keep their columns' dictionaries alive
+  r->held_cols = table->cols;
+  cudaEventRecord(r->ev_done, s);
+  *out = r;
+  return CQ_OK;
+}
+
+extern "C" int cq_query_run(cq_table* table, const cq_plan* plan, void* cuda_stream, cq_result** out) {
+  return cq_query_run_ex(table, plan, nullptr, cuda_stream, out);
+}
+
+extern "C" int cq_result_wait(cq_result* r, uint64_t timeout_us) {
+  clear_error();
+  if (!r) return set_error(CQ_ERR_INVALID_ARG, "NULL result");
+  if (r->waited) return r->status;
+  cudaSetDevice(r->ctx->device);
+  if (timeout_us != UINT64_MAX) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      const cudaError_t q = cudaEventQuery(r->ev_done);
+      if (q == cudaSuccess) break;
+      if (q != cudaErrorNotReady) return set_error(CQ_ERR_CUDA, "query failed: %s", cudaGetErrorString(q));
+      const auto us = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+      if ((uint64_t)us >= timeout_us) return set_error(CQ_ERR_NOT_READY, "query still running");
+      std::this_thread::yield();
+    }
+  }
+  cudaError_t e = cudaEventSynchronize(r->ev_done);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "query failed: %s", cudaGetErrorString(e));
+  int err = 0;
+  unsigned long long cnt = 0;
+  e = cudaMemcpy(&err, r->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&cnt, r->count_dev, sizeof(cnt), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "status read-back failed: %s", cudaGetErrorString(e));
+  r->waited = true;
+  r->n_groups = cnt;
+  r->status = err;
+  if (err == CQ_ERR_OVERFLOW) return set_error(err, "a SUM does not fit int64");
+  if (err == CQ_ERR_TIMEOUT) return set_error(err, "a bounded device wait gave up");
+  if (err == CQ_ERR_INVALID_ARG) return set_error(err, "a group-by value outside its column's recorded range");
+  if (err) return set_error(err, "device status %d", err);
+  return CQ_OK;
+}
+
+extern "C" int cq_result_num_groups(cq_result* r, uint64_t* n) {
+  if (!r || !n) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  int rc = cq_result_wait(r, UINT64_MAX);
+  if (rc != CQ_OK && rc != CQ_ERR_OVERFLOW) return rc;
+  *n = r->n_groups;
+  return rc;
+}
+
+extern "C" int cq_result_num_columns(cq_result* r, uint32_t* n) {
+  if (!r || !n) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  *n = r->n_out;
+  return CQ_OK;
+}
+
+extern "C" int cq_result_column_kind(cq_result* r, uint32_t out_col, uint32_t* kind) {
+  if (!r || !kind || out_col >= r->n_out) return set_error(CQ_ERR_INVALID_ARG, "bad output column");
+  *kind = r->out_kind[out_col];
+  return CQ_OK;
+}
+
+extern "C" int cq_result_fetch(cq_result* r, uint32_t out_col, void* host_dst, uint64_t dst_bytes) {
+  clear_error();
+  if (!r || out_col >= r->n_out) return set_error(CQ_ERR_INVALID_ARG, "bad output column");
+  int rc = cq_result_wait(r, UINT64_MAX);
+  if (rc != CQ_OK) return rc;
+  const uint64_t bytes = r->n_groups * 8;
+  if (dst_bytes < bytes) return set_error(CQ_ERR_SIZE_MISMATCH, "destination holds %llu bytes, %llu needed", (unsigned long long)dst_bytes, (unsigned long long)bytes);
+  if (bytes) CQ_CUDA(cudaMemcpy(host_dst, r->out_dev[out_col], bytes, cudaMemcpyDeviceToHost));
+  return CQ_OK;
+}
+
+extern "C" int cq_result_device_column(cq_result* r, uint32_t out_col, const void** dptr) {
+  if (!r || !dptr || out_col >= r->n_out) return set_error(CQ_ERR_INVALID_ARG, "bad output column");
+  *dptr = r->out_dev[out_col];
+  return CQ_OK;
+}
+
+extern "C" int cq_result_key_string(cq_result* r, uint32_t key_col, uint64_t row, const char** s, uint32_t* len) {
+  clear_error();
+  if (!r || !s || !len || key_col >= r->n_out || r->out_key_col[key_col] < 0)
+    return set_error(CQ_ERR_INVALID_ARG, "output column %u is not a group key", key_col);
+  const cq_column* c = r->key_cols[key_col];
+  if (!c || c->enc != ENC_DICT) return set_error(CQ_ERR_INVALID_ARG, "key column is not a dictionary column");
+  int rc = cq_result_wait(r, UINT64_MAX);
+  if (rc != CQ_OK) return rc;
+  if (row >= r->n_groups) return set_error(CQ_ERR_INVALID_ARG, "row out of range");
+  long long code = 0;
+  CQ_CUDA(cudaMemcpy(&code, reinterpret_cast<const long long*>(r->out_dev[key_col]) + row, 8, cudaMemcpyDeviceToHost));
+  if (code < 0 || (uint64_t)code >= c->n_entries) return set_error(CQ_ERR_INVALID_ARG, "code out of range");
+  *s = c->dict_bytes.data() + c->dict_offsets[code];
+  *len = (uint32_t)(c->dict_offsets[code + 1] - c->dict_offsets[code]);
+  return CQ_OK;
+}
+
+extern "C" int cq_result_device_time_us(cq_result* r, double* us) {
+  if (!r || !us) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  cudaError_t e = cudaEventSynchronize(r->ev_done);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "%s", cudaGetErrorString(e));
+  float ms = 0.f;
+  e = cudaEventElapsedTime(&ms, r->ev_start, r->ev_done);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "%s", cudaGetErrorString(e));
+  *us = ms * 1000.0;
+  return CQ_OK;
+}
+
+extern "C" int cq_result_destroy(cq_result* r) {
+  clear_error();
+  if (!r) return CQ_OK;
+  cudaSetDevice(r->ctx->device);
+  cudaStreamSynchronize(r->stream);
+  std::vector<cq_column*> held = r->held_cols;
+  free_result(r);
+  for (cq_column* c : held) cq_column_destroy(c);
+  return CQ_OK;
+}
+
+// ====================================================================== alignment
+extern "C" int cq_align_segments(cq_ctx* ctx, cq_column* const* cols, uint32_t k, void* cuda_stream,
+                                 int64_t* seg_ends, int64_t* ridx, uint64_t capacity, uint64_t* n_segments) {
+  clear_error();
+  if (!ctx || !cols || !n_segments) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  if (k == 0 || k > (uint32_t)kMaxBitmapCols) return set_error(CQ_ERR_INVALID_ARG, "k must be in 1..%d", kMaxBitmapCols);
+  for (uint32_t j = 0; j < k; ++j) {
+    if (!cols[j] || cols[j]->enc != ENC_RLE) return set_error(CQ_ERR_INVALID_ARG, "column %u is not RLE", j);
+    if (cols[j]->n_rows != cols[0]->n_rows) return set_error(CQ_ERR_SIZE_MISMATCH, "row counts differ");
+  }
+  if (capacity && (!seg_ends || !ridx)) return set_error(CQ_ERR_INVALID_ARG, "NULL output buffer");
+  CQ_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = cuda_stream ? reinterpret_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  const unsigned long long n_rows = cols[0]->n_rows;
+  const unsigned long long n_tiles = (n_rows + 4095) / 4096;
+  *n_segments = 0;
+  if (n_tiles == 0) return CQ_OK;
+  void* scratch = nullptr;
+  CQ_CUDA(cudaMallocFromPoolAsync(&scratch, 8 * n_tiles, ctx->pool, s));
+  std::vector<unsigned long long> host(n_tiles);
+  unsigned long long ns = 0;
+  cudaError_t e = align_segments(cols, k, s, scratch, n_tiles, n_rows, reinterpret_cast<long long*>(seg_ends),
+                                 reinterpret_cast<long long*>(ridx), capacity, host.data(), &ns);
+  cudaFreeAsync(scratch, s);
+  cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "alignment failed: %s", cudaGetErrorString(e));
+  *n_segments = ns;
+  if (ns > capacity) return set_error(CQ_ERR_SIZE_MISMATCH, "%llu segments, capacity %llu", ns, (unsigned long long)capacity);
+  return CQ_OK;
+}

@@ -1,0 +1,233 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle,
+element by element on the same seeded inputs.  Every result of this method is
+an exact integer (plus one correctly rounded division for AVG), so the bar is
+bit-exact equality for keys, SUM, COUNT, MIN, MAX and AVG alike."""
+import numpy as np
+import pytest
+
+from paper_2506_10092_gb300 import datagen as dg
+from tests.helpers import random_column, random_plan
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cq():
+    from paper_2506_10092_gb300 import cq as _cq
+    return _cq
+
+
+@pytest.fixture(scope="module")
+def ctx(cq):
+    return cq.cq_ctx_create(0)
+
+
+def run(cq, ctx, table, plan, device=False, opts=None):
+    t, cols = cq.table_from(ctx, table, device=device)
+    res = cq.cq_query_run(t, plan, opts=opts)
+    return cq.fetch_all(res)
+
+
+def check(got, ref, msg=""):
+    want = ref.keys + ref.aggs
+    assert len(got) == len(want), msg
+    for i, (g, w) in enumerate(zip(got, want)):
+        assert g.dtype == w.dtype, (msg, i, g.dtype, w.dtype)
+        np.testing.assert_array_equal(g, w, err_msg=f"{msg} output column {i}")
+
+
+# ------------------------------------------------------------------ the two workloads at test sizes
+def test_tiny_two_rle_1m_rows(cq, ctx, oracle_mod):
+    table, plan = dg.tiny_two_rle(1_000_000)
+    check(run(cq, ctx, table, plan), oracle_mod.query(table, plan), "tiny")
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_heterogeneous_2m_rows(cq, ctx, oracle_mod, device):
+    table, plan = dg.heterogeneous(2_000_000 + 777, seed=3)     # ragged last tile
+    check(run(cq, ctx, table, plan, device=device), oracle_mod.query(table, plan, n_threads=4), "hetero")
+
+
+def test_heterogeneous_with_index_default_and_string_keys(cq, ctx, oracle_mod):
+    table, plan = dg.heterogeneous(1_000_000, seed=5, index_default=-7)
+    plan = dg.Plan(plan.preds, plan.group_by,
+                   plan.aggs + [dg.Agg("avg", 2), dg.Agg("min", 2), dg.Agg("max", 2), dg.Agg("avg", 4),
+                                dg.Agg("min", 1), dg.Agg("max", 0)])
+    t, cols = cq.table_from(ctx, table)
+    res = cq.cq_query_run(t, plan)
+    got = cq.fetch_all(res)
+    ref = oracle_mod.query(table, plan, n_threads=4)
+    check(got, ref, "hetero+")
+    strings = table.columns[1].strings
+    for row in [0, len(got[0]) // 2, len(got[0]) - 1]:
+        assert cq.cq_result_key_string(res, 1, row) == strings[int(got[1][row])]
+
+
+# ------------------------------------------------------------------ random tables, every encoding
+ENCS = ["rle", "plain", "packed", "index", "dict"]
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_tables(cq, ctx, oracle_mod, seed):
+    rng = np.random.default_rng(5000 + seed)
+    n = int(rng.choice([1, 31, 1000, 4095, 4096, 4097, 20000, 70001]))
+    ncol = int(rng.integers(1, 5))
+    cols = [random_column(rng, n, str(rng.choice(ENCS))) for _ in range(ncol)]
+    table = dg.Table(cols, n)
+    plan = random_plan(rng, table)
+    ref = oracle_mod.query(table, plan)
+    tile = int(rng.choice([1024, 2048, 4096, 8192]))
+    opts = cq.exec_options(tile_rows=tile, stages=int(rng.choice([2, 3, 4])),
+                           table_slots=int(rng.choice([128, 1024])))
+    check(run(cq, ctx, table, plan, device=bool(seed % 2), opts=opts), ref, f"seed {seed} tile {tile}")
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_decompress_then_scan_matches(cq, ctx, oracle_mod, seed):
+    rng = np.random.default_rng(9000 + seed)
+    n = int(rng.choice([100, 5000, 50001]))
+    cols = [random_column(rng, n, str(rng.choice(ENCS))) for _ in range(3)]
+    table = dg.Table(cols, n)
+    plan = random_plan(rng, table)
+    ref = oracle_mod.query(table, plan)
+    check(run(cq, ctx, table, plan, opts=cq.exec_options(mode=cq.CQ_EXEC_DECOMPRESS_THEN_SCAN)), ref, "dts")
+
+
+# ------------------------------------------------------------------ segment-mode edge cases
+def _rle(vals, ends, n, vt=np.int64, et=np.int64):
+    return dg.RLE(np.asarray(vals, dtype=vt), np.asarray(ends, dtype=et), n)
+
+
+@pytest.mark.parametrize("case", ["one_run", "unit_runs", "same_bounds", "tile_edges", "int32", "long_table"])
+def test_rle_shapes(cq, ctx, oracle_mod, case):
+    rng = np.random.default_rng(hash(case) % 1000)
+    n = 50_000
+    if case == "one_run":
+        a = _rle([7], [n], n)
+        b = dg.make_rle(rng, n, 3.0, 0, 9, np.int64, np.int64)
+    elif case == "unit_runs":
+        a = _rle(rng.integers(0, 5, n), np.arange(1, n + 1), n)
+        b = _rle(rng.integers(0, 3, n), np.arange(1, n + 1), n)
+    elif case == "same_bounds":
+        ends = dg.geometric_ends(rng, n, 7.0, np.int64)
+        a = _rle(rng.integers(0, 50, ends.shape[0]), ends, n)
+        b = _rle(rng.integers(0, 4, ends.shape[0]), ends, n)
+    elif case == "tile_edges":
+        ends = np.arange(1024, n, 1024).tolist() + [n]
+        a = _rle(rng.integers(0, 50, len(ends)), ends, n)
+        b = _rle(rng.integers(0, 4, len(ends) + 1), sorted(set(ends + [4096 * 3 + 1])), n)
+    elif case == "int32":
+        a = dg.make_rle(rng, n, 4.0, -100, 100, np.int32, np.int32)
+        b = dg.make_rle(rng, n, 2.0, 0, 20, np.int32, np.int32)
+    else:
+        n = 3_000_001
+        a = dg.make_rle(rng, n, 30.0, 0, 99, np.int64, np.int64)
+        b = dg.make_rle(rng, n, 300.0, 0, 9, np.int64, np.int64)
+    table = dg.Table([a, b], n)
+    plan = dg.Plan([dg.Pred(0, "lt", 25)], [1], [dg.Agg("sum", 0), dg.Agg("count"), dg.Agg("min", 0),
+                                                 dg.Agg("max", 0), dg.Agg("avg", 0)])
+    check(run(cq, ctx, table, plan), oracle_mod.query(table, plan), case)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
+def test_materialised_alignment(cq, ctx, oracle_mod, k):
+    import torch
+    rng = np.random.default_rng(k)
+    n = 100_003
+    cols = [dg.make_rle(rng, n, float(rng.choice([1.5, 6.0, 400.0])), 0, 9, np.int64,
+                        np.int64 if j % 2 else np.int32) for j in range(k)]
+    seg, ridx = oracle_mod.align([c.run_ends for c in cols], n)
+    handles = [cq.column_from(ctx, c) for c in cols]
+    S = cq.cq_align_segments(ctx, handles)
+    assert S == seg.shape[0]
+    d_seg = torch.empty(S, dtype=torch.int64, device="cuda")
+    d_ridx = torch.empty(k * S, dtype=torch.int64, device="cuda")
+    assert cq.cq_align_segments(ctx, handles, d_seg, d_ridx, S) == S
+    np.testing.assert_array_equal(d_seg.cpu().numpy(), seg)
+    np.testing.assert_array_equal(d_ridx.cpu().numpy().reshape(k, S), ridx)
+
+
+# ------------------------------------------------------------------ packed widths and index density
+@pytest.mark.parametrize("w", [1, 3, 7, 13, 20, 31, 32, 33, 47, 63, 64])
+def test_bit_widths(cq, ctx, oracle_mod, w):
+    rng = np.random.default_rng(w)
+    n = 9000 + w
+    off = rng.integers(0, 2**63, size=n, dtype=np.uint64) & np.uint64((1 << w) - 1 if w < 64 else 2**64 - 1)
+    base = -(1 << 40) if w < 40 else 0
+    p = dg.make_packed(off, w, base)
+    key = dg.Plain(rng.integers(0, 3, n).astype(np.int64))
+    table = dg.Table([p, key], n)
+    plan = dg.Plan([dg.Pred(0, "ge", base + 1)], [1], [dg.Agg("min", 0), dg.Agg("max", 0), dg.Agg("count"),
+                                                      dg.Agg("avg", 0)])
+    check(run(cq, ctx, table, plan), oracle_mod.query(table, plan), f"w={w}")
+
+
+@pytest.mark.parametrize("nnz", ["zero", "all", "one"])
+def test_index_density(cq, ctx, oracle_mod, nnz):
+    rng = np.random.default_rng(11)
+    n = 20_000
+    k = {"zero": 0, "all": n, "one": 1}[nnz]
+    x = dg.make_index(rng, n, k, -1000, 1000, default=5)
+    key = dg.make_rle(rng, n, 100.0, 0, 4, np.int64, np.int64)
+    table = dg.Table([x, key], n)
+    plan = dg.Plan([], [1], [dg.Agg("sum", 0), dg.Agg("min", 0), dg.Agg("max", 0), dg.Agg("count")])
+    check(run(cq, ctx, table, plan), oracle_mod.query(table, plan), nnz)
+    plan = dg.Plan([dg.Pred(0, "ne", 5)], [0], [dg.Agg("count")])
+    check(run(cq, ctx, table, plan), oracle_mod.query(table, plan), nnz + " key")
+
+
+# ------------------------------------------------------------------ degenerate plans and errors
+def test_no_group_by_nothing_passes(cq, ctx, oracle_mod):
+    table, plan = dg.tiny_two_rle(10_000)
+    plan = dg.Plan([dg.Pred(0, "lt", -1)], [], [dg.Agg("sum", 0), dg.Agg("count"), dg.Agg("min", 0),
+                                                dg.Agg("avg", 0)])
+    got = run(cq, ctx, table, plan)
+    check(got, oracle_mod.query(table, plan), "empty")
+    assert got[1][0] == 0
+
+
+def test_in_list_with_unknown_strings(cq, ctx, oracle_mod):
+    table, plan = dg.heterogeneous(300_000, seed=9)
+    plan = dg.Plan([dg.Pred(1, "in", strs=[b"not-a-word", b"zzzz"])], [0], [dg.Agg("count")])
+    got = run(cq, ctx, table, plan)
+    check(got, oracle_mod.query(table, plan), "unknown")
+    assert len(got[0]) == 0
+
+
+def test_sum_overflow_is_an_error(cq, ctx):
+    big = 2**62 + 1
+    table = dg.Table([_rle([big, big], [3, 5], 5)], 5)
+    t, cols = cq.table_from(ctx, table)
+    res = cq.cq_query_run(t, dg.Plan([], [], [dg.Agg("sum", 0)]))
+    with pytest.raises(cq.CQError) as e:
+        cq.cq_result_wait(res)
+    assert e.value.status == cq.CQ_ERR_OVERFLOW
+    # AVG of the same values is still exact
+    res = cq.cq_query_run(t, dg.Plan([], [], [dg.Agg("avg", 0)]))
+    assert cq.fetch_all(res)[0][0] == float(5 * big) / 5.0
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "short", "pos_range", "code_range", "few_words"])
+def test_malformed_columns_rejected(cq, ctx, bad):
+    n = 10
+    with pytest.raises(cq.CQError) as e:
+        if bad == "unsorted":
+            cq.cq_column_create_rle(ctx, np.array([1, 2]), np.array([6, 4]), n)
+        elif bad == "short":
+            cq.cq_column_create_rle(ctx, np.array([1, 2]), np.array([4, 9]), n)
+        elif bad == "pos_range":
+            cq.cq_column_create_index(ctx, np.array([1]), np.array([10]), 0, n)
+        elif bad == "code_range":
+            cq.column_from(ctx, dg.make_dict([b"x", b"y", b"z"], np.full(n, 3, dtype=np.uint64), 2))
+        else:
+            cq.cq_column_create_bitpacked(ctx, np.zeros(2, dtype=np.uint32), 7, 0, n)
+    assert e.value.status in (cq.CQ_ERR_UNSORTED, cq.CQ_ERR_SIZE_MISMATCH, cq.CQ_ERR_INVALID_ARG)
+
+
+def test_repeat_runs_are_deterministic(cq, ctx):
+    table, plan = dg.heterogeneous(500_000, seed=1)
+    t, cols = cq.table_from(ctx, table)
+    a = cq.fetch_all(cq.cq_query_run(t, plan))
+    b = cq.fetch_all(cq.cq_query_run(t, plan))
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
