@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the compressed-domain query path on one GB300 (or N replicas).
+
+Workload (default): the heterogeneous 100M-row table -- int32 RLE key (mean
+run 1000), 10,000-entry dictionary column with Zipf(1.1) codes packed in 14
+bits, 1%-dense index-encoded int64, plain int32, 20-bit bit-packed int64 --
+and SELECT c1, c2, SUM(c3), SUM(c5), MIN(c5), MAX(c5), COUNT(*) WHERE c2 IN
+(64 strings) AND c4 BETWEEN 250000 AND 749999 GROUP BY c1, c2.
+
+One step = one query (plan, init, fused kernel, finalize) over the table
+resident in HBM.  The inputs (838 MB compressed) are larger than the 129 MB
+L2, so no flush is needed between steps.  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "logical rows/s"
+UNIT = "rows/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cq", choices=["cq", "reference"])
+    ap.add_argument("--workload", default="heterogeneous", choices=["heterogeneous", "tiny"])
+    ap.add_argument("--rows", type=int, default=0, help="override the workload's row count")
+    ap.add_argument("--seed", type=int, default=20250611)
+    ap.add_argument("--mode", default="fused", choices=["fused", "decompress_then_scan"])
+    ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--table-slots", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2506_10092_gb300 import datagen as dg
+    if args.workload == "tiny":
+        n = args.rows or 1_000_000
+        table, plan = dg.tiny_two_rle(n, seed=args.seed)
+        name = f"tiny-two-rle-{n}"
+    else:
+        n = args.rows or 100_000_000
+        table, plan = dg.heterogeneous(n, seed=args.seed)
+        name = f"heterogeneous-5col-{n}"
+    return name, table, plan
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2506_10092_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(workload_name: str):
+    """dram bytes per launch of the fused kernel from the committed ncu summary,
+    when it was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "fused_query_kernel_heterogeneous.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("kernel_sources_sha256_16") != kernel_source_hash():
+            return None
+        if d.get("workload") != workload_name:
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def exec_opts(cq, args):
+    mode = cq.CQ_EXEC_FUSED if args.mode == "fused" else cq.CQ_EXEC_DECOMPRESS_THEN_SCAN
+    return cq.exec_options(mode=mode, tile_rows=args.tile_rows, stages=args.stages, table_slots=args.table_slots)
+
+
+def cpu_oracle_rate(table, plan, seconds: float):
+    """The oracle as it stands, on this host's cores, over a bounded prefix
+    sample of the workload.  Returns (rows/s, cores, sample description)."""
+    from oracle import oracle
+    cores = oracle.cores()
+    probe = min(table.n_rows, 2_000_000)
+    t0 = time.perf_counter()
+    oracle.query(table, plan, row_ranges=[(0, probe)], n_threads=cores)
+    dt = max(1e-3, time.perf_counter() - t0)
+    rows = int(min(table.n_rows, max(probe, probe * seconds / dt)))
+    t0 = time.perf_counter()
+    oracle.query(table, plan, row_ranges=[(0, rows)], n_threads=cores)
+    dt = time.perf_counter() - t0
+    return rows / dt, cores, f"first {rows} rows of the same table, {cores} threads, {dt:.1f} s"
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return
+    name, table, plan = workload(args)
+    from oracle import oracle
+    cores = oracle.cores()
+    probe = min(table.n_rows, 1_000_000)
+    t0 = time.perf_counter()
+    oracle.query(table, plan, row_ranges=[(0, probe)], n_threads=cores)
+    rate = probe / max(1e-3, time.perf_counter() - t0)
+    budget = 90.0 / max(1, args.steps + args.warmup)      # seconds per step
+    rows = int(min(table.n_rows, max(100_000, rate * budget)))
+    for _ in range(args.warmup):
+        oracle.query(table, plan, row_ranges=[(0, rows)], n_threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.query(table, plan, row_ranges=[(0, rows)], n_threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = rows * args.steps / total
+    sample = f"first {rows} rows per step of the same table, {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": name, "rows": table.n_rows, "sample_rows": rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def pinned_copy(torch, a):
+    import numpy as np
+    t = torch.empty(a.shape[0], dtype=getattr(torch, str(a.dtype)) if str(a.dtype) != "uint32" else torch.int32,
+                    pin_memory=True)
+    t.numpy()[:] = a.view(np.int32) if str(a.dtype) == "uint32" else a
+    return t
+
+
+def run_cq(args):
+    import numpy as np
+    import torch
+    from paper_2506_10092_gb300 import cq
+    from paper_2506_10092_gb300 import datagen as dg
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    name, table, plan = workload(args)
+    used = dg.plan_columns(plan)
+    alg_bytes = dg.compressed_bytes(table, used)
+    ctx = cq.cq_ctx_create(local, stream)
+    t, cols = cq.table_from(ctx, table)
+    ps = cq.PlanStruct(plan)
+    opts = exec_opts(cq, args)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    for _ in range(max(3, args.warmup)):
+        r = cq.cq_query_run(t, ps, stream=stream, opts=opts)
+        cq.cq_result_wait(r)
+        r.close()
+    n_groups = None
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    time.sleep(0.2)
+    results = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        results.append(cq.cq_query_run(t, ps, stream=stream, opts=opts))
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    kernel_us = [cq.cq_result_kernel_time_us(r) for r in results]
+    n_groups = cq.cq_result_num_groups(results[-1])
+    for r in results:
+        cq.cq_result_wait(r)
+        r.close()
+    if ws > 1:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = table.n_rows * args.steps * ws / (elapsed_ms / 1000.0)
+    k_us = statistics.mean(kernel_us)
+    peak, peak_src = measured_peak()
+    achieved = alg_bytes / (k_us * 1e-6) / 1e9
+    traffic = profile_traffic(name)
+
+    # end to end through the public API: pinned host buffers -> columns ->
+    # query -> result read back, every step
+    e2e = None
+    if not args.no_e2e:
+        host = []
+        h2d = 0
+        for c in table.columns:
+            if c.enc == "rle":
+                host.append((c, pinned_copy(torch, c.run_values), pinned_copy(torch, c.run_ends)))
+                h2d += c.run_values.nbytes + c.run_ends.nbytes
+            elif c.enc in ("dict", "packed"):
+                need = (c.n_rows * c.bit_width + 31) // 32
+                host.append((c, pinned_copy(torch, c.words[:((need + 3) // 4) * 4 + 4]), None))
+                h2d += need * 4
+            elif c.enc == "index":
+                host.append((c, pinned_copy(torch, c.values), pinned_copy(torch, c.positions)))
+                h2d += c.values.nbytes + c.positions.nbytes
+            else:
+                host.append((c, pinned_copy(torch, c.values), None))
+                h2d += c.values.nbytes
+
+        def e2e_step():
+            hc = []
+            for c, a, b in host:
+                if c.enc == "rle":
+                    hc.append(cq.cq_column_create_rle(ctx, a, b, c.n_rows))
+                elif c.enc == "dict":
+                    hc.append(cq.cq_column_create_dict(ctx, c.strings, a, c.bit_width, c.n_rows))
+                elif c.enc == "packed":
+                    hc.append(cq.cq_column_create_bitpacked(ctx, a, c.bit_width, c.base, c.n_rows))
+                elif c.enc == "index":
+                    hc.append(cq.cq_column_create_index(ctx, a, b, c.default, c.n_rows))
+                else:
+                    hc.append(cq.cq_column_create_plain(ctx, a))
+            tb = cq.cq_table_bind(ctx, hc)
+            res = cq.cq_query_run(tb, ps, stream=stream, opts=opts)
+            out = cq.fetch_all(res)
+            res.close()
+            tb.close()
+            for h in hc:
+                h.close()
+            return sum(o.nbytes for o in out)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.e2e_steps):
+            d2h = e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            tt = torch.tensor([dt], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e = {"value": table.n_rows * args.e2e_steps * ws / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h + 16, "steps": args.e2e_steps,
+               "note": "columns created from pinned host buffers (library copy + validation), query, result fetch"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(table, plan, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": name, "rows": table.n_rows, "compressed_bytes": alg_bytes, "groups": n_groups,
+                       "mode": args.mode, "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2 (compressed columns exceed 129 MB); no flush"},
+            "compressed_gbs": alg_bytes * args.steps * ws / (elapsed_ms / 1000.0) / 1e9,
+            "pct_hbm_peak": alg_bytes * args.steps / (elapsed_ms / 1000.0) / 1e9 / peak,
+            "kernel_us": k_us,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "fused_query_kernel", "peak_source": f"{peak_src} hbm_gbs",
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": 5 * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cq(args)
+
+
+if __name__ == "__main__":
+    main()

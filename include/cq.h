@@ -259,6 +259,10 @@ int cq_result_key_string(cq_result* res, uint32_t key_col, uint64_t row,
  * (CUDA events on the query's stream; waits for the query). */
 int cq_result_device_time_us(cq_result* res, double* us);
 
+/* Microseconds of the fused compressed-domain kernel alone (CUDA events
+ * recorded on the query's stream immediately around that launch; waits). */
+int cq_result_kernel_time_us(cq_result* res, double* us);
+
 int cq_result_destroy(cq_result* res);
 
 /* ------------------------------------------------------------------ alignment

@@ -95,6 +95,7 @@ _SIGS = {
     "cq_result_device_column": [_VP, C.c_uint32, C.POINTER(_VP)],
     "cq_result_key_string": [_VP, C.c_uint32, C.c_uint64, C.POINTER(C.c_char_p), C.POINTER(C.c_uint32)],
     "cq_result_device_time_us": [_VP, C.POINTER(C.c_double)],
+    "cq_result_kernel_time_us": [_VP, C.POINTER(C.c_double)],
     "cq_result_destroy": [_VP],
     "cq_align_segments": [_VP, _VP, C.c_uint32, _VP, _VP, _VP, C.c_uint64, C.POINTER(C.c_uint64)],
     "cq_server_create": [_VP, C.POINTER(cq_server_options), C.POINTER(_VP)],
@@ -141,7 +142,7 @@ def _is_dev(a) -> bool:
 def _ptr(a):
     if a is None:
         return None
-    if _is_dev(a):
+    if _is_dev(a) or hasattr(a, "data_ptr"):     # CUDA tensor, or a (pinned) host tensor
         return a.data_ptr() if a.numel() else None
     return a.ctypes.data if a.size else None
 
@@ -342,6 +343,12 @@ def cq_result_key_string(res, key_col: int, row: int) -> bytes:
 def cq_result_device_time_us(res) -> float:
     t = C.c_double()
     _check(lib.cq_result_device_time_us(res.ptr, C.byref(t)))
+    return t.value
+
+
+def cq_result_kernel_time_us(res) -> float:
+    t = C.c_double()
+    _check(lib.cq_result_kernel_time_us(res.ptr, C.byref(t)))
     return t.value
 
 

@@ -551,8 +551,10 @@ static void set_members(PredDesc& d, std::vector<int64_t> vals, std::vector<uint
   }
 }
 
-static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
-                      const cq_exec_options* opts, const cq_ctx* ctx, Planned* P) {
+static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
+                           const cq_exec_options* opts, const cq_ctx* ctx, uint32_t tile, Planned* P,
+                           bool* no_fit) {
+  *no_fit = false;
   if (!plan) return set_error(CQ_ERR_INVALID_ARG, "plan is NULL");
   if (plan->n_preds > (uint32_t)kMaxPreds || plan->n_group_by > (uint32_t)kMaxKeys || plan->n_aggs > (uint32_t)kMaxAggs)
     return set_error(CQ_ERR_INVALID_ARG, "plan exceeds 16 predicates / 8 group-by columns / 16 aggregates");
@@ -585,9 +587,6 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
       return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: SUM/AVG of a dictionary column", i);
   }
   // ---- tile / pipeline shape
-  uint32_t tile = opts && opts->tile_rows ? opts->tile_rows : 4096;
-  if (tile < 1024 || tile > 8192 || (tile & (tile - 1)))
-    return set_error(CQ_ERR_INVALID_ARG, "tile_rows must be 1024, 2048, 4096 or 8192");
   q.tile_rows = tile;
   q.n_tiles = (n_rows + tile - 1) / tile;
   q.n_cols = (uint8_t)order.size();
@@ -860,6 +859,7 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
     }
     if (!q.seg_mode && q.stages > 2) { q.stages--; continue; }
     if (!q.table_dense && q.table_slots > 128) { q.table_slots /= 2; continue; }
+    *no_fit = true;
     return set_error(CQ_ERR_UNSUPPORTED, "query does not fit in %zu bytes of shared memory (tile_rows %u)",
                      ctx->smem_optin, tile);
   }
@@ -881,6 +881,21 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
     P->out_key_col.push_back(-1);
   }
   return CQ_OK;
+}
+
+// Plan with the requested tile, halving it while the query does not fit in
+// shared memory.
+static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
+                      const cq_exec_options* opts, const cq_ctx* ctx, Planned* P) {
+  uint32_t tile = opts && opts->tile_rows ? opts->tile_rows : 4096;
+  if (tile < 1024 || tile > 8192 || (tile & (tile - 1)))
+    return set_error(CQ_ERR_INVALID_ARG, "tile_rows must be 1024, 2048, 4096 or 8192");
+  for (;;) {
+    bool no_fit = false;
+    const int rc = plan_query_tile(tcols, n_rows, plan, opts, ctx, tile, P, &no_fit);
+    if (rc == CQ_OK || !no_fit || tile <= 1024) return rc;
+    tile /= 2;
+  }
 }
 
 // Carve one pool allocation into the query's device buffers and enqueue
@@ -916,7 +931,9 @@ static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r)
     if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "aux upload failed: %s", cudaGetErrorString(e));
   }
   e = launch_init_global(q, s);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev_k0, s);
   if (e == cudaSuccess) e = launch_query(q, s, ctx->num_sms, P.ctas_per_sm);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev_k1, s);
   if (e == cudaSuccess) e = launch_finalize(q, s);
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
   r->desc = q;
@@ -935,6 +952,8 @@ static cq_result* new_result(cq_ctx* ctx, cudaStream_t s) {
   r->stream = s;
   cudaEventCreate(&r->ev_start);
   cudaEventCreate(&r->ev_done);
+  cudaEventCreate(&r->ev_k0);
+  cudaEventCreate(&r->ev_k1);
   return r;
 }
 
@@ -944,6 +963,8 @@ static void free_result(cq_result* r) {
   for (void* p : r->extra_dev) cudaFreeAsync(p, r->stream);
   if (r->ev_start) cudaEventDestroy(r->ev_start);
   if (r->ev_done) cudaEventDestroy(r->ev_done);
+  if (r->ev_k0) cudaEventDestroy(r->ev_k0);
+  if (r->ev_k1) cudaEventDestroy(r->ev_k1);
   delete r;
 }
 
@@ -1113,6 +1134,17 @@ extern "C" int cq_result_device_time_us(cq_result* r, double* us) {
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "%s", cudaGetErrorString(e));
   float ms = 0.f;
   e = cudaEventElapsedTime(&ms, r->ev_start, r->ev_done);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "%s", cudaGetErrorString(e));
+  *us = ms * 1000.0;
+  return CQ_OK;
+}
+
+extern "C" int cq_result_kernel_time_us(cq_result* r, double* us) {
+  if (!r || !us) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  cudaError_t e = cudaEventSynchronize(r->ev_done);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "%s", cudaGetErrorString(e));
+  float ms = 0.f;
+  e = cudaEventElapsedTime(&ms, r->ev_k0, r->ev_k1);
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "%s", cudaGetErrorString(e));
   *us = ms * 1000.0;
   return CQ_OK;

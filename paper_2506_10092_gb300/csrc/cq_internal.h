@@ -189,6 +189,7 @@ struct cq_result {
   cq_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;   // around the fused kernel
   void* dev_block = nullptr;       // one pool allocation holding every device buffer
   size_t dev_bytes = 0;
   cq::QueryDesc desc;              // as launched
