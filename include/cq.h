@@ -204,7 +204,8 @@ typedef struct {
   uint32_t ctas_per_sm;  /* 0 = default */
   uint32_t stages;       /* bulk-copy pipeline depth (2..8); 0 = default */
   uint32_t table_slots;  /* shared-memory group-table slots per CTA (power of 2); 0 = default */
-  uint32_t reserved[3];
+  uint32_t grid_ctas;    /* CTAs of the fused kernel; 0 = SMs x ctas_per_sm */
+  uint32_t reserved[2];
 } cq_exec_options;
 
 /* ------------------------------------------------------------------ queries */

@@ -56,7 +56,8 @@ class cq_plan(C.Structure):
 
 class cq_exec_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile_rows", C.c_uint32), ("ctas_per_sm", C.c_uint32),
-                ("stages", C.c_uint32), ("table_slots", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+                ("stages", C.c_uint32), ("table_slots", C.c_uint32), ("grid_ctas", C.c_uint32),
+                ("reserved", C.c_uint32 * 2)]
 
 
 class cq_server_options(C.Structure):
@@ -287,9 +288,11 @@ class PlanStruct:
         self.plan = plan
 
 
-def exec_options(mode=CQ_EXEC_FUSED, tile_rows=0, ctas_per_sm=0, stages=0, table_slots=0) -> cq_exec_options:
+def exec_options(mode=CQ_EXEC_FUSED, tile_rows=0, ctas_per_sm=0, stages=0, table_slots=0,
+                 grid_ctas=0) -> cq_exec_options:
     o = cq_exec_options()
     o.mode, o.tile_rows, o.ctas_per_sm, o.stages, o.table_slots = mode, tile_rows, ctas_per_sm, stages, table_slots
+    o.grid_ctas = grid_ctas
     return o
 
 

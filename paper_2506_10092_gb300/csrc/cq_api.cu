@@ -461,6 +461,7 @@ struct Planned {
   std::vector<uint32_t> out_kind;
   std::vector<int> out_key_col;
   int ctas_per_sm = 1;
+  uint32_t grid_ctas = 0;
 };
 
 static bool is_dict(const PlanCol& c) { return c.src && c.src->enc == ENC_DICT; }
@@ -864,6 +865,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
                      ctx->smem_optin, tile);
   }
   P->ctas_per_sm = opts && opts->ctas_per_sm ? (int)opts->ctas_per_sm : 1;
+  P->grid_ctas = opts ? opts->grid_ctas : 0u;
   // ---- outputs
   q.n_out = plan->n_group_by + plan->n_aggs;
   P->out_kind.clear();
@@ -932,7 +934,7 @@ static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r)
   }
   e = launch_init_global(q, s);
   if (e == cudaSuccess) e = cudaEventRecord(r->ev_k0, s);
-  if (e == cudaSuccess) e = launch_query(q, s, ctx->num_sms, P.ctas_per_sm);
+  if (e == cudaSuccess) e = launch_query(q, s, ctx->num_sms, P.ctas_per_sm, P.grid_ctas);
   if (e == cudaSuccess) e = cudaEventRecord(r->ev_k1, s);
   if (e == cudaSuccess) e = launch_finalize(q, s);
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));

@@ -215,7 +215,7 @@ int set_error(int status, const char* fmt, ...);
 void clear_error();
 
 // kernels / launchers (cq_query.cu)
-cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ctas_per_sm);
+cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ctas_per_sm, uint32_t grid_ctas);
 cudaError_t launch_init_global(const QueryDesc& q, cudaStream_t s);
 cudaError_t launch_finalize(const QueryDesc& q, cudaStream_t s);
 size_t query_kernel_smem(const QueryDesc& q);

@@ -214,14 +214,17 @@ __device__ __forceinline__ bool key_digit(const QueryDesc& q, const KeyDesc& k, 
 }
 
 // ------------------------------------------------------------------ group table
-__device__ __forceinline__ uint32_t hash_gid(uint32_t g) { return g * 0x9E3779B1u; }
+// multiplicative hashing: the top bits of gid * golden ratio select the slot
+__device__ __forceinline__ uint32_t hash_gid(uint32_t g, uint32_t log2_slots) {
+  return (g * 0x9E3779B1u) >> (32 - log2_slots);
+}
 
 // Shared-memory slot of gid, or -1 when the probe limit is hit (caller then
 // updates the global accumulators directly).
 __device__ __forceinline__ int table_slot(const QueryDesc& q, const Smem& sm, uint32_t gid) {
   if (q.table_dense) return (int)gid;
   const uint32_t mask = q.table_slots - 1;
-  uint32_t h = (hash_gid(gid) >> 7) & mask;
+  uint32_t h = hash_gid(gid, 31 - __clz(q.table_slots)) & mask;
   for (int probe = 0; probe < 32; ++probe) {
     uint32_t k = sm.tkeys[h];
     if (k == gid) return (int)h;
@@ -939,8 +942,9 @@ cudaError_t launch_init_global(const QueryDesc& q, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ctas_per_sm) {
-  const unsigned long long want = (unsigned long long)num_sms * (unsigned long long)ctas_per_sm;
+cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ctas_per_sm, uint32_t grid_ctas) {
+  const unsigned long long want =
+      grid_ctas ? (unsigned long long)grid_ctas : (unsigned long long)num_sms * (unsigned long long)ctas_per_sm;
   const unsigned grid = (unsigned)(q.n_tiles < want ? q.n_tiles : want);
   if (grid == 0) return cudaSuccess;
   if (q.seg_mode) fused_query_kernel<true><<<grid, kThreads, q.smem_bytes, s>>>(q);

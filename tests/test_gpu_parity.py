@@ -231,3 +231,22 @@ def test_repeat_runs_are_deterministic(cq, ctx):
     b = cq.fetch_all(cq.cq_query_run(t, plan))
     for x, y in zip(a, b):
         np.testing.assert_array_equal(x, y)
+
+
+# ------------------------------------------------------------------ many tiles per CTA
+@pytest.mark.parametrize("grid,tile,slots", [(1, 1024, 128), (3, 4096, 1024), (7, 2048, 256), (16, 8192, 0)])
+def test_many_tiles_per_cta_heterogeneous(cq, ctx, oracle_mod, grid, tile, slots):
+    """Few CTAs walk many tiles each: bulk-copy stages are reused, run and
+    position cursors carry across tiles and the group table flushes often."""
+    table, plan = dg.heterogeneous(3_000_000 + 123, seed=21, index_default=3)
+    ref = oracle_mod.query(table, plan, n_threads=4)
+    opts = cq.exec_options(tile_rows=tile, grid_ctas=grid, table_slots=slots)
+    check(run(cq, ctx, table, plan, opts=opts), ref, f"grid {grid}")
+
+
+@pytest.mark.parametrize("grid", [1, 5])
+def test_many_tiles_per_cta_segments(cq, ctx, oracle_mod, grid):
+    table, plan = dg.tiny_two_rle(1_000_000, seed=3)
+    plan = dg.Plan(plan.preds, [1, 0], plan.aggs + [dg.Agg("max", 0)])
+    ref = oracle_mod.query(table, plan)
+    check(run(cq, ctx, table, plan, opts=cq.exec_options(grid_ctas=grid, tile_rows=1024)), ref, f"seg grid {grid}")
