@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--table-slots", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -156,7 +157,8 @@ def dist():
 
 def exec_opts(cq, args):
     mode = cq.CQ_EXEC_FUSED if args.mode == "fused" else cq.CQ_EXEC_DECOMPRESS_THEN_SCAN
-    return cq.exec_options(mode=mode, tile_rows=args.tile_rows, stages=args.stages, table_slots=args.table_slots)
+    return cq.exec_options(mode=mode, tile_rows=args.tile_rows, stages=args.stages, table_slots=args.table_slots,
+                           ctas_per_sm=args.ctas_per_sm)
 
 
 def cpu_oracle_rate(table, plan, seconds: float):

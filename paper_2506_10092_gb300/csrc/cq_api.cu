@@ -155,6 +155,10 @@ extern "C" int cq_ctx_create(int device, void* cuda_stream, cq_ctx** out) {
   int smem = 0;
   CQ_CUDA(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
   c->smem_optin = (size_t)smem;
+  int per_sm = 0, reserved = 0;
+  CQ_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+  CQ_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
+  c->smem_two = (size_t)(per_sm / 2 - reserved);
   cudaMemPoolProps props{};
   props.allocType = cudaMemAllocationTypePinned;
   props.location.type = cudaMemLocationTypeDevice;
@@ -553,8 +557,8 @@ static void set_members(PredDesc& d, std::vector<int64_t> vals, std::vector<uint
 }
 
 static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
-                           const cq_exec_options* opts, const cq_ctx* ctx, uint32_t tile, Planned* P,
-                           bool* no_fit) {
+                           const cq_exec_options* opts, const cq_ctx* ctx, uint32_t tile, int ncw,
+                           size_t smem_limit, Planned* P, bool* no_fit) {
   *no_fit = false;
   if (!plan) return set_error(CQ_ERR_INVALID_ARG, "plan is NULL");
   if (plan->n_preds > (uint32_t)kMaxPreds || plan->n_group_by > (uint32_t)kMaxKeys || plan->n_aggs > (uint32_t)kMaxAggs)
@@ -626,6 +630,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   q.seg_mode = nrow == 0;
   q.stage_bytes = stage_off;
   q.stages = (uint8_t)(opts && opts->stages ? opts->stages : 4);
+  q.ncw = (uint8_t)ncw;
   if (q.stages < 2 || q.stages > 8) return set_error(CQ_ERR_INVALID_ARG, "stages must be in 2..8");
   auto& aux = P->aux;
   // ---- predicates
@@ -705,6 +710,37 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
         in_count[ci]++;
         break;
       }
+    }
+  }
+  // ---- 32-bit evaluation where the column's raw values fit int32
+  for (uint32_t i = 0; i < plan->n_preds; ++i) {
+    PredDesc& d = q.preds[i];
+    const ColDesc& cd = q.cols[d.col];
+    const PlanCol& pc = tcols[plan->preds[i].col];
+    bool narrow = false;
+    switch (cd.enc) {
+      case ENC_PLAIN: narrow = !cd.v64; break;
+      case ENC_PACKED: narrow = cd.raw_is_offset && cd.bw <= 31; break;
+      case ENC_DICT: narrow = cd.bw <= 31; break;
+      case ENC_RLE: narrow = !cd.v64; break;
+      case ENC_INDEX: narrow = !cd.v64 && pc.base >= INT_MIN && pc.base <= INT_MAX; break;
+    }
+    d.n32 = 0;
+    if (!narrow) continue;
+    if (d.kind == PK_RANGE) {
+      const int64_t lo = std::max<int64_t>(d.lo, INT_MIN), hi = std::min<int64_t>(d.hi, INT_MAX);
+      if (lo > hi) { d.kind = PK_FALSE; continue; }
+      d.lo32 = (int32_t)lo;
+      d.hi32 = (int32_t)hi;
+      d.n32 = 1;
+    } else if (d.kind == PK_NE) {
+      if (d.lo < INT_MIN || d.lo > INT_MAX) { d.kind = PK_TRUE; continue; }
+      d.lo32 = (int32_t)d.lo;
+      d.n32 = 1;
+    } else if (d.kind == PK_BITMAP && d.lo >= INT_MIN && d.hi <= INT_MAX) {
+      d.lo32 = (int32_t)d.lo;
+      d.hi32 = (int32_t)d.hi;
+      d.n32 = 1;
     }
   }
   // ---- group keys (dense mixed radix, first key most significant)
@@ -815,11 +851,20 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
         d.base = 0;
       }
       d.wide = bound * (i128)q.flush_rows >= ((i128)1 << 62) ? 1 : 0;
+      // raw values small enough to be summed across a warp in 32 bits
+      i128 rlo, rhi;
+      if (cd.raw_is_offset) { rlo = pc.stats.min_raw; rhi = pc.stats.max_raw; }
+      else { rlo = pc.stats.min_val; rhi = pc.stats.max_val; }
+      d.red32 = (!idx && !d.wide && rlo > -((i128)1 << 26) && rhi < ((i128)1 << 26)) ? 1 : 0;
       d.sw = (uint8_t)sw;
       sw += d.wide ? 2 : 1;
       d.gw = gw;
       gw += 3;
     } else {  // MIN / MAX
+      i128 rlo, rhi;
+      if (idx || cd.raw_is_offset) { rlo = pc.stats.min_raw; rhi = pc.stats.max_raw; }
+      else { rlo = pc.stats.min_val; rhi = pc.stats.max_val; }
+      d.w32 = (rlo >= (i128)INT_MIN && rhi <= (i128)INT_MAX) ? 1 : 0;
       if (idx) {
         d.kind = a.op == CQ_MIN ? AK_IMIN : AK_IMAX;
         d.base = pc.base;
@@ -851,10 +896,11 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     q.table_slots = slots;
   }
   // ---- fit shared memory: fewer stages, then fewer slots
+  q.aux_words = (uint32_t)aux.size();
   for (;;) {
     q.smem_bytes = 0;
     const size_t need = query_kernel_smem(q);
-    if (need <= ctx->smem_optin) {
+    if (need <= smem_limit) {
       q.smem_bytes = (uint32_t)need;
       break;
     }
@@ -862,9 +908,9 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     if (!q.table_dense && q.table_slots > 128) { q.table_slots /= 2; continue; }
     *no_fit = true;
     return set_error(CQ_ERR_UNSUPPORTED, "query does not fit in %zu bytes of shared memory (tile_rows %u)",
-                     ctx->smem_optin, tile);
+                     smem_limit, tile);
   }
-  P->ctas_per_sm = opts && opts->ctas_per_sm ? (int)opts->ctas_per_sm : 1;
+  P->ctas_per_sm = (!q.seg_mode && ncw == 8) ? 2 : 1;
   P->grid_ctas = opts ? opts->grid_ctas : 0u;
   // ---- outputs
   q.n_out = plan->n_group_by + plan->n_aggs;
@@ -885,19 +931,50 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   return CQ_OK;
 }
 
-// Plan with the requested tile, halving it while the query does not fit in
-// shared memory.
+// Plan the query, trying kernel shapes in order of preference until one fits
+// in shared memory.  Row mode prefers two CTAs per SM of 8 compute warps with
+// 4096-row tiles, then one CTA of 16 compute warps with 8192-row tiles; tiles
+// halve down to 1024 rows.  Segment mode runs one 512-thread CTA per SM.
+// Options pin the tile size (smaller ones are tried when it does not fit)
+// and / or the CTAs per SM.
 static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
                       const cq_exec_options* opts, const cq_ctx* ctx, Planned* P) {
-  uint32_t tile = opts && opts->tile_rows ? opts->tile_rows : 4096;
-  if (tile < 1024 || tile > 8192 || (tile & (tile - 1)))
+  if (!plan) return set_error(CQ_ERR_INVALID_ARG, "plan is NULL");
+  const uint32_t want_tile = opts ? opts->tile_rows : 0;
+  const uint32_t want_ctas = opts ? opts->ctas_per_sm : 0;
+  if (want_tile && (want_tile < 1024 || want_tile > 8192 || (want_tile & (want_tile - 1))))
     return set_error(CQ_ERR_INVALID_ARG, "tile_rows must be 1024, 2048, 4096 or 8192");
-  for (;;) {
-    bool no_fit = false;
-    const int rc = plan_query_tile(tcols, n_rows, plan, opts, ctx, tile, P, &no_fit);
-    if (rc == CQ_OK || !no_fit || tile <= 1024) return rc;
-    tile /= 2;
+  if (want_ctas > 2) return set_error(CQ_ERR_INVALID_ARG, "ctas_per_sm must be 0, 1 or 2");
+  // segment mode when every referenced column is RLE or index-encoded
+  bool seg = true;
+  auto look = [&](uint32_t c) {
+    if (c < tcols.size() && tcols[c].enc != ENC_RLE && tcols[c].enc != ENC_INDEX) seg = false;
+  };
+  for (uint32_t i = 0; i < plan->n_preds && plan->preds; ++i) look(plan->preds[i].col);
+  for (uint32_t i = 0; i < plan->n_group_by && plan->group_by; ++i) look(plan->group_by[i]);
+  for (uint32_t i = 0; i < plan->n_aggs && plan->aggs; ++i)
+    if (plan->aggs[i].op != CQ_COUNT) look(plan->aggs[i].col);
+  struct Shape { int ncw; uint32_t tile; size_t limit; };
+  std::vector<Shape> shapes;
+  auto add = [&](int ncw, uint32_t first, size_t limit) {
+    // a tile is ncw * 32 * GPW rows with GPW in {2, 4, 8, 16}
+    const uint32_t max_tile = (uint32_t)ncw * 32u * 16u;
+    for (uint32_t t = want_tile ? want_tile : first; t >= 1024; t /= 2)
+      if (t <= max_tile) shapes.push_back({ncw, t, limit});
+  };
+  if (seg) {
+    add(16, 4096, ctx->smem_optin);
+  } else {
+    if (want_ctas != 1) add(8, 4096, ctx->smem_two);
+    if (want_ctas != 2) add(16, 8192, ctx->smem_optin);
   }
+  int rc = CQ_ERR_UNSUPPORTED;
+  for (const Shape& sh : shapes) {
+    bool no_fit = false;
+    rc = plan_query_tile(tcols, n_rows, plan, opts, ctx, sh.tile, sh.ncw, sh.limit, P, &no_fit);
+    if (rc == CQ_OK || !no_fit) return rc;
+  }
+  return rc;
 }
 
 // Carve one pool allocation into the query's device buffers and enqueue
@@ -925,6 +1002,7 @@ static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r)
   q.aux = reinterpret_cast<const uint32_t*>(b + off_aux);
   q.aux_words = (uint32_t)P.aux.size();
   q.err = reinterpret_cast<int*>(b + off_err);
+  q.err_info = reinterpret_cast<unsigned long long*>(b + off_err + 8);
   q.out_count = reinterpret_cast<unsigned long long*>(b + off_cnt);
   q.block_counts = reinterpret_cast<unsigned int*>(b + off_blk);
   if (!P.aux.empty()) {
@@ -1043,10 +1121,29 @@ extern "C" int cq_query_run(cq_table* table, const cq_plan* plan, void* cuda_str
   return cq_query_run_ex(table, plan, nullptr, cuda_stream, out);
 }
 
+// Message for a device-side status, with the detail the kernel recorded.
+static int report_status(cq_result* r) {
+  const int err = r->status;
+  if (!err) return CQ_OK;
+  unsigned long long st[4] = {0, 0, 0, 0};
+  cudaMemcpy(st, r->err_dev, sizeof(st), cudaMemcpyDeviceToHost);
+  const unsigned long long what = st[1] & 0xFF, idx = st[1] >> 8;
+  if (err == CQ_ERR_OVERFLOW)
+    return set_error(err, "SUM of aggregate %llu does not fit int64 (dense group %llu)", idx, st[2]);
+  if (err == CQ_ERR_TIMEOUT) return set_error(err, "a bounded device wait gave up");
+  if (err == CQ_ERR_INVALID_ARG && what == 1)
+    return set_error(err, "group-by key %llu at row %llu has value %lld outside its recorded domain", idx, st[2],
+                     (long long)st[3]);
+  if (err == CQ_ERR_INVALID_ARG && what == 2)
+    return set_error(err, "bitmap column %llu: boundary %llu lies before tile row %llu (corrupt cursor)", idx,
+                     st[3], st[2]);
+  return set_error(err, "device status %d", err);
+}
+
 extern "C" int cq_result_wait(cq_result* r, uint64_t timeout_us) {
   clear_error();
   if (!r) return set_error(CQ_ERR_INVALID_ARG, "NULL result");
-  if (r->waited) return r->status;
+  if (r->waited) return report_status(r);
   cudaSetDevice(r->ctx->device);
   if (timeout_us != UINT64_MAX) {
     const auto t0 = std::chrono::steady_clock::now();
@@ -1061,19 +1158,16 @@ extern "C" int cq_result_wait(cq_result* r, uint64_t timeout_us) {
   }
   cudaError_t e = cudaEventSynchronize(r->ev_done);
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "query failed: %s", cudaGetErrorString(e));
-  int err = 0;
+  unsigned long long st[4] = {0, 0, 0, 0};   // status word, then what / where / value
   unsigned long long cnt = 0;
-  e = cudaMemcpy(&err, r->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+  e = cudaMemcpy(st, r->err_dev, sizeof(st), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&cnt, r->count_dev, sizeof(cnt), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "status read-back failed: %s", cudaGetErrorString(e));
+  const int err = (int)(uint32_t)st[0];
   r->waited = true;
   r->n_groups = cnt;
   r->status = err;
-  if (err == CQ_ERR_OVERFLOW) return set_error(err, "a SUM does not fit int64");
-  if (err == CQ_ERR_TIMEOUT) return set_error(err, "a bounded device wait gave up");
-  if (err == CQ_ERR_INVALID_ARG) return set_error(err, "a group-by value outside its column's recorded range");
-  if (err) return set_error(err, "device status %d", err);
-  return CQ_OK;
+  return report_status(r);
 }
 
 extern "C" int cq_result_num_groups(cq_result* r, uint64_t* n) {

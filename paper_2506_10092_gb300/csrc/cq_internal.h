@@ -70,10 +70,11 @@ struct ColDesc {
 struct PredDesc {
   uint8_t col;       // index into QueryDesc::cols
   uint8_t kind;
-  uint16_t pad0;
+  uint8_t n32;       // raw values and bounds fit int32: evaluate in 32 bits (lo32 / hi32)
+  uint8_t pad0;
   uint32_t aux_off;  // 32-bit words into the aux area (bitmap or list of int64 as word pairs)
   uint32_t aux_len;  // bitmap words / list entries
-  uint32_t pad1;
+  int32_t lo32, hi32;
   int64_t lo, hi;
 };
 
@@ -98,7 +99,8 @@ struct AggDesc {
   uint32_t gw;       // first global accumulator word
   uint8_t op;        // cq_agg_op (for finalize)
   uint8_t out_kind;  // 0 int64, 1 uint64, 2 double
-  uint16_t pad0;
+  uint8_t red32;     // SUM: raw values fit int32 with |v| < 2^26 -> warp-reduced in 32 bits (row mode)
+  uint8_t w32;       // MIN/MAX: raw values fit int32 -> 32-bit shared accumulator, warp-reduced
   int64_t base;      // value added back at finalize (packed base or index default)
 };
 
@@ -111,6 +113,7 @@ struct QueryDesc {
   uint8_t n_bitmaps;       // RLE/INDEX columns with a per-tile bitmap
   uint8_t n_row_cols;      // columns staged per tile (row mode)
   uint8_t stages;
+  uint8_t ncw;             // row mode: compute warps per CTA (8: two CTAs per SM, 16: one)
   uint32_t stage_bytes;    // bytes of one stage (all row-level columns)
   uint32_t table_slots;    // shared-memory group-table slots (power of two)
   uint8_t table_dense;     // 1: slot = gid (gid domain fits the table)
@@ -130,6 +133,7 @@ struct QueryDesc {
   // global state
   unsigned long long* gacc;  // [n_gw][n_groups]
   int* err;                  // device status word (cq_status, 0 = ok)
+  unsigned long long* err_info;  // what / where / value of the first device error
   // outputs
   uint32_t n_out;
   uint8_t out_is_key[kMaxKeys + kMaxAggs];
@@ -153,7 +157,8 @@ struct cq_ctx {
   cudaStream_t stream = nullptr;
   cudaMemPool_t pool = nullptr;
   int num_sms = 0;
-  size_t smem_optin = 0;
+  size_t smem_optin = 0;     // max dynamic shared memory of one CTA
+  size_t smem_two = 0;       // max dynamic shared memory per CTA with two CTAs per SM
   std::mutex mu;
   // pinned staging for small host <-> device transfers
 };

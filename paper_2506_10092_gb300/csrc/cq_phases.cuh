@@ -1,0 +1,652 @@
+// cq_phases.cuh -- device building blocks shared by the two fused query
+// kernels (segment mode in cq_query.cu, row mode in cq_row.cu): shared-memory
+// layouts, column readers, predicate tests, the shared-memory group table and
+// the filter / aggregate phases of one tile.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <type_traits>
+
+#include "cq_device.cuh"
+#include "cq_internal.h"
+
+namespace cq {
+
+constexpr uint32_t kWin = 256;                           // prefetched run ends / positions per column and tile
+constexpr uint32_t kAuxSmemWords = 4096;                 // aux tables up to 16 KB live in shared memory
+
+// ------------------------------------------------------------------ shared-memory layout
+struct SmemLayout {
+  uint32_t stage, mbar, tkeys, tacc, bm, pre, tcur, win, ubm, upre, seg, clist, aux, flags, misc, total;
+};
+
+__host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+// Segment mode keeps one bitmap set (built by every warp); row mode double
+// buffers bitmaps, start cursors and prefetch windows (built by the helper
+// warp one tile ahead).
+__host__ __device__ inline SmemLayout smem_layout(const QueryDesc& q) {
+  SmemLayout L;
+  const uint32_t nwords = q.tile_rows / 32;
+  const uint32_t nbuf = q.seg_mode ? 1u : 2u;
+  const uint32_t nb = q.n_bitmaps;
+  uint32_t off = 0;
+  L.stage = off;
+  off += q.seg_mode ? 0u : q.stages * q.stage_bytes;
+  off = align_up(off, 16);
+  L.mbar = off;
+  off += 8u * (q.seg_mode ? 0u : q.stages);
+  off = align_up(off, 16);
+  L.tkeys = off;
+  off += q.table_dense ? 0u : 4u * q.table_slots;
+  off = align_up(off, 16);
+  L.tacc = off;
+  off += 8u * q.n_sw * q.table_slots;
+  L.bm = off;
+  off += 4u * nwords * nb * nbuf;
+  L.pre = off;
+  off += 4u * (nwords + 1) * nb * nbuf;
+  off = align_up(off, 8);
+  L.tcur = off;
+  off += 8u * kMaxBitmapCols * nbuf;
+  L.win = off;
+  off += q.seg_mode ? 0u : 8u * kWin * nb * 2;
+  L.ubm = off;
+  off += q.seg_mode ? 4u * nwords : 0u;
+  L.upre = off;
+  off += q.seg_mode ? 4u * (nwords + 1) : 0u;
+  L.seg = off;
+  off += q.seg_mode ? 2u * (q.tile_rows + 2) : 0u;
+  off = align_up(off, 16);
+  L.clist = off;
+  off += 2u * q.tile_rows;
+  off = align_up(off, 16);
+  L.aux = off;
+  off += q.aux_words <= kAuxSmemWords ? 4u * q.aux_words : 0u;
+  off = align_up(off, 16);
+  L.flags = off;
+  off += 4u * 2 * kMaxBitmapCols;
+  L.misc = off;
+  off += 4u * 8;
+  L.total = align_up(off, 128);
+  return L;
+}
+
+struct Smem {
+  uint8_t* stage;
+  uint64_t* mbar;
+  uint32_t* tkeys;
+  unsigned long long* tacc;
+  uint32_t* bm;
+  uint32_t* pre;
+  unsigned long long* tcur;
+  uint8_t* win;
+  uint32_t* ubm;
+  uint32_t* upre;
+  uint16_t* seg;
+  uint16_t* clist;
+  uint32_t* aux;
+  int* flags;   // segment mode: [j] column done, [kMaxBitmapCols + j] run ends exactly at the tile end
+  int* misc;    // 0 occupancy, 2 segments of the tile
+};
+
+extern __shared__ __align__(128) uint8_t g_smem[];
+
+__device__ __forceinline__ Smem carve(const QueryDesc& q) {
+  const SmemLayout L = smem_layout(q);
+  Smem s;
+  s.stage = g_smem + L.stage;
+  s.mbar = reinterpret_cast<uint64_t*>(g_smem + L.mbar);
+  s.tkeys = reinterpret_cast<uint32_t*>(g_smem + L.tkeys);
+  s.tacc = reinterpret_cast<unsigned long long*>(g_smem + L.tacc);
+  s.bm = reinterpret_cast<uint32_t*>(g_smem + L.bm);
+  s.pre = reinterpret_cast<uint32_t*>(g_smem + L.pre);
+  s.tcur = reinterpret_cast<unsigned long long*>(g_smem + L.tcur);
+  s.win = g_smem + L.win;
+  s.ubm = reinterpret_cast<uint32_t*>(g_smem + L.ubm);
+  s.upre = reinterpret_cast<uint32_t*>(g_smem + L.upre);
+  s.seg = reinterpret_cast<uint16_t*>(g_smem + L.seg);
+  s.clist = reinterpret_cast<uint16_t*>(g_smem + L.clist);
+  s.aux = reinterpret_cast<uint32_t*>(g_smem + L.aux);
+  s.flags = reinterpret_cast<int*>(g_smem + L.flags);
+  s.misc = reinterpret_cast<int*>(g_smem + L.misc);
+  return s;
+}
+
+// Everything a column reader needs about the tile being processed.
+struct TileView {
+  const uint32_t* bm;                // bitmaps of this tile [n_bitmaps][nwords]
+  const uint32_t* pre;               // word prefix popcounts [n_bitmaps][nwords + 1]
+  const unsigned long long* cur;     // first run / position of each bitmap column in this tile
+  const uint8_t* stage;              // staged row-level columns of this tile
+  const uint32_t* aux;               // predicate / key tables (shared or global memory)
+  uint32_t nwords;
+};
+
+// ------------------------------------------------------------------ dispatch
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+template <class F>
+__device__ __forceinline__ void dispatch_enc(uint8_t enc, F&& f) {
+  switch (enc) {
+    case ENC_PLAIN: f(IC<ENC_PLAIN>()); break;
+    case ENC_PACKED: f(IC<ENC_PACKED>()); break;
+    case ENC_DICT: f(IC<ENC_DICT>()); break;
+    case ENC_RLE: f(IC<ENC_RLE>()); break;
+    default: f(IC<ENC_INDEX>()); break;
+  }
+}
+
+// Encodings that can occur: segment mode has only RLE and index columns.
+template <bool SEG, class F>
+__device__ __forceinline__ void dispatch_col(uint8_t enc, F&& f) {
+  if constexpr (SEG) {
+    if (enc == ENC_RLE) f(IC<ENC_RLE>());
+    else f(IC<ENC_INDEX>());
+  } else {
+    dispatch_enc(enc, f);
+  }
+}
+
+// Predicate kinds evaluated per row; a narrow (32-bit) variant of each
+// comparison kind is used when the planner proved the column's raw values fit.
+enum { PT_RANGE = 0, PT_NE = 1, PT_BITMAP = 2, PT_LIST = 3, PT_RANGE32 = 4, PT_NE32 = 5, PT_BITMAP32 = 6 };
+
+template <class F>
+__device__ __forceinline__ void dispatch_test(const PredDesc& p, F&& f) {
+  if (p.n32) {
+    switch (p.kind) {
+      case PK_RANGE: f(IC<PT_RANGE32>()); return;
+      case PK_NE: f(IC<PT_NE32>()); return;
+      case PK_BITMAP: f(IC<PT_BITMAP32>()); return;
+      default: break;
+    }
+  }
+  switch (p.kind) {
+    case PK_RANGE: f(IC<PT_RANGE>()); break;
+    case PK_NE: f(IC<PT_NE>()); break;
+    case PK_BITMAP: f(IC<PT_BITMAP>()); break;
+    default: f(IC<PT_LIST>()); break;
+  }
+}
+
+// ------------------------------------------------------------------ column readers
+// Raw value of column c at tile row o (the logical value for RLE / index /
+// plain columns; the unsigned field for dictionary codes and, when
+// raw_is_offset, bit-packed offsets).
+template <int ENC>
+__device__ __forceinline__ long long col_raw(const ColDesc& c, const TileView& t, uint32_t o) {
+  if constexpr (ENC == ENC_PLAIN) {
+    const uint8_t* p = t.stage + c.stage_off;
+    return c.v64 ? reinterpret_cast<const long long*>(p)[o] : (long long)reinterpret_cast<const int*>(p)[o];
+  } else if constexpr (ENC == ENC_PACKED || ENC == ENC_DICT) {
+    const uint64_t f = extract_field(reinterpret_cast<const uint32_t*>(t.stage + c.stage_off), o, c.bw);
+    return c.raw_is_offset ? (long long)f : (long long)(f + (uint64_t)c.base);
+  } else if constexpr (ENC == ENC_RLE) {
+    const uint32_t* B = t.bm + c.bslot * t.nwords;
+    const uint32_t* P = t.pre + c.bslot * (t.nwords + 1);
+    return ldg_val(c.vals, t.cur[c.bslot] + rank_incl(B, P, o), c.v64);
+  } else {  // ENC_INDEX
+    const uint32_t* B = t.bm + c.bslot * t.nwords;
+    const uint32_t wv = B[o >> 5];
+    if (!((wv >> (o & 31)) & 1u)) return c.base;
+    const uint32_t* P = t.pre + c.bslot * (t.nwords + 1);
+    return ldg_val(c.vals, t.cur[c.bslot] + P[o >> 5] + __popc(wv & ((1u << (o & 31)) - 1u)), c.v64);
+  }
+}
+
+// 32-bit raw value; valid only for columns the planner marked narrow.
+template <int ENC>
+__device__ __forceinline__ int col_raw32(const ColDesc& c, const TileView& t, uint32_t o) {
+  if constexpr (ENC == ENC_PLAIN) {
+    return reinterpret_cast<const int*>(t.stage + c.stage_off)[o];
+  } else if constexpr (ENC == ENC_PACKED || ENC == ENC_DICT) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(t.stage + c.stage_off);
+    const uint32_t bit = o * (uint32_t)c.bw;
+    const uint32_t q = bit >> 5;
+    const uint32_t v = __funnelshift_r(w[q], w[q + 1], bit & 31);
+    return (int)(c.bw >= 32 ? v : (v & ((1u << c.bw) - 1u)));
+  } else if constexpr (ENC == ENC_RLE) {
+    const uint32_t* B = t.bm + c.bslot * t.nwords;
+    const uint32_t* P = t.pre + c.bslot * (t.nwords + 1);
+    return __ldg(reinterpret_cast<const int*>(c.vals) + t.cur[c.bslot] + rank_incl(B, P, o));
+  } else {
+    const uint32_t* B = t.bm + c.bslot * t.nwords;
+    const uint32_t wv = B[o >> 5];
+    if (!((wv >> (o & 31)) & 1u)) return (int)c.base;
+    const uint32_t* P = t.pre + c.bslot * (t.nwords + 1);
+    return __ldg(reinterpret_cast<const int*>(c.vals) + t.cur[c.bslot] + P[o >> 5] +
+                 __popc(wv & ((1u << (o & 31)) - 1u)));
+  }
+}
+
+__device__ __forceinline__ long long col_value(const ColDesc& c, const TileView& t, uint32_t o) {
+  switch (c.enc) {
+    case ENC_PLAIN: return col_raw<ENC_PLAIN>(c, t, o);
+    case ENC_PACKED: return col_raw<ENC_PACKED>(c, t, o);
+    case ENC_DICT: return col_raw<ENC_DICT>(c, t, o);
+    case ENC_RLE: return col_raw<ENC_RLE>(c, t, o);
+    default: return col_raw<ENC_INDEX>(c, t, o);
+  }
+}
+
+// Index column at o: listed? and value.
+__device__ __forceinline__ bool index_lookup(const ColDesc& c, const TileView& t, uint32_t o, long long* v) {
+  const uint32_t* B = t.bm + c.bslot * t.nwords;
+  const uint32_t wv = B[o >> 5];
+  if (!((wv >> (o & 31)) & 1u)) return false;
+  const uint32_t* P = t.pre + c.bslot * (t.nwords + 1);
+  *v = ldg_val(c.vals, t.cur[c.bslot] + P[o >> 5] + __popc(wv & ((1u << (o & 31)) - 1u)), c.v64);
+  return true;
+}
+
+// ------------------------------------------------------------------ predicates and keys
+template <int K>
+__device__ __forceinline__ bool pred_test(const PredDesc& p, const uint32_t* aux, long long v) {
+  if constexpr (K == PT_RANGE) {
+    return v >= p.lo && v <= p.hi;
+  } else if constexpr (K == PT_NE) {
+    return v != p.lo;
+  } else if constexpr (K == PT_BITMAP) {
+    if (v < p.lo || v > p.hi) return false;
+    const unsigned long long d = (unsigned long long)(v - p.lo);
+    return (aux[p.aux_off + (uint32_t)(d >> 5)] >> (d & 31)) & 1u;
+  } else {  // PT_LIST
+    const long long* L = reinterpret_cast<const long long*>(aux + p.aux_off);
+    uint32_t lo = 0, hi = p.aux_len;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (L[mid] < v) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo < p.aux_len && L[lo] == v;
+  }
+}
+
+template <int K>
+__device__ __forceinline__ bool pred_test32(const PredDesc& p, const uint32_t* aux, int v) {
+  if constexpr (K == PT_RANGE32) {
+    return (unsigned)v - (unsigned)p.lo32 <= (unsigned)p.hi32 - (unsigned)p.lo32;
+  } else if constexpr (K == PT_NE32) {
+    return v != p.lo32;
+  } else {  // PT_BITMAP32
+    const unsigned d = (unsigned)v - (unsigned)p.lo32;
+    if (d > (unsigned)p.hi32 - (unsigned)p.lo32) return false;
+    return (aux[p.aux_off + (d >> 5)] >> (d & 31)) & 1u;
+  }
+}
+
+// digit of key k for raw value v; false when v is outside the key's domain
+__device__ __forceinline__ bool key_digit(const KeyDesc& k, const uint32_t* aux, long long v, uint32_t* digit) {
+  const unsigned long long d = (unsigned long long)(v - k.kmin);
+  if (!k.remap) {
+    if (v < k.kmin || d >= k.card) return false;
+    *digit = (uint32_t)d;
+    return true;
+  }
+  if (v < k.kmin || d >= 32ull * k.aux_len) return false;
+  const uint32_t w = aux[k.aux_off + (uint32_t)(d >> 5)];
+  if (!((w >> (d & 31)) & 1u)) return false;
+  *digit = aux[k.prefix_off + (uint32_t)(d >> 5)] + __popc(w & ((1u << (d & 31)) - 1u));
+  return true;
+}
+
+// First device error wins; its detail (what, where, value) is kept for the host.
+__device__ __forceinline__ void report(const QueryDesc& q, int code, unsigned long long what,
+                                       unsigned long long where, unsigned long long value) {
+  if (atomicCAS(q.err, 0, code) == 0) {
+    q.err_info[0] = what;
+    q.err_info[1] = where;
+    q.err_info[2] = value;
+  }
+}
+
+// ------------------------------------------------------------------ group table
+// Shared-memory group table, structure of arrays over `table_slots` slots of
+// 64-bit words: word 0 holds the slot's COUNT in its low 32 bits; every
+// aggregate owns words from a.sw on (a SUM one or two, MIN / MAX one -- in
+// its low 32 bits when a.w32 -- index MIN / MAX a value and a listed count).
+
+// multiplicative hashing: the top bits of gid * golden ratio select the slot
+__device__ __forceinline__ uint32_t hash_gid(uint32_t g, uint32_t log2_slots) {
+  return (g * 0x9E3779B1u) >> (32 - log2_slots);
+}
+
+// Shared-memory slot of gid, or -1 when the probe limit is hit (caller then
+// updates the global accumulators directly).
+__device__ __forceinline__ int table_slot(const QueryDesc& q, const Smem& sm, uint32_t gid) {
+  if (q.table_dense) return (int)gid;
+  const uint32_t mask = q.table_slots - 1;
+  uint32_t h = hash_gid(gid, 31 - __clz(q.table_slots)) & mask;
+  for (int probe = 0; probe < 32; ++probe) {
+    uint32_t k = sm.tkeys[h];
+    if (k == gid) return (int)h;
+    if (k == kEmptyKey) {
+      k = atomicCAS(&sm.tkeys[h], kEmptyKey, gid);
+      if (k == kEmptyKey) {
+        atomicAdd(&sm.misc[0], 1);
+        return (int)h;
+      }
+      if (k == gid) return (int)h;
+    }
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ unsigned long long* gword(const QueryDesc& q, uint32_t w, uint32_t gid) {
+  return q.gacc + (size_t)w * q.n_groups + gid;
+}
+
+__device__ __forceinline__ unsigned long long* sword(const QueryDesc& q, const Smem& sm, uint32_t w, int slot) {
+  return &sm.tacc[(size_t)w * q.table_slots + slot];
+}
+
+__device__ __forceinline__ int* sword32(const QueryDesc& q, const Smem& sm, uint32_t w, int slot) {
+  return reinterpret_cast<int*>(sword(q, sm, w, slot));   // low half (little endian)
+}
+
+// 128-bit value of (v - base) for an index column's listed row
+__device__ __forceinline__ I128 index_delta(long long v, long long base) {
+  I128 x;
+  x.lo = (unsigned long long)v - (unsigned long long)base;
+  x.hi = (v < 0 ? -1ll : 0ll) - (base < 0 ? -1ll : 0ll) - ((unsigned long long)v < (unsigned long long)base ? 1ll : 0ll);
+  return x;
+}
+
+// Narrow SUM accumulator: one 64-bit shared word used as a low unsigned and a
+// high signed 32-bit half.  The old low half returned by the 32-bit atomic
+// tells whether this addend carried, so the word always holds the exact
+// two's-complement sum while only native 32-bit shared atomics are used.
+__device__ __forceinline__ void smem_add64(unsigned long long* w, long long x) {
+  unsigned* p = reinterpret_cast<unsigned*>(w);
+  const unsigned xl = (unsigned)(unsigned long long)x;
+  const unsigned old = atomicAdd(p, xl);
+  const unsigned h = (unsigned)((unsigned long long)x >> 32) + ((old + xl) < old ? 1u : 0u);
+  if (h) atomicAdd(p + 1, h);
+}
+
+// Add a 128-bit contribution to a SUM accumulator in shared memory (slot >= 0)
+// or straight into the global limbs.
+__device__ __forceinline__ void sum_add(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot, uint32_t gid,
+                                        I128 x) {
+  if (slot >= 0) {
+    if (!a.wide) smem_add64(sword(q, sm, a.sw, slot), (long long)x.lo);
+    else atomic_add_i128(sword(q, sm, a.sw, slot), sword(q, sm, a.sw + 1, slot), x);
+  } else {
+    global_add_limbs(gword(q, a.gw, gid), gword(q, a.gw + 1, gid), gword(q, a.gw + 2, gid), x);
+  }
+}
+
+__device__ __forceinline__ void minmax_add(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot,
+                                           uint32_t gid, long long v, bool is_min) {
+  if (slot >= 0) {
+    if (a.w32) {
+      if (is_min) atomicMin(sword32(q, sm, a.sw, slot), (int)v);
+      else atomicMax(sword32(q, sm, a.sw, slot), (int)v);
+    } else {
+      if (is_min) atomicMin(reinterpret_cast<long long*>(sword(q, sm, a.sw, slot)), v);
+      else atomicMax(reinterpret_cast<long long*>(sword(q, sm, a.sw, slot)), v);
+    }
+  } else {
+    if (is_min) atomicMin(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
+    else atomicMax(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
+  }
+}
+
+__device__ __forceinline__ void reset_slot(const QueryDesc& q, const Smem& sm, uint32_t s) {
+  sm.tacc[s] = 0;
+  for (int i = 0; i < q.n_aggs; ++i) {
+    const AggDesc& a = q.aggs[i];
+    switch (a.kind) {
+      case AK_SUM:
+      case AK_ISUM:
+        *sword(q, sm, a.sw, s) = 0;
+        if (a.wide) *sword(q, sm, a.sw + 1, s) = 0;
+        break;
+      case AK_MIN:
+      case AK_IMIN:
+        *sword(q, sm, a.sw, s) = a.w32 ? (unsigned long long)(unsigned)INT_MAX : (unsigned long long)LLONG_MAX;
+        if (a.kind == AK_IMIN) *sword(q, sm, a.sw + 1, s) = 0;
+        break;
+      case AK_MAX:
+      case AK_IMAX:
+        *sword(q, sm, a.sw, s) = a.w32 ? (unsigned long long)(unsigned)INT_MIN : (unsigned long long)LLONG_MIN;
+        if (a.kind == AK_IMAX) *sword(q, sm, a.sw + 1, s) = 0;
+        break;
+      default:
+        break;
+    }
+  }
+  if (!q.table_dense) sm.tkeys[s] = kEmptyKey;
+}
+
+// Add every occupied slot into the global accumulators and clear the table.
+__device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
+  const uint32_t S = q.table_slots;
+  for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
+    const unsigned cnt = *reinterpret_cast<const unsigned*>(&sm.tacc[s]);
+    if (cnt == 0) {
+      if (!q.table_dense) sm.tkeys[s] = kEmptyKey;
+      continue;
+    }
+    const uint32_t gid = q.table_dense ? s : sm.tkeys[s];
+    atomicAdd(gword(q, 0, gid), (unsigned long long)cnt);
+    for (int i = 0; i < q.n_aggs; ++i) {
+      const AggDesc& a = q.aggs[i];
+      switch (a.kind) {
+        case AK_SUM:
+        case AK_ISUM: {
+          I128 x;
+          if (a.wide) {
+            x.lo = *sword(q, sm, a.sw, s);
+            x.hi = (long long)*sword(q, sm, a.sw + 1, s);
+          } else {
+            x = sext((long long)*sword(q, sm, a.sw, s));
+          }
+          global_add_limbs(gword(q, a.gw, gid), gword(q, a.gw + 1, gid), gword(q, a.gw + 2, gid), x);
+          break;
+        }
+        case AK_MIN:
+        case AK_IMIN: {
+          const long long v = a.w32 ? (long long)*sword32(q, sm, a.sw, s) : (long long)*sword(q, sm, a.sw, s);
+          if (v != (a.w32 ? (long long)INT_MAX : LLONG_MAX)) atomicMin(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
+          break;
+        }
+        case AK_MAX:
+        case AK_IMAX: {
+          const long long v = a.w32 ? (long long)*sword32(q, sm, a.sw, s) : (long long)*sword(q, sm, a.sw, s);
+          if (v != (a.w32 ? (long long)INT_MIN : LLONG_MIN)) atomicMax(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
+          break;
+        }
+        default:
+          break;
+      }
+      if (a.kind == AK_IMIN || a.kind == AK_IMAX) {
+        const unsigned long long lc = *sword(q, sm, a.sw + 1, s);
+        if (lc) atomicAdd(gword(q, a.gw + 1, gid), lc);
+      }
+    }
+    reset_slot(q, sm, s);
+  }
+}
+
+// ------------------------------------------------------------------ tile phases
+// Filter: bit g of the result says item (wbase + 32 g + lane) passes every
+// predicate.  Items are rows (row mode) or aligned segments (segment mode,
+// item -> first row through seg[]).  Predicates are evaluated one at a time
+// over all of the warp's items, with the column / test dispatch hoisted out of
+// the item loop.
+template <bool SEG, int GPW>
+__device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileView& t, const uint16_t* seg,
+                                                 uint32_t wbase, uint32_t n_items) {
+  const int lane = threadIdx.x & 31;
+  uint32_t valid = 0;
+#pragma unroll
+  for (int g = 0; g < GPW; ++g) valid |= (wbase + g * 32 + lane < n_items ? 1u : 0u) << g;
+  uint32_t pm = valid;
+  for (int pi = 0; pi < q.n_preds; ++pi) {
+    if (!__any_sync(0xFFFFFFFFu, pm != 0)) break;
+    const PredDesc& p = q.preds[pi];
+    if (p.kind == PK_TRUE) continue;
+    if (p.kind == PK_FALSE) {
+      pm = 0;
+      continue;
+    }
+    const ColDesc& c = q.cols[p.col];
+    dispatch_col<SEG>(c.enc, [&](auto et) {
+      dispatch_test(p, [&](auto kt) {
+        constexpr int E = decltype(et)::value;
+        constexpr int K = decltype(kt)::value;
+#pragma unroll 2
+        for (int g = 0; g < GPW; ++g) {
+          if (!((pm >> g) & 1u)) continue;
+          const uint32_t it = wbase + g * 32 + lane;
+          const uint32_t o = SEG ? (uint32_t)seg[it] : it;
+          bool ok;
+          if constexpr (K >= PT_RANGE32) ok = pred_test32<K>(p, t.aux, col_raw32<E>(c, t, o));
+          else ok = pred_test<K>(p, t.aux, col_raw<E>(c, t, o));
+          if (!ok) pm &= ~(1u << g);
+        }
+      });
+    });
+  }
+  return pm & valid;
+}
+
+// Compact the passing items of this warp into list[] (item indices).
+template <int GPW>
+__device__ __forceinline__ uint32_t compact(uint32_t pm, uint32_t wbase, uint16_t* list) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t n = 0;
+#pragma unroll
+  for (int g = 0; g < GPW; ++g) {
+    const bool ok = (pm >> g) & 1u;
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
+    if (ok) list[n + __popc(bal & lt)] = (uint16_t)(wbase + g * 32 + lane);
+    n += __popc(bal);
+  }
+  __syncwarp();
+  return n;
+}
+
+// Aggregate: one passing item per lane.  Each lane updates its group's shared
+// slot with native 32-bit shared atomics (or the global accumulators when the
+// table has no free slot within the probe limit).  When every active lane of
+// the warp belongs to one group, the warp reduces first and one lane updates.
+template <bool SEG>
+__device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& sm, const TileView& t,
+                                                const uint16_t* seg, const uint16_t* list, uint32_t n_pass,
+                                                unsigned long long tile_row0) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t j0 = 0; j0 < n_pass; j0 += 32) {
+    const uint32_t j = j0 + lane;
+    const bool act = j < n_pass;
+    const uint32_t amask = __ballot_sync(0xFFFFFFFFu, act);
+    if (act) {
+      const uint32_t itm = list[j];
+      uint32_t o, len;
+      if (SEG) {
+        o = seg[itm];
+        len = (uint32_t)seg[itm + 1] - o;
+      } else {
+        o = itm;
+        len = 1;
+      }
+      uint32_t gid = 0;
+      bool bad = false;
+      int last_col = -1;
+      long long last_v = 0;
+      for (int ki = 0; ki < q.n_keys; ++ki) {
+        const KeyDesc& k = q.keys[ki];
+        const long long v = col_value(q.cols[k.col], t, o);
+        last_col = k.col;
+        last_v = v;
+        uint32_t d;
+        if (key_digit(k, t.aux, v, &d)) {
+          gid += d * (uint32_t)k.stride;
+        } else if (!bad) {
+          bad = true;
+          report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)ki << 8), tile_row0 + o, (unsigned long long)v);
+        }
+      }
+      const uint32_t gmask = __ballot_sync(amask, !bad);
+      if (!bad) {
+        const int first = __ffs(gmask) - 1;
+        const bool uniform = __all_sync(gmask, gid == __shfl_sync(gmask, gid, first));
+        const bool lead = lane == first;
+        int slot;
+        if (uniform) {
+          slot = lead ? table_slot(q, sm, gid) : 0;
+          slot = __shfl_sync(gmask, slot, first);
+        } else {
+          slot = table_slot(q, sm, gid);
+        }
+        if (slot >= 0) {
+          if (uniform) {
+            const uint32_t tot = SEG ? __reduce_add_sync(gmask, len) : (uint32_t)__popc(gmask);
+            if (lead) atomicAdd(reinterpret_cast<unsigned*>(&sm.tacc[slot]), tot);
+          } else {
+            atomicAdd(reinterpret_cast<unsigned*>(&sm.tacc[slot]), len);
+          }
+        } else {
+          atomicAdd(gword(q, 0, gid), (unsigned long long)len);
+        }
+        for (int ai = 0; ai < q.n_aggs; ++ai) {
+          const AggDesc& a = q.aggs[ai];
+          if (a.kind == AK_COUNT) continue;
+          const ColDesc& c = q.cols[a.col];
+          if (a.kind == AK_ISUM || a.kind == AK_IMIN || a.kind == AK_IMAX) {
+            // index column: only listed rows differ from the default, which
+            // the finalize step adds back from COUNT
+            long long v;
+            if (index_lookup(c, t, o, &v)) {
+              if (a.kind == AK_ISUM) {
+                sum_add(q, sm, a, slot, gid, index_delta(v, a.base));
+              } else {
+                minmax_add(q, sm, a, slot, gid, v, a.kind == AK_IMIN);
+                if (slot >= 0) atomicAdd(reinterpret_cast<unsigned*>(sword(q, sm, a.sw + 1, slot)), 1u);
+                else atomicAdd(gword(q, a.gw + 1, gid), 1ull);
+              }
+            }
+            continue;
+          }
+          long long v;
+          if (a.col == last_col) {
+            v = last_v;
+          } else {
+            v = col_value(c, t, o);
+            last_col = a.col;
+            last_v = v;
+          }
+          if (a.kind == AK_SUM) {
+            if (uniform && !SEG && a.red32 && slot >= 0) {
+              const int r = __reduce_add_sync(gmask, (int)v);
+              if (lead) smem_add64(sword(q, sm, a.sw, slot), (long long)r);
+            } else {
+              sum_add(q, sm, a, slot, gid, len == 1 ? sext(v) : mul_s64(v, (long long)len));
+            }
+          } else {
+            const bool is_min = a.kind == AK_MIN;
+            if (uniform && a.w32 && slot >= 0) {
+              const int r = is_min ? __reduce_min_sync(gmask, (int)v) : __reduce_max_sync(gmask, (int)v);
+              if (lead) {
+                if (is_min) atomicMin(sword32(q, sm, a.sw, slot), r);
+                else atomicMax(sword32(q, sm, a.sw, slot), r);
+              }
+            } else {
+              minmax_add(q, sm, a, slot, gid, v, is_min);
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace cq

@@ -1,384 +1,27 @@
-// cq_query.cu -- the fused compressed-domain query kernel and its helpers.
+// cq_query.cu -- segment-mode fused kernel, global init / finalize kernels
+// and the launchers of both fused kernels.
 //
-// One persistent kernel evaluates a filter -> group-by -> aggregate plan over
-// a table's compressed columns without decompressing them (Sections 6-7 of
-// the paper).  The table's rows are cut into tiles of `tile_rows` rows; each
-// CTA walks a contiguous range of tiles:
-//
-//  * Alignment (Section 6, Algorithm 1 generalised to k columns).  For each
-//    RLE column the run ends that fall inside the tile are set as bits of a
-//    tile-long bitmap, and for each index column its listed positions.  The
-//    run (or listed entry) covering tile row o is then a popcount rank, so
-//    the common refinement of all columns' runs never has to be sorted or
-//    materialised.  In segment mode (every referenced column RLE or index)
-//    the OR of the bitmaps gives the aligned segments themselves and the
-//    kernel works per segment, weighting SUM by run length and COUNT by
-//    length (Section 7, aggregating phase).
-//  * Row-level columns (bit-packed, dictionary codes, plain) are streamed
-//    tile by tile into shared memory with 1-D bulk copies on the TMA engine,
-//    `stages` tiles ahead, each stage completing on an mbarrier; fields are
-//    unpacked from shared memory.
-//  * Predicates (a conjunction) run first over every row / segment; each
-//    warp compacts its passing items, then computes their dense group id and
-//    updates a shared-memory group table (dense bins for small key domains,
-//    open addressing otherwise) that is flushed into exact global
-//    accumulators.
+// The compressed-domain method (Sections 6-7 of the paper): a table's rows are
+// cut into tiles of `tile_rows` rows and each CTA walks a contiguous range of
+// tiles.  Alignment (Section 6, Algorithm 1 generalised to k columns): the run
+// ends of every RLE column that fall in a tile are set as bits of a tile-long
+// bitmap, the listed positions of every index column likewise, and the run
+// (or listed entry) covering tile row o is a popcount rank -- the common
+// refinement of all runs is never sorted or materialised.  When every
+// referenced column is RLE or index-encoded (segment mode, this file) the OR
+// of the bitmaps gives the aligned segments themselves and the kernel works
+// per segment: SUM adds value x run length, COUNT adds length (Section 7).
+// Queries with row-level columns run in the row-mode kernel (cq_row.cu).
 #include <cuda_runtime.h>
 
 #include <climits>
 #include <cstdio>
-#include <type_traits>
 
-#include "cq_device.cuh"
-#include "cq_internal.h"
+#include "cq_phases.cuh"
 
 namespace cq {
 
-// ------------------------------------------------------------------ smem layout
-struct SmemLayout {
-  uint32_t stage, mbar, tkeys, tacc, bm, pre, ubm, upre, seg, clist, cursor, flags, misc, total;
-};
-
-__host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
-
-__host__ __device__ inline SmemLayout smem_layout(const QueryDesc& q) {
-  SmemLayout L;
-  const uint32_t nwords = q.tile_rows / 32;
-  uint32_t off = 0;
-  L.stage = off;
-  off += q.seg_mode ? 0u : q.stages * q.stage_bytes;
-  off = align_up(off, 16);
-  L.mbar = off;
-  off += 8u * (q.seg_mode ? 0u : q.stages);
-  off = align_up(off, 16);
-  L.tkeys = off;
-  off += q.table_dense ? 0u : 4u * q.table_slots;
-  off = align_up(off, 16);
-  L.tacc = off;
-  off += 8u * q.n_sw * q.table_slots;
-  L.bm = off;
-  off += 4u * nwords * q.n_bitmaps;
-  L.pre = off;
-  off += 4u * (nwords + 1) * q.n_bitmaps;
-  L.ubm = off;
-  off += q.seg_mode ? 4u * nwords : 0u;
-  L.upre = off;
-  off += q.seg_mode ? 4u * (nwords + 1) : 0u;
-  L.seg = off;
-  off += q.seg_mode ? 2u * (q.tile_rows + 2) : 0u;
-  off = align_up(off, 16);
-  L.clist = off;
-  off += 2u * q.tile_rows;
-  off = align_up(off, 16);
-  L.cursor = off;
-  off += 8u * kMaxBitmapCols;
-  L.flags = off;
-  off += 4u * 2 * kMaxBitmapCols;
-  L.misc = off;
-  off += 4u * 8;
-  L.total = align_up(off, 128);
-  return L;
-}
-
 size_t query_kernel_smem(const QueryDesc& q) { return smem_layout(q).total; }
-
-struct Smem {
-  uint8_t* stage;
-  uint64_t* mbar;
-  uint32_t* tkeys;
-  unsigned long long* tacc;
-  uint32_t* bm;
-  uint32_t* pre;
-  uint32_t* ubm;
-  uint32_t* upre;
-  uint16_t* seg;
-  uint16_t* clist;
-  unsigned long long* cursor;
-  int* flags;   // [0..kMaxBitmapCols) done, [kMaxBitmapCols..) run ends exactly at the tile end
-  int* misc;    // 0 occupancy, 1 rows since flush, 2 n segments
-};
-
-extern __shared__ __align__(128) uint8_t g_smem[];
-
-__device__ __forceinline__ Smem carve(const QueryDesc& q) {
-  const SmemLayout L = smem_layout(q);
-  Smem s;
-  s.stage = g_smem + L.stage;
-  s.mbar = reinterpret_cast<uint64_t*>(g_smem + L.mbar);
-  s.tkeys = reinterpret_cast<uint32_t*>(g_smem + L.tkeys);
-  s.tacc = reinterpret_cast<unsigned long long*>(g_smem + L.tacc);
-  s.bm = reinterpret_cast<uint32_t*>(g_smem + L.bm);
-  s.pre = reinterpret_cast<uint32_t*>(g_smem + L.pre);
-  s.ubm = reinterpret_cast<uint32_t*>(g_smem + L.ubm);
-  s.upre = reinterpret_cast<uint32_t*>(g_smem + L.upre);
-  s.seg = reinterpret_cast<uint16_t*>(g_smem + L.seg);
-  s.clist = reinterpret_cast<uint16_t*>(g_smem + L.clist);
-  s.cursor = reinterpret_cast<unsigned long long*>(g_smem + L.cursor);
-  s.flags = reinterpret_cast<int*>(g_smem + L.flags);
-  s.misc = reinterpret_cast<int*>(g_smem + L.misc);
-  return s;
-}
-
-template <int V>
-using IC = std::integral_constant<int, V>;
-
-template <class F>
-__device__ __forceinline__ void dispatch_enc(uint8_t enc, F&& f) {
-  switch (enc) {
-    case ENC_PLAIN: f(IC<ENC_PLAIN>()); break;
-    case ENC_PACKED: f(IC<ENC_PACKED>()); break;
-    case ENC_DICT: f(IC<ENC_DICT>()); break;
-    case ENC_RLE: f(IC<ENC_RLE>()); break;
-    default: f(IC<ENC_INDEX>()); break;
-  }
-}
-
-// Per-tile state needed to read a column at tile-relative row / segment start o.
-struct TileCtx {
-  const uint8_t* stage;   // current stage (row mode)
-  uint32_t nwords;
-};
-
-// Raw value of column c at tile row o (see PredKind for "raw").
-template <int ENC>
-__device__ __forceinline__ long long col_raw(const ColDesc& c, const Smem& sm, const TileCtx& t, uint32_t o) {
-  if constexpr (ENC == ENC_PLAIN) {
-    const uint8_t* p = t.stage + c.stage_off;
-    return c.v64 ? reinterpret_cast<const long long*>(p)[o] : (long long)reinterpret_cast<const int*>(p)[o];
-  } else if constexpr (ENC == ENC_PACKED || ENC == ENC_DICT) {
-    const uint32_t* w = reinterpret_cast<const uint32_t*>(t.stage + c.stage_off);
-    const uint64_t f = extract_field(w, o, c.bw);
-    return c.raw_is_offset ? (long long)f : (long long)(f + (uint64_t)c.base);
-  } else if constexpr (ENC == ENC_RLE) {
-    const uint32_t* B = sm.bm + c.bslot * t.nwords;
-    const uint32_t* P = sm.pre + c.bslot * (t.nwords + 1);
-    const uint64_t idx = sm.cursor[c.bslot] + rank_incl(B, P, o);
-    return ldg_val(c.vals, idx, c.v64);
-  } else {  // ENC_INDEX
-    const uint32_t* B = sm.bm + c.bslot * t.nwords;
-    const uint32_t wv = B[o >> 5];
-    if (!((wv >> (o & 31)) & 1u)) return c.base;
-    const uint32_t* P = sm.pre + c.bslot * (t.nwords + 1);
-    const uint64_t idx = sm.cursor[c.bslot] + P[o >> 5] + __popc(wv & ((1u << (o & 31)) - 1u));
-    return ldg_val(c.vals, idx, c.v64);
-  }
-}
-
-// Index column at o: listed? and value.
-__device__ __forceinline__ bool index_lookup(const ColDesc& c, const Smem& sm, const TileCtx& t, uint32_t o,
-                                             long long* v) {
-  const uint32_t* B = sm.bm + c.bslot * t.nwords;
-  const uint32_t wv = B[o >> 5];
-  if (!((wv >> (o & 31)) & 1u)) return false;
-  const uint32_t* P = sm.pre + c.bslot * (t.nwords + 1);
-  *v = ldg_val(c.vals, sm.cursor[c.bslot] + P[o >> 5] + __popc(wv & ((1u << (o & 31)) - 1u)), c.v64);
-  return true;
-}
-
-__device__ __forceinline__ bool pred_eval(const QueryDesc& q, const PredDesc& p, long long v) {
-  switch (p.kind) {
-    case PK_RANGE: return v >= p.lo && v <= p.hi;
-    case PK_NE: return v != p.lo;
-    case PK_BITMAP: {
-      if (v < p.lo || v > p.hi) return false;
-      const unsigned long long d = (unsigned long long)(v - p.lo);
-      return (__ldg(q.aux + p.aux_off + (uint32_t)(d >> 5)) >> (d & 31)) & 1u;
-    }
-    case PK_LIST: {
-      const long long* L = reinterpret_cast<const long long*>(q.aux + p.aux_off);
-      uint32_t lo = 0, hi = p.aux_len;
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(L + mid) < v) lo = mid + 1; else hi = mid;
-      }
-      return lo < p.aux_len && __ldg(L + lo) == v;
-    }
-    case PK_FALSE: return false;
-    default: return true;
-  }
-}
-
-// digit of key k for raw value v; returns false when v is outside the domain
-__device__ __forceinline__ bool key_digit(const QueryDesc& q, const KeyDesc& k, long long v, uint32_t* digit) {
-  const unsigned long long d = (unsigned long long)(v - k.kmin);
-  if (!k.remap) {
-    if (v < k.kmin || d >= k.card) return false;
-    *digit = (uint32_t)d;
-    return true;
-  }
-  if (v < k.kmin || d >= 32ull * k.aux_len) return false;
-  const uint32_t w = __ldg(q.aux + k.aux_off + (uint32_t)(d >> 5));
-  if (!((w >> (d & 31)) & 1u)) return false;
-  *digit = __ldg(q.aux + k.prefix_off + (uint32_t)(d >> 5)) + __popc(w & ((1u << (d & 31)) - 1u));
-  return true;
-}
-
-// ------------------------------------------------------------------ group table
-// multiplicative hashing: the top bits of gid * golden ratio select the slot
-__device__ __forceinline__ uint32_t hash_gid(uint32_t g, uint32_t log2_slots) {
-  return (g * 0x9E3779B1u) >> (32 - log2_slots);
-}
-
-// Shared-memory slot of gid, or -1 when the probe limit is hit (caller then
-// updates the global accumulators directly).
-__device__ __forceinline__ int table_slot(const QueryDesc& q, const Smem& sm, uint32_t gid) {
-  if (q.table_dense) return (int)gid;
-  const uint32_t mask = q.table_slots - 1;
-  uint32_t h = hash_gid(gid, 31 - __clz(q.table_slots)) & mask;
-  for (int probe = 0; probe < 32; ++probe) {
-    uint32_t k = sm.tkeys[h];
-    if (k == gid) return (int)h;
-    if (k == kEmptyKey) {
-      k = atomicCAS(&sm.tkeys[h], kEmptyKey, gid);
-      if (k == kEmptyKey) {
-        atomicAdd(&sm.misc[0], 1);
-        return (int)h;
-      }
-      if (k == gid) return (int)h;
-    }
-    h = (h + 1) & mask;
-  }
-  return -1;
-}
-
-__device__ __forceinline__ unsigned long long* gword(const QueryDesc& q, uint32_t w, uint32_t gid) {
-  return q.gacc + (size_t)w * q.n_groups + gid;
-}
-
-// Apply one item (value v of aggregate a, weight len) to shared slot or global gid.
-__device__ __forceinline__ void agg_update(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot,
-                                           uint32_t gid, long long v, uint32_t len) {
-  const uint32_t S = q.table_slots;
-  switch (a.kind) {
-    case AK_SUM:
-    case AK_ISUM: {
-      if (slot >= 0) {
-        if (!a.wide) {
-          const long long x = len == 1 ? v : v * (long long)len;
-          atomicAdd(&sm.tacc[(size_t)a.sw * S + slot], (unsigned long long)x);
-        } else {
-          atomic_add_i128(&sm.tacc[(size_t)a.sw * S + slot], &sm.tacc[(size_t)(a.sw + 1) * S + slot],
-                          len == 1 ? sext(v) : mul_s64(v, (long long)len));
-        }
-      } else {
-        global_add_limbs(gword(q, a.gw, gid), gword(q, a.gw + 1, gid), gword(q, a.gw + 2, gid),
-                         len == 1 ? sext(v) : mul_s64(v, (long long)len));
-      }
-      break;
-    }
-    case AK_MIN:
-    case AK_IMIN:
-      if (slot >= 0) atomicMin(reinterpret_cast<long long*>(&sm.tacc[(size_t)a.sw * S + slot]), v);
-      else atomicMin(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
-      break;
-    case AK_MAX:
-    case AK_IMAX:
-      if (slot >= 0) atomicMax(reinterpret_cast<long long*>(&sm.tacc[(size_t)a.sw * S + slot]), v);
-      else atomicMax(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
-      break;
-    default:
-      break;
-  }
-  if (a.kind == AK_IMIN || a.kind == AK_IMAX) {   // listed count
-    if (slot >= 0) atomicAdd(&sm.tacc[(size_t)(a.sw + 1) * S + slot], (unsigned long long)len);
-    else atomicAdd(gword(q, a.gw + 1, gid), (unsigned long long)len);
-  }
-}
-
-// Index column SUM: add (value - default) of a listed passing row (listed
-// rows are single-row items, so the weight is 1).
-__device__ __forceinline__ void isum_update(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot,
-                                            uint32_t gid, long long v) {
-  I128 x;
-  x.lo = (unsigned long long)v - (unsigned long long)a.base;
-  // borrow-aware high word of sext(v) - sext(base)
-  x.hi = (v < 0 ? -1ll : 0ll) - (a.base < 0 ? -1ll : 0ll) - ((unsigned long long)v < (unsigned long long)a.base ? 1ll : 0ll);
-  const uint32_t S = q.table_slots;
-  if (slot >= 0) {
-    if (!a.wide) atomicAdd(&sm.tacc[(size_t)a.sw * S + slot], x.lo);
-    else atomic_add_i128(&sm.tacc[(size_t)a.sw * S + slot], &sm.tacc[(size_t)(a.sw + 1) * S + slot], x);
-  } else {
-    global_add_limbs(gword(q, a.gw, gid), gword(q, a.gw + 1, gid), gword(q, a.gw + 2, gid), x);
-  }
-}
-
-__device__ __forceinline__ void reset_slot(const QueryDesc& q, const Smem& sm, uint32_t s) {
-  const uint32_t S = q.table_slots;
-  sm.tacc[s] = 0;
-  for (int i = 0; i < q.n_aggs; ++i) {
-    const AggDesc& a = q.aggs[i];
-    switch (a.kind) {
-      case AK_SUM:
-      case AK_ISUM:
-        sm.tacc[(size_t)a.sw * S + s] = 0;
-        if (a.wide) sm.tacc[(size_t)(a.sw + 1) * S + s] = 0;
-        break;
-      case AK_MIN:
-      case AK_IMIN:
-        sm.tacc[(size_t)a.sw * S + s] = (unsigned long long)LLONG_MAX;
-        if (a.kind == AK_IMIN) sm.tacc[(size_t)(a.sw + 1) * S + s] = 0;
-        break;
-      case AK_MAX:
-      case AK_IMAX:
-        sm.tacc[(size_t)a.sw * S + s] = (unsigned long long)LLONG_MIN;
-        if (a.kind == AK_IMAX) sm.tacc[(size_t)(a.sw + 1) * S + s] = 0;
-        break;
-      default:
-        break;
-    }
-  }
-  if (!q.table_dense) sm.tkeys[s] = kEmptyKey;
-}
-
-// Add every occupied slot into the global accumulators and clear the table.
-__device__ void flush_table(const QueryDesc& q, const Smem& sm) {
-  const uint32_t S = q.table_slots;
-  for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
-    const unsigned long long cnt = sm.tacc[s];
-    if (cnt == 0) {
-      if (!q.table_dense) sm.tkeys[s] = kEmptyKey;
-      continue;
-    }
-    const uint32_t gid = q.table_dense ? s : sm.tkeys[s];
-    atomicAdd(gword(q, 0, gid), cnt);
-    for (int i = 0; i < q.n_aggs; ++i) {
-      const AggDesc& a = q.aggs[i];
-      switch (a.kind) {
-        case AK_SUM:
-        case AK_ISUM: {
-          I128 x;
-          if (a.wide) {
-            x.lo = sm.tacc[(size_t)a.sw * S + s];
-            x.hi = (long long)sm.tacc[(size_t)(a.sw + 1) * S + s];
-          } else {
-            x = sext((long long)sm.tacc[(size_t)a.sw * S + s]);
-          }
-          global_add_limbs(gword(q, a.gw, gid), gword(q, a.gw + 1, gid), gword(q, a.gw + 2, gid), x);
-          break;
-        }
-        case AK_MIN:
-        case AK_IMIN: {
-          const long long v = (long long)sm.tacc[(size_t)a.sw * S + s];
-          if (v != LLONG_MAX) atomicMin(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
-          break;
-        }
-        case AK_MAX:
-        case AK_IMAX: {
-          const long long v = (long long)sm.tacc[(size_t)a.sw * S + s];
-          if (v != LLONG_MIN) atomicMax(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
-          break;
-        }
-        default:
-          break;
-      }
-      if (a.kind == AK_IMIN || a.kind == AK_IMAX) {
-        const unsigned long long lc = sm.tacc[(size_t)(a.sw + 1) * S + s];
-        if (lc) atomicAdd(gword(q, a.gw + 1, gid), lc);
-      }
-    }
-    reset_slot(q, sm, s);
-  }
-}
 
 // ------------------------------------------------------------------ tile alignment
 // Build the per-tile bitmaps of every RLE / index column for rows [s, e) and
@@ -391,7 +34,6 @@ __device__ void build_bitmaps(const QueryDesc& q, const Smem& sm, unsigned long 
   const int nb = q.n_bitmaps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (uint32_t i = threadIdx.x; i < nwords * nb; i += blockDim.x) sm.bm[i] = 0;
-  if (threadIdx.x < 2 * kMaxBitmapCols) sm.flags[threadIdx.x] = 0;
   __syncthreads();
   if (nb > 0) {
     // warps are dealt to columns round-robin; warp w serves column w % nb
@@ -402,7 +44,7 @@ __device__ void build_bitmaps(const QueryDesc& q, const Smem& sm, unsigned long 
     for (int c = 0; c < q.n_cols; ++c)
       if (q.cols[c].bslot == j) cd = &q.cols[c];
     const bool is_rle = cd->enc == ENC_RLE;
-    const unsigned long long cur = sm.cursor[j];
+    const unsigned long long cur = sm.tcur[j];
     uint32_t* B = sm.bm + j * nwords;
     for (int it = 0;; ++it) {
       const int col_done = __shfl_sync(0xFFFFFFFFu, sm.flags[j], 0);
@@ -414,7 +56,7 @@ __device__ void build_bitmaps(const QueryDesc& q, const Smem& sm, unsigned long 
           if ((unsigned long long)x < e) {
             // a boundary before the tile would mean a corrupt cursor: flag it, never write
             if ((unsigned long long)x < s || (is_rle && (unsigned long long)x == s)) {
-              atomicCAS(q.err, 0, (int)CQ_ERR_INVALID_ARG);
+              report(q, CQ_ERR_INVALID_ARG, 2ull + ((unsigned long long)j << 8), s, (unsigned long long)x);
             } else {
               const uint32_t o = (uint32_t)((unsigned long long)x - s);
               atomicOr(&B[o >> 5], 1u << (o & 31));
@@ -525,9 +167,10 @@ __device__ void build_segments(const QueryDesc& q, const Smem& sm, uint32_t nwor
   __syncthreads();
 }
 
-// ------------------------------------------------------------------ the kernel
-template <bool SEG>
-__global__ void __launch_bounds__(kThreads, 1) fused_query_kernel(const __grid_constant__ QueryDesc q) {
+// ------------------------------------------------------------------ segment-mode kernel
+// GPW: groups of 32 segments per warp per tile (tile_rows / kThreads).
+template <int GPW>
+__global__ void __launch_bounds__(kThreads, 1) seg_query_kernel(const __grid_constant__ QueryDesc q) {
   const Smem sm = carve(q);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t T = q.tile_rows;
@@ -536,208 +179,58 @@ __global__ void __launch_bounds__(kThreads, 1) fused_query_kernel(const __grid_c
   const unsigned long long t_end = (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;
   if (t_begin >= t_end) return;
 
-  // ---- init shared group table, barriers, cursors
   for (uint32_t sl = threadIdx.x; sl < q.table_slots; sl += blockDim.x) reset_slot(q, sm, sl);
   if (threadIdx.x < 8) sm.misc[threadIdx.x] = 0;
-  if (!SEG && threadIdx.x == 0) {
-    for (int st = 0; st < q.stages; ++st) mbar_init(&sm.mbar[st], 1);
-    fence_barrier_init();
-  }
+  if (threadIdx.x < 2 * kMaxBitmapCols) sm.flags[threadIdx.x] = 0;
+  const bool aux_smem = q.aux_words <= kAuxSmemWords;
+  if (aux_smem)
+    for (uint32_t i = threadIdx.x; i < q.aux_words; i += blockDim.x) sm.aux[i] = __ldg(q.aux + i);
   if (warp < q.n_bitmaps) {
     const ColDesc* cd = nullptr;
     for (int c = 0; c < q.n_cols; ++c)
       if (q.cols[c].bslot == warp) cd = &q.cols[c];
     const long long s0 = (long long)(t_begin * T);
-    // RLE: first run whose exclusive end exceeds s0; index: first position >= s0
-    const unsigned long long cur =
-        warp_count_below(cd->ends, cd->e64, cd->n, s0, /*strict=*/cd->enc == ENC_INDEX);
-    if (lane == 0) sm.cursor[warp] = cur;
+    const unsigned long long cur = warp_count_below(cd->ends, cd->e64, cd->n, s0, cd->enc == ENC_INDEX);
+    if (lane == 0) sm.tcur[warp] = cur;
   }
   __syncthreads();
 
-  // ---- bulk-copy producer (thread 0): tile u -> stage (u - t_begin) % stages
-  auto issue = [&](unsigned long long u) {
-    const uint32_t st = (uint32_t)((u - t_begin) % q.stages);
-    uint8_t* dst = sm.stage + (size_t)st * q.stage_bytes;
-    const unsigned long long r0 = u * T;
-    const unsigned long long rows = (q.n_rows - r0) < (unsigned long long)T ? (q.n_rows - r0) : (unsigned long long)T;
-    uint32_t total = 0;
-    uint32_t bytes[kMaxCols];
-    for (int i = 0; i < q.n_row_cols; ++i) {
-      const ColDesc& c = q.cols[q.row_cols[i]];
-      const uint32_t bits = c.enc == ENC_PLAIN ? (c.v64 ? 64u : 32u) : (uint32_t)c.bw;
-      bytes[i] = (uint32_t)(((rows * bits + 7) / 8 + 15) / 16 * 16);
-      total += bytes[i];
-    }
-    mbar_arrive_expect_tx(&sm.mbar[st], total);
-    for (int i = 0; i < q.n_row_cols; ++i) {
-      const ColDesc& c = q.cols[q.row_cols[i]];
-      const uint32_t bits = c.enc == ENC_PLAIN ? (c.v64 ? 64u : 32u) : (uint32_t)c.bw;
-      const uint8_t* src = reinterpret_cast<const uint8_t*>(c.vals) + r0 * bits / 8;
-      bulk_g2s(dst + c.stage_off, src, bytes[i], &sm.mbar[st]);
-    }
-  };
-  if (!SEG && threadIdx.x == 0) {
-    for (unsigned long long u = t_begin; u < t_end && u < t_begin + q.stages - 1; ++u) issue(u);
-  }
+  TileView tv;
+  tv.bm = sm.bm;
+  tv.pre = sm.pre;
+  tv.cur = sm.tcur;
+  tv.stage = nullptr;
+  tv.aux = aux_smem ? sm.aux : q.aux;
+  tv.nwords = nwords;
+  uint32_t rows_since_flush = 0;
+  uint16_t* mylist = sm.clist + warp * (GPW * 32);
+  const uint32_t wbase = warp * (GPW * 32);
 
   for (unsigned long long t = t_begin; t < t_end; ++t) {
     const unsigned long long s = t * T;
     const unsigned long long e = (s + T < q.n_rows) ? s + T : q.n_rows;
     const uint32_t rows = (uint32_t)(e - s);
-    if (!SEG && threadIdx.x == 0 && t + q.stages - 1 < t_end) issue(t + q.stages - 1);
-
     build_bitmaps(q, sm, s, e, nwords);
-    if (SEG) build_segments(q, sm, nwords, rows);
-
-    TileCtx tc;
-    tc.nwords = nwords;
-    tc.stage = sm.stage;
-    if (!SEG) {
-      const uint32_t st = (uint32_t)((t - t_begin) % q.stages);
-      const uint32_t parity = (uint32_t)(((t - t_begin) / q.stages) & 1ull);
-      tc.stage = sm.stage + (size_t)st * q.stage_bytes;
-      mbar_wait_bounded(&sm.mbar[st], parity, q.err);
-    }
-
-    // ---- phase P: predicates over this warp's items, compact the passing ones
-    const uint32_t n_items = SEG ? (uint32_t)sm.misc[2] : rows;
-    const uint32_t per_warp = ((n_items + kWarps * 32 - 1) / (kWarps * 32)) * 32;
-    const uint32_t first = warp * per_warp;
-    const int groups = (int)(per_warp / 32);
-    uint32_t item[kMaxGroupsPerWarp];
-    bool ok[kMaxGroupsPerWarp];
-#pragma unroll
-    for (int g = 0; g < kMaxGroupsPerWarp; ++g) {
-      const uint32_t it = first + g * 32 + lane;
-      ok[g] = g < groups && it < n_items;
-      item[g] = it;
-    }
-    for (int pi = 0; pi < q.n_preds; ++pi) {
-      const PredDesc& p = q.preds[pi];
-      const ColDesc& c = q.cols[p.col];
-      dispatch_enc(c.enc, [&](auto tag) {
-        constexpr int E = decltype(tag)::value;
-#pragma unroll
-        for (int g = 0; g < kMaxGroupsPerWarp; ++g) {
-          if (ok[g]) {
-            const uint32_t o = SEG ? (uint32_t)sm.seg[item[g]] : item[g];
-            ok[g] = pred_eval(q, p, col_raw<E>(c, sm, tc, o));
-          }
-        }
-      });
-    }
-    uint16_t* mylist = sm.clist + warp * (T / kWarps);
-    uint32_t n_pass = 0;
-#pragma unroll
-    for (int g = 0; g < kMaxGroupsPerWarp; ++g) {
-      if (g < groups) {
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok[g]);
-        if (ok[g]) mylist[n_pass + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)item[g];
-        n_pass += __popc(bal);
-      }
-    }
-    __syncwarp();
-
-    // ---- phase A: group id, slot, aggregate updates for the passing items
-    for (uint32_t base = 0; base < n_pass; base += 32 * kMaxGroupsPerWarp) {
-      uint32_t gid[kMaxGroupsPerWarp];
-      uint32_t off[kMaxGroupsPerWarp];
-      uint32_t len[kMaxGroupsPerWarp];
-      bool act[kMaxGroupsPerWarp];
-      bool bad[kMaxGroupsPerWarp];
-#pragma unroll
-      for (int m = 0; m < kMaxGroupsPerWarp; ++m) {
-        const uint32_t j = base + m * 32 + lane;
-        act[m] = j < n_pass;
-        bad[m] = false;
-        gid[m] = 0;
-        off[m] = 0;
-        len[m] = 1;
-        if (act[m]) {
-          const uint32_t itm = mylist[j];
-          if (SEG) {
-            off[m] = sm.seg[itm];
-            len[m] = (uint32_t)sm.seg[itm + 1] - off[m];
-          } else {
-            off[m] = itm;
-          }
-        }
-      }
-      for (int ki = 0; ki < q.n_keys; ++ki) {
-        const KeyDesc& k = q.keys[ki];
-        const ColDesc& c = q.cols[k.col];
-        dispatch_enc(c.enc, [&](auto tag) {
-          constexpr int E = decltype(tag)::value;
-#pragma unroll
-          for (int m = 0; m < kMaxGroupsPerWarp; ++m) {
-            if (act[m]) {
-              uint32_t d;
-              if (key_digit(q, k, col_raw<E>(c, sm, tc, off[m]), &d)) gid[m] += d * (uint32_t)k.stride;
-              else bad[m] = true;
-            }
-          }
-        });
-      }
-      int slot[kMaxGroupsPerWarp];
-#pragma unroll
-      for (int m = 0; m < kMaxGroupsPerWarp; ++m) {
-        slot[m] = -1;
-        if (act[m] && bad[m]) {
-          atomicCAS(q.err, 0, (int)CQ_ERR_INVALID_ARG);
-          act[m] = false;
-        }
-        if (act[m]) {
-          slot[m] = table_slot(q, sm, gid[m]);
-          if (slot[m] >= 0) atomicAdd(&sm.tacc[slot[m]], (unsigned long long)len[m]);
-          else atomicAdd(gword(q, 0, gid[m]), (unsigned long long)len[m]);
-        }
-      }
-      for (int ai = 0; ai < q.n_aggs; ++ai) {
-        const AggDesc& a = q.aggs[ai];
-        if (a.kind == AK_COUNT) continue;
-        const ColDesc& c = q.cols[a.col];
-        if (a.kind == AK_ISUM || a.kind == AK_IMIN || a.kind == AK_IMAX) {
-#pragma unroll
-          for (int m = 0; m < kMaxGroupsPerWarp; ++m) {
-            long long v;
-            if (act[m] && index_lookup(c, sm, tc, off[m], &v)) {
-              if (a.kind == AK_ISUM) isum_update(q, sm, a, slot[m], gid[m], v);
-              else agg_update(q, sm, a, slot[m], gid[m], v, len[m]);
-            }
-          }
-          continue;
-        }
-        dispatch_enc(c.enc, [&](auto tag) {
-          constexpr int E = decltype(tag)::value;
-#pragma unroll
-          for (int m = 0; m < kMaxGroupsPerWarp; ++m) {
-            if (act[m]) agg_update(q, sm, a, slot[m], gid[m], col_raw<E>(c, sm, tc, off[m]), len[m]);
-          }
-        });
-      }
-    }
+    build_segments(q, sm, nwords, rows);
+    const uint32_t pm = phase_filter<true, GPW>(q, tv, sm.seg, wbase, (uint32_t)sm.misc[2]);
+    const uint32_t n_pass = compact<GPW>(pm, wbase, mylist);
+    phase_aggregate<true>(q, sm, tv, sm.seg, mylist, n_pass, s);
     __syncthreads();
-
-    // ---- advance cursors, flush the table when needed
     if (threadIdx.x < q.n_bitmaps) {
       const int j = threadIdx.x;
       const uint32_t* P = sm.pre + j * (nwords + 1);
-      sm.cursor[j] += P[nwords] + (unsigned long long)sm.flags[kMaxBitmapCols + j];
+      sm.tcur[j] += P[nwords] + (unsigned long long)sm.flags[kMaxBitmapCols + j];
+      sm.flags[j] = 0;
+      sm.flags[kMaxBitmapCols + j] = 0;
     }
-    if (threadIdx.x == 0) sm.misc[1] += (int)rows;
-    __syncthreads();
-    const bool last = (t + 1 == t_end);
-    const bool need = last || (!q.table_dense && sm.misc[0] * 2 > (int)q.table_slots) ||
-                      (unsigned)sm.misc[1] + T > q.flush_rows;
+    rows_since_flush += rows;
+    const bool need = (t + 1 == t_end) || (!q.table_dense && sm.misc[0] * 2 > (int)q.table_slots) ||
+                      rows_since_flush + T > q.flush_rows;
     if (need) {
       flush_table(q, sm);
       __syncthreads();
-      if (threadIdx.x == 0) {
-        sm.misc[0] = 0;
-        sm.misc[1] = 0;
-      }
-      __syncthreads();
+      if (threadIdx.x == 0) sm.misc[0] = 0;
+      rows_since_flush = 0;
     }
   }
 }
@@ -896,7 +389,7 @@ __global__ void finalize_write_kernel(const __grid_constant__ QueryDesc q) {
           reinterpret_cast<double*>(q.out[oc])[row] = cnt ? i128_to_double(x) / __ull2double_rn(cnt) : 0.0;
         } else {
           const bool fits = (x.hi == 0 && (long long)x.lo >= 0) || (x.hi == -1 && (long long)x.lo < 0);
-          if (!fits) atomicCAS(q.err, 0, (int)CQ_ERR_OVERFLOW);
+          if (!fits) report(q, CQ_ERR_OVERFLOW, 3ull + ((unsigned long long)idx << 8), g, x.lo);
           reinterpret_cast<long long*>(q.out[oc])[row] = (long long)x.lo;
         }
         break;
@@ -928,11 +421,19 @@ __global__ void finalize_write_kernel(const __grid_constant__ QueryDesc q) {
 }
 
 // ------------------------------------------------------------------ launchers
+template <int GPW>
+__global__ void row_query_kernel(const __grid_constant__ QueryDesc q);   // cq_row.cu
+cudaError_t row_kernel_set_smem(int bytes);
+cudaError_t launch_row_kernel(const QueryDesc& q, unsigned grid, cudaStream_t s);
+
 cudaError_t query_kernel_set_smem(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(fused_query_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fused_query_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e;
+  const int b = (int)bytes;
+  if ((e = cudaFuncSetAttribute(seg_query_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+  if ((e = cudaFuncSetAttribute(seg_query_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+  if ((e = cudaFuncSetAttribute(seg_query_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+  if ((e = cudaFuncSetAttribute(seg_query_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+  return row_kernel_set_smem(b);
 }
 
 cudaError_t launch_init_global(const QueryDesc& q, cudaStream_t s) {
@@ -947,8 +448,13 @@ cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ct
       grid_ctas ? (unsigned long long)grid_ctas : (unsigned long long)num_sms * (unsigned long long)ctas_per_sm;
   const unsigned grid = (unsigned)(q.n_tiles < want ? q.n_tiles : want);
   if (grid == 0) return cudaSuccess;
-  if (q.seg_mode) fused_query_kernel<true><<<grid, kThreads, q.smem_bytes, s>>>(q);
-  else fused_query_kernel<false><<<grid, kThreads, q.smem_bytes, s>>>(q);
+  if (!q.seg_mode) return launch_row_kernel(q, grid, s);
+  switch (q.tile_rows / kThreads) {
+    case 2: seg_query_kernel<2><<<grid, kThreads, q.smem_bytes, s>>>(q); break;
+    case 4: seg_query_kernel<4><<<grid, kThreads, q.smem_bytes, s>>>(q); break;
+    case 8: seg_query_kernel<8><<<grid, kThreads, q.smem_bytes, s>>>(q); break;
+    default: seg_query_kernel<16><<<grid, kThreads, q.smem_bytes, s>>>(q); break;
+  }
   return cudaGetLastError();
 }
 

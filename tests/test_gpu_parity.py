@@ -234,14 +234,15 @@ def test_repeat_runs_are_deterministic(cq, ctx):
 
 
 # ------------------------------------------------------------------ many tiles per CTA
+@pytest.mark.parametrize("ctas", [1, 2])
 @pytest.mark.parametrize("grid,tile,slots", [(1, 1024, 128), (3, 4096, 1024), (7, 2048, 256), (16, 8192, 0)])
-def test_many_tiles_per_cta_heterogeneous(cq, ctx, oracle_mod, grid, tile, slots):
+def test_many_tiles_per_cta_heterogeneous(cq, ctx, oracle_mod, grid, tile, slots, ctas):
     """Few CTAs walk many tiles each: bulk-copy stages are reused, run and
     position cursors carry across tiles and the group table flushes often."""
     table, plan = dg.heterogeneous(3_000_000 + 123, seed=21, index_default=3)
     ref = oracle_mod.query(table, plan, n_threads=4)
-    opts = cq.exec_options(tile_rows=tile, grid_ctas=grid, table_slots=slots)
-    check(run(cq, ctx, table, plan, opts=opts), ref, f"grid {grid}")
+    opts = cq.exec_options(tile_rows=tile, grid_ctas=grid, table_slots=slots, ctas_per_sm=ctas)
+    check(run(cq, ctx, table, plan, opts=opts), ref, f"grid {grid} ctas/SM {ctas}")
 
 
 @pytest.mark.parametrize("grid", [1, 5])
@@ -250,3 +251,12 @@ def test_many_tiles_per_cta_segments(cq, ctx, oracle_mod, grid):
     plan = dg.Plan(plan.preds, [1, 0], plan.aggs + [dg.Agg("max", 0)])
     ref = oracle_mod.query(table, plan)
     check(run(cq, ctx, table, plan, opts=cq.exec_options(grid_ctas=grid, tile_rows=1024)), ref, f"seg grid {grid}")
+
+
+@pytest.mark.parametrize("tile,ctas", [(2048, 2), (4096, 2), (4096, 1), (8192, 1)])
+def test_heterogeneous_20m_rows_all_tiles(cq, ctx, oracle_mod, tile, ctas):
+    """20M rows: every CTA walks many tiles at every tile size (this shape
+    once exposed a device-side key error at 8192-row tiles)."""
+    table, plan = dg.heterogeneous(20_000_000, seed=20250611)
+    ref = oracle_mod.query(table, plan, n_threads=oracle_mod.cores())
+    check(run(cq, ctx, table, plan, opts=cq.exec_options(tile_rows=tile, ctas_per_sm=ctas)), ref, f"20M tile {tile}")
