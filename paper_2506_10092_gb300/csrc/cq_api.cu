@@ -820,7 +820,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   if (q.flush_rows < tile) q.flush_rows = tile;
   // ---- aggregates
   q.n_aggs = (uint8_t)plan->n_aggs;
-  uint32_t sw = 1, gw = 1;
+  uint32_t sw = 0, sw32 = 1, gw = 1;   // 32-bit word 0 is COUNT
   q.has_index_agg = 0;
   for (uint32_t i = 0; i < plan->n_aggs; ++i) {
     const cq_aggregate& a = plan->aggs[i];
@@ -865,24 +865,27 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       if (idx || cd.raw_is_offset) { rlo = pc.stats.min_raw; rhi = pc.stats.max_raw; }
       else { rlo = pc.stats.min_val; rhi = pc.stats.max_val; }
       d.w32 = (rlo >= (i128)INT_MIN && rhi <= (i128)INT_MAX) ? 1 : 0;
+      // value: a 32-bit word when it fits, else a 64-bit one; index
+      // columns add a 32-bit listed count
+      d.sw = (uint8_t)sw;
+      d.sw32 = (uint8_t)sw32;
+      if (d.w32) sw32 += 1; else sw += 1;
       if (idx) {
         d.kind = a.op == CQ_MIN ? AK_IMIN : AK_IMAX;
         d.base = pc.base;
-        d.sw = (uint8_t)sw;
-        sw += 2;
+        sw32 += 1;
         d.gw = gw;
         gw += 2;
       } else {
         d.kind = a.op == CQ_MIN ? AK_MIN : AK_MAX;
         d.base = (cd.raw_is_offset && pc.enc == ENC_PACKED) ? pc.base : 0;
-        d.sw = (uint8_t)sw;
-        sw += 1;
         d.gw = gw;
         gw += 1;
       }
     }
   }
   q.n_sw = (uint8_t)sw;
+  q.n_sw32 = (uint8_t)sw32;
   q.n_gw = (uint8_t)gw;
   // ---- shared-memory group table: dense bins when the whole domain fits
   uint32_t slots = opts && opts->table_slots ? opts->table_slots : 1024;

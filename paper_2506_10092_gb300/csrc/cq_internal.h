@@ -94,8 +94,9 @@ struct KeyDesc {
 struct AggDesc {
   uint8_t kind;
   uint8_t col;       // index into QueryDesc::cols (unused for COUNT)
-  uint8_t sw;        // first shared-memory accumulator word
+  uint8_t sw;        // first 64-bit shared-memory accumulator word
   uint8_t wide;      // SUM accumulates 128-bit in shared memory (two words)
+  uint8_t sw32;      // first 32-bit shared-memory accumulator word
   uint32_t gw;       // first global accumulator word
   uint8_t op;        // cq_agg_op (for finalize)
   uint8_t out_kind;  // 0 int64, 1 uint64, 2 double
@@ -117,7 +118,8 @@ struct QueryDesc {
   uint32_t stage_bytes;    // bytes of one stage (all row-level columns)
   uint32_t table_slots;    // shared-memory group-table slots (power of two)
   uint8_t table_dense;     // 1: slot = gid (gid domain fits the table)
-  uint8_t n_sw;            // shared accumulator words per slot (word 0 = COUNT)
+  uint8_t n_sw;            // 64-bit shared accumulator words per slot
+  uint8_t n_sw32;          // 32-bit shared accumulator words per slot (word 0 = COUNT)
   uint8_t n_gw;            // global accumulator words per group (word 0 = COUNT)
   uint8_t has_index_agg;
   uint32_t flush_rows;     // flush the shared table at least this often (rows)

@@ -14,12 +14,12 @@
 
 namespace cq {
 
-constexpr uint32_t kWin = 256;                           // prefetched run ends / positions per column and tile
+constexpr uint32_t kWin = 128;                           // prefetched run ends / positions per column and tile
 constexpr uint32_t kAuxSmemWords = 4096;                 // aux tables up to 16 KB live in shared memory
 
 // ------------------------------------------------------------------ shared-memory layout
 struct SmemLayout {
-  uint32_t stage, mbar, tkeys, tacc, bm, pre, tcur, win, ubm, upre, seg, clist, aux, flags, misc, total;
+  uint32_t stage, mbar, tkeys, tacc, tacc32, bm, pre, tcur, win, ubm, upre, seg, clist, aux, flags, misc, total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -44,6 +44,9 @@ __host__ __device__ inline SmemLayout smem_layout(const QueryDesc& q) {
   off = align_up(off, 16);
   L.tacc = off;
   off += 8u * q.n_sw * q.table_slots;
+  L.tacc32 = off;
+  off += 4u * q.n_sw32 * q.table_slots;
+  off = align_up(off, 16);
   L.bm = off;
   off += 4u * nwords * nb * nbuf;
   L.pre = off;
@@ -79,6 +82,7 @@ struct Smem {
   uint64_t* mbar;
   uint32_t* tkeys;
   unsigned long long* tacc;
+  unsigned* tacc32;
   uint32_t* bm;
   uint32_t* pre;
   unsigned long long* tcur;
@@ -101,6 +105,7 @@ __device__ __forceinline__ Smem carve(const QueryDesc& q) {
   s.mbar = reinterpret_cast<uint64_t*>(g_smem + L.mbar);
   s.tkeys = reinterpret_cast<uint32_t*>(g_smem + L.tkeys);
   s.tacc = reinterpret_cast<unsigned long long*>(g_smem + L.tacc);
+  s.tacc32 = reinterpret_cast<unsigned*>(g_smem + L.tacc32);
   s.bm = reinterpret_cast<uint32_t*>(g_smem + L.bm);
   s.pre = reinterpret_cast<uint32_t*>(g_smem + L.pre);
   s.tcur = reinterpret_cast<unsigned long long*>(g_smem + L.tcur);
@@ -305,10 +310,9 @@ __device__ __forceinline__ void report(const QueryDesc& q, int code, unsigned lo
 }
 
 // ------------------------------------------------------------------ group table
-// Shared-memory group table, structure of arrays over `table_slots` slots of
-// 64-bit words: word 0 holds the slot's COUNT in its low 32 bits; every
-// aggregate owns words from a.sw on (a SUM one or two, MIN / MAX one -- in
-// its low 32 bits when a.w32 -- index MIN / MAX a value and a listed count).
+// Shared-memory group table, structure of arrays over `table_slots` slots: a
+// 64-bit word array (SUMs, wide MIN / MAX) and a 32-bit word array (COUNT in
+// word 0, MIN / MAX whose values fit 32 bits, listed counts of index columns).
 
 // multiplicative hashing: the top bits of gid * golden ratio select the slot
 __device__ __forceinline__ uint32_t hash_gid(uint32_t g, uint32_t log2_slots) {
@@ -346,7 +350,16 @@ __device__ __forceinline__ unsigned long long* sword(const QueryDesc& q, const S
 }
 
 __device__ __forceinline__ int* sword32(const QueryDesc& q, const Smem& sm, uint32_t w, int slot) {
-  return reinterpret_cast<int*>(sword(q, sm, w, slot));   // low half (little endian)
+  return reinterpret_cast<int*>(&sm.tacc32[(size_t)w * q.table_slots + slot]);
+}
+
+__device__ __forceinline__ unsigned* scount(const QueryDesc& q, const Smem& sm, int slot) {
+  return &sm.tacc32[slot];
+}
+
+// 32-bit word of an index column's listed count
+__device__ __forceinline__ unsigned* slisted(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot) {
+  return reinterpret_cast<unsigned*>(sword32(q, sm, a.sw32 + (a.w32 ? 1 : 0), slot));
 }
 
 // 128-bit value of (v - base) for an index column's listed row
@@ -385,8 +398,8 @@ __device__ __forceinline__ void minmax_add(const QueryDesc& q, const Smem& sm, c
                                            uint32_t gid, long long v, bool is_min) {
   if (slot >= 0) {
     if (a.w32) {
-      if (is_min) atomicMin(sword32(q, sm, a.sw, slot), (int)v);
-      else atomicMax(sword32(q, sm, a.sw, slot), (int)v);
+      if (is_min) atomicMin(sword32(q, sm, a.sw32, slot), (int)v);
+      else atomicMax(sword32(q, sm, a.sw32, slot), (int)v);
     } else {
       if (is_min) atomicMin(reinterpret_cast<long long*>(sword(q, sm, a.sw, slot)), v);
       else atomicMax(reinterpret_cast<long long*>(sword(q, sm, a.sw, slot)), v);
@@ -398,7 +411,7 @@ __device__ __forceinline__ void minmax_add(const QueryDesc& q, const Smem& sm, c
 }
 
 __device__ __forceinline__ void reset_slot(const QueryDesc& q, const Smem& sm, uint32_t s) {
-  sm.tacc[s] = 0;
+  *scount(q, sm, s) = 0;
   for (int i = 0; i < q.n_aggs; ++i) {
     const AggDesc& a = q.aggs[i];
     switch (a.kind) {
@@ -409,14 +422,14 @@ __device__ __forceinline__ void reset_slot(const QueryDesc& q, const Smem& sm, u
         break;
       case AK_MIN:
       case AK_IMIN:
-        *sword(q, sm, a.sw, s) = a.w32 ? (unsigned long long)(unsigned)INT_MAX : (unsigned long long)LLONG_MAX;
-        if (a.kind == AK_IMIN) *sword(q, sm, a.sw + 1, s) = 0;
-        break;
       case AK_MAX:
-      case AK_IMAX:
-        *sword(q, sm, a.sw, s) = a.w32 ? (unsigned long long)(unsigned)INT_MIN : (unsigned long long)LLONG_MIN;
-        if (a.kind == AK_IMAX) *sword(q, sm, a.sw + 1, s) = 0;
+      case AK_IMAX: {
+        const bool mn = a.kind == AK_MIN || a.kind == AK_IMIN;
+        if (a.w32) *sword32(q, sm, a.sw32, s) = mn ? INT_MAX : INT_MIN;
+        else *sword(q, sm, a.sw, s) = mn ? (unsigned long long)LLONG_MAX : (unsigned long long)LLONG_MIN;
+        if (a.kind == AK_IMIN || a.kind == AK_IMAX) *slisted(q, sm, a, s) = 0;
         break;
+      }
       default:
         break;
     }
@@ -428,7 +441,7 @@ __device__ __forceinline__ void reset_slot(const QueryDesc& q, const Smem& sm, u
 __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
   const uint32_t S = q.table_slots;
   for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
-    const unsigned cnt = *reinterpret_cast<const unsigned*>(&sm.tacc[s]);
+    const unsigned cnt = *scount(q, sm, s);
     if (cnt == 0) {
       if (!q.table_dense) sm.tkeys[s] = kEmptyKey;
       continue;
@@ -452,13 +465,13 @@ __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
         }
         case AK_MIN:
         case AK_IMIN: {
-          const long long v = a.w32 ? (long long)*sword32(q, sm, a.sw, s) : (long long)*sword(q, sm, a.sw, s);
+          const long long v = a.w32 ? (long long)*sword32(q, sm, a.sw32, s) : (long long)*sword(q, sm, a.sw, s);
           if (v != (a.w32 ? (long long)INT_MAX : LLONG_MAX)) atomicMin(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
           break;
         }
         case AK_MAX:
         case AK_IMAX: {
-          const long long v = a.w32 ? (long long)*sword32(q, sm, a.sw, s) : (long long)*sword(q, sm, a.sw, s);
+          const long long v = a.w32 ? (long long)*sword32(q, sm, a.sw32, s) : (long long)*sword(q, sm, a.sw, s);
           if (v != (a.w32 ? (long long)INT_MIN : LLONG_MIN)) atomicMax(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
           break;
         }
@@ -466,8 +479,8 @@ __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
           break;
       }
       if (a.kind == AK_IMIN || a.kind == AK_IMAX) {
-        const unsigned long long lc = *sword(q, sm, a.sw + 1, s);
-        if (lc) atomicAdd(gword(q, a.gw + 1, gid), lc);
+        const unsigned lc = *slisted(q, sm, a, s);
+        if (lc) atomicAdd(gword(q, a.gw + 1, gid), (unsigned long long)lc);
       }
     }
     reset_slot(q, sm, s);
@@ -501,15 +514,28 @@ __device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileV
       dispatch_test(p, [&](auto kt) {
         constexpr int E = decltype(et)::value;
         constexpr int K = decltype(kt)::value;
+        if constexpr (SEG) {
 #pragma unroll 2
-        for (int g = 0; g < GPW; ++g) {
-          if (!((pm >> g) & 1u)) continue;
-          const uint32_t it = wbase + g * 32 + lane;
-          const uint32_t o = SEG ? (uint32_t)seg[it] : it;
-          bool ok;
-          if constexpr (K >= PT_RANGE32) ok = pred_test32<K>(p, t.aux, col_raw32<E>(c, t, o));
-          else ok = pred_test<K>(p, t.aux, col_raw<E>(c, t, o));
-          if (!ok) pm &= ~(1u << g);
+          for (int g = 0; g < GPW; ++g) {
+            if (!((pm >> g) & 1u)) continue;
+            const uint32_t o = (uint32_t)seg[wbase + g * 32 + lane];
+            bool ok;
+            if constexpr (K >= PT_RANGE32) ok = pred_test32<K>(p, t.aux, col_raw32<E>(c, t, o));
+            else ok = pred_test<K>(p, t.aux, col_raw<E>(c, t, o));
+            if (!ok) pm &= ~(1u << g);
+          }
+        } else {
+          // rows of a tile are always readable (stale beyond the last row,
+          // masked by `valid`), so every group is evaluated without branches
+          // and the unrolled loads of several groups overlap
+#pragma unroll 4
+          for (int g = 0; g < GPW; ++g) {
+            const uint32_t o = wbase + g * 32 + lane;
+            bool ok;
+            if constexpr (K >= PT_RANGE32) ok = pred_test32<K>(p, t.aux, col_raw32<E>(c, t, o));
+            else ok = pred_test<K>(p, t.aux, col_raw<E>(c, t, o));
+            pm &= ok ? 0xFFFFFFFFu : ~(1u << g);
+          }
         }
       });
     });
@@ -589,9 +615,9 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
         if (slot >= 0) {
           if (uniform) {
             const uint32_t tot = SEG ? __reduce_add_sync(gmask, len) : (uint32_t)__popc(gmask);
-            if (lead) atomicAdd(reinterpret_cast<unsigned*>(&sm.tacc[slot]), tot);
+            if (lead) atomicAdd(scount(q, sm, slot), tot);
           } else {
-            atomicAdd(reinterpret_cast<unsigned*>(&sm.tacc[slot]), len);
+            atomicAdd(scount(q, sm, slot), len);
           }
         } else {
           atomicAdd(gword(q, 0, gid), (unsigned long long)len);
@@ -609,7 +635,7 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
                 sum_add(q, sm, a, slot, gid, index_delta(v, a.base));
               } else {
                 minmax_add(q, sm, a, slot, gid, v, a.kind == AK_IMIN);
-                if (slot >= 0) atomicAdd(reinterpret_cast<unsigned*>(sword(q, sm, a.sw + 1, slot)), 1u);
+                if (slot >= 0) atomicAdd(slisted(q, sm, a, slot), 1u);
                 else atomicAdd(gword(q, a.gw + 1, gid), 1ull);
               }
             }
@@ -635,8 +661,8 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
             if (uniform && a.w32 && slot >= 0) {
               const int r = is_min ? __reduce_min_sync(gmask, (int)v) : __reduce_max_sync(gmask, (int)v);
               if (lead) {
-                if (is_min) atomicMin(sword32(q, sm, a.sw, slot), r);
-                else atomicMax(sword32(q, sm, a.sw, slot), r);
+                if (is_min) atomicMin(sword32(q, sm, a.sw32, slot), r);
+                else atomicMax(sword32(q, sm, a.sw32, slot), r);
               }
             } else {
               minmax_add(q, sm, a, slot, gid, v, is_min);
