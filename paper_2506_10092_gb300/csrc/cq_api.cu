@@ -851,11 +851,12 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
         d.base = 0;
       }
       d.wide = bound * (i128)q.flush_rows >= ((i128)1 << 62) ? 1 : 0;
-      // raw values small enough to be summed across a warp in 32 bits
+      // raw values small enough to be summed across a warp batch in 32 bits
       i128 rlo, rhi;
       if (cd.raw_is_offset) { rlo = pc.stats.min_raw; rhi = pc.stats.max_raw; }
       else { rlo = pc.stats.min_val; rhi = pc.stats.max_val; }
-      d.red32 = (!idx && !d.wide && rlo > -((i128)1 << 26) && rhi < ((i128)1 << 26)) ? 1 : 0;
+      // a warp reduces up to 128 values (4 per lane) in 32 bits
+      d.red32 = (!idx && !d.wide && rlo > -((i128)1 << 24) && rhi < ((i128)1 << 24)) ? 1 : 0;
       d.sw = (uint8_t)sw;
       sw += d.wide ? 2 : 1;
       d.gw = gw;

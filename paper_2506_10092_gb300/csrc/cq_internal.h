@@ -100,7 +100,7 @@ struct AggDesc {
   uint32_t gw;       // first global accumulator word
   uint8_t op;        // cq_agg_op (for finalize)
   uint8_t out_kind;  // 0 int64, 1 uint64, 2 double
-  uint8_t red32;     // SUM: raw values fit int32 with |v| < 2^26 -> warp-reduced in 32 bits (row mode)
+  uint8_t red32;     // SUM: |raw| < 2^24 -> a warp batch (<= 128 values) is reduced in 32 bits
   uint8_t w32;       // MIN/MAX: raw values fit int32 -> 32-bit shared accumulator, warp-reduced
   int64_t base;      // value added back at finalize (packed base or index default)
 };

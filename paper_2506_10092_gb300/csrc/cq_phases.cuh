@@ -560,118 +560,144 @@ __device__ __forceinline__ uint32_t compact(uint32_t pm, uint32_t wbase, uint16_
   return n;
 }
 
-// Aggregate: one passing item per lane.  Each lane updates its group's shared
-// slot with native 32-bit shared atomics (or the global accumulators when the
-// table has no free slot within the probe limit).  When every active lane of
-// the warp belongs to one group, the warp reduces first and one lane updates.
-template <bool SEG>
+// One aggregate's update for one item (slot >= 0: shared table; else global).
+__device__ __forceinline__ void agg_item(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot,
+                                         uint32_t gid, long long v, uint32_t len) {
+  if (a.kind == AK_SUM) sum_add(q, sm, a, slot, gid, len == 1 ? sext(v) : mul_s64(v, (long long)len));
+  else minmax_add(q, sm, a, slot, gid, v, a.kind == AK_MIN);
+}
+
+// Aggregate: passing items in batches of 32 * MI per warp, MI per lane.  Keys,
+// slots and every aggregate are separate passes over the batch with the key /
+// aggregate dispatch hoisted out, so the MI items of a lane form independent
+// chains.  Each item updates its group's shared slot with native 32-bit
+// shared atomics (or the global accumulators when the table has no free slot
+// within the probe limit).  A single-group query reduces across the warp
+// first and one lane updates.
+template <bool SEG, int MI>
 __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& sm, const TileView& t,
                                                 const uint16_t* seg, const uint16_t* list, uint32_t n_pass,
                                                 unsigned long long tile_row0) {
   const int lane = threadIdx.x & 31;
-  for (uint32_t j0 = 0; j0 < n_pass; j0 += 32) {
-    const uint32_t j = j0 + lane;
-    const bool act = j < n_pass;
-    const uint32_t amask = __ballot_sync(0xFFFFFFFFu, act);
-    if (act) {
-      const uint32_t itm = list[j];
-      uint32_t o, len;
+  const bool one_group = q.n_groups == 1;
+  for (uint32_t j0 = 0; j0 < n_pass; j0 += 32 * MI) {
+    uint32_t o[MI], len[MI], gid[MI];
+    int slot[MI];
+    bool act[MI];
+#pragma unroll
+    for (int m = 0; m < MI; ++m) {
+      const uint32_t j = j0 + m * 32 + lane;
+      act[m] = j < n_pass;
+      const uint32_t itm = act[m] ? list[j] : list[j0];
       if (SEG) {
-        o = seg[itm];
-        len = (uint32_t)seg[itm + 1] - o;
+        o[m] = seg[itm];
+        len[m] = act[m] ? (uint32_t)seg[itm + 1] - o[m] : 0u;
       } else {
-        o = itm;
-        len = 1;
+        o[m] = itm;
+        len[m] = act[m] ? 1u : 0u;
       }
-      uint32_t gid = 0;
-      bool bad = false;
-      int last_col = -1;
-      long long last_v = 0;
-      for (int ki = 0; ki < q.n_keys; ++ki) {
-        const KeyDesc& k = q.keys[ki];
-        const long long v = col_value(q.cols[k.col], t, o);
-        last_col = k.col;
-        last_v = v;
-        uint32_t d;
-        if (key_digit(k, t.aux, v, &d)) {
-          gid += d * (uint32_t)k.stride;
-        } else if (!bad) {
-          bad = true;
-          report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)ki << 8), tile_row0 + o, (unsigned long long)v);
-        }
-      }
-      const uint32_t gmask = __ballot_sync(amask, !bad);
-      if (!bad) {
-        const int first = __ffs(gmask) - 1;
-        const bool uniform = __all_sync(gmask, gid == __shfl_sync(gmask, gid, first));
-        const bool lead = lane == first;
-        int slot;
-        if (uniform) {
-          slot = lead ? table_slot(q, sm, gid) : 0;
-          slot = __shfl_sync(gmask, slot, first);
-        } else {
-          slot = table_slot(q, sm, gid);
-        }
-        if (slot >= 0) {
-          if (uniform) {
-            const uint32_t tot = SEG ? __reduce_add_sync(gmask, len) : (uint32_t)__popc(gmask);
-            if (lead) atomicAdd(scount(q, sm, slot), tot);
-          } else {
-            atomicAdd(scount(q, sm, slot), len);
-          }
-        } else {
-          atomicAdd(gword(q, 0, gid), (unsigned long long)len);
-        }
-        for (int ai = 0; ai < q.n_aggs; ++ai) {
-          const AggDesc& a = q.aggs[ai];
-          if (a.kind == AK_COUNT) continue;
-          const ColDesc& c = q.cols[a.col];
-          if (a.kind == AK_ISUM || a.kind == AK_IMIN || a.kind == AK_IMAX) {
-            // index column: only listed rows differ from the default, which
-            // the finalize step adds back from COUNT
-            long long v;
-            if (index_lookup(c, t, o, &v)) {
-              if (a.kind == AK_ISUM) {
-                sum_add(q, sm, a, slot, gid, index_delta(v, a.base));
-              } else {
-                minmax_add(q, sm, a, slot, gid, v, a.kind == AK_IMIN);
-                if (slot >= 0) atomicAdd(slisted(q, sm, a, slot), 1u);
-                else atomicAdd(gword(q, a.gw + 1, gid), 1ull);
-              }
-            }
-            continue;
-          }
-          long long v;
-          if (a.col == last_col) {
-            v = last_v;
-          } else {
-            v = col_value(c, t, o);
-            last_col = a.col;
-            last_v = v;
-          }
-          if (a.kind == AK_SUM) {
-            if (uniform && !SEG && a.red32 && slot >= 0) {
-              const int r = __reduce_add_sync(gmask, (int)v);
-              if (lead) smem_add64(sword(q, sm, a.sw, slot), (long long)r);
-            } else {
-              sum_add(q, sm, a, slot, gid, len == 1 ? sext(v) : mul_s64(v, (long long)len));
-            }
-          } else {
-            const bool is_min = a.kind == AK_MIN;
-            if (uniform && a.w32 && slot >= 0) {
-              const int r = is_min ? __reduce_min_sync(gmask, (int)v) : __reduce_max_sync(gmask, (int)v);
-              if (lead) {
-                if (is_min) atomicMin(sword32(q, sm, a.sw32, slot), r);
-                else atomicMax(sword32(q, sm, a.sw32, slot), r);
-              }
-            } else {
-              minmax_add(q, sm, a, slot, gid, v, is_min);
-            }
+      gid[m] = 0;
+      slot[m] = -1;
+    }
+    // ---- group ids
+    for (int ki = 0; ki < q.n_keys; ++ki) {
+      const KeyDesc& k = q.keys[ki];
+      const ColDesc& c = q.cols[k.col];
+      dispatch_col<SEG>(c.enc, [&](auto et) {
+        constexpr int E = decltype(et)::value;
+#pragma unroll
+        for (int m = 0; m < MI; ++m) {
+          const long long v = col_raw<E>(c, t, o[m]);
+          uint32_t d;
+          if (key_digit(k, t.aux, v, &d)) {
+            gid[m] += d * (uint32_t)k.stride;
+          } else if (act[m]) {
+            act[m] = false;
+            report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)ki << 8), tile_row0 + o[m], (unsigned long long)v);
           }
         }
+      });
+    }
+    // ---- slots and COUNT
+    if (one_group) {
+      uint32_t tot = 0;
+#pragma unroll
+      for (int m = 0; m < MI; ++m) tot += act[m] ? len[m] : 0u;
+      tot = __reduce_add_sync(0xFFFFFFFFu, tot);
+      if (lane == 0) atomicAdd(scount(q, sm, 0), tot);
+#pragma unroll
+      for (int m = 0; m < MI; ++m) slot[m] = 0;
+    } else {
+#pragma unroll
+      for (int m = 0; m < MI; ++m) {
+        if (!act[m]) continue;
+        slot[m] = table_slot(q, sm, gid[m]);
+        if (slot[m] >= 0) atomicAdd(scount(q, sm, slot[m]), len[m]);
+        else atomicAdd(gword(q, 0, gid[m]), (unsigned long long)len[m]);
       }
     }
-    __syncwarp();
+    // ---- aggregates
+    int last_col = -1;
+    long long val[MI];
+#pragma unroll
+    for (int m = 0; m < MI; ++m) val[m] = 0;
+    for (int ai = 0; ai < q.n_aggs; ++ai) {
+      const AggDesc& a = q.aggs[ai];
+      if (a.kind == AK_COUNT) continue;
+      const ColDesc& c = q.cols[a.col];
+      if (a.kind == AK_ISUM || a.kind == AK_IMIN || a.kind == AK_IMAX) {
+        // index column: only listed rows differ from the default, which the
+        // finalize step adds back from COUNT
+#pragma unroll
+        for (int m = 0; m < MI; ++m) {
+          long long v;
+          if (act[m] && index_lookup(c, t, o[m], &v)) {
+            if (a.kind == AK_ISUM) {
+              sum_add(q, sm, a, slot[m], gid[m], index_delta(v, a.base));
+            } else {
+              minmax_add(q, sm, a, slot[m], gid[m], v, a.kind == AK_IMIN);
+              if (slot[m] >= 0) atomicAdd(slisted(q, sm, a, slot[m]), 1u);
+              else atomicAdd(gword(q, a.gw + 1, gid[m]), 1ull);
+            }
+          }
+        }
+        continue;
+      }
+      if (a.col != last_col) {
+        dispatch_col<SEG>(c.enc, [&](auto et) {
+          constexpr int E = decltype(et)::value;
+#pragma unroll
+          for (int m = 0; m < MI; ++m) val[m] = col_raw<E>(c, t, o[m]);
+        });
+        last_col = a.col;
+      }
+      if (one_group && !SEG && (a.kind == AK_SUM ? a.red32 : a.w32)) {
+        // warp reduction of the whole batch, one shared update
+        int r;
+        if (a.kind == AK_SUM) {
+          int x = 0;
+#pragma unroll
+          for (int m = 0; m < MI; ++m) x += act[m] ? (int)val[m] : 0;
+          r = __reduce_add_sync(0xFFFFFFFFu, x);
+          if (lane == 0) smem_add64(sword(q, sm, a.sw, 0), (long long)r);
+        } else {
+          const bool mn = a.kind == AK_MIN;
+          int x = mn ? INT_MAX : INT_MIN;
+#pragma unroll
+          for (int m = 0; m < MI; ++m)
+            if (act[m]) x = mn ? min(x, (int)val[m]) : max(x, (int)val[m]);
+          r = mn ? __reduce_min_sync(0xFFFFFFFFu, x) : __reduce_max_sync(0xFFFFFFFFu, x);
+          if (lane == 0) {
+            if (mn) atomicMin(sword32(q, sm, a.sw32, 0), r);
+            else atomicMax(sword32(q, sm, a.sw32, 0), r);
+          }
+        }
+        continue;
+      }
+#pragma unroll
+      for (int m = 0; m < MI; ++m)
+        if (act[m]) agg_item(q, sm, a, slot[m], gid[m], val[m], len[m]);
+    }
   }
 }
 

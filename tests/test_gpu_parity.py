@@ -260,3 +260,15 @@ def test_heterogeneous_20m_rows_all_tiles(cq, ctx, oracle_mod, tile, ctas):
     table, plan = dg.heterogeneous(20_000_000, seed=20250611)
     ref = oracle_mod.query(table, plan, n_threads=oracle_mod.cores())
     check(run(cq, ctx, table, plan, opts=cq.exec_options(tile_rows=tile, ctas_per_sm=ctas)), ref, f"20M tile {tile}")
+
+
+@pytest.mark.parametrize("seg", [False, True])
+def test_single_group_queries(cq, ctx, oracle_mod, seg):
+    """No GROUP BY: every passing item lands in one group (warp-reduced path)."""
+    table, plan = dg.heterogeneous(1_000_000, seed=12) if not seg else dg.tiny_two_rle(1_000_000, seed=12)
+    if not seg:
+        plan = dg.Plan(plan.preds, [], [dg.Agg("sum", 4), dg.Agg("min", 4), dg.Agg("max", 4), dg.Agg("count"),
+                                         dg.Agg("sum", 3), dg.Agg("avg", 2), dg.Agg("max", 0)])
+    else:
+        plan = dg.Plan(plan.preds, [], [dg.Agg("sum", 0), dg.Agg("count"), dg.Agg("min", 1), dg.Agg("avg", 0)])
+    check(run(cq, ctx, table, plan), oracle_mod.query(table, plan, n_threads=4), f"one group seg={seg}")
