@@ -914,6 +914,17 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     return set_error(CQ_ERR_UNSUPPORTED, "query does not fit in %zu bytes of shared memory (tile_rows %u)",
                      smem_limit, tile);
   }
+  // grow the hash table into the shared memory left over (fewer flushes)
+  if (!q.table_dense && !(opts && opts->table_slots)) {
+    while (q.table_slots < 4096) {
+      q.table_slots *= 2;
+      if (query_kernel_smem(q) > smem_limit) {
+        q.table_slots /= 2;
+        break;
+      }
+    }
+    q.smem_bytes = (uint32_t)query_kernel_smem(q);
+  }
   P->ctas_per_sm = (!q.seg_mode && ncw == 8) ? 2 : 1;
   P->grid_ctas = opts ? opts->grid_ctas : 0u;
   // ---- outputs
@@ -936,9 +947,9 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
 }
 
 // Plan the query, trying kernel shapes in order of preference until one fits
-// in shared memory.  Row mode prefers two CTAs per SM of 8 compute warps with
-// 4096-row tiles, then one CTA of 16 compute warps with 8192-row tiles; tiles
-// halve down to 1024 rows.  Segment mode runs one 512-thread CTA per SM.
+// in shared memory.  Row mode runs one CTA of 16 compute warps per SM with
+// 8192-row tiles (two CTAs of 8 compute warps with 4096-row tiles when asked);
+// tiles halve down to 1024 rows.  Segment mode runs one 512-thread CTA per SM.
 // Options pin the tile size (smaller ones are tried when it does not fit)
 // and / or the CTAs per SM.
 static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
@@ -968,9 +979,10 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   };
   if (seg) {
     add(16, 4096, ctx->smem_optin);
+  } else if (want_ctas == 2) {
+    add(8, 4096, ctx->smem_two);
   } else {
-    if (want_ctas != 1) add(8, 4096, ctx->smem_two);
-    if (want_ctas != 2) add(16, 8192, ctx->smem_optin);
+    add(16, 8192, ctx->smem_optin);
   }
   int rc = CQ_ERR_UNSUPPORTED;
   for (const Shape& sh : shapes) {

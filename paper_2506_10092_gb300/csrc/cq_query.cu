@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1) seg_query_kernel(const __grid_con
     build_segments(q, sm, nwords, rows);
     const uint32_t pm = phase_filter<true, GPW>(q, tv, sm.seg, wbase, (uint32_t)sm.misc[2]);
     const uint32_t n_pass = compact<GPW>(pm, wbase, mylist);
-    phase_aggregate<true, 4>(q, sm, tv, sm.seg, mylist, n_pass, s);
+    phase_aggregate<true, 2>(q, sm, tv, sm.seg, mylist, n_pass, s);
     __syncthreads();
     if (threadIdx.x < q.n_bitmaps) {
       const int j = threadIdx.x;

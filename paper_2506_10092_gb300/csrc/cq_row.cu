@@ -229,7 +229,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, (NCW <= 8 ? 2 : 1)) row_query_
       tv.nwords = nwords;
       const uint32_t pm = phase_filter<false, GPW>(q, tv, nullptr, wbase, rows);
       const uint32_t n_pass = compact<GPW>(pm, wbase, mylist);
-      phase_aggregate<false, 4>(q, sm, tv, nullptr, mylist, n_pass, s);
+      phase_aggregate<false, 2>(q, sm, tv, nullptr, mylist, n_pass, s);
     } else if (nb && t + 1 < t_end) {
       helper_build(q, sm, buf ^ 1, e, (e + T < q.n_rows) ? e + T : q.n_rows, nwords);
       if (t + 2 < t_end) prefetch_windows(q, sm, buf);
