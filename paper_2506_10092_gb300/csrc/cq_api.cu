@@ -972,8 +972,9 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   struct Shape { int ncw; uint32_t tile; size_t limit; };
   std::vector<Shape> shapes;
   auto add = [&](int ncw, uint32_t first, size_t limit) {
-    // a tile is ncw * 32 * GPW rows with GPW in {2, 4, 8, 16}
-    const uint32_t max_tile = (uint32_t)ncw * 32u * 16u;
+    // a tile is 16 compute warps * 32 * GPW rows with GPW in {2, 4, 8, 16};
+    // the two-CTA shape (marked ncw == 8) stops at GPW 8
+    const uint32_t max_tile = ncw == 8 ? 4096u : 8192u;
     for (uint32_t t = want_tile ? want_tile : first; t >= 1024; t /= 2)
       if (t <= max_tile) shapes.push_back({ncw, t, limit});
   };

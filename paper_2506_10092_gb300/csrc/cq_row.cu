@@ -141,9 +141,10 @@ __device__ void helper_build(const QueryDesc& q, const Smem& sm, int buf, unsign
 }
 
 // NCW compute warps (+1 helper); GPW groups of 32 rows per compute warp, so a
-// tile holds NCW * GPW * 32 rows.  With 8 compute warps two CTAs share an SM.
-template <int NCW, int GPW>
-__global__ void __launch_bounds__((NCW + 1) * 32, (NCW <= 8 ? 2 : 1)) row_query_kernel(const __grid_constant__ QueryDesc q) {
+// tile holds NCW * GPW * 32 rows.  MINB CTAs share an SM (registers are
+// capped so that MINB CTAs fit).
+template <int NCW, int GPW, int MINB>
+__global__ void __launch_bounds__((NCW + 1) * 32, MINB) row_query_kernel(const __grid_constant__ QueryDesc q) {
   const Smem sm = carve(q);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t T = q.tile_rows;
@@ -253,35 +254,30 @@ __global__ void __launch_bounds__((NCW + 1) * 32, (NCW <= 8 ? 2 : 1)) row_query_
   }
 }
 
-template <int NCW>
-static cudaError_t set_smem_ncw(int bytes) {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(row_query_kernel<NCW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-  if ((e = cudaFuncSetAttribute(row_query_kernel<NCW, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-  if ((e = cudaFuncSetAttribute(row_query_kernel<NCW, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-  return cudaFuncSetAttribute(row_query_kernel<NCW, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
+#define CQ_ROW_SHAPES(X) X(16, 2, 1) X(16, 4, 1) X(16, 8, 1) X(16, 16, 1) X(16, 2, 2) X(16, 4, 2) X(16, 8, 2)
 
 cudaError_t row_kernel_set_smem(int bytes) {
-  cudaError_t e = set_smem_ncw<8>(bytes);
-  if (e != cudaSuccess) return e;
-  return set_smem_ncw<16>(bytes);
-}
-
-template <int NCW>
-static void launch_ncw(const QueryDesc& q, unsigned grid, cudaStream_t s) {
-  const int threads = (NCW + 1) * 32;
-  switch (q.tile_rows / (NCW * 32)) {
-    case 2: row_query_kernel<NCW, 2><<<grid, threads, q.smem_bytes, s>>>(q); break;
-    case 4: row_query_kernel<NCW, 4><<<grid, threads, q.smem_bytes, s>>>(q); break;
-    case 8: row_query_kernel<NCW, 8><<<grid, threads, q.smem_bytes, s>>>(q); break;
-    default: row_query_kernel<NCW, 16><<<grid, threads, q.smem_bytes, s>>>(q); break;
-  }
+  cudaError_t e = cudaSuccess;
+#define CQ_SET(N, G, M)                                                                                   \
+  if (e == cudaSuccess)                                                                                   \
+    e = cudaFuncSetAttribute(row_query_kernel<N, G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  CQ_ROW_SHAPES(CQ_SET)
+#undef CQ_SET
+  return e;
 }
 
 cudaError_t launch_row_kernel(const QueryDesc& q, unsigned grid, cudaStream_t s) {
-  if (q.ncw == 8) launch_ncw<8>(q, grid, s);
-  else launch_ncw<16>(q, grid, s);
+  const int gpw = (int)(q.tile_rows / (16 * 32));
+  const int minb = q.ncw == 8 ? 2 : 1;   // ncw field: 8 marks the two-CTA shape
+  bool launched = false;
+#define CQ_GO(N, G, M)                                                                \
+  if (!launched && gpw == G && minb == M) {                                           \
+    row_query_kernel<N, G, M><<<grid, (N + 1) * 32, q.smem_bytes, s>>>(q);            \
+    launched = true;                                                                  \
+  }
+  CQ_ROW_SHAPES(CQ_GO)
+#undef CQ_GO
+  if (!launched) return cudaErrorInvalidConfiguration;
   return cudaGetLastError();
 }
 
