@@ -281,6 +281,31 @@ int cq_align_segments(cq_ctx* ctx, cq_column* const* cols, uint32_t k, void* cud
                       int64_t* seg_ends, int64_t* ridx, uint64_t capacity,
                       uint64_t* n_segments);
 
+/* Allocation-free form of cq_align_segments, for callers that cannot
+ * allocate device memory while they run (a memory budget owned by someone
+ * else, a pre-sized arena, code that must stay out of the CUDA allocator).
+ * The paper has no counterpart: this is an interface for such callers.
+ * Inputs are raw DEVICE arrays instead of column handles: run_ends[j] holds
+ * n_runs[j] exclusive run ends of column j (int64 when end_is_i64[j] is
+ * non-zero, else int32), strictly increasing, the last equal to n_rows.
+ * Outputs, capacity and the return value are those of cq_align_segments
+ * (seg_ends / ridx are device buffers; *n_segments is host memory).
+ * No device memory is allocated and none is freed: the only scratch is a
+ * fixed device array of CQ_STATIC_ALIGN_MAX_TILES + 8 64-bit words (512 KB)
+ * inside the library, held by every GPU that loads it until the process
+ * exits; n_rows above CQ_STATIC_ALIGN_MAX_TILES * 4096 is rejected with
+ * CQ_ERR_INVALID_ARG.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress, with the device current); make that
+ * first call before capturing any stream.  All calls share the array and it
+ * keeps the last call's contents (the call clears what must start at zero),
+ * so calls that overlap on the GPU -- from several host threads or streams --
+ * race and must be serialised by the caller.  Synchronous on cuda_stream
+ * (NULL: the legacy default stream) of the current device. */
+#define CQ_STATIC_ALIGN_MAX_TILES 65536
+int cq_align_segments_static(uint32_t k, const void* const* run_ends, const uint32_t* end_is_i64,
+                             const uint64_t* n_runs, uint64_t n_rows, void* cuda_stream,
+                             int64_t* seg_ends, int64_t* ridx, uint64_t capacity, uint64_t* n_segments);
+
 /* ------------------------------------------------------------------ serving
  * A serving loop that keeps tables resident, admits queries by their device
  * memory footprint and batches the queries that arrive while others run

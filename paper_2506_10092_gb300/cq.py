@@ -99,6 +99,8 @@ _SIGS = {
     "cq_result_kernel_time_us": [_VP, C.POINTER(C.c_double)],
     "cq_result_destroy": [_VP],
     "cq_align_segments": [_VP, _VP, C.c_uint32, _VP, _VP, _VP, C.c_uint64, C.POINTER(C.c_uint64)],
+    "cq_align_segments_static": [C.c_uint32, _VP, _VP, _VP, C.c_uint64, _VP, _VP, _VP, C.c_uint64,
+                                 C.POINTER(C.c_uint64)],
     "cq_server_create": [_VP, C.POINTER(cq_server_options), C.POINTER(_VP)],
     "cq_server_submit": [_VP, _VP, C.POINTER(cq_plan), C.POINTER(C.c_uint64)],
     "cq_server_wait": [_VP, C.c_uint64, C.c_uint64, C.POINTER(_VP), C.POINTER(C.c_double)],
@@ -367,6 +369,21 @@ def cq_align_segments(ctx, cols: Sequence[Handle], seg_ends=None, ridx=None, cap
     n = C.c_uint64()
     rc = lib.cq_align_segments(ctx.ptr, C.addressof(arr), len(cols), _stream_ptr(stream),
                                _ptr(seg_ends), _ptr(ridx), capacity, C.byref(n))
+    if rc not in (CQ_OK, CQ_ERR_SIZE_MISMATCH) or (rc == CQ_ERR_SIZE_MISMATCH and capacity):
+        _check(rc)
+    return n.value
+
+
+def cq_align_segments_static(run_ends, n_rows: int, seg_ends=None, ridx=None, capacity: int = 0, stream=None):
+    """Allocation-free alignment over CUDA tensors of run ends (int32 / int64);
+    returns the segment count and fills seg_ends / ridx when given."""
+    k = len(run_ends)
+    ptrs = (C.c_void_p * k)(*[e.data_ptr() for e in run_ends])
+    is64 = (C.c_uint32 * k)(*[1 if str(e.dtype).endswith("int64") else 0 for e in run_ends])
+    nr = (C.c_uint64 * k)(*[int(e.numel()) for e in run_ends])
+    n = C.c_uint64()
+    rc = lib.cq_align_segments_static(k, C.addressof(ptrs), C.addressof(is64), C.addressof(nr), int(n_rows),
+                                      _stream_ptr(stream), _ptr(seg_ends), _ptr(ridx), capacity, C.byref(n))
     if rc not in (CQ_OK, CQ_ERR_SIZE_MISMATCH) or (rc == CQ_ERR_SIZE_MISMATCH and capacity):
         _check(rc)
     return n.value

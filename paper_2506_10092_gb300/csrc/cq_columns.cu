@@ -354,3 +354,38 @@ cudaError_t expand_column(const cq_column* c, long long* out, cudaStream_t s, in
 }
 
 }  // namespace cq
+
+namespace cq {
+
+// Launchers of the alignment kernels over raw device run-end arrays, for
+// callers that hold no column handles (the allocation-free entry point).
+cudaError_t align_launch_count_raw(const void* const* ends, const uint8_t* e64, const unsigned long long* n, uint32_t k,
+                                   unsigned long long n_rows, unsigned long long n_tiles, unsigned long long* counts,
+                                   cudaStream_t s) {
+  AlignCols A{};
+  A.k = (int)k;
+  for (uint32_t j = 0; j < k; ++j) {
+    A.ends[j] = ends[j];
+    A.e64[j] = e64[j];
+    A.n[j] = n[j];
+  }
+  align_count_kernel<<<(unsigned)n_tiles, kAlignThreads, 0, s>>>(A, n_rows, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t align_launch_write_raw(const void* const* ends, const uint8_t* e64, const unsigned long long* n, uint32_t k,
+                                   unsigned long long n_rows, unsigned long long n_tiles,
+                                   const unsigned long long* offsets, long long* seg_ends, long long* ridx,
+                                   unsigned long long capacity, cudaStream_t s) {
+  AlignCols A{};
+  A.k = (int)k;
+  for (uint32_t j = 0; j < k; ++j) {
+    A.ends[j] = ends[j];
+    A.e64[j] = e64[j];
+    A.n[j] = n[j];
+  }
+  align_write_kernel<<<(unsigned)n_tiles, kAlignThreads, 0, s>>>(A, n_rows, offsets, seg_ends, ridx, capacity);
+  return cudaGetLastError();
+}
+
+}  // namespace cq
