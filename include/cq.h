@@ -205,7 +205,9 @@ typedef struct {
   uint32_t stages;       /* bulk-copy pipeline depth (2..8); 0 = default */
   uint32_t table_slots;  /* shared-memory group-table slots per CTA (power of 2); 0 = default */
   uint32_t grid_ctas;    /* CTAs of the fused kernel; 0 = SMs x ctas_per_sm */
-  uint32_t reserved[2];
+  uint32_t items_per_cta;  /* batches: work items per CTA the tiles are cut into
+                              (load balance vs per-item overhead); 0 = default */
+  uint32_t reserved;
 } cq_exec_options;
 
 /* ------------------------------------------------------------------ queries */
@@ -224,12 +226,42 @@ int cq_query_run(cq_table* table, const cq_plan* plan, void* cuda_stream, cq_res
 int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_exec_options* opts,
                     void* cuda_stream, cq_result** out);
 
-/* Run n independent queries (tables[i], plans[i]) as ONE persistent fused
- * launch over a shared work list of (query, tile) items, replayed from a
- * cached CUDA graph when the same batch shape recurs.  results[i] receives
- * the handle of query i.  Same semantics per query as cq_query_run. */
+/* Run n independent queries (tables[i], plans[i], any tables of the same
+ * context, of any sizes) as ONE persistent fused launch.  No counterpart in
+ * the paper, which runs one query at a time; the per-query method is the
+ * one of cq_query_run.
+ *
+ * Each query's tiles are cut into work items of at most C tiles, C chosen so
+ * that the batch has about items_per_cta items per CTA; items are ordered
+ * larger first and a one-CTA-per-SM persistent kernel takes them from a
+ * global counter.  Every item adds its partial aggregates into its own
+ * query's accumulators, so results[i] equals cq_query_run's result for
+ * query i exactly (integer aggregates are order-independent).
+ *
+ * The launch (upload of descriptors and work list, init, persistent kernel,
+ * finalize) is a CUDA graph instantiated once per control-block capacity and
+ * replayed for every later batch that fits it; only the upload size changes.
+ * opts: mode must be CQ_EXEC_FUSED; tile_rows and items_per_cta select the
+ * shape (0 = the autotuned shape of cq_batch_tune for this kind of batch,
+ * else tile 4096 rows for all-RLE/index queries and 8192 otherwise, 4 items
+ * per CTA); ctas_per_sm, stages and grid_ctas are ignored.
+ * Asynchronous like cq_query_run; results[i] is owned by the caller (the
+ * device buffers of the batch are freed when its last result is destroyed).
+ * Errors (synchronous, no result is returned): those of cq_query_run for any
+ * query (the message names the query), CQ_ERR_INVALID_ARG for n == 0 or
+ * tables of different contexts. */
 int cq_batch_run(uint32_t n, cq_table* const* tables, const cq_plan* plans,
                  const cq_exec_options* opts, void* cuda_stream, cq_result** results);
+
+/* Autotuner for batches: run the batch once per candidate shape (tile rows
+ * 1024..8192 and mode default, 1 to 8 items per CTA), time each launch with
+ * CUDA events (best of two runs after a warm-up), and remember the fastest
+ * for batches of the same kind -- keyed by the number of queries and total
+ * rows (powers of two) and the share of all-RLE/index queries -- so that
+ * cq_batch_run with tile_rows == 0 uses it.  *best receives the chosen shape
+ * and *best_us its launch time.  Synchronous; no results are kept. */
+int cq_batch_tune(uint32_t n, cq_table* const* tables, const cq_plan* plans, void* cuda_stream,
+                  cq_exec_options* best, double* best_us);
 
 /* Wait up to timeout_us microseconds (UINT64_MAX = forever) for the query
  * to finish.  Returns CQ_OK, CQ_ERR_NOT_READY, or the query's own error

@@ -57,7 +57,7 @@ class cq_plan(C.Structure):
 class cq_exec_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile_rows", C.c_uint32), ("ctas_per_sm", C.c_uint32),
                 ("stages", C.c_uint32), ("table_slots", C.c_uint32), ("grid_ctas", C.c_uint32),
-                ("reserved", C.c_uint32 * 2)]
+                ("items_per_cta", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class cq_server_options(C.Structure):
@@ -88,6 +88,7 @@ _SIGS = {
     "cq_query_run": [_VP, C.POINTER(cq_plan), _VP, C.POINTER(_VP)],
     "cq_query_run_ex": [_VP, C.POINTER(cq_plan), C.POINTER(cq_exec_options), _VP, C.POINTER(_VP)],
     "cq_batch_run": [C.c_uint32, _VP, _VP, C.POINTER(cq_exec_options), _VP, _VP],
+    "cq_batch_tune": [C.c_uint32, _VP, _VP, _VP, C.POINTER(cq_exec_options), C.POINTER(C.c_double)],
     "cq_result_wait": [_VP, C.c_uint64],
     "cq_result_num_groups": [_VP, C.POINTER(C.c_uint64)],
     "cq_result_num_columns": [_VP, C.POINTER(C.c_uint32)],
@@ -291,11 +292,44 @@ class PlanStruct:
 
 
 def exec_options(mode=CQ_EXEC_FUSED, tile_rows=0, ctas_per_sm=0, stages=0, table_slots=0,
-                 grid_ctas=0) -> cq_exec_options:
+                 grid_ctas=0, items_per_cta=0) -> cq_exec_options:
     o = cq_exec_options()
     o.mode, o.tile_rows, o.ctas_per_sm, o.stages, o.table_slots = mode, tile_rows, ctas_per_sm, stages, table_slots
-    o.grid_ctas = grid_ctas
+    o.grid_ctas, o.items_per_cta = grid_ctas, items_per_cta
     return o
+
+
+class _Batch:
+    """The cq_table* / cq_plan arrays of one batch call."""
+
+    def __init__(self, tables, plans):
+        if len(tables) != len(plans):
+            raise ValueError("one plan per table")
+        self.plans = [p if isinstance(p, PlanStruct) else PlanStruct(p) for p in plans]
+        self.tables = list(tables)
+        self.n = len(self.tables)
+        self.tarr = (C.c_void_p * max(1, self.n))(*[t.ptr for t in self.tables])
+        self.parr = (cq_plan * max(1, self.n))(*[ps.s for ps in self.plans])
+
+
+def cq_batch_run(tables, plans, stream=None, opts: Optional[cq_exec_options] = None) -> list:
+    """Run query i = (tables[i], plans[i]) for every i as one persistent launch;
+    returns one result handle per query."""
+    b = _Batch(tables, plans)
+    out = (C.c_void_p * max(1, b.n))()
+    _check(lib.cq_batch_run(b.n, C.addressof(b.tarr), C.addressof(b.parr),
+                            C.byref(opts) if opts is not None else None, _stream_ptr(stream), C.addressof(out)))
+    return [Handle(out[i], lib.cq_result_destroy, [b.tables[i], b.plans[i]]) for i in range(b.n)]
+
+
+def cq_batch_tune(tables, plans, stream=None):
+    """Autotune the batch shape; returns (cq_exec_options, launch microseconds)."""
+    b = _Batch(tables, plans)
+    best = cq_exec_options()
+    us = C.c_double()
+    _check(lib.cq_batch_tune(b.n, C.addressof(b.tarr), C.addressof(b.parr), _stream_ptr(stream),
+                             C.byref(best), C.byref(us)))
+    return best, us.value
 
 
 def cq_query_run(table, plan, stream=None, opts: Optional[cq_exec_options] = None) -> Handle:

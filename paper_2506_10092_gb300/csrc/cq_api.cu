@@ -30,13 +30,6 @@ int set_error(int status, const char* fmt, ...) {
 
 void clear_error() { g_err.clear(); }
 
-#define CQ_CUDA(call)                                                                           \
-  do {                                                                                          \
-    cudaError_t _e = (call);                                                                    \
-    if (_e != cudaSuccess)                                                                      \
-      return set_error(CQ_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(_e));            \
-  } while (0)
-
 // kernels (cq_columns.cu / cq_query.cu)
 cudaError_t run_column_check(const cq_column* c, void* d_out, cudaStream_t s);
 cudaError_t align_segments(cq_column* const* cols, uint32_t k, cudaStream_t s, void* scratch_counts,
@@ -174,7 +167,9 @@ extern "C" int cq_ctx_create(int device, void* cuda_stream, cq_ctx** out) {
 extern "C" int cq_ctx_destroy(cq_ctx* ctx) {
   clear_error();
   if (!ctx) return CQ_OK;
+  cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  if (!ctx->graphs.empty()) cudaDeviceSynchronize();   // batch graphs may still be running
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
   return CQ_OK;
@@ -458,15 +453,6 @@ static PlanCol view_of(const cq_column* c) {
   p.src = c;
   return p;
 }
-
-struct Planned {
-  QueryDesc q;
-  std::vector<uint32_t> aux;
-  std::vector<uint32_t> out_kind;
-  std::vector<int> out_key_col;
-  int ctas_per_sm = 1;
-  uint32_t grid_ctas = 0;
-};
 
 static bool is_dict(const PlanCol& c) { return c.src && c.src->enc == ENC_DICT; }
 
@@ -953,7 +939,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
 // Options pin the tile size (smaller ones are tried when it does not fit)
 // and / or the CTAs per SM.
 static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
-                      const cq_exec_options* opts, const cq_ctx* ctx, Planned* P) {
+                      const cq_exec_options* opts, const cq_ctx* ctx, Planned* P, size_t batch_limit = 0) {
   if (!plan) return set_error(CQ_ERR_INVALID_ARG, "plan is NULL");
   const uint32_t want_tile = opts ? opts->tile_rows : 0;
   const uint32_t want_ctas = opts ? opts->ctas_per_sm : 0;
@@ -978,7 +964,11 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
     for (uint32_t t = want_tile ? want_tile : first; t >= 1024; t /= 2)
       if (t <= max_tile) shapes.push_back({ncw, t, limit});
   };
-  if (seg) {
+  if (batch_limit) {
+    // a batch shares one kernel shape: 16 compute warps (+ the helper warp in
+    // row mode), one CTA per SM, shared memory within the batch kernel's limit
+    add(16, seg ? 4096u : 8192u, batch_limit);
+  } else if (seg) {
     add(16, 4096, ctx->smem_optin);
   } else if (want_ctas == 2) {
     add(8, 4096, ctx->smem_two);
@@ -994,37 +984,64 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   return rc;
 }
 
+// Byte offsets of one query's device buffers inside one allocation.
+QueryBlock query_block_layout(const Planned& P, bool with_aux) {
+  const QueryDesc& q = P.q;
+  const uint64_t G = q.n_groups;
+  const uint64_t nb = (G + 1023) / 1024;
+  auto al = [](uint64_t x) { return (x + 255) / 256 * 256; };
+  QueryBlock L;
+  L.gacc = 0;
+  L.out = L.gacc + al(8ull * q.n_gw * G);
+  L.aux = L.out + al(8ull * q.n_out * G);
+  L.err = L.aux + (with_aux ? al(4ull * (P.aux.size() + 2)) : 0);
+  L.cnt = L.err + 256;
+  L.blk = L.cnt + 256;
+  L.total = L.blk + al(4ull * (nb + 1));
+  return L;
+}
+
+// Point the descriptor at the buffers of a block laid out by
+// query_block_layout (aux tables at `aux_dev`).
+void bind_query_block(Planned& P, uint8_t* b, const QueryBlock& L, const uint32_t* aux_dev) {
+  QueryDesc& q = P.q;
+  const uint64_t G = q.n_groups;
+  q.gacc = reinterpret_cast<unsigned long long*>(b + L.gacc);
+  for (uint32_t i = 0; i < q.n_out; ++i) q.out[i] = b + L.out + (uint64_t)i * 8 * G;
+  q.aux = aux_dev;
+  q.aux_words = (uint32_t)P.aux.size();
+  q.err = reinterpret_cast<int*>(b + L.err);
+  q.err_info = reinterpret_cast<unsigned long long*>(b + L.err + 8);
+  q.out_count = reinterpret_cast<unsigned long long*>(b + L.cnt);
+  q.block_counts = reinterpret_cast<unsigned int*>(b + L.blk);
+}
+
+// Record in the result where its status, count and output columns live.
+void attach_outputs(cq_result* r, const Planned& P) {
+  r->desc = P.q;
+  r->err_dev = P.q.err;
+  r->count_dev = P.q.out_count;
+  r->n_out = P.q.n_out;
+  r->out_kind = P.out_kind;
+  r->out_key_col = P.out_key_col;
+  r->out_dev.assign(P.q.out, P.q.out + P.q.n_out);
+}
+
 // Carve one pool allocation into the query's device buffers and enqueue
 // init -> fused kernel -> finalize on `s`.
 static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r) {
   QueryDesc& q = P.q;
-  const uint64_t G = q.n_groups;
-  const uint64_t nb = (G + 1023) / 1024;
-  auto al = [](uint64_t x) { return (x + 255) / 256 * 256; };
-  const uint64_t off_gacc = 0;
-  const uint64_t off_out = off_gacc + al(8ull * q.n_gw * G);
-  const uint64_t off_aux = off_out + al(8ull * q.n_out * G) * 1;
-  const uint64_t off_err = off_aux + al(4ull * (P.aux.size() + 2));
-  const uint64_t off_cnt = off_err + 256;
-  const uint64_t off_blk = off_cnt + 256;
-  const uint64_t total = off_blk + al(4ull * (nb + 1));
+  const QueryBlock L = query_block_layout(P, true);
   void* base = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync(&base, total, ctx->pool, s);
-  if (e != cudaSuccess) return set_error(CQ_ERR_OOM, "device pool allocation of %llu bytes failed: %s", (unsigned long long)total, cudaGetErrorString(e));
+  cudaError_t e = cudaMallocFromPoolAsync(&base, L.total, ctx->pool, s);
+  if (e != cudaSuccess) return set_error(CQ_ERR_OOM, "device pool allocation of %llu bytes failed: %s", (unsigned long long)L.total, cudaGetErrorString(e));
   r->dev_block = base;
-  r->dev_bytes = total;
+  r->dev_bytes = L.total;
   uint8_t* b = reinterpret_cast<uint8_t*>(base);
-  q.gacc = reinterpret_cast<unsigned long long*>(b + off_gacc);
-  for (uint32_t i = 0; i < q.n_out; ++i) q.out[i] = b + off_out + (uint64_t)i * 8 * G;
-  q.aux = reinterpret_cast<const uint32_t*>(b + off_aux);
-  q.aux_words = (uint32_t)P.aux.size();
-  q.err = reinterpret_cast<int*>(b + off_err);
-  q.err_info = reinterpret_cast<unsigned long long*>(b + off_err + 8);
-  q.out_count = reinterpret_cast<unsigned long long*>(b + off_cnt);
-  q.block_counts = reinterpret_cast<unsigned int*>(b + off_blk);
+  bind_query_block(P, b, L, reinterpret_cast<const uint32_t*>(b + L.aux));
   if (!P.aux.empty()) {
     // the descriptor's aux words travel through the stream like the launch itself
-    e = cudaMemcpyAsync(b + off_aux, P.aux.data(), 4 * P.aux.size(), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(b + L.aux, P.aux.data(), 4 * P.aux.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "aux upload failed: %s", cudaGetErrorString(e));
   }
   e = launch_init_global(q, s);
@@ -1033,36 +1050,49 @@ static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r)
   if (e == cudaSuccess) e = cudaEventRecord(r->ev_k1, s);
   if (e == cudaSuccess) e = launch_finalize(q, s);
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
-  r->desc = q;
-  r->err_dev = q.err;
-  r->count_dev = q.out_count;
-  r->n_out = q.n_out;
-  r->out_kind = P.out_kind;
-  r->out_key_col = P.out_key_col;
-  r->out_dev.assign(q.out, q.out + q.n_out);
+  attach_outputs(r, P);
   return CQ_OK;
 }
 
-static cq_result* new_result(cq_ctx* ctx, cudaStream_t s) {
+cq_result* new_result(cq_ctx* ctx, cudaStream_t s, bool own_events) {
   cq_result* r = new cq_result;
   r->ctx = ctx;
   r->stream = s;
-  cudaEventCreate(&r->ev_start);
-  cudaEventCreate(&r->ev_done);
-  cudaEventCreate(&r->ev_k0);
-  cudaEventCreate(&r->ev_k1);
+  r->own_events = own_events;
+  if (own_events) {
+    cudaEventCreate(&r->ev_start);
+    cudaEventCreate(&r->ev_done);
+    cudaEventCreate(&r->ev_k0);
+    cudaEventCreate(&r->ev_k1);
+  }
   return r;
 }
 
-static void free_result(cq_result* r) {
+void free_result(cq_result* r) {
   if (!r) return;
   if (r->dev_block) cudaFreeAsync(r->dev_block, r->stream);
   for (void* p : r->extra_dev) cudaFreeAsync(p, r->stream);
-  if (r->ev_start) cudaEventDestroy(r->ev_start);
-  if (r->ev_done) cudaEventDestroy(r->ev_done);
-  if (r->ev_k0) cudaEventDestroy(r->ev_k0);
-  if (r->ev_k1) cudaEventDestroy(r->ev_k1);
+  if (r->own_events) {
+    if (r->ev_start) cudaEventDestroy(r->ev_start);
+    if (r->ev_done) cudaEventDestroy(r->ev_done);
+    if (r->ev_k0) cudaEventDestroy(r->ev_k0);
+    if (r->ev_k1) cudaEventDestroy(r->ev_k1);
+  }
   delete r;
+}
+
+// Plan one query of a batch (see plan_query): the shared kernel shape, tiles
+// of `tile_rows` rows (0 = the mode's default), shared memory within
+// `smem_limit` bytes.
+int plan_batch_query(cq_table* table, const cq_plan* plan, uint32_t tile_rows, size_t smem_limit, Planned* P) {
+  if (!table) return set_error(CQ_ERR_INVALID_ARG, "NULL table");
+  std::vector<PlanCol> cols;
+  cols.reserve(table->cols.size());
+  for (cq_column* c : table->cols) cols.push_back(view_of(c));
+  cq_exec_options o;
+  memset(&o, 0, sizeof(o));
+  o.tile_rows = tile_rows;
+  return plan_query(cols, table->n_rows, plan, &o, table->ctx, P, smem_limit);
 }
 
 }  // namespace cq
@@ -1081,7 +1111,7 @@ extern "C" int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_ex
     return set_error(CQ_ERR_INVALID_ARG, "unknown execution mode %d", mode);
   std::vector<PlanCol> cols;
   for (cq_column* c : table->cols) cols.push_back(view_of(c));
-  cq_result* r = new_result(ctx, s);
+  cq_result* r = new_result(ctx, s, true);
   cudaEventRecord(r->ev_start, s);
   if (mode == CQ_EXEC_DECOMPRESS_THEN_SCAN) {
     // expand every referenced column to a flat int64 array first

@@ -1,0 +1,86 @@
+// cq_batch.cu -- persistent kernel of a query batch.
+//
+// Many queries, over tables (or partitions) of very different sizes, run in
+// one launch.  The host cuts every query's tiles into work items (query, tile
+// range), orders them larger first, and uploads them with the queries'
+// descriptors.  Each CTA of a one-CTA-per-SM grid repeatedly takes the next
+// item from a global counter, copies that query's descriptor into shared
+// memory, lays out the dynamic shared memory for it, and walks the item's
+// tiles with the one-query steps: segment mode (cq_seg.cuh) or row mode with
+// its helper warp (cq_rowpath.cuh).  Each item flushes its group table into
+// the query's own global accumulators, so items of one query may run on any
+// CTAs in any order.  The batch kernel's block is the row-mode shape, 16
+// compute warps plus the helper warp; in segment mode the helper warp only
+// joins the block barriers.
+#include <cuda_runtime.h>
+
+#include "cq_rowpath.cuh"
+#include "cq_seg.cuh"
+
+namespace cq {
+
+constexpr int kBatchThreads = (kWarps + 1) * 32;
+static_assert(sizeof(QueryDesc) % 8 == 0, "descriptor is copied in 8-byte words");
+
+__global__ void __launch_bounds__(kBatchThreads, 1) batch_query_kernel(BatchCtl* ctl) {
+  __shared__ __align__(16) QueryDesc qs;
+  __shared__ unsigned long long item_id;
+  const uint32_t n_items = ctl->n_items;
+  for (;;) {
+    // the previous item is finished with every shared-memory word; its
+    // generic accesses are ordered before the next item's bulk copies
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) item_id = atomicAdd(&ctl->next_item, 1ull);
+    __syncthreads();
+    const unsigned long long it = item_id;
+    if (it >= n_items) break;
+    const BatchItem item = ctl->items[it];
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(ctl->descs + item.query);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&qs);
+    for (uint32_t i = threadIdx.x; i < sizeof(QueryDesc) / 8; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    const Smem sm = carve(qs);
+    const unsigned long long t0 = item.t_begin, t1 = item.t_begin + item.n_tiles;
+    const uint32_t gpw = qs.tile_rows / (kWarps * 32);
+    if (qs.seg_mode) {
+      switch (gpw) {
+        case 2: seg_range<2>(qs, sm, t0, t1); break;
+        case 4: seg_range<4>(qs, sm, t0, t1); break;
+        case 8: seg_range<8>(qs, sm, t0, t1); break;
+        default: seg_range<16>(qs, sm, t0, t1); break;
+      }
+    } else {
+      switch (gpw) {
+        case 2: row_range<kWarps, 2>(qs, sm, t0, t1); break;
+        case 4: row_range<kWarps, 4>(qs, sm, t0, t1); break;
+        case 8: row_range<kWarps, 8>(qs, sm, t0, t1); break;
+        default: row_range<kWarps, 16>(qs, sm, t0, t1); break;
+      }
+    }
+  }
+}
+
+cudaError_t batch_kernel_static_smem(size_t* bytes) {
+  cudaFuncAttributes a;
+  const cudaError_t e = cudaFuncGetAttributes(&a, batch_query_kernel);
+  if (e == cudaSuccess) *bytes = a.sharedSizeBytes;
+  return e;
+}
+
+cudaError_t batch_kernel_set_smem(size_t bytes) {
+  return cudaFuncSetAttribute(batch_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_batch_init(const BatchCtl* ctl, cudaStream_t s, unsigned grid);       // cq_query.cu
+cudaError_t launch_batch_finalize(const BatchCtl* ctl, cudaStream_t s, unsigned grid);   // cq_query.cu
+
+cudaError_t launch_batch(BatchCtl* ctl_dev, cudaStream_t s, unsigned grid, size_t dyn_smem, unsigned aux_grid) {
+  cudaError_t e = launch_batch_init(ctl_dev, s, aux_grid);
+  if (e != cudaSuccess) return e;
+  batch_query_kernel<<<grid, kBatchThreads, dyn_smem, s>>>(ctl_dev);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_batch_finalize(ctl_dev, s, aux_grid);
+}
+
+}  // namespace cq

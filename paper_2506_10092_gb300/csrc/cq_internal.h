@@ -145,11 +145,58 @@ struct QueryDesc {
   unsigned int* block_counts;      // finalize scratch
 };
 
+// ---------------------------------------------------------------- batches
+// One unit of a batch's work list: tiles [t_begin, t_begin + n_tiles) of query
+// `query`.  A persistent kernel's CTAs take items in list order.
+struct BatchItem {
+  uint32_t query;
+  uint32_t n_tiles;
+  uint64_t t_begin;
+};
+
+// Header of a batch's control block (device memory, uploaded per launch):
+// counts, the work counter and the arrays that follow the header.
+struct BatchCtl {
+  uint32_t n_queries;
+  uint32_t n_items;
+  uint32_t n_init_blocks;              // init blocks of all queries (kInitGroups groups each)
+  uint32_t n_fin_blocks;               // finalize blocks of all queries (1024 groups each)
+  unsigned long long next_item;        // work counter, 0 at upload
+  const QueryDesc* descs;              // [n_queries]
+  const BatchItem* items;              // [n_items], larger items first
+  const uint32_t* init_first;          // [n_queries + 1] first init block of each query
+  const uint32_t* fin_first;           // [n_queries + 1] first finalize block of each query
+};
+
+constexpr uint32_t kInitGroups = 1024;  // groups initialised per batch init block
+
 // ---------------------------------------------------------------- host objects
 struct ColumnStats {
   int64_t min_raw = 0, max_raw = -1;     // raw value range (empty when max < min)
   int64_t min_val = 0, max_val = -1;     // logical value range
   uint64_t max_abs_val = 0;              // max |logical value| (saturating)
+};
+
+// A planned query: descriptor, aux tables and output description.
+struct Planned {
+  QueryDesc q;
+  std::vector<uint32_t> aux;
+  std::vector<uint32_t> out_kind;
+  std::vector<int> out_key_col;
+  int ctas_per_sm = 1;
+  uint32_t grid_ctas = 0;
+};
+
+// Byte offsets of one query's device buffers inside one allocation.
+struct QueryBlock {
+  uint64_t gacc, out, aux, err, cnt, blk, total;
+};
+
+struct BatchGraph;   // cq_serve.cu
+struct TunedShape {  // autotuner choice for a batch signature
+  uint64_t key;
+  uint32_t tile_rows;
+  uint32_t items_per_cta;
 };
 
 }  // namespace cq
@@ -162,7 +209,12 @@ struct cq_ctx {
   size_t smem_optin = 0;     // max dynamic shared memory of one CTA
   size_t smem_two = 0;       // max dynamic shared memory per CTA with two CTAs per SM
   std::mutex mu;
-  // pinned staging for small host <-> device transfers
+  // batches: cached launch graphs and autotuned shapes
+  std::mutex batch_mu;
+  std::vector<cq::BatchGraph*> graphs;   // owned; freed by the destructor (cq_serve.cu)
+  std::vector<cq::TunedShape> tuned;
+  size_t batch_smem = 0;     // dynamic shared memory of the batch kernel
+  ~cq_ctx();
 };
 
 struct cq_column {
@@ -212,7 +264,8 @@ struct cq_result {
   std::vector<void*> out_dev;
   std::vector<void*> extra_dev;     // further pool allocations (flat columns of the comparison path)
   std::vector<cq_column*> held_cols; // columns referenced until the result is destroyed
-  std::shared_ptr<void> batch_keepalive;  // batch launches: shared device block
+  std::shared_ptr<void> batch_keepalive;  // batch launches: shared device block and events
+  bool own_events = true;          // false: the events belong to the batch
 };
 
 namespace cq {
@@ -221,11 +274,32 @@ namespace cq {
 int set_error(int status, const char* fmt, ...);
 void clear_error();
 
+#define CQ_CUDA(call)                                                                           \
+  do {                                                                                          \
+    cudaError_t _e = (call);                                                                    \
+    if (_e != cudaSuccess)                                                                      \
+      return set_error(CQ_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(_e));            \
+  } while (0)
+
 // kernels / launchers (cq_query.cu)
 cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ctas_per_sm, uint32_t grid_ctas);
 cudaError_t launch_init_global(const QueryDesc& q, cudaStream_t s);
 cudaError_t launch_finalize(const QueryDesc& q, cudaStream_t s);
 size_t query_kernel_smem(const QueryDesc& q);
 cudaError_t query_kernel_set_smem(size_t bytes);
+
+// batches (cq_batch.cu): the persistent kernel's static shared memory, its
+// dynamic-size attribute, and the launch of init -> items -> finalize
+cudaError_t batch_kernel_static_smem(size_t* bytes);
+cudaError_t batch_kernel_set_smem(size_t bytes);
+cudaError_t launch_batch(BatchCtl* ctl_dev, cudaStream_t s, unsigned grid, size_t dyn_smem, unsigned aux_grid);
+
+// planner / results (cq_api.cu)
+int plan_batch_query(cq_table* table, const cq_plan* plan, uint32_t tile_rows, size_t smem_limit, Planned* P);
+QueryBlock query_block_layout(const Planned& P, bool with_aux);
+void bind_query_block(Planned& P, uint8_t* base, const QueryBlock& L, const uint32_t* aux_dev);
+void attach_outputs(cq_result* r, const Planned& P);
+cq_result* new_result(cq_ctx* ctx, cudaStream_t s, bool own_events);
+void free_result(cq_result* r);
 
 }  // namespace cq

@@ -17,253 +17,57 @@
 #include <climits>
 #include <cstdio>
 
-#include "cq_phases.cuh"
+#include "cq_seg.cuh"
 
 namespace cq {
 
 size_t query_kernel_smem(const QueryDesc& q) { return smem_layout(q).total; }
 
-// ------------------------------------------------------------------ tile alignment
-// Build the per-tile bitmaps of every RLE / index column for rows [s, e) and
-// their word prefix popcounts.  RLE: bit o set when a run ends at row s + o
-// (exclusive end), i.e. row s + o starts a new run.  Index: bit o set when
-// row s + o is listed.  Column j's cursor must hold the first run with end
-// > s (RLE) / the first position >= s (index).
-__device__ void build_bitmaps(const QueryDesc& q, const Smem& sm, unsigned long long s, unsigned long long e,
-                              uint32_t nwords) {
-  const int nb = q.n_bitmaps;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (uint32_t i = threadIdx.x; i < nwords * nb; i += blockDim.x) sm.bm[i] = 0;
-  __syncthreads();
-  if (nb > 0) {
-    // warps are dealt to columns round-robin; warp w serves column w % nb
-    const int j = warp % nb;
-    const int gi = warp / nb;
-    const int G = (kWarps - j + nb - 1) / nb;
-    const ColDesc* cd = nullptr;
-    for (int c = 0; c < q.n_cols; ++c)
-      if (q.cols[c].bslot == j) cd = &q.cols[c];
-    const bool is_rle = cd->enc == ENC_RLE;
-    const unsigned long long cur = sm.tcur[j];
-    uint32_t* B = sm.bm + j * nwords;
-    for (int it = 0;; ++it) {
-      const int col_done = __shfl_sync(0xFFFFFFFFu, sm.flags[j], 0);
-      if (!col_done) {
-        const unsigned long long idx = cur + ((unsigned long long)it * G + gi) * 32 + lane;
-        bool stop = false;
-        if (idx < cd->n) {
-          const long long x = ldg_val(cd->ends, idx, cd->e64);
-          if ((unsigned long long)x < e) {
-            // a boundary before the tile would mean a corrupt cursor: flag it, never write
-            if ((unsigned long long)x < s || (is_rle && (unsigned long long)x == s)) {
-              report(q, CQ_ERR_INVALID_ARG, 2ull + ((unsigned long long)j << 8), s, (unsigned long long)x);
-            } else {
-              const uint32_t o = (uint32_t)((unsigned long long)x - s);
-              atomicOr(&B[o >> 5], 1u << (o & 31));
-            }
-          } else {
-            stop = true;
-            if (is_rle && (unsigned long long)x == e) sm.flags[kMaxBitmapCols + j] = 1;
-          }
-        } else {
-          stop = true;
-        }
-        if (__any_sync(0xFFFFFFFFu, stop) && lane == 0) sm.flags[j] = 1;
-      }
-      __syncthreads();
-      bool all = true;
-      for (int c = 0; c < nb; ++c) all = all && sm.flags[c];
-      __syncthreads();
-      if (all) break;
-    }
-    // word prefix popcounts, one warp per column
-    for (int c = warp; c < nb; c += kWarps) {
-      const uint32_t* Bc = sm.bm + c * nwords;
-      uint32_t* Pc = sm.pre + c * (nwords + 1);
-      const uint32_t per = (nwords + 31) / 32;
-      uint32_t local = 0;
-      for (uint32_t k = 0; k < per; ++k) {
-        const uint32_t w = lane * per + k;
-        if (w < nwords) local += __popc(Bc[w]);
-      }
-      uint32_t incl = local;
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= d) incl += y;
-      }
-      uint32_t run = incl - local;
-      for (uint32_t k = 0; k < per; ++k) {
-        const uint32_t w = lane * per + k;
-        if (w < nwords) {
-          Pc[w] = run;
-          run += __popc(Bc[w]);
-        }
-      }
-      if (lane == 31) Pc[nwords] = incl;
-    }
-  }
-  __syncthreads();
-}
-
-// Segment mode: union of all bitmaps -> segment start list in sm.seg.
-// Index columns split the tile before and after every listed row.
-__device__ void build_segments(const QueryDesc& q, const Smem& sm, uint32_t nwords, uint32_t rows) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) {
-    uint32_t u = 0;
-    for (int c = 0; c < q.n_cols; ++c) {
-      const ColDesc& cd = q.cols[c];
-      if (cd.bslot == 0xFF) continue;
-      const uint32_t* B = sm.bm + cd.bslot * nwords;
-      if (cd.enc == ENC_RLE) {
-        u |= B[w];
-      } else {
-        const uint32_t prev = w ? B[w - 1] : 0u;
-        u |= B[w] | (B[w] << 1) | (prev >> 31);
-      }
-    }
-    if (w == 0) u &= ~1u;   // row 0 always starts a segment
-    if (w == (rows >> 5) && (rows & 31)) u &= (1u << (rows & 31)) - 1u;
-    if (w > (rows >> 5) || (w == (rows >> 5) && !(rows & 31))) u = 0;
-    sm.ubm[w] = u;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t per = (nwords + 31) / 32;
-    uint32_t local = 0;
-    for (uint32_t k = 0; k < per; ++k) {
-      const uint32_t w = lane * per + k;
-      if (w < nwords) local += __popc(sm.ubm[w]);
-    }
-    uint32_t incl = local;
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-      if (lane >= d) incl += y;
-    }
-    uint32_t run = incl - local;
-    for (uint32_t k = 0; k < per; ++k) {
-      const uint32_t w = lane * per + k;
-      if (w < nwords) {
-        sm.upre[w] = run;
-        run += __popc(sm.ubm[w]);
-      }
-    }
-    if (lane == 31) {
-      sm.misc[2] = (int)(incl + 1);
-      sm.seg[0] = 0;
-      sm.seg[incl + 1] = (uint16_t)rows;
-    }
-  }
-  __syncthreads();
-  for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) {
-    uint32_t u = sm.ubm[w];
-    uint32_t k = 1 + sm.upre[w];
-    while (u) {
-      const int b = __ffs(u) - 1;
-      sm.seg[k++] = (uint16_t)(w * 32 + b);
-      u &= u - 1;
-    }
-  }
-  __syncthreads();
-}
-
 // ------------------------------------------------------------------ segment-mode kernel
-// GPW: groups of 32 segments per warp per tile (tile_rows / kThreads).
+// GPW: groups of 32 segments per warp per tile (tile_rows / kThreads).  Each
+// CTA walks one contiguous range of tiles.
 template <int GPW>
 __global__ void __launch_bounds__(kThreads, 1) seg_query_kernel(const __grid_constant__ QueryDesc q) {
-  const Smem sm = carve(q);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t T = q.tile_rows;
-  const uint32_t nwords = T / 32;
   const unsigned long long t_begin = (unsigned long long)blockIdx.x * q.n_tiles / gridDim.x;
   const unsigned long long t_end = (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;
   if (t_begin >= t_end) return;
+  seg_range<GPW>(q, carve(q), t_begin, t_end);
+}
 
-  for (uint32_t sl = threadIdx.x; sl < q.table_slots; sl += blockDim.x) reset_slot(q, sm, sl);
-  if (threadIdx.x < 8) sm.misc[threadIdx.x] = 0;
-  if (threadIdx.x < 2 * kMaxBitmapCols) sm.flags[threadIdx.x] = 0;
-  const bool aux_smem = q.aux_words <= kAuxSmemWords;
-  if (aux_smem)
-    for (uint32_t i = threadIdx.x; i < q.aux_words; i += blockDim.x) sm.aux[i] = __ldg(q.aux + i);
-  if (warp < q.n_bitmaps) {
-    const ColDesc* cd = nullptr;
-    for (int c = 0; c < q.n_cols; ++c)
-      if (q.cols[c].bslot == warp) cd = &q.cols[c];
-    const long long s0 = (long long)(t_begin * T);
-    const unsigned long long cur = warp_count_below(cd->ends, cd->e64, cd->n, s0, cd->enc == ENC_INDEX);
-    if (lane == 0) sm.tcur[warp] = cur;
-  }
-  __syncthreads();
-
-  TileView tv;
-  tv.bm = sm.bm;
-  tv.pre = sm.pre;
-  tv.cur = sm.tcur;
-  tv.stage = nullptr;
-  tv.aux = aux_smem ? sm.aux : q.aux;
-  tv.nwords = nwords;
-  uint32_t rows_since_flush = 0;
-  uint16_t* mylist = sm.clist + warp * (GPW * 32);
-  const uint32_t wbase = warp * (GPW * 32);
-
-  for (unsigned long long t = t_begin; t < t_end; ++t) {
-    const unsigned long long s = t * T;
-    const unsigned long long e = (s + T < q.n_rows) ? s + T : q.n_rows;
-    const uint32_t rows = (uint32_t)(e - s);
-    build_bitmaps(q, sm, s, e, nwords);
-    build_segments(q, sm, nwords, rows);
-    const uint32_t pm = phase_filter<true, GPW>(q, tv, sm.seg, wbase, (uint32_t)sm.misc[2]);
-    const uint32_t n_pass = compact<GPW>(pm, wbase, mylist);
-    phase_aggregate<true, 2>(q, sm, tv, sm.seg, mylist, n_pass, s);
-    __syncthreads();
-    if (threadIdx.x < q.n_bitmaps) {
-      const int j = threadIdx.x;
-      const uint32_t* P = sm.pre + j * (nwords + 1);
-      sm.tcur[j] += P[nwords] + (unsigned long long)sm.flags[kMaxBitmapCols + j];
-      sm.flags[j] = 0;
-      sm.flags[kMaxBitmapCols + j] = 0;
-    }
-    rows_since_flush += rows;
-    const bool need = (t + 1 == t_end) || (!q.table_dense && sm.misc[0] * 2 > (int)q.table_slots) ||
-                      rows_since_flush + T > q.flush_rows;
-    if (need) {
-      flush_table(q, sm);
-      __syncthreads();
-      if (threadIdx.x == 0) sm.misc[0] = 0;
-      rows_since_flush = 0;
+// ------------------------------------------------------------------ init / finalize
+// Identity values of group i's global accumulators.
+__device__ __forceinline__ void init_group(const QueryDesc& q, size_t i) {
+  const size_t G = q.n_groups;
+  q.gacc[i] = 0;
+  for (int ai = 0; ai < q.n_aggs; ++ai) {
+    const AggDesc& a = q.aggs[ai];
+    switch (a.kind) {
+      case AK_SUM:
+      case AK_ISUM:
+        q.gacc[(size_t)a.gw * G + i] = 0;
+        q.gacc[(size_t)(a.gw + 1) * G + i] = 0;
+        q.gacc[(size_t)(a.gw + 2) * G + i] = 0;
+        break;
+      case AK_MIN:
+      case AK_IMIN:
+        q.gacc[(size_t)a.gw * G + i] = (unsigned long long)LLONG_MAX;
+        if (a.kind == AK_IMIN) q.gacc[(size_t)(a.gw + 1) * G + i] = 0;
+        break;
+      case AK_MAX:
+      case AK_IMAX:
+        q.gacc[(size_t)a.gw * G + i] = (unsigned long long)LLONG_MIN;
+        if (a.kind == AK_IMAX) q.gacc[(size_t)(a.gw + 1) * G + i] = 0;
+        break;
+      default:
+        break;
     }
   }
 }
 
-// ------------------------------------------------------------------ init / finalize
 __global__ void init_global_kernel(const __grid_constant__ QueryDesc q) {
   const size_t G = q.n_groups;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < G; i += (size_t)gridDim.x * blockDim.x) {
-    q.gacc[i] = 0;
-    for (int ai = 0; ai < q.n_aggs; ++ai) {
-      const AggDesc& a = q.aggs[ai];
-      switch (a.kind) {
-        case AK_SUM:
-        case AK_ISUM:
-          q.gacc[(size_t)a.gw * G + i] = 0;
-          q.gacc[(size_t)(a.gw + 1) * G + i] = 0;
-          q.gacc[(size_t)(a.gw + 2) * G + i] = 0;
-          break;
-        case AK_MIN:
-        case AK_IMIN:
-          q.gacc[(size_t)a.gw * G + i] = (unsigned long long)LLONG_MAX;
-          if (a.kind == AK_IMIN) q.gacc[(size_t)(a.gw + 1) * G + i] = 0;
-          break;
-        case AK_MAX:
-        case AK_IMAX:
-          q.gacc[(size_t)a.gw * G + i] = (unsigned long long)LLONG_MIN;
-          if (a.kind == AK_IMAX) q.gacc[(size_t)(a.gw + 1) * G + i] = 0;
-          break;
-        default:
-          break;
-      }
-    }
-  }
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < G; i += (size_t)gridDim.x * blockDim.x)
+    init_group(q, i);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *q.err = 0;
     *q.out_count = 0;
@@ -276,14 +80,19 @@ __device__ __forceinline__ bool group_present(const QueryDesc& q, size_t g) {
   return q.gacc[g] != 0 || (q.n_keys == 0 && g == 0);
 }
 
-__global__ void finalize_count_kernel(const __grid_constant__ QueryDesc q) {
-  const size_t g = blockIdx.x * (size_t)kFinBlock + threadIdx.x;
+// Finalize runs in three steps over blocks of kFinBlock dense groups: count
+// the present groups of each block, scan the block counts, then write each
+// present group's key and aggregates to its compacted result row.
+__device__ __forceinline__ void fin_count_block(const QueryDesc& q, unsigned blk) {
+  const size_t g = blk * (size_t)kFinBlock + threadIdx.x;
   const bool p = g < q.n_groups && group_present(q, g);
   const int c = __syncthreads_count(p);
-  if (threadIdx.x == 0) q.block_counts[blockIdx.x] = (unsigned)c;
+  if (threadIdx.x == 0) q.block_counts[blk] = (unsigned)c;
 }
 
-__global__ void finalize_scan_kernel(const __grid_constant__ QueryDesc q, unsigned n_blocks) {
+__global__ void finalize_count_kernel(const __grid_constant__ QueryDesc q) { fin_count_block(q, blockIdx.x); }
+
+__device__ __forceinline__ void fin_scan(const QueryDesc& q, unsigned n_blocks) {
   __shared__ unsigned warp_tot[32];
   __shared__ unsigned long long carry;
   if (threadIdx.x == 0) carry = 0;
@@ -318,6 +127,8 @@ __global__ void finalize_scan_kernel(const __grid_constant__ QueryDesc q, unsign
   if (threadIdx.x == 0) *q.out_count = carry;
 }
 
+__global__ void finalize_scan_kernel(const __grid_constant__ QueryDesc q, unsigned n_blocks) { fin_scan(q, n_blocks); }
+
 __device__ __forceinline__ I128 read_sum(const QueryDesc& q, uint32_t gw, size_t g) {
   const size_t G = q.n_groups;
   const unsigned long long w0 = q.gacc[(size_t)gw * G + g];
@@ -339,9 +150,9 @@ __device__ __forceinline__ I128 add128(I128 a, I128 b) {
   return r;
 }
 
-__global__ void finalize_write_kernel(const __grid_constant__ QueryDesc q) {
+__device__ __forceinline__ void fin_write_block(const QueryDesc& q, unsigned blk) {
   __shared__ unsigned warp_cnt[kFinBlock / 32];
-  const size_t g = blockIdx.x * (size_t)kFinBlock + threadIdx.x;
+  const size_t g = blk * (size_t)kFinBlock + threadIdx.x;
   const bool p = g < q.n_groups && group_present(q, g);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned bal = __ballot_sync(0xFFFFFFFFu, p);
@@ -358,7 +169,7 @@ __global__ void finalize_write_kernel(const __grid_constant__ QueryDesc q) {
   }
   __syncthreads();
   if (!p) return;
-  const size_t row = q.block_counts[blockIdx.x] + warp_cnt[warp] + __popc(bal & ((1u << lane) - 1u));
+  const size_t row = q.block_counts[blk] + warp_cnt[warp] + __popc(bal & ((1u << lane) - 1u));
   const unsigned long long cnt = q.gacc[g];
   for (uint32_t oc = 0; oc < q.n_out; ++oc) {
     const uint32_t idx = q.out_index[oc];
@@ -418,6 +229,76 @@ __global__ void finalize_write_kernel(const __grid_constant__ QueryDesc q) {
         break;
     }
   }
+}
+
+__global__ void finalize_write_kernel(const __grid_constant__ QueryDesc q) { fin_write_block(q, blockIdx.x); }
+
+// ------------------------------------------------------------------ batched init / finalize
+// The same steps over every query of a batch: blocks of all queries are
+// numbered consecutively (init_first / fin_first give each query's first
+// block) and a fixed grid strides over them, so one launch configuration
+// serves any batch.
+
+// Query owning block b: the last query whose first block is <= b.
+__device__ __forceinline__ uint32_t owner_query(const uint32_t* first, uint32_t n_queries, uint32_t b) {
+  uint32_t lo = 0, hi = n_queries;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (first[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void batch_init_kernel(const BatchCtl* ctl) {
+  const uint32_t nq = ctl->n_queries, nblk = ctl->n_init_blocks;
+  for (uint32_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const uint32_t qi = owner_query(ctl->init_first, nq, b);
+    const QueryDesc& q = ctl->descs[qi];
+    const size_t g0 = (size_t)(b - ctl->init_first[qi]) * kInitGroups;
+    const size_t g1 = g0 + kInitGroups < q.n_groups ? g0 + kInitGroups : q.n_groups;
+    for (size_t i = g0 + threadIdx.x; i < g1; i += blockDim.x) init_group(q, i);
+    if (g0 == 0 && threadIdx.x == 0) {
+      *q.err = 0;
+      *q.out_count = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kFinBlock) batch_fin_count_kernel(const BatchCtl* ctl) {
+  const uint32_t nq = ctl->n_queries, nblk = ctl->n_fin_blocks;
+  for (uint32_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const uint32_t qi = owner_query(ctl->fin_first, nq, b);
+    fin_count_block(ctl->descs[qi], b - ctl->fin_first[qi]);
+  }
+}
+
+__global__ void __launch_bounds__(kFinBlock) batch_fin_scan_kernel(const BatchCtl* ctl) {
+  for (uint32_t qi = blockIdx.x; qi < ctl->n_queries; qi += gridDim.x) {
+    fin_scan(ctl->descs[qi], ctl->fin_first[qi + 1] - ctl->fin_first[qi]);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kFinBlock) batch_fin_write_kernel(const BatchCtl* ctl) {
+  const uint32_t nq = ctl->n_queries, nblk = ctl->n_fin_blocks;
+  for (uint32_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const uint32_t qi = owner_query(ctl->fin_first, nq, b);
+    fin_write_block(ctl->descs[qi], b - ctl->fin_first[qi]);
+    __syncthreads();   // the block's warp counts are reused by the next block
+  }
+}
+
+cudaError_t launch_batch_init(const BatchCtl* ctl, cudaStream_t s, unsigned grid) {
+  batch_init_kernel<<<grid, 256, 0, s>>>(ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(const BatchCtl* ctl, cudaStream_t s, unsigned grid) {
+  batch_fin_count_kernel<<<grid, kFinBlock, 0, s>>>(ctl);
+  batch_fin_scan_kernel<<<grid, kFinBlock, 0, s>>>(ctl);
+  batch_fin_write_kernel<<<grid, kFinBlock, 0, s>>>(ctl);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ launchers

@@ -14,245 +14,18 @@
 // accumulators when it fills.
 #include <cuda_runtime.h>
 
-#include "cq_phases.cuh"
+#include "cq_rowpath.cuh"
 
 namespace cq {
 
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// helper-warp state lives in the (otherwise unused) flags / misc words:
-// hcur[j] = first run / position of bitmap column j in the next tile to build
-__device__ __forceinline__ unsigned long long* helper_cursor(const Smem& sm) {
-  return reinterpret_cast<unsigned long long*>(sm.flags);
-}
-
-__device__ __forceinline__ const ColDesc& bitmap_col(const QueryDesc& q, int j) {
-  int idx = 0;
-  for (int c = 0; c < q.n_cols; ++c)
-    if (q.cols[c].bslot == j) idx = c;
-  return q.cols[idx];
-}
-
-__device__ __forceinline__ uint8_t* window(const QueryDesc& q, const Smem& sm, int buf, int j) {
-  return sm.win + ((size_t)buf * q.n_bitmaps + j) * kWin * 8;
-}
-
-// Prefetch kWin run ends / positions of every bitmap column, from the helper
-// cursor on, into window buffer `buf` (helper warp).
-__device__ void prefetch_windows(const QueryDesc& q, const Smem& sm, int buf) {
-  const int lane = threadIdx.x & 31;
-  const unsigned long long* hcur = helper_cursor(sm);
-  for (int j = 0; j < q.n_bitmaps; ++j) {
-    const ColDesc& cd = bitmap_col(q, j);
-    const unsigned long long cur = hcur[j];
-    const uint32_t avail = cur < cd.n ? (uint32_t)((cd.n - cur) < kWin ? (cd.n - cur) : kWin) : 0u;
-    uint8_t* dst = window(q, sm, buf, j);
-    for (uint32_t i = lane; i < avail; i += 32) {
-      if (cd.e64) cp_async8(dst + 8 * i, reinterpret_cast<const long long*>(cd.ends) + cur + i);
-      else cp_async4(dst + 4 * i, reinterpret_cast<const int*>(cd.ends) + cur + i);
-    }
-  }
-  cp_async_commit();
-}
-
-// Build the bitmaps of tile [s, e) into buffer `buf` from the prefetched
-// windows (falling back to global loads past a window), record the tile's
-// start cursors and advance the helper cursors (helper warp).
-__device__ void helper_build(const QueryDesc& q, const Smem& sm, int buf, unsigned long long s, unsigned long long e,
-                             uint32_t nwords) {
-  const int lane = threadIdx.x & 31;
-  const int nb = q.n_bitmaps;
-  unsigned long long* hcur = helper_cursor(sm);
-  cp_async_wait_all();
-  __syncwarp();
-  for (int j = 0; j < nb; ++j) {
-    const ColDesc& cd = bitmap_col(q, j);
-    const bool is_rle = cd.enc == ENC_RLE;
-    uint32_t* B = sm.bm + ((size_t)buf * nb + j) * nwords;
-    uint32_t* P = sm.pre + ((size_t)buf * nb + j) * (nwords + 1);
-    for (uint32_t w = lane; w < nwords; w += 32) B[w] = 0;
-    __syncwarp();
-    const unsigned long long cur = hcur[j];
-    const uint32_t avail = cur < cd.n ? (uint32_t)((cd.n - cur) < kWin ? (cd.n - cur) : kWin) : 0u;
-    const uint8_t* win = window(q, sm, buf, j);
-    unsigned long long cnt = 0;
-    int eq = 0;
-    for (unsigned long long base = 0;; base += 32) {
-      const unsigned long long idx = cur + base + lane;
-      long long x = 0;
-      bool have = true;
-      if (base + lane < avail) {
-        x = cd.e64 ? reinterpret_cast<const long long*>(win)[base + lane]
-                   : (long long)reinterpret_cast<const int*>(win)[base + lane];
-      } else if (idx < cd.n) {
-        x = ldg_val(cd.ends, idx, cd.e64);
-      } else {
-        have = false;
-      }
-      const bool in_tile = have && (unsigned long long)x < e;
-      if (in_tile) {
-        // a boundary before the tile would mean a corrupt cursor: flag it, never write
-        if ((unsigned long long)x < s || (is_rle && (unsigned long long)x == s)) {
-          report(q, CQ_ERR_INVALID_ARG, 2ull + ((unsigned long long)j << 8), s, (unsigned long long)x);
-        } else {
-          const uint32_t o = (uint32_t)((unsigned long long)x - s);
-          atomicOr(&B[o >> 5], 1u << (o & 31));
-        }
-      }
-      const uint32_t stop = __ballot_sync(0xFFFFFFFFu, !in_tile);
-      if (stop) {
-        const int f = __ffs(stop) - 1;
-        cnt = base + f;
-        const long long xf = __shfl_sync(0xFFFFFFFFu, x, f);
-        const bool hf = __shfl_sync(0xFFFFFFFFu, have, f);
-        eq = (is_rle && hf && (unsigned long long)xf == e) ? 1 : 0;
-        break;
-      }
-    }
-    __syncwarp();
-    // word prefix popcounts
-    const uint32_t per = nwords / 32;
-    uint32_t local = 0;
-    for (uint32_t k = 0; k < per; ++k) local += __popc(B[lane * per + k]);
-    uint32_t incl = local;
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-      if (lane >= d) incl += y;
-    }
-    uint32_t run = incl - local;
-    for (uint32_t k = 0; k < per; ++k) {
-      P[lane * per + k] = run;
-      run += __popc(B[lane * per + k]);
-    }
-    if (lane == 31) P[nwords] = incl;
-    if (lane == 0) {
-      sm.tcur[buf * kMaxBitmapCols + j] = cur;
-      hcur[j] = cur + cnt + (unsigned long long)eq;
-    }
-    __syncwarp();
-  }
-}
-
-// NCW compute warps (+1 helper); GPW groups of 32 rows per compute warp, so a
-// tile holds NCW * GPW * 32 rows.  MINB CTAs share an SM (registers are
-// capped so that MINB CTAs fit).
 template <int NCW, int GPW, int MINB>
 __global__ void __launch_bounds__((NCW + 1) * 32, MINB) row_query_kernel(const __grid_constant__ QueryDesc q) {
-  const Smem sm = carve(q);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t T = q.tile_rows;
-  const uint32_t nwords = T / 32;
   const unsigned long long t_begin = (unsigned long long)blockIdx.x * q.n_tiles / gridDim.x;
   const unsigned long long t_end = (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;
   if (t_begin >= t_end) return;
-  const bool helper = warp == NCW;
-  const int nb = q.n_bitmaps;
-
-  // ---- init: group table, aux tables, barriers, helper cursors
-  for (uint32_t sl = threadIdx.x; sl < q.table_slots; sl += blockDim.x) reset_slot(q, sm, sl);
-  if (threadIdx.x < 8) sm.misc[threadIdx.x] = 0;
-  const bool aux_smem = q.aux_words <= kAuxSmemWords;
-  if (aux_smem)
-    for (uint32_t i = threadIdx.x; i < q.aux_words; i += blockDim.x) sm.aux[i] = __ldg(q.aux + i);
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < q.stages; ++st) mbar_init(&sm.mbar[st], 1);
-    fence_barrier_init();
-  }
-  if (helper) {
-    for (int j = 0; j < nb; ++j) {
-      const ColDesc& cd = bitmap_col(q, j);
-      // RLE: first run whose exclusive end exceeds the first row; index: first position >= it
-      const unsigned long long c0 =
-          warp_count_below(cd.ends, cd.e64, cd.n, (long long)(t_begin * T), cd.enc == ENC_INDEX);
-      if (lane == 0) helper_cursor(sm)[j] = c0;
-    }
-  }
-  __syncthreads();
-
-  // ---- bulk-copy producer (helper lane 0): tile u -> stage (u - t_begin) % stages
-  auto issue = [&](unsigned long long u) {
-    const uint32_t st = (uint32_t)((u - t_begin) % q.stages);
-    uint8_t* dst = sm.stage + (size_t)st * q.stage_bytes;
-    const unsigned long long r0 = u * T;
-    const unsigned long long rows = (q.n_rows - r0) < (unsigned long long)T ? (q.n_rows - r0) : (unsigned long long)T;
-    uint32_t total = 0;
-    for (int i = 0; i < q.n_row_cols; ++i) {
-      const ColDesc& c = q.cols[q.row_cols[i]];
-      const uint32_t bits = c.enc == ENC_PLAIN ? (c.v64 ? 64u : 32u) : (uint32_t)c.bw;
-      total += (uint32_t)(((rows * bits + 7) / 8 + 15) / 16 * 16);
-    }
-    mbar_arrive_expect_tx(&sm.mbar[st], total);
-    for (int i = 0; i < q.n_row_cols; ++i) {
-      const ColDesc& c = q.cols[q.row_cols[i]];
-      const uint32_t bits = c.enc == ENC_PLAIN ? (c.v64 ? 64u : 32u) : (uint32_t)c.bw;
-      const uint32_t bytes = (uint32_t)(((rows * bits + 7) / 8 + 15) / 16 * 16);
-      bulk_g2s(dst + c.stage_off, reinterpret_cast<const uint8_t*>(c.vals) + r0 * bits / 8, bytes, &sm.mbar[st]);
-    }
-  };
-
-  // ---- prologue: first tile's bitmaps, windows of the second, the first stages
-  if (helper) {
-    if (lane == 0)
-      for (unsigned long long u = t_begin; u < t_end && u < t_begin + q.stages; ++u) issue(u);
-    if (nb) {
-      prefetch_windows(q, sm, 0);
-      helper_build(q, sm, 0, t_begin * T, ((t_begin + 1) * T < q.n_rows) ? (t_begin + 1) * T : q.n_rows, nwords);
-      if (t_begin + 1 < t_end) prefetch_windows(q, sm, 1);
-    }
-  }
-  __syncthreads();
-
-  uint32_t rows_since_flush = 0;
-  uint16_t* mylist = sm.clist + (helper ? 0 : warp) * (GPW * 32);
-  const uint32_t wbase = warp * (GPW * 32);
-
-  for (unsigned long long t = t_begin; t < t_end; ++t) {
-    const unsigned long long s = t * T;
-    const unsigned long long e = (s + T < q.n_rows) ? s + T : q.n_rows;
-    const uint32_t rows = (uint32_t)(e - s);
-    const int buf = (int)((t - t_begin) & 1ull);
-    if (!helper) {
-      const uint32_t st = (uint32_t)((t - t_begin) % q.stages);
-      mbar_wait_bounded(&sm.mbar[st], (uint32_t)(((t - t_begin) / q.stages) & 1ull), q.err);
-      TileView tv;
-      tv.bm = sm.bm + (size_t)buf * nb * nwords;
-      tv.pre = sm.pre + (size_t)buf * nb * (nwords + 1);
-      tv.cur = sm.tcur + buf * kMaxBitmapCols;
-      tv.stage = sm.stage + (size_t)st * q.stage_bytes;
-      tv.aux = aux_smem ? sm.aux : q.aux;
-      tv.nwords = nwords;
-      const uint32_t pm = phase_filter<false, GPW>(q, tv, nullptr, wbase, rows);
-      const uint32_t n_pass = compact<GPW>(pm, wbase, mylist);
-      phase_aggregate<false, 2>(q, sm, tv, nullptr, mylist, n_pass, s);
-    } else if (nb && t + 1 < t_end) {
-      helper_build(q, sm, buf ^ 1, e, (e + T < q.n_rows) ? e + T : q.n_rows, nwords);
-      if (t + 2 < t_end) prefetch_windows(q, sm, buf);
-    }
-    // one barrier per tile; thread 0 decides the flush from the occupancy it
-    // sees (an early or late flush is harmless: a full table falls back to
-    // the global accumulators)
-    rows_since_flush += rows;
-    const bool last = t + 1 == t_end;
-    const int need = __syncthreads_or(threadIdx.x == 0 &&
-                                      (last || (!q.table_dense && sm.misc[0] * 2 > (int)q.table_slots) ||
-                                       rows_since_flush + T > q.flush_rows));
-    // tile t's stage is free: refill it with tile t + stages
-    if (helper && lane == 0 && t + q.stages < t_end) issue(t + q.stages);
-    if (need) {
-      flush_table(q, sm);
-      if (threadIdx.x == 0) sm.misc[0] = 0;
-      __syncthreads();
-      rows_since_flush = 0;
-    }
-  }
+  row_range<NCW, GPW>(q, carve(q), t_begin, t_end);
 }
+
 
 #define CQ_ROW_SHAPES(X) X(16, 2, 1) X(16, 4, 1) X(16, 8, 1) X(16, 16, 1) X(16, 2, 2) X(16, 4, 2) X(16, 8, 2)
 

@@ -1,14 +1,430 @@
-// cq_serve.cu -- batched launches and the serving loop (entry points).
+// cq_serve.cu -- batched launches (host side), the batch autotuner and the
+// serving loop.
+//
+// A batch is planned query by query with the one-query planner, constrained
+// to the persistent kernel's shape; the descriptors, work items and aux
+// tables are packed into one control block that a cached CUDA graph uploads
+// and runs (init -> persistent kernel -> finalize).  Result buffers of all
+// queries of a batch share one pool allocation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
 #include "cq_internal.h"
+
+namespace cq {
+
+// ------------------------------------------------------------------ launch graphs
+// One instantiated launch graph and its control block.  The graph's first
+// node uploads the pinned staging copy of the control block; an event node
+// right after it tells the host when the staging copy may be rewritten.
+struct BatchGraph {
+  int device = 0;
+  size_t cap = 0;                 // control-block bytes
+  unsigned grid = 0;              // persistent CTAs
+  uint8_t* host = nullptr;        // pinned staging
+  uint8_t* dev = nullptr;         // control block (device)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t upload = nullptr;
+  cudaEvent_t uploaded = nullptr;
+  bool filling = false;           // a host thread is writing the staging copy
+  ~BatchGraph() {
+    cudaSetDevice(device);
+    if (uploaded) cudaEventSynchronize(uploaded);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (uploaded) cudaEventDestroy(uploaded);
+    if (dev) cudaFree(dev);
+    if (host) cudaFreeHost(host);
+  }
+};
+
+// Device block and events shared by the results of one batch.
+struct BatchShared {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* block = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  ~BatchShared() {
+    cudaSetDevice(device);
+    if (block) cudaFreeAsync(block, stream);
+    if (ev_start) cudaEventDestroy(ev_start);
+    if (ev_done) cudaEventDestroy(ev_done);
+  }
+};
+
+static size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Dynamic shared memory of the batch kernel: the per-block opt-in limit less
+// the kernel's static shared memory (its descriptor copy).
+static int ensure_batch_kernel(cq_ctx* ctx) {
+  if (ctx->batch_smem) return CQ_OK;
+  size_t st = 0;
+  cudaError_t e = batch_kernel_static_smem(&st);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "batch kernel attributes: %s", cudaGetErrorString(e));
+  const size_t dyn = (ctx->smem_optin - st) / 128 * 128;
+  e = batch_kernel_set_smem(dyn);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "batch kernel shared memory: %s", cudaGetErrorString(e));
+  ctx->batch_smem = dyn;
+  return CQ_OK;
+}
+
+static int capture_graph(cq_ctx* ctx, BatchGraph* g) {
+  cudaStream_t cs = nullptr;
+  CQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->dev, g->host, g->cap, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(g->uploaded, cs);
+  if (e == cudaSuccess)
+    e = launch_batch(reinterpret_cast<BatchCtl*>(g->dev), cs, g->grid, ctx->batch_smem, (unsigned)ctx->num_sms * 2);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  if (e == cudaSuccess) e = e2;
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return set_error(CQ_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+  }
+  g->graph = graph;
+  size_t n_nodes = 0;
+  CQ_CUDA(cudaGraphGetNodes(graph, nullptr, &n_nodes));
+  std::vector<cudaGraphNode_t> nodes(n_nodes);
+  CQ_CUDA(cudaGraphGetNodes(graph, nodes.data(), &n_nodes));
+  for (cudaGraphNode_t n : nodes) {
+    cudaGraphNodeType t;
+    CQ_CUDA(cudaGraphNodeGetType(n, &t));
+    if (t == cudaGraphNodeTypeMemcpy) g->upload = n;
+  }
+  if (!g->upload) return set_error(CQ_ERR_CUDA, "batch graph has no upload node");
+  CQ_CUDA(cudaGraphInstantiate(&g->exec, graph, 0));
+  return CQ_OK;
+}
+
+// A launch graph whose control block holds `bytes`, marked as being filled.
+static int acquire_graph(cq_ctx* ctx, size_t bytes, unsigned grid, BatchGraph** out) {
+  std::unique_lock<std::mutex> lk(ctx->batch_mu);
+  for (int pass = 0; pass < 2; ++pass) {
+    for (auto& g : ctx->graphs) {
+      if (g->filling || g->cap < bytes || g->grid != grid) continue;
+      // pass 0 takes an idle graph; pass 1 waits for the upload of a busy one
+      const cudaError_t q = cudaEventQuery(g->uploaded);
+      if (q == cudaErrorNotReady && pass == 0) continue;
+      g->filling = true;
+      BatchGraph* r = g;
+      lk.unlock();
+      if (q == cudaErrorNotReady) cudaEventSynchronize(r->uploaded);
+      *out = r;
+      return CQ_OK;
+    }
+    if (pass == 0 && ctx->graphs.size() < 16) break;   // room for another graph
+  }
+  std::unique_ptr<BatchGraph> g(new BatchGraph);
+  g->device = ctx->device;
+  g->cap = 256 * 1024;
+  while (g->cap < bytes) g->cap *= 2;
+  g->grid = grid;
+  CQ_CUDA(cudaMalloc(&g->dev, g->cap));
+  CQ_CUDA(cudaMallocHost(&g->host, g->cap));
+  CQ_CUDA(cudaEventCreateWithFlags(&g->uploaded, cudaEventDisableTiming));
+  int rc = capture_graph(ctx, g.get());
+  if (rc != CQ_OK) return rc;
+  g->filling = true;
+  *out = g.get();
+  ctx->graphs.push_back(g.release());
+  return CQ_OK;
+}
+
+static void release_graph(cq_ctx* ctx, BatchGraph* g) {
+  std::lock_guard<std::mutex> lk(ctx->batch_mu);
+  g->filling = false;
+}
+
+// ------------------------------------------------------------------ batch kinds
+// Whether every column the plan references is RLE or index-encoded (the
+// planner then runs the query in segment mode).
+static bool plan_is_segment(const cq_table* t, const cq_plan* p) {
+  auto ok = [&](uint32_t c) {
+    return c < t->cols.size() && (t->cols[c]->enc == ENC_RLE || t->cols[c]->enc == ENC_INDEX);
+  };
+  for (uint32_t i = 0; i < p->n_preds && p->preds; ++i)
+    if (!ok(p->preds[i].col)) return false;
+  for (uint32_t i = 0; i < p->n_group_by && p->group_by; ++i)
+    if (!ok(p->group_by[i])) return false;
+  for (uint32_t i = 0; i < p->n_aggs && p->aggs; ++i)
+    if (p->aggs[i].op != CQ_COUNT && !ok(p->aggs[i].col)) return false;
+  return true;
+}
+
+static uint32_t ceil_log2(uint64_t x) {
+  uint32_t r = 0;
+  while ((1ull << r) < x && r < 63) ++r;
+  return r;
+}
+
+// Autotuner key: log2 of the query count and of the total rows, and the
+// share of segment-mode queries in eighths.
+static uint64_t batch_key(uint32_t n, cq_table* const* tables, const cq_plan* plans) {
+  uint64_t rows = 0;
+  uint32_t seg = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    rows += tables[i] ? tables[i]->n_rows : 0;
+    if (tables[i] && plan_is_segment(tables[i], &plans[i])) ++seg;
+  }
+  return ((uint64_t)ceil_log2(n) << 16) | ((uint64_t)ceil_log2(rows + 1) << 8) | (uint64_t)(seg * 8 / n);
+}
+
+// ------------------------------------------------------------------ one batch
+static int run_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, uint32_t tile_rows,
+                     uint32_t items_per_cta, cudaStream_t s, cq_result** results) {
+  cq_ctx* ctx = tables[0]->ctx;
+  // ---- plan every query for the batch kernel's shape
+  std::vector<Planned> P(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    const int rc = plan_batch_query(tables[i], &plans[i], tile_rows, ctx->batch_smem, &P[i]);
+    if (rc != CQ_OK) {
+      const std::string msg = cq_last_error();
+      return set_error(rc, "batch query %u: %s", i, msg.c_str());
+    }
+  }
+  // ---- work items: C tiles at most, about items_per_cta per CTA, larger first
+  const unsigned grid = (unsigned)ctx->num_sms;
+  uint64_t total_tiles = 0;
+  for (const Planned& p : P) total_tiles += p.q.n_tiles;
+  const uint64_t target = (uint64_t)grid * (items_per_cta ? items_per_cta : 4u);
+  uint64_t chunk = (total_tiles + target - 1) / (target ? target : 1);
+  if (chunk < 1) chunk = 1;
+  if (chunk > 0xFFFFFFFFull) chunk = 0xFFFFFFFFull;
+  std::vector<BatchItem> items;
+  for (uint32_t i = 0; i < n; ++i)
+    for (uint64_t t = 0; t < P[i].q.n_tiles; t += chunk) {
+      BatchItem it;
+      it.query = i;
+      it.n_tiles = (uint32_t)std::min<uint64_t>(chunk, P[i].q.n_tiles - t);
+      it.t_begin = t;
+      items.push_back(it);
+    }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const BatchItem& a, const BatchItem& b) { return a.n_tiles > b.n_tiles; });
+  // ---- control block layout: header, descriptors, items, block prefixes, aux tables
+  const size_t off_desc = al256(sizeof(BatchCtl));
+  const size_t off_items = al16(off_desc + (size_t)n * sizeof(QueryDesc));
+  const size_t off_init = al16(off_items + items.size() * sizeof(BatchItem));
+  const size_t off_fin = al16(off_init + 4 * ((size_t)n + 1));
+  size_t off_aux = al16(off_fin + 4 * ((size_t)n + 1));
+  std::vector<size_t> aux_at(n);
+  size_t bytes = off_aux;
+  for (uint32_t i = 0; i < n; ++i) {
+    aux_at[i] = bytes;
+    bytes = al16(bytes + 4 * P[i].aux.size());
+  }
+  // ---- result buffers: one pool allocation, one block per query
+  std::vector<QueryBlock> L(n);
+  std::vector<size_t> blk_at(n);
+  size_t blk_bytes = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    L[i] = query_block_layout(P[i], false);
+    blk_at[i] = blk_bytes;
+    blk_bytes += al256(L[i].total);
+  }
+  std::shared_ptr<BatchShared> sh(new BatchShared);
+  sh->device = ctx->device;
+  sh->stream = s;
+  cudaError_t e = cudaMallocFromPoolAsync(&sh->block, blk_bytes, ctx->pool, s);
+  if (e != cudaSuccess) {
+    sh->block = nullptr;
+    return set_error(CQ_ERR_OOM, "device pool allocation of %llu bytes failed: %s", (unsigned long long)blk_bytes,
+                     cudaGetErrorString(e));
+  }
+  CQ_CUDA(cudaEventCreate(&sh->ev_start));
+  CQ_CUDA(cudaEventCreate(&sh->ev_done));
+  // ---- fill the staging copy of a launch graph's control block
+  BatchGraph* g = nullptr;
+  int rc = acquire_graph(ctx, bytes, grid, &g);
+  if (rc != CQ_OK) return rc;
+  uint8_t* h = g->host;
+  uint8_t* d = g->dev;
+  uint8_t* blk = reinterpret_cast<uint8_t*>(sh->block);
+  BatchCtl ctl;
+  memset(&ctl, 0, sizeof(ctl));
+  ctl.n_queries = n;
+  ctl.n_items = (uint32_t)items.size();
+  ctl.descs = reinterpret_cast<const QueryDesc*>(d + off_desc);
+  ctl.items = reinterpret_cast<const BatchItem*>(d + off_items);
+  ctl.init_first = reinterpret_cast<const uint32_t*>(d + off_init);
+  ctl.fin_first = reinterpret_cast<const uint32_t*>(d + off_fin);
+  uint32_t* init_first = reinterpret_cast<uint32_t*>(h + off_init);
+  uint32_t* fin_first = reinterpret_cast<uint32_t*>(h + off_fin);
+  uint32_t ib = 0, fb = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    bind_query_block(P[i], blk + blk_at[i], L[i], reinterpret_cast<const uint32_t*>(d + aux_at[i]));
+    memcpy(h + off_desc + (size_t)i * sizeof(QueryDesc), &P[i].q, sizeof(QueryDesc));
+    if (!P[i].aux.empty()) memcpy(h + aux_at[i], P[i].aux.data(), 4 * P[i].aux.size());
+    init_first[i] = ib;
+    fin_first[i] = fb;
+    const uint64_t G = P[i].q.n_groups ? P[i].q.n_groups : 1;
+    ib += (uint32_t)((G + kInitGroups - 1) / kInitGroups);
+    fb += (uint32_t)((G + 1023) / 1024);
+  }
+  init_first[n] = ib;
+  fin_first[n] = fb;
+  ctl.n_init_blocks = ib;
+  ctl.n_fin_blocks = fb;
+  memcpy(h, &ctl, sizeof(ctl));
+  if (!items.empty()) memcpy(h + off_items, items.data(), items.size() * sizeof(BatchItem));
+  // ---- replay: upload only the bytes in use
+  e = cudaGraphExecMemcpyNodeSetParams1D(g->exec, g->upload, g->dev, g->host, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaEventRecord(sh->ev_start, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(sh->ev_done, s);
+  release_graph(ctx, g);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
+  // ---- results
+  for (uint32_t i = 0; i < n; ++i) {
+    cq_result* r = new_result(ctx, s, false);
+    r->ev_start = r->ev_k0 = sh->ev_start;
+    r->ev_done = r->ev_k1 = sh->ev_done;
+    attach_outputs(r, P[i]);
+    for (int kc : P[i].out_key_col) r->key_cols.push_back(kc >= 0 ? tables[i]->cols[kc] : nullptr);
+    for (cq_column* c : tables[i]->cols) c->refs++;
+    r->held_cols = tables[i]->cols;
+    r->batch_keepalive = sh;
+    results[i] = r;
+  }
+  return CQ_OK;
+}
+
+static int check_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, cq_result** results,
+                       cq_ctx** ctx_out) {
+  if (n == 0) return set_error(CQ_ERR_INVALID_ARG, "empty batch");
+  if (!tables || !plans) return set_error(CQ_ERR_INVALID_ARG, "NULL tables or plans");
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!tables[i]) return set_error(CQ_ERR_INVALID_ARG, "batch query %u: NULL table", i);
+    if (tables[i]->ctx != tables[0]->ctx) return set_error(CQ_ERR_INVALID_ARG, "batch query %u: another context", i);
+  }
+  if (results)
+    for (uint32_t i = 0; i < n; ++i) results[i] = nullptr;
+  cq_ctx* ctx = tables[0]->ctx;
+  CQ_CUDA(cudaSetDevice(ctx->device));
+  {
+    std::lock_guard<std::mutex> lk(ctx->batch_mu);
+    const int rc = ensure_batch_kernel(ctx);
+    if (rc != CQ_OK) return rc;
+  }
+  *ctx_out = ctx;
+  return CQ_OK;
+}
+
+static bool tuned_shape(cq_ctx* ctx, uint64_t key, uint32_t* tile, uint32_t* ipc) {
+  std::lock_guard<std::mutex> lk(ctx->batch_mu);
+  for (const TunedShape& t : ctx->tuned)
+    if (t.key == key) {
+      *tile = t.tile_rows;
+      *ipc = t.items_per_cta;
+      return true;
+    }
+  return false;
+}
+
+}  // namespace cq
 
 using namespace cq;
 
-extern "C" int cq_batch_run(uint32_t n, cq_table* const* tables, const cq_plan* plans, const cq_exec_options* opts,
-                            void* cuda_stream, cq_result** results) {
-  (void)n; (void)tables; (void)plans; (void)opts; (void)cuda_stream; (void)results;
-  return set_error(CQ_ERR_UNSUPPORTED, "batched launches are not built yet");
+cq_ctx::~cq_ctx() {
+  for (BatchGraph* g : graphs) delete g;
 }
 
+extern "C" int cq_batch_run(uint32_t n, cq_table* const* tables, const cq_plan* plans, const cq_exec_options* opts,
+                            void* cuda_stream, cq_result** results) {
+  clear_error();
+  if (!results) return set_error(CQ_ERR_INVALID_ARG, "results is NULL");
+  cq_ctx* ctx = nullptr;
+  int rc = check_batch(n, tables, plans, results, &ctx);
+  if (rc != CQ_OK) return rc;
+  if (opts && opts->mode != CQ_EXEC_FUSED) return set_error(CQ_ERR_UNSUPPORTED, "batches run the fused path only");
+  uint32_t tile = opts ? opts->tile_rows : 0, ipc = opts ? opts->items_per_cta : 0;
+  if (tile == 0 && ipc == 0) tuned_shape(ctx, batch_key(n, tables, plans), &tile, &ipc);
+  if (tile && (tile < 1024 || tile > 8192 || (tile & (tile - 1))))
+    return set_error(CQ_ERR_INVALID_ARG, "tile_rows must be 1024, 2048, 4096 or 8192");
+  cudaStream_t s = cuda_stream ? reinterpret_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  rc = run_batch(n, tables, plans, tile, ipc, s, results);
+  if (rc != CQ_OK)
+    for (uint32_t i = 0; i < n; ++i)
+      if (results[i]) {
+        cq_result_destroy(results[i]);
+        results[i] = nullptr;
+      }
+  return rc;
+}
+
+extern "C" int cq_batch_tune(uint32_t n, cq_table* const* tables, const cq_plan* plans, void* cuda_stream,
+                             cq_exec_options* best, double* best_us) {
+  clear_error();
+  cq_ctx* ctx = nullptr;
+  int rc = check_batch(n, tables, plans, nullptr, &ctx);
+  if (rc != CQ_OK) return rc;
+  cudaStream_t s = cuda_stream ? reinterpret_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  static const uint32_t kTiles[] = {0, 1024, 2048, 4096, 8192};
+  static const uint32_t kIpc[] = {1, 2, 4, 8};
+  std::vector<cq_result*> res(n, nullptr);
+  double best_t = 1e300;
+  uint32_t best_tile = 0, best_ipc = 4;
+  for (uint32_t tile : kTiles)
+    for (uint32_t ipc : kIpc) {
+      double t_min = 1e300;
+      bool ok = true;
+      for (int rep = 0; rep < 3 && ok; ++rep) {   // warm-up, then best of two
+        rc = run_batch(n, tables, plans, tile, ipc, s, res.data());
+        if (rc != CQ_OK) {
+          ok = false;   // e.g. a tile that leaves no room in shared memory
+          break;
+        }
+        double us = 0;
+        rc = cq_result_wait(res[0], UINT64_MAX);
+        if (rc == CQ_OK) rc = cq_result_device_time_us(res[0], &us);
+        for (cq_result*& r : res) {
+          cq_result_destroy(r);
+          r = nullptr;
+        }
+        if (rc != CQ_OK) return rc;
+        if (rep > 0) t_min = std::min(t_min, us);
+      }
+      if (ok && t_min < best_t) {
+        best_t = t_min;
+        best_tile = tile;
+        best_ipc = ipc;
+      }
+    }
+  clear_error();
+  if (best_t >= 1e300) return set_error(CQ_ERR_UNSUPPORTED, "no candidate shape fits this batch");
+  {
+    const uint64_t key = batch_key(n, tables, plans);
+    std::lock_guard<std::mutex> lk(ctx->batch_mu);
+    bool found = false;
+    for (TunedShape& t : ctx->tuned)
+      if (t.key == key) {
+        t.tile_rows = best_tile;
+        t.items_per_cta = best_ipc;
+        found = true;
+      }
+    if (!found) ctx->tuned.push_back({key, best_tile, best_ipc});
+  }
+  if (best) {
+    memset(best, 0, sizeof(*best));
+    best->mode = CQ_EXEC_FUSED;
+    best->tile_rows = best_tile;
+    best->items_per_cta = best_ipc;
+  }
+  if (best_us) *best_us = best_t;
+  return CQ_OK;
+}
+
+// ---------------------------------------------------------------- serving loop
 extern "C" int cq_server_create(cq_ctx* ctx, const cq_server_options* opts, cq_server** out) {
   (void)ctx; (void)opts; (void)out;
   return set_error(CQ_ERR_UNSUPPORTED, "the serving loop is not built yet");

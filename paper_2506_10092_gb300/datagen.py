@@ -333,6 +333,168 @@ def heterogeneous(n_rows: int = 100_000_000, seed: int = DEFAULT_SEED, n_in: int
     return table, plan
 
 
+# --------------------------------------------------------------------------
+# counter-based per-row values
+# --------------------------------------------------------------------------
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix64(seed: int, col: int, idx: np.ndarray) -> np.ndarray:
+    """h(seed, col, i): the SplitMix64 output function (Steele, Lea and Flood,
+    "Fast splittable pseudorandom number generators", OOPSLA 2014) applied to
+    the counter state (seed XOR col << 56) + (i + 1) * 0x9E3779B97F4A7C15,
+    all arithmetic mod 2^64.  A pure function of (seed, col, i), so any row or
+    prefix can be produced alone."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (np.uint64(seed & 0xFFFFFFFFFFFFFFFF) ^ (np.uint64(col & 0xFF) << np.uint64(56))) + \
+            (idx + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def _nested_ends(rng, n_rows: int, mean: float, parent_ends: Optional[np.ndarray], end_dtype) -> np.ndarray:
+    """Run ends of a column sorted inside its parent's runs: the parent's ends
+    plus geometric(mean) boundaries of its own."""
+    own = geometric_ends(rng, n_rows, mean, np.int64)
+    if parent_ends is None:
+        return own.astype(end_dtype)
+    return np.union1d(own, parent_ends.astype(np.int64)).astype(end_dtype)
+
+
+def _increasing_in_parent(rng, ends: np.ndarray, parent_ends: np.ndarray, domain: int) -> np.ndarray:
+    """Run values strictly increasing inside every parent run, in 0..domain-1:
+    the j-th of k runs of a parent run takes a seeded value in its own slice
+    [floor(j*domain/k), floor((j+1)*domain/k)) (non-decreasing if k > domain)."""
+    parent_of = np.searchsorted(parent_ends.astype(np.int64), ends.astype(np.int64), side="left")
+    first = np.searchsorted(parent_of, np.arange(parent_ends.shape[0]), side="left")
+    k = np.diff(np.concatenate([first, [ends.shape[0]]]))[parent_of]
+    j = np.arange(ends.shape[0]) - first[parent_of]
+    lo = (j * domain) // k
+    hi = ((j + 1) * domain) // k
+    width = np.maximum(hi - lo, 1)
+    v = lo + rng.integers(0, 1 << 62, size=ends.shape[0]) % width
+    return np.minimum(v, domain - 1)
+
+
+NESTED_BASE7 = (1 << 20) - 3
+NESTED_BASE8 = 777_777
+
+
+def nested_codes4(seed: int, c3_ends: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """c4 of the nested table at the given rows: inside each c3 run of
+    length L the code is the number of the run's 15 cut points
+    h(seed, 4, 15 * run + k) mod L (k = 0..14) at or before the row's offset
+    in the run -- non-decreasing along the run, 0..15."""
+    ends = c3_ends.astype(np.int64)
+    rows = np.asarray(rows, dtype=np.int64)
+    run = np.searchsorted(ends, rows, side="right")
+    start = np.where(run > 0, ends[np.maximum(run - 1, 0)], 0)
+    length = (ends[run] - start).astype(np.uint64)
+    off = (rows - start).astype(np.uint64)
+    code = np.zeros(rows.shape[0], dtype=np.uint32)
+    base = run.astype(np.uint64) * np.uint64(15)
+    for k in range(15):
+        cut = splitmix64(seed, 4, base + np.uint64(k)) % length
+        code += (off >= cut).astype(np.uint32)
+    return code
+
+
+def nested_codes4_all(seed: int, c3_ends: np.ndarray, n_rows: int) -> np.ndarray:
+    """nested_codes4 for every row at once: each cut point adds one at its
+    row, and the code is the running count inside the run."""
+    ends = c3_ends.astype(np.int64)
+    if n_rows == 0:
+        return np.zeros(0, np.uint32)
+    starts = np.concatenate([[0], ends[:-1]])
+    length = (ends - starts).astype(np.uint64)
+    base = np.arange(ends.shape[0], dtype=np.uint64) * np.uint64(15)
+    inc = np.zeros(n_rows + 1, dtype=np.int32)
+    for k in range(15):
+        cut = (splitmix64(seed, 4, base + np.uint64(k)) % length).astype(np.int64)
+        np.add.at(inc, starts + cut, 1)
+    run_total = np.cumsum(inc[:-1], dtype=np.int64)
+    before = np.concatenate([[0], run_total])[starts]        # count before each run starts
+    return (run_total - np.repeat(before, ends - starts)).astype(np.uint32)
+
+
+def nested_row_values(seed: int, col: int, rows: np.ndarray) -> np.ndarray:
+    """Per-row fields of columns c5..c8 of the nested table (unsigned codes /
+    offsets): c5 8 bits, c6 16 bits, c7 8 bits, c8 12 bits of h(seed, col, row)."""
+    bits = {5: 8, 6: 16, 7: 8, 8: 12}[col]
+    return (splitmix64(seed, col, rows) & np.uint64((1 << bits) - 1)).astype(np.uint32)
+
+
+def nested(n_rows: int, seed: int = DEFAULT_SEED, lo3: int = 200, hi3: int = 699, lean: bool = False):
+    """A lexicographically sorted 8-column table (nested RLE).
+    c1 RLE, runs mean 1e6, value = run ordinal;
+    c2 RLE inside c1 runs (own boundaries mean 1e4), values strictly
+       increasing within each c1 run, 0..9999;
+    c3 RLE inside c2 runs (own boundaries mean 1e2), increasing within each
+       c2 run, 0..999;
+    c4 4-bit dictionary code, non-decreasing within each c3 run (15 seeded
+       cut points per run), bit-packed;
+    c5 8-bit and c6 16-bit dictionary codes, c7 int64 = 2^20-3 + 8-bit offset,
+    c8 int64 = 777777 + 12-bit offset, all per-row counter-based values
+       (splitmix64), bit-packed.
+    Run ends are int64 when n_rows >= 2^31.  ``lean`` leaves out c5 and c6,
+    which the query does not read (column indices then shift; use
+    nested_plan(..., lean=True)).
+    Query: SELECT c2, c4, SUM(c7), SUM(c8) WHERE c3 BETWEEN lo3 AND hi3
+           GROUP BY c2, c4."""
+    rng = np.random.default_rng([seed, 3])
+    ed = np.int32 if n_rows < 2**31 else np.int64
+    e1 = _nested_ends(rng, n_rows, 1e6, None, ed)
+    e2 = _nested_ends(rng, n_rows, 1e4, e1, ed)
+    e3 = _nested_ends(rng, n_rows, 1e2, e2, ed)
+    c1 = RLE(np.arange(e1.shape[0], dtype=np.int32), e1, n_rows)
+    c2 = RLE(_increasing_in_parent(rng, e2, e1, 10_000).astype(np.int32), e2, n_rows)
+    c3 = RLE(_increasing_in_parent(rng, e3, e2, 1_000).astype(np.int32), e3, n_rows)
+    rows = np.arange(n_rows, dtype=np.int64)
+    c4 = make_dict([b"g%02d" % i for i in range(16)], nested_codes4_all(seed, e3, n_rows), 4)
+    c7 = make_packed(nested_row_values(seed, 7, rows), 8, NESTED_BASE7, "i64")
+    c8 = make_packed(nested_row_values(seed, 8, rows), 12, NESTED_BASE8, "i64")
+    if lean:
+        table = Table([c1, c2, c3, c4, c7, c8], n_rows, ["c1", "c2", "c3", "c4", "c7", "c8"])
+        return table, nested_plan(lo3, hi3, lean=True)
+    c5 = make_dict([b"h%03d" % i for i in range(256)], nested_row_values(seed, 5, rows), 8)
+    c6 = make_dict([b"w%05d" % i for i in range(1 << 16)], nested_row_values(seed, 6, rows), 16)
+    table = Table([c1, c2, c3, c4, c5, c6, c7, c8], n_rows, ["c1", "c2", "c3", "c4", "c5", "c6", "c7", "c8"])
+    return table, nested_plan(lo3, hi3)
+
+
+def nested_plan(lo3: int = 200, hi3: int = 699, lean: bool = False) -> Plan:
+    m7, m8 = (4, 5) if lean else (6, 7)
+    return Plan([Pred(2, "between", lo3, hi3)], [1, 3], [Agg("sum", m7), Agg("sum", m8)])
+
+
+def tiny_plan(threshold: int = 50) -> Plan:
+    return Plan([Pred(0, "lt", threshold)], [1], [Agg("sum", 0), Agg("count")])
+
+
+def partition_sizes(rng, n_parts: int, lo: float = 1e4, hi: float = 5e7) -> np.ndarray:
+    """Partition row counts drawn log-uniform in [lo, hi]."""
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_parts)).astype(np.int64)
+
+
+def batch_queries(rng, n_queries: int, n_parts: int):
+    """The batched workload's query list: (partition, kind, plan) with kind
+    "tiny" (A < t, t uniform in 0..99, GROUP BY B on the partition's
+    two-RLE table) or "nested" (c3 BETWEEN lo AND lo + w on its nested
+    table), half each, partitions uniform."""
+    out = []
+    for i in range(n_queries):
+        part = int(rng.integers(0, n_parts))
+        if i % 2 == 0:
+            out.append((part, "tiny", tiny_plan(int(rng.integers(0, 100)))))
+        else:
+            lo = int(rng.integers(0, 1000))
+            hi = min(999, lo + int(rng.integers(0, 1000)))
+            out.append((part, "nested", nested_plan(lo, hi)))
+    return out
+
+
 def compressed_bytes(table: Table, cols: Optional[Sequence[int]] = None) -> int:
     """Bytes the method must read for the listed columns (all by default):
     RLE R*(value+end), packed/dict N*w/8, index nnz*(position+value),
