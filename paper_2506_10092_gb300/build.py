@@ -38,19 +38,32 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+GEN = os.path.join(HERE, "gen")
+GEN_LIB = os.path.join(HERE, "libcqgen.so")
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    """Build libcq.so (the query library) and libcqgen.so (the device-side
+    input generator); returns the path of libcq.so."""
     os.makedirs(BUILD, exist_ok=True)
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         [os.path.join(HERE, "..", "include", "cq.h")]
+    gen_headers = [os.path.join(HERE, "..", "include", "cq_gen.h")]
     nvcc = _nvcc()
     jobs = []
     objs = []
+    gen_objs = []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             cmd = [nvcc] + ARCH + NVFLAGS + list(extra_flags) + ["-c", src, "-o", obj]
             jobs.append(cmd)
+    for src in sorted(glob.glob(os.path.join(GEN, "*.cu"))):
+        obj = os.path.join(BUILD, "gen_" + os.path.basename(src)[:-3] + ".o")
+        gen_objs.append(obj)
+        if force or _stale(obj, [src] + gen_headers):
+            jobs.append([nvcc] + ARCH + NVFLAGS + list(extra_flags) + ["-c", src, "-o", obj])
 
     def run(cmd):
         if verbose:
@@ -64,10 +77,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for out in ex.map(run, jobs):
             if verbose and out.strip():
                 print(out)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
-        os.replace(tmp, LIB)
+    for lib, lib_objs in ((LIB, objs), (GEN_LIB, gen_objs)):
+        if force or _stale(lib, lib_objs):
+            tmp = lib + f".tmp{os.getpid()}"
+            run([nvcc] + ARCH + ["-shared", "-o", tmp] + lib_objs + ["-lpthread"])
+            os.replace(tmp, lib)
     return LIB
 
 

@@ -10,6 +10,7 @@ is missing; there is no fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 from typing import List, Optional, Sequence
@@ -160,6 +161,19 @@ def _stream_ptr(stream) -> Optional[int]:
 
 
 # ---------------------------------------------------------------- handles
+_EXITING = False
+
+
+def _at_exit():
+    # the process is ending: leave handles to the driver instead of calling
+    # into CUDA while the interpreter (and torch) tear down in any order
+    global _EXITING
+    _EXITING = True
+
+
+atexit.register(_at_exit)
+
+
 class Handle:
     def __init__(self, ptr, destroy, keep=()):
         self.ptr = ptr
@@ -167,7 +181,7 @@ class Handle:
         self.keep = list(keep)
 
     def close(self):
-        if self.ptr:
+        if self.ptr and not _EXITING:
             self._destroy(self.ptr)
             self.ptr = None
 
@@ -210,7 +224,7 @@ def cq_column_create_rle(ctx, run_values, run_ends, n_rows: int) -> Handle:
     out = C.c_void_p()
     _check(lib.cq_column_create_rle(ctx.ptr, _dt(v), _ptr(v), _dt(e), _ptr(e), int(e.shape[0]), int(n_rows),
                                     _mem(v, e), C.byref(out)))
-    return Handle(out.value, lib.cq_column_destroy, [v, e] if _is_dev(v) else [])
+    return Handle(out.value, lib.cq_column_destroy, [ctx] + ([v, e] if _is_dev(v) else []))
 
 
 def cq_column_create_dict(ctx, strings: Sequence[bytes], packed_codes, bit_width: int, n_rows: int) -> Handle:
@@ -223,7 +237,7 @@ def cq_column_create_dict(ctx, strings: Sequence[bytes], packed_codes, bit_width
     n_words = int(w.shape[0]) if not _is_dev(w) else int(w.numel())
     _check(lib.cq_column_create_dict(ctx.ptr, C.addressof(bb), offs.ctypes.data, len(strings), _ptr(w), n_words,
                                      int(bit_width), int(n_rows), _mem(w), C.byref(out)))
-    return Handle(out.value, lib.cq_column_destroy, [w] if _is_dev(w) else [])
+    return Handle(out.value, lib.cq_column_destroy, [ctx] + ([w] if _is_dev(w) else []))
 
 
 def cq_column_create_index(ctx, values, positions, default_value: int, n_rows: int) -> Handle:
@@ -231,7 +245,7 @@ def cq_column_create_index(ctx, values, positions, default_value: int, n_rows: i
     out = C.c_void_p()
     _check(lib.cq_column_create_index(ctx.ptr, _dt(v), _ptr(v), _dt(p), _ptr(p), int(p.shape[0]),
                                       int(default_value), int(n_rows), _mem(v, p), C.byref(out)))
-    return Handle(out.value, lib.cq_column_destroy, [v, p] if _is_dev(v) else [])
+    return Handle(out.value, lib.cq_column_destroy, [ctx] + ([v, p] if _is_dev(v) else []))
 
 
 def cq_column_create_bitpacked(ctx, words, bit_width: int, base: int, n_rows: int, logical=CQ_I64) -> Handle:
@@ -240,14 +254,14 @@ def cq_column_create_bitpacked(ctx, words, bit_width: int, base: int, n_rows: in
     n_words = int(w.shape[0]) if not _is_dev(w) else int(w.numel())
     _check(lib.cq_column_create_bitpacked(ctx.ptr, logical, _ptr(w), n_words, int(bit_width), int(base),
                                           int(n_rows), _mem(w), C.byref(out)))
-    return Handle(out.value, lib.cq_column_destroy, [w] if _is_dev(w) else [])
+    return Handle(out.value, lib.cq_column_destroy, [ctx] + ([w] if _is_dev(w) else []))
 
 
 def cq_column_create_plain(ctx, values) -> Handle:
     v = _contig(values)
     out = C.c_void_p()
     _check(lib.cq_column_create_plain(ctx.ptr, _dt(v), _ptr(v), int(v.shape[0]), _mem(v), C.byref(out)))
-    return Handle(out.value, lib.cq_column_destroy, [v] if _is_dev(v) else [])
+    return Handle(out.value, lib.cq_column_destroy, [ctx] + ([v] if _is_dev(v) else []))
 
 
 def cq_column_device_bytes(col) -> int:
@@ -260,7 +274,7 @@ def cq_table_bind(ctx, cols: Sequence[Handle]) -> Handle:
     arr = (C.c_void_p * len(cols))(*[c.ptr for c in cols])
     out = C.c_void_p()
     _check(lib.cq_table_bind(ctx.ptr, C.addressof(arr), len(cols), C.byref(out)))
-    return Handle(out.value, lib.cq_table_destroy, list(cols))
+    return Handle(out.value, lib.cq_table_destroy, [ctx] + list(cols))
 
 
 # ---------------------------------------------------------------- plans

@@ -6,6 +6,7 @@
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -164,14 +165,35 @@ extern "C" int cq_ctx_create(int device, void* cuda_stream, cq_ctx** out) {
   return CQ_OK;
 }
 
-extern "C" int cq_ctx_destroy(cq_ctx* ctx) {
-  clear_error();
-  if (!ctx) return CQ_OK;
+namespace cq {
+void ctx_release(cq_ctx* ctx) {
+  if (--ctx->refs > 0) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   if (!ctx->graphs.empty()) cudaDeviceSynchronize();   // batch graphs may still be running
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
+}
+
+void clear_stale_error(const char* where) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    static const bool dbg = getenv("CQ_DEBUG") != nullptr;
+    if (dbg) fprintf(stderr, "cq: stale CUDA error before %s: %s\n", where, cudaGetErrorString(e));
+  }
+}
+}  // namespace cq
+
+cq_column::~cq_column() {
+  if (ctx) ctx_release(ctx);
+}
+
+// The context lives on while columns created in it do (tables and results
+// hold their columns), whatever order the handles are destroyed in.
+extern "C" int cq_ctx_destroy(cq_ctx* ctx) {
+  clear_error();
+  if (!ctx) return CQ_OK;
+  ctx_release(ctx);
   return CQ_OK;
 }
 
@@ -187,6 +209,7 @@ static int new_column(cq_ctx* ctx, uint8_t enc, uint64_t n_rows, cq_column** out
   *out = nullptr;
   c->reset(new cq_column);
   (*c)->ctx = ctx;
+  ctx->refs++;
   (*c)->enc = enc;
   (*c)->n_rows = n_rows;
   CQ_CUDA(cudaSetDevice(ctx->device));
@@ -1031,6 +1054,7 @@ void attach_outputs(cq_result* r, const Planned& P) {
 // init -> fused kernel -> finalize on `s`.
 static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r) {
   QueryDesc& q = P.q;
+  clear_stale_error("a query launch");
   const QueryBlock L = query_block_layout(P, true);
   void* base = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync(&base, L.total, ctx->pool, s);
@@ -1044,12 +1068,17 @@ static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r)
     e = cudaMemcpyAsync(b + L.aux, P.aux.data(), 4 * P.aux.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "aux upload failed: %s", cudaGetErrorString(e));
   }
+  const char* step = "init";
   e = launch_init_global(q, s);
-  if (e == cudaSuccess) e = cudaEventRecord(r->ev_k0, s);
-  if (e == cudaSuccess) e = launch_query(q, s, ctx->num_sms, P.ctas_per_sm, P.grid_ctas);
-  if (e == cudaSuccess) e = cudaEventRecord(r->ev_k1, s);
-  if (e == cudaSuccess) e = launch_finalize(q, s);
-  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  if (e == cudaSuccess && (step = "event", true)) e = cudaEventRecord(r->ev_k0, s);
+  if (e == cudaSuccess && (step = "fused kernel", true))
+    e = launch_query(q, s, ctx->num_sms, P.ctas_per_sm, P.grid_ctas);
+  if (e == cudaSuccess && (step = "event", true)) e = cudaEventRecord(r->ev_k1, s);
+  if (e == cudaSuccess && (step = "finalize", true)) e = launch_finalize(q, s);
+  if (e != cudaSuccess)
+    return set_error(CQ_ERR_CUDA, "%s launch failed: %s (tile %u, %llu tiles, %llu groups, %u B shared)", step,
+                     cudaGetErrorString(e), q.tile_rows, (unsigned long long)q.n_tiles,
+                     (unsigned long long)q.n_groups, q.smem_bytes);
   attach_outputs(r, P);
   return CQ_OK;
 }

@@ -202,6 +202,7 @@ struct TunedShape {  // autotuner choice for a batch signature
 }  // namespace cq
 
 struct cq_ctx {
+  std::atomic<int> refs{1};  // the creator's reference plus one per live column
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaMemPool_t pool = nullptr;
@@ -236,6 +237,7 @@ struct cq_column {
   uint32_t n_entries = 0;
   cq::ColumnStats stats;
   uint64_t device_bytes = 0;
+  ~cq_column();              // drops the column's reference to its context
 };
 
 struct cq_table {
@@ -269,6 +271,13 @@ struct cq_result {
 };
 
 namespace cq {
+
+// Drop one reference to the context; the last one tears it down.
+void ctx_release(cq_ctx* ctx);
+
+// Clear a non-sticky error left by an earlier runtime call, so that the
+// error read after a launch belongs to that launch (CQ_DEBUG=1 reports it).
+void clear_stale_error(const char* where);
 
 // error reporting (thread-local message)
 int set_error(int status, const char* fmt, ...);

@@ -114,6 +114,9 @@ static int acquire_graph(cq_ctx* ctx, size_t bytes, unsigned grid, BatchGraph** 
       if (g->filling || g->cap < bytes || g->grid != grid) continue;
       // pass 0 takes an idle graph; pass 1 waits for the upload of a busy one
       const cudaError_t q = cudaEventQuery(g->uploaded);
+      if (q != cudaSuccess && q != cudaErrorNotReady)
+        return set_error(CQ_ERR_CUDA, "batch graph state: %s", cudaGetErrorString(q));
+      if (q == cudaErrorNotReady) (void)cudaGetLastError();   // not an error: clear it
       if (q == cudaErrorNotReady && pass == 0) continue;
       g->filling = true;
       BatchGraph* r = g;
@@ -278,6 +281,7 @@ static int run_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, 
   memcpy(h, &ctl, sizeof(ctl));
   if (!items.empty()) memcpy(h + off_items, items.data(), items.size() * sizeof(BatchItem));
   // ---- replay: upload only the bytes in use
+  clear_stale_error("a batch launch");
   e = cudaGraphExecMemcpyNodeSetParams1D(g->exec, g->upload, g->dev, g->host, bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaEventRecord(sh->ev_start, s);
   if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, s);

@@ -443,16 +443,9 @@ def nested(n_rows: int, seed: int = DEFAULT_SEED, lo3: int = 200, hi3: int = 699
     nested_plan(..., lean=True)).
     Query: SELECT c2, c4, SUM(c7), SUM(c8) WHERE c3 BETWEEN lo3 AND hi3
            GROUP BY c2, c4."""
-    rng = np.random.default_rng([seed, 3])
-    ed = np.int32 if n_rows < 2**31 else np.int64
-    e1 = _nested_ends(rng, n_rows, 1e6, None, ed)
-    e2 = _nested_ends(rng, n_rows, 1e4, e1, ed)
-    e3 = _nested_ends(rng, n_rows, 1e2, e2, ed)
-    c1 = RLE(np.arange(e1.shape[0], dtype=np.int32), e1, n_rows)
-    c2 = RLE(_increasing_in_parent(rng, e2, e1, 10_000).astype(np.int32), e2, n_rows)
-    c3 = RLE(_increasing_in_parent(rng, e3, e2, 1_000).astype(np.int32), e3, n_rows)
+    c1, c2, c3 = nested_runs(n_rows, seed)
     rows = np.arange(n_rows, dtype=np.int64)
-    c4 = make_dict([b"g%02d" % i for i in range(16)], nested_codes4_all(seed, e3, n_rows), 4)
+    c4 = make_dict(NESTED_DICT4, nested_codes4_all(seed, c3.run_ends, n_rows), 4)
     c7 = make_packed(nested_row_values(seed, 7, rows), 8, NESTED_BASE7, "i64")
     c8 = make_packed(nested_row_values(seed, 8, rows), 12, NESTED_BASE8, "i64")
     if lean:
@@ -462,6 +455,23 @@ def nested(n_rows: int, seed: int = DEFAULT_SEED, lo3: int = 200, hi3: int = 699
     c6 = make_dict([b"w%05d" % i for i in range(1 << 16)], nested_row_values(seed, 6, rows), 16)
     table = Table([c1, c2, c3, c4, c5, c6, c7, c8], n_rows, ["c1", "c2", "c3", "c4", "c5", "c6", "c7", "c8"])
     return table, nested_plan(lo3, hi3)
+
+
+NESTED_DICT4 = [b"g%02d" % i for i in range(16)]
+
+
+def nested_runs(n_rows: int, seed: int = DEFAULT_SEED):
+    """The three RLE columns c1, c2, c3 of the nested table (see nested);
+    drawn on the host, the per-row columns come from counter-based values."""
+    rng = np.random.default_rng([seed, 3])
+    ed = np.int32 if n_rows < 2**31 else np.int64
+    e1 = _nested_ends(rng, n_rows, 1e6, None, ed)
+    e2 = _nested_ends(rng, n_rows, 1e4, e1, ed)
+    e3 = _nested_ends(rng, n_rows, 1e2, e2, ed)
+    c1 = RLE(np.arange(e1.shape[0], dtype=np.int32), e1, n_rows)
+    c2 = RLE(_increasing_in_parent(rng, e2, e1, 10_000).astype(np.int32), e2, n_rows)
+    c3 = RLE(_increasing_in_parent(rng, e3, e2, 1_000).astype(np.int32), e3, n_rows)
+    return c1, c2, c3
 
 
 def nested_plan(lo3: int = 200, hi3: int = 699, lean: bool = False) -> Plan:
@@ -478,11 +488,11 @@ def partition_sizes(rng, n_parts: int, lo: float = 1e4, hi: float = 5e7) -> np.n
     return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_parts)).astype(np.int64)
 
 
-def batch_queries(rng, n_queries: int, n_parts: int):
+def batch_queries(rng, n_queries: int, n_parts: int, lean: bool = True):
     """The batched workload's query list: (partition, kind, plan) with kind
     "tiny" (A < t, t uniform in 0..99, GROUP BY B on the partition's
     two-RLE table) or "nested" (c3 BETWEEN lo AND lo + w on its nested
-    table), half each, partitions uniform."""
+    table, lean layout unless lean=False), half each, partitions uniform."""
     out = []
     for i in range(n_queries):
         part = int(rng.integers(0, n_parts))
@@ -491,7 +501,7 @@ def batch_queries(rng, n_queries: int, n_parts: int):
         else:
             lo = int(rng.integers(0, 1000))
             hi = min(999, lo + int(rng.integers(0, 1000)))
-            out.append((part, "nested", nested_plan(lo, hi)))
+            out.append((part, "nested", nested_plan(lo, hi, lean)))
     return out
 
 
