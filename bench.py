@@ -37,7 +37,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cq", choices=["cq", "reference"])
-    ap.add_argument("--workload", default="heterogeneous", choices=["heterogeneous", "tiny"])
+    ap.add_argument("--workload", default="heterogeneous", choices=["heterogeneous", "tiny", "nested", "batched"])
+    ap.add_argument("--queries", type=int, default=4096, help="batched: queries per batch")
+    ap.add_argument("--parts", type=int, default=256, help="batched: partitions in the pool")
+    ap.add_argument("--part-max", type=float, default=5e7, help="batched: largest partition (rows)")
+    ap.add_argument("--dts-sample", type=int, default=128,
+                    help="batched: queries timed on the decompress-then-scan path")
     ap.add_argument("--rows", type=int, default=0, help="override the workload's row count")
     ap.add_argument("--seed", type=int, default=20250611)
     ap.add_argument("--mode", default="fused", choices=["fused", "decompress_then_scan"])
@@ -58,6 +63,10 @@ def workload(args):
         n = args.rows or 1_000_000
         table, plan = dg.tiny_two_rle(n, seed=args.seed)
         name = f"tiny-two-rle-{n}"
+    elif args.workload == "nested":
+        # generated in device memory by run_cq (too large for the host)
+        n = args.rows or 20_000_000_000
+        return f"nested-lean-{n}", None, dg.nested_plan(lean=True)
     else:
         n = args.rows or 100_000_000
         table, plan = dg.heterogeneous(n, seed=args.seed)
@@ -178,10 +187,14 @@ def cpu_oracle_rate(table, plan, seconds: float):
 
 
 def run_reference(args):
+    from paper_2506_10092_gb300 import datagen as dg
     ws, rank, _ = dist()
     if rank != 0:
         return
     name, table, plan = workload(args)
+    if table is None:
+        # the nested table has no host copy at full size: time a same-shape sample
+        table, plan = dg.nested(min(args.rows or 20_000_000_000, 20_000_000), seed=args.seed, lean=True)
     from oracle import oracle
     cores = oracle.cores()
     probe = min(table.n_rows, 1_000_000)
@@ -232,9 +245,22 @@ def run_cq(args):
     stream = torch.cuda.Stream()
     name, table, plan = workload(args)
     used = dg.plan_columns(plan)
-    alg_bytes = dg.compressed_bytes(table, used)
     ctx = cq.cq_ctx_create(local, stream)
-    t, cols = cq.table_from(ctx, table)
+    dn = None
+    if table is None:
+        # nested table: RLE runs from the host, per-row columns generated on the device
+        from paper_2506_10092_gb300 import devgen
+        n_rows = args.rows or 20_000_000_000
+        t_gen = time.perf_counter()
+        dn = devgen.DeviceNested(cq, ctx, n_rows, seed=args.seed)
+        torch.cuda.synchronize()
+        t_gen = time.perf_counter() - t_gen
+        t = dn.table
+        alg_bytes = dn.query_bytes(plan)
+    else:
+        n_rows = table.n_rows
+        alg_bytes = dg.compressed_bytes(table, used)
+        t, cols = cq.table_from(ctx, table)
     ps = cq.PlanStruct(plan)
     opts = exec_opts(cq, args)
 
@@ -277,7 +303,7 @@ def run_cq(args):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         elapsed_ms = float(tt.item())
     ms_per_step = elapsed_ms / args.steps
-    value = table.n_rows * args.steps * ws / (elapsed_ms / 1000.0)
+    value = n_rows * args.steps * ws / (elapsed_ms / 1000.0)
     k_us = statistics.mean(kernel_us)
     peak, peak_src = measured_peak()
     achieved = alg_bytes / (k_us * 1e-6) / 1e9
@@ -286,7 +312,10 @@ def run_cq(args):
     # end to end through the public API: pinned host buffers -> columns ->
     # query -> result read back, every step
     e2e = None
-    if not args.no_e2e:
+    if dn is not None:
+        e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+               "note": "per-row columns are generated in device memory; the table has no host copy"}
+    elif not args.no_e2e:
         host = []
         h2d = 0
         for c in table.columns:
@@ -345,7 +374,10 @@ def run_cq(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cores, sample = cpu_oracle_rate(table, plan, args.cpu_seconds)
+        sample_table = table
+        if dn is not None:
+            sample_table = dg.nested_subtable(dn.runs, args.seed, [(0, min(n_rows, 20_000_000))])
+        rate, cores, sample = cpu_oracle_rate(sample_table, plan, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -353,7 +385,7 @@ def run_cq(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": name, "rows": table.n_rows, "compressed_bytes": alg_bytes, "groups": n_groups,
+            "config": {"workload": name, "rows": n_rows, "compressed_bytes": alg_bytes, "groups": n_groups,
                        "mode": args.mode, "parallelism": f"replicas{ws}",
                        "l2": "inputs larger than L2 (compressed columns exceed 129 MB); no flush"},
             "compressed_gbs": alg_bytes * args.steps * ws / (elapsed_ms / 1000.0) / 1e9,
@@ -373,10 +405,168 @@ def run_cq(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------- batched workload
+def _tiny_part(n, seed):
+    from paper_2506_10092_gb300 import datagen as dg
+    t, _ = dg.tiny_two_rle(int(n), seed=int(seed))
+    return t
+
+
+def build_pool(args, cq, ctx, torch):
+    """The partition pool of the batched workload: sizes log-uniform in
+    [1e4, part_max]; each partition holds the two-RLE table (drawn on the host
+    by a spawn process pool) and the nested table (RLE runs on the host,
+    per-row columns generated on the device)."""
+    import multiprocessing as mp
+    import numpy as np
+    from paper_2506_10092_gb300 import datagen as dg
+    from paper_2506_10092_gb300 import devgen
+    rng = np.random.default_rng([args.seed, 4])
+    sizes = dg.partition_sizes(rng, args.parts, 1e4, args.part_max)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        tiny = pool.starmap(_tiny_part, [(int(n), args.seed + 1000 + i) for i, n in enumerate(sizes)])
+    parts = []
+    for i, n in enumerate(sizes):
+        th, tcols = cq.table_from(ctx, tiny[i], device=True)
+        nest = devgen.DeviceNested(cq, ctx, int(n), seed=args.seed + 2000 + i)
+        parts.append({"n": int(n), "tiny": (tiny[i], th, tcols), "nested": nest})
+    torch.cuda.synchronize()
+    return sizes, parts
+
+
+def query_bytes(part, kind, plan):
+    """Compressed bytes the query reads (its referenced columns)."""
+    from paper_2506_10092_gb300 import datagen as dg
+    if kind == "tiny":
+        return dg.compressed_bytes(part["tiny"][0], dg.plan_columns(plan))
+    return part["nested"].query_bytes(plan)
+
+
+def run_batched(args):
+    import numpy as np
+    import torch
+    from paper_2506_10092_gb300 import cq
+    from paper_2506_10092_gb300 import datagen as dg
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = cq.cq_ctx_create(local, stream)
+    t_gen = time.perf_counter()
+    sizes, parts = build_pool(args, cq, ctx, torch)
+    t_gen = time.perf_counter() - t_gen
+    rng = np.random.default_rng([args.seed, 5])
+    qs = dg.batch_queries(rng, args.queries, len(parts), lean=True)
+    handles, plans, rows, nbytes = [], [], 0, 0
+    for part_i, kind, plan in qs:
+        part = parts[part_i]
+        handles.append(part["tiny"][1] if kind == "tiny" else part["nested"].table)
+        plans.append(cq.PlanStruct(plan))
+        rows += part["n"]
+        nbytes += query_bytes(part, kind, plan)
+    torch.cuda.synchronize()
+
+    # autotune the batch shape, then time batches with the tuned shape
+    best, tuned_us = cq.cq_batch_tune(handles, plans, stream=stream)
+
+    def batch_step():
+        return cq.cq_batch_run(handles, plans, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        for r in batch_step():
+            r.close()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.2)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    held = []
+    t_host = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        held.append(batch_step())
+    ev1.record(stream)
+    ev1.synchronize()
+    t_host = time.perf_counter() - t_host
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    launch_us = [cq.cq_result_device_time_us(h[0]) for h in held]
+    for h in held:
+        for r in h:
+            r.close()
+    held = None
+    peak, peak_src = measured_peak()
+
+    # one query at a time: the same queries, one cq_query_run each
+    ev0.record(stream)
+    solo = [cq.cq_query_run(h, p, stream=stream) for h, p in zip(handles, plans)]
+    ev1.record(stream)
+    ev1.synchronize()
+    solo_s = ev0.elapsed_time(ev1) / 1000.0
+    for r in solo:
+        r.close()
+
+    # decompress-then-scan on a sample of the queries
+    n_dts = min(args.dts_sample, len(handles))
+    dts_opts = cq.exec_options(mode=cq.CQ_EXEC_DECOMPRESS_THEN_SCAN)
+    dts_rows = sum(parts[q[0]]["n"] for q in qs[:n_dts])
+    ev0.record(stream)
+    dts = [cq.cq_query_run(handles[i], plans[i], stream=stream, opts=dts_opts) for i in range(n_dts)]
+    ev1.record(stream)
+    ev1.synchronize()
+    dts_s = ev0.elapsed_time(ev1) / 1000.0
+    for r in dts:
+        r.close()
+
+    # end to end: plan + launch + every result fetched to the host, per batch
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.e2e_steps):
+        res = batch_step()
+        for r in res:
+            d2h = d2h + sum(o.nbytes for o in cq.fetch_all(r))
+            r.close()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    d2h //= args.e2e_steps
+
+    per_step = elapsed / args.steps
+    line = {
+        "metric": METRIC, "value": rows / per_step, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step * 1000, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"batched-{args.queries}q-{len(parts)}parts", "queries": args.queries,
+                   "partitions": len(parts), "pool_rows": int(sizes.sum()), "logical_rows_per_batch": rows,
+                   "compressed_bytes_per_batch": nbytes, "tuned": {"tile_rows": best.tile_rows,
+                                                                    "items_per_cta": best.items_per_cta,
+                                                                    "launch_us": tuned_us},
+                   "pool_generation_s": t_gen, "parallelism": "replicas1",
+                   "l2": "each batch reads far more than L2 (129 MB); no flush"},
+        "queries_per_s": args.queries / per_step,
+        "compressed_gbs": nbytes / per_step / 1e9,
+        "pct_hbm_peak": nbytes / per_step / 1e9 / peak,
+        "launch_us_median": statistics.median(launch_us),
+        "host_submit_ms_per_batch": 1000 * t_host / args.steps,
+        "one_query_at_a_time": {"queries_per_s": len(handles) / solo_s, "rows_per_s": rows / solo_s,
+                                "speedup_of_batch": solo_s / per_step},
+        "decompress_then_scan": {"queries": n_dts, "queries_per_s": n_dts / dts_s, "rows_per_s": dts_rows / dts_s},
+        "roofline": {"bound": "hbm", "achieved": nbytes / per_step / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": nbytes / per_step / 1e9 / peak, "traffic": None, "kernel": "batch_query_kernel",
+                     "peak_source": f"{peak_src} hbm_gbs", "algorithmic_bytes_per_launch": nbytes},
+        "e2e": {"value": rows / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
+                "note": "tables resident; per batch: plan, launch, fetch every result"},
+        "clocks": clk,
+        "gpu_launches": 5 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_cq(args)
 

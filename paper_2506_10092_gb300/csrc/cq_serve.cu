@@ -20,8 +20,10 @@ namespace cq {
 
 // ------------------------------------------------------------------ launch graphs
 // One instantiated launch graph and its control block.  The graph's first
-// node uploads the pinned staging copy of the control block; an event node
-// right after it tells the host when the staging copy may be rewritten.
+// node uploads the pinned staging copy of the control block.  An event
+// recorded on the launching stream after each replay tells the host when
+// the staging copy may be rewritten (an event recorded inside the graph
+// cannot be queried from the host).
 struct BatchGraph {
   int device = 0;
   size_t cap = 0;                 // control-block bytes
@@ -31,14 +33,14 @@ struct BatchGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t upload = nullptr;
-  cudaEvent_t uploaded = nullptr;
+  cudaEvent_t done = nullptr;      // recorded after the last replay
   bool filling = false;           // a host thread is writing the staging copy
   ~BatchGraph() {
     cudaSetDevice(device);
-    if (uploaded) cudaEventSynchronize(uploaded);
+    if (done) cudaEventSynchronize(done);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    if (uploaded) cudaEventDestroy(uploaded);
+    if (done) cudaEventDestroy(done);
     if (dev) cudaFree(dev);
     if (host) cudaFreeHost(host);
   }
@@ -80,7 +82,6 @@ static int capture_graph(cq_ctx* ctx, BatchGraph* g) {
   CQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->dev, g->host, g->cap, cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaEventRecord(g->uploaded, cs);
   if (e == cudaSuccess)
     e = launch_batch(reinterpret_cast<BatchCtl*>(g->dev), cs, g->grid, ctx->batch_smem, (unsigned)ctx->num_sms * 2);
   cudaGraph_t graph = nullptr;
@@ -112,8 +113,8 @@ static int acquire_graph(cq_ctx* ctx, size_t bytes, unsigned grid, BatchGraph** 
   for (int pass = 0; pass < 2; ++pass) {
     for (auto& g : ctx->graphs) {
       if (g->filling || g->cap < bytes || g->grid != grid) continue;
-      // pass 0 takes an idle graph; pass 1 waits for the upload of a busy one
-      const cudaError_t q = cudaEventQuery(g->uploaded);
+      // pass 0 takes an idle graph; pass 1 waits for a busy one
+      const cudaError_t q = cudaEventQuery(g->done);
       if (q != cudaSuccess && q != cudaErrorNotReady)
         return set_error(CQ_ERR_CUDA, "batch graph state: %s", cudaGetErrorString(q));
       if (q == cudaErrorNotReady) (void)cudaGetLastError();   // not an error: clear it
@@ -121,7 +122,7 @@ static int acquire_graph(cq_ctx* ctx, size_t bytes, unsigned grid, BatchGraph** 
       g->filling = true;
       BatchGraph* r = g;
       lk.unlock();
-      if (q == cudaErrorNotReady) cudaEventSynchronize(r->uploaded);
+      if (q == cudaErrorNotReady) cudaEventSynchronize(r->done);
       *out = r;
       return CQ_OK;
     }
@@ -134,7 +135,7 @@ static int acquire_graph(cq_ctx* ctx, size_t bytes, unsigned grid, BatchGraph** 
   g->grid = grid;
   CQ_CUDA(cudaMalloc(&g->dev, g->cap));
   CQ_CUDA(cudaMallocHost(&g->host, g->cap));
-  CQ_CUDA(cudaEventCreateWithFlags(&g->uploaded, cudaEventDisableTiming));
+  CQ_CUDA(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming));
   int rc = capture_graph(ctx, g.get());
   if (rc != CQ_OK) return rc;
   g->filling = true;
@@ -285,6 +286,7 @@ static int run_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, 
   e = cudaGraphExecMemcpyNodeSetParams1D(g->exec, g->upload, g->dev, g->host, bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaEventRecord(sh->ev_start, s);
   if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(g->done, s);
   if (e == cudaSuccess) e = cudaEventRecord(sh->ev_done, s);
   release_graph(ctx, g);
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
@@ -378,6 +380,7 @@ extern "C" int cq_batch_tune(uint32_t n, cq_table* const* tables, const cq_plan*
   std::vector<cq_result*> res(n, nullptr);
   double best_t = 1e300;
   uint32_t best_tile = 0, best_ipc = 4;
+  std::string first_failure;
   for (uint32_t tile : kTiles)
     for (uint32_t ipc : kIpc) {
       double t_min = 1e300;
@@ -386,6 +389,7 @@ extern "C" int cq_batch_tune(uint32_t n, cq_table* const* tables, const cq_plan*
         rc = run_batch(n, tables, plans, tile, ipc, s, res.data());
         if (rc != CQ_OK) {
           ok = false;   // e.g. a tile that leaves no room in shared memory
+          if (first_failure.empty()) first_failure = cq_last_error();
           break;
         }
         double us = 0;
@@ -405,7 +409,9 @@ extern "C" int cq_batch_tune(uint32_t n, cq_table* const* tables, const cq_plan*
       }
     }
   clear_error();
-  if (best_t >= 1e300) return set_error(CQ_ERR_UNSUPPORTED, "no candidate shape fits this batch");
+  if (best_t >= 1e300)
+    return set_error(CQ_ERR_UNSUPPORTED, "no candidate shape runs this batch (first failure: %s)",
+                     first_failure.c_str());
   {
     const uint64_t key = batch_key(n, tables, plans);
     std::lock_guard<std::mutex> lk(ctx->batch_mu);

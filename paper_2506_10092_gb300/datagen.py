@@ -360,7 +360,11 @@ def _nested_ends(rng, n_rows: int, mean: float, parent_ends: Optional[np.ndarray
     own = geometric_ends(rng, n_rows, mean, np.int64)
     if parent_ends is None:
         return own.astype(end_dtype)
-    return np.union1d(own, parent_ends.astype(np.int64)).astype(end_dtype)
+    # merge two sorted unique arrays: insert the parent ends the child lacks
+    par = parent_ends.astype(np.int64)
+    pos = np.searchsorted(own, par, side="left")
+    new = (pos >= own.shape[0]) | (own[np.minimum(pos, own.shape[0] - 1)] != par)
+    return np.insert(own, pos[new], par[new]).astype(end_dtype)
 
 
 def _increasing_in_parent(rng, ends: np.ndarray, parent_ends: np.ndarray, domain: int) -> np.ndarray:
@@ -472,6 +476,45 @@ def nested_runs(n_rows: int, seed: int = DEFAULT_SEED):
     c2 = RLE(_increasing_in_parent(rng, e2, e1, 10_000).astype(np.int32), e2, n_rows)
     c3 = RLE(_increasing_in_parent(rng, e3, e2, 1_000).astype(np.int32), e3, n_rows)
     return c1, c2, c3
+
+
+def _rle_rows(col: RLE, ranges) -> RLE:
+    """The rows of the given sorted disjoint ranges [(start, end), ...] of an
+    RLE column, concatenated, as an RLE column (runs cut at range edges)."""
+    ends = col.run_ends.astype(np.int64)
+    vals, out_ends, base = [], [], 0
+    for a, b in ranges:
+        i0 = int(np.searchsorted(ends, a, side="right"))
+        i1 = int(np.searchsorted(ends, b, side="left"))
+        e = np.minimum(ends[i0:i1 + 1], b) - a + base
+        vals.append(col.run_values[i0:i1 + 1])
+        out_ends.append(e)
+        base += b - a
+    v = np.concatenate(vals) if vals else col.run_values[:0]
+    e = np.concatenate(out_ends) if out_ends else np.zeros(0, np.int64)
+    return RLE(v.copy(), e.astype(np.int64), int(base))
+
+
+def nested_subtable(runs, seed: int, ranges) -> Table:
+    """The lean nested table restricted to the given sorted disjoint row
+    ranges of the full table (rows concatenated in order): RLE columns cut at
+    the range edges, per-row columns evaluated at the original row numbers.
+    With ranges [(0, n)] it is the table's first n rows."""
+    c1, c2, c3 = (_rle_rows(c, ranges) for c in runs)
+    rows = np.concatenate([np.arange(a, b, dtype=np.int64) for a, b in ranges]) if ranges else np.zeros(0, np.int64)
+    n = int(rows.shape[0])
+    c4 = make_dict(NESTED_DICT4, nested_codes4(seed, runs[2].run_ends, rows), 4)
+    c7 = make_packed(nested_row_values(seed, 7, rows), 8, NESTED_BASE7, "i64")
+    c8 = make_packed(nested_row_values(seed, 8, rows), 12, NESTED_BASE8, "i64")
+    return Table([c1, c2, c3, c4, c7, c8], n, ["c1", "c2", "c3", "c4", "c7", "c8"])
+
+
+def value_ranges(col: RLE, value: int):
+    """Row ranges [(start, end), ...] of the runs of an RLE column holding `value`."""
+    ends = col.run_ends.astype(np.int64)
+    starts = np.concatenate([[0], ends[:-1]])
+    idx = np.flatnonzero(col.run_values == value)
+    return [(int(starts[i]), int(ends[i])) for i in idx]
 
 
 def nested_plan(lo3: int = 200, hi3: int = 699, lean: bool = False) -> Plan:

@@ -87,6 +87,16 @@ class DeviceNested:
         self.columns = handles
         self.table = cq.cq_table_bind(ctx, handles)
 
+    def query_bytes(self, plan) -> int:
+        """Compressed bytes a plan over this table reads (its columns)."""
+        total = 0
+        for c in dg.plan_columns(plan):
+            if c < 3:
+                total += self.runs[c].run_values.nbytes + self.runs[c].run_ends.nbytes
+            else:
+                total += (self.n_rows * {3: 4, 4: 8, 5: 12}[c] + 7) // 8
+        return total
+
     def host_table(self) -> dg.Table:
         """The same table on the host (all rows; for tests at small sizes)."""
         import numpy as np

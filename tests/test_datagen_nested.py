@@ -82,3 +82,24 @@ def test_batch_queries_alternate_templates():
     assert all(0 <= p < 8 for p, _, _ in qs)
     sizes = dg.partition_sizes(rng, 1000)
     assert sizes.min() >= 10_000 and sizes.max() <= 50_000_000
+
+
+def test_subtable_is_the_selected_rows():
+    n = 50_000
+    full, _ = dg.nested(n, seed=6, lean=True)
+    runs = full.columns[:3]
+    ranges = [(0, 100), (1234, 5000), (49_990, 50_000)]
+    sub = dg.nested_subtable(runs, 6, ranges)
+    rows = np.concatenate([np.arange(a, b) for a, b in ranges])
+    from oracle import oracle
+    for j in range(6):
+        np.testing.assert_array_equal(oracle.decode(sub.columns[j]), oracle.decode(full.columns[j])[rows])
+    pre = dg.nested_subtable(runs, 6, [(0, n)])
+    for j in range(6):
+        np.testing.assert_array_equal(oracle.decode(pre.columns[j]), oracle.decode(full.columns[j]))
+    c2 = runs[1]
+    v = int(c2.run_values[c2.run_values.shape[0] // 2])
+    vr = dg.value_ranges(c2, v)
+    dec = oracle.decode(c2)
+    assert sum(b - a for a, b in vr) == int((dec == v).sum())
+    assert all((dec[a:b] == v).all() for a, b in vr)
