@@ -488,18 +488,20 @@ __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
 }
 
 // ------------------------------------------------------------------ tile phases
-// Filter: bit g of the result says item (wbase + 32 g + lane) passes every
-// predicate.  Items are rows (row mode) or aligned segments (segment mode,
+// Filter: bit g of the result says item (wbase + g * gstride + lane) passes
+// every predicate.  Callers deal 32-item groups to warps round-robin
+// (wbase = 32 * warp, gstride = 32 * warps), so that the clustered passing
+// rows of sorted data spread evenly over the warps.  Items are rows (row mode) or aligned segments (segment mode,
 // item -> first row through seg[]).  Predicates are evaluated one at a time
 // over all of the warp's items, with the column / test dispatch hoisted out of
 // the item loop.
 template <bool SEG, int GPW>
 __device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileView& t, const uint16_t* seg,
-                                                 uint32_t wbase, uint32_t n_items) {
+                                                 uint32_t wbase, uint32_t gstride, uint32_t n_items) {
   const int lane = threadIdx.x & 31;
   uint32_t valid = 0;
 #pragma unroll
-  for (int g = 0; g < GPW; ++g) valid |= (wbase + g * 32 + lane < n_items ? 1u : 0u) << g;
+  for (int g = 0; g < GPW; ++g) valid |= (wbase + g * gstride + lane < n_items ? 1u : 0u) << g;
   uint32_t pm = valid;
   for (int pi = 0; pi < q.n_preds; ++pi) {
     if (!__any_sync(0xFFFFFFFFu, pm != 0)) break;
@@ -518,7 +520,7 @@ __device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileV
 #pragma unroll 2
           for (int g = 0; g < GPW; ++g) {
             if (!((pm >> g) & 1u)) continue;
-            const uint32_t o = (uint32_t)seg[wbase + g * 32 + lane];
+            const uint32_t o = (uint32_t)seg[wbase + g * gstride + lane];
             bool ok;
             if constexpr (K >= PT_RANGE32) ok = pred_test32<K>(p, t.aux, col_raw32<E>(c, t, o));
             else ok = pred_test<K>(p, t.aux, col_raw<E>(c, t, o));
@@ -530,7 +532,7 @@ __device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileV
           // and the unrolled loads of several groups overlap
 #pragma unroll 4
           for (int g = 0; g < GPW; ++g) {
-            const uint32_t o = wbase + g * 32 + lane;
+            const uint32_t o = wbase + g * gstride + lane;
             bool ok;
             if constexpr (K >= PT_RANGE32) ok = pred_test32<K>(p, t.aux, col_raw32<E>(c, t, o));
             else ok = pred_test<K>(p, t.aux, col_raw<E>(c, t, o));
@@ -545,7 +547,7 @@ __device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileV
 
 // Compact the passing items of this warp into list[] (item indices).
 template <int GPW>
-__device__ __forceinline__ uint32_t compact(uint32_t pm, uint32_t wbase, uint16_t* list) {
+__device__ __forceinline__ uint32_t compact(uint32_t pm, uint32_t wbase, uint32_t gstride, uint16_t* list) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t n = 0;
@@ -553,7 +555,7 @@ __device__ __forceinline__ uint32_t compact(uint32_t pm, uint32_t wbase, uint16_
   for (int g = 0; g < GPW; ++g) {
     const bool ok = (pm >> g) & 1u;
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
-    if (ok) list[n + __popc(bal & lt)] = (uint16_t)(wbase + g * 32 + lane);
+    if (ok) list[n + __popc(bal & lt)] = (uint16_t)(wbase + g * gstride + lane);
     n += __popc(bal);
   }
   __syncwarp();

@@ -204,7 +204,7 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
 
   uint32_t rows_since_flush = 0;
   uint16_t* mylist = sm.clist + (helper ? 0 : warp) * (GPW * 32);
-  const uint32_t wbase = warp * (GPW * 32);
+  const uint32_t wbase = warp * 32, gstride = NCW * 32;
 
   for (unsigned long long t = t_begin; t < t_end; ++t) {
     const unsigned long long s = t * T;
@@ -221,8 +221,8 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
       tv.stage = sm.stage + (size_t)st * q.stage_bytes;
       tv.aux = aux_smem ? sm.aux : q.aux;
       tv.nwords = nwords;
-      const uint32_t pm = phase_filter<false, GPW>(q, tv, nullptr, wbase, rows);
-      const uint32_t n_pass = compact<GPW>(pm, wbase, mylist);
+      const uint32_t pm = phase_filter<false, GPW>(q, tv, nullptr, wbase, gstride, rows);
+      const uint32_t n_pass = compact<GPW>(pm, wbase, gstride, mylist);
       phase_aggregate<false, 2>(q, sm, tv, nullptr, mylist, n_pass, s);
     } else if (nb && t + 1 < t_end) {
       helper_build(q, sm, buf ^ 1, e, (e + T < q.n_rows) ? e + T : q.n_rows, nwords);

@@ -40,8 +40,13 @@ __device__ inline void build_bitmaps(const QueryDesc& q, const Smem& sm, unsigne
     const bool is_rle = cd->enc == ENC_RLE;
     const unsigned long long cur = sm.tcur[j];
     uint32_t* B = sm.bm + j * nwords;
+    // A column is done once an entry at or past the tile end was seen.  The
+    // done flags are written only before the first barrier of an iteration
+    // and read only between its two barriers, so every warp of a column
+    // sees the same state: a warp must not skip its entries of an iteration
+    // because another warp of the column stopped in that same iteration.
+    bool col_done = false;
     for (int it = 0;; ++it) {
-      const int col_done = __shfl_sync(0xFFFFFFFFu, sm.flags[j], 0);
       if (active && !col_done) {
         const unsigned long long idx = cur + ((unsigned long long)it * G + gi) * 32 + lane;
         bool stop = false;
@@ -67,6 +72,7 @@ __device__ inline void build_bitmaps(const QueryDesc& q, const Smem& sm, unsigne
       __syncthreads();
       bool all = true;
       for (int c = 0; c < nb; ++c) all = all && sm.flags[c];
+      col_done = sm.flags[j] != 0;
       __syncthreads();
       if (all) break;
     }
@@ -198,7 +204,7 @@ __device__ __forceinline__ void seg_range(const QueryDesc& q, const Smem& sm, un
   tv.nwords = nwords;
   uint32_t rows_since_flush = 0;
   uint16_t* mylist = sm.clist + (warp < kWarps ? warp : 0) * (GPW * 32);
-  const uint32_t wbase = warp * (GPW * 32);
+  const uint32_t wbase = warp * 32, gstride = kWarps * 32;
 
   for (unsigned long long t = t_begin; t < t_end; ++t) {
     const unsigned long long s = t * T;
@@ -207,8 +213,8 @@ __device__ __forceinline__ void seg_range(const QueryDesc& q, const Smem& sm, un
     build_bitmaps(q, sm, s, e, nwords);
     build_segments(q, sm, nwords, rows);
     if (warp < kWarps) {
-      const uint32_t pm = phase_filter<true, GPW>(q, tv, sm.seg, wbase, (uint32_t)sm.misc[2]);
-      const uint32_t n_pass = compact<GPW>(pm, wbase, mylist);
+      const uint32_t pm = phase_filter<true, GPW>(q, tv, sm.seg, wbase, gstride, (uint32_t)sm.misc[2]);
+      const uint32_t n_pass = compact<GPW>(pm, wbase, gstride, mylist);
       phase_aggregate<true, 2>(q, sm, tv, sm.seg, mylist, n_pass, s);
     }
     __syncthreads();

@@ -133,3 +133,16 @@ def test_autotuner_choice_is_used_and_exact(cq, ctx, pool, oracle_mod):
     res = cq.cq_batch_run(handles, plans)     # no options: the tuned shape
     for i, r in enumerate(res):
         check(cq.fetch_all(r), oracle_mod.query(tabs[i], plans[i]), f"query {i}")
+
+
+def test_repeated_mixed_batches_are_exact(cq, ctx, pool, oracle_mod):
+    """Twenty replays of one mixed batch: every result exact every time (a
+    race between warps building one column's tile bitmap once showed up
+    here as rare, timing-dependent wrong counts)."""
+    rng = np.random.default_rng(4096 + 2 + 11)
+    tabs, handles, plans = workload(rng, pool, 40)
+    refs = [oracle_mod.query(t, p) for t, p in zip(tabs, plans)]
+    opts = cq.exec_options(tile_rows=4096, items_per_cta=2)
+    for rep in range(20):
+        for i, r in enumerate(cq.cq_batch_run(handles, plans, opts=opts)):
+            check(cq.fetch_all(r), refs[i], f"replay {rep} query {i}")
