@@ -37,7 +37,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cq", choices=["cq", "reference"])
-    ap.add_argument("--workload", default="heterogeneous", choices=["heterogeneous", "tiny", "nested", "batched"])
+    ap.add_argument("--workload", default="heterogeneous",
+                    choices=["heterogeneous", "tiny", "nested", "batched", "serving"])
+    ap.add_argument("--rates", default="100,500,1000,2000,5000", help="serving: arrival rates (queries/s)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving: arrivals per rate and mode")
+    ap.add_argument("--serve-modes", default="batched,one_at_a_time,decompress_then_scan")
     ap.add_argument("--queries", type=int, default=4096, help="batched: queries per batch")
     ap.add_argument("--parts", type=int, default=256, help="batched: partitions in the pool")
     ap.add_argument("--part-max", type=float, default=5e7, help="batched: largest partition (rows)")
@@ -561,10 +565,125 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- serving workload
+def run_serving(args):
+    """Poisson arrivals over resident tables (60% two-RLE 1M-row table, 30%
+    heterogeneous 100M-row table, 10% nested partitions), served by the
+    continuous-batching loop, by one query at a time, and by one query at a
+    time on the decompress-then-scan path; p50 / p99 latency and achieved
+    queries/s per arrival rate."""
+    import threading
+    import numpy as np
+    import torch
+    from paper_2506_10092_gb300 import cq, devgen
+    from paper_2506_10092_gb300 import datagen as dg
+
+    torch.cuda.set_device(0)
+    ctx = cq.cq_ctx_create(0)
+    tiny_t, _ = dg.tiny_two_rle(1_000_000, seed=args.seed)
+    het_t, het_plan = dg.heterogeneous(100_000_000, seed=args.seed)
+    tiny = cq.table_from(ctx, tiny_t)
+    het = cq.table_from(ctx, het_t)
+    del het_t
+    rng = np.random.default_rng([args.seed, 6])
+    nest = [devgen.DeviceNested(cq, ctx, int(n), seed=args.seed + 3000 + i)
+            for i, n in enumerate(dg.partition_sizes(rng, 16, 1e4, args.part_max))]
+    torch.cuda.synchronize()
+
+    def request(r):
+        u = r.random()
+        if u < 0.6:
+            return tiny[0], cq.PlanStruct(dg.tiny_plan(int(r.integers(0, 100))))
+        if u < 0.9:
+            lo = int(r.integers(0, 750_001))
+            return het[0], cq.PlanStruct(dg.Plan([het_plan.preds[0], dg.Pred(3, "between", lo, lo + 249_999)],
+                                                 het_plan.group_by, het_plan.aggs))
+        lo = int(r.integers(0, 1000))
+        return nest[int(r.integers(0, len(nest)))].table, cq.PlanStruct(dg.nested_plan(lo, min(999, lo + 499),
+                                                                                        lean=True))
+
+    def pct(xs, p):
+        return float(np.percentile(np.asarray(xs), p)) if xs else None
+
+    def run_mode(mode, rate, reqs, arrivals):
+        n = len(reqs)
+        lat = [None] * n
+        done_t = [0.0] * n
+        t0 = time.perf_counter() + 0.05
+        if mode == "batched":
+            srv = cq.cq_server_create(ctx, cq.server_options(max_batch=256, n_streams=4, max_wait_us=200))
+            tickets = [None] * n
+            got = threading.Event()
+
+            def submit():
+                for i, (tb, ps) in enumerate(reqs):
+                    dt = t0 + arrivals[i] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    tickets[i] = cq.cq_server_submit(srv, tb, ps)
+                    if i == 0:
+                        got.set()
+            th = threading.Thread(target=submit)
+            th.start()
+            for i in range(n):
+                while tickets[i] is None:
+                    time.sleep(5e-5)
+                res, us = cq.cq_server_wait(srv, tickets[i])
+                lat[i] = us
+                done_t[i] = time.perf_counter()
+                res.close()
+            th.join()
+            launches, _ = cq.cq_server_stats(srv)
+            srv.close()
+        else:
+            opts = cq.exec_options(mode=cq.CQ_EXEC_DECOMPRESS_THEN_SCAN) if mode == "decompress_then_scan" else None
+            launches = n
+            for i, (tb, ps) in enumerate(reqs):
+                arr = t0 + arrivals[i]
+                dt = arr - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                r = cq.cq_query_run(tb, ps, opts=opts)
+                cq.cq_result_wait(r)
+                done_t[i] = time.perf_counter()
+                lat[i] = (done_t[i] - arr) * 1e6
+                r.close()
+        span = max(done_t) - t0
+        return {"mode": mode, "rate": rate, "queries": n, "achieved_qps": n / span, "p50_us": pct(lat, 50),
+                "p99_us": pct(lat, 99), "launches": launches}
+
+    rows = []
+    modes = [m for m in args.serve_modes.split(",") if m]
+    for rate in [float(x) for x in args.rates.split(",")]:
+        n = max(20, int(rate * args.serve_seconds))
+        r = np.random.default_rng([args.seed, 7, int(rate)])
+        arrivals = np.cumsum(r.exponential(1.0 / rate, size=n))
+        reqs = [request(r) for _ in range(n)]
+        for mode in modes:
+            # the comparison path is slow: a bounded prefix of the same arrivals
+            k = n if mode != "decompress_then_scan" else min(n, 1500)
+            rows.append(run_mode(mode, rate, reqs[:k], arrivals[:k]))
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    best = max((x for x in rows if x["mode"] == "batched"), key=lambda x: x["achieved_qps"], default=None)
+    line = {
+        "metric": "served queries/s", "value": best["achieved_qps"] if best else None, "unit": "queries/s",
+        "n_gpus": 1, "steps": len(rows), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "serving-mix-60-30-10", "rates": args.rates, "seconds_per_rate": args.serve_seconds,
+                   "tables": "two-RLE 1M, heterogeneous 100M, 16 nested partitions", "parallelism": "replicas1"},
+        "p50_us": best["p50_us"] if best else None, "p99_us": best["p99_us"] if best else None,
+        "by_rate": rows,
+        "gpu_launches": sum(x["launches"] for x in rows),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     elif args.workload == "batched":
         run_batched(args)
     else:

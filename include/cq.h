@@ -339,34 +339,56 @@ int cq_align_segments_static(uint32_t k, const void* const* run_ends, const uint
                              int64_t* seg_ends, int64_t* ridx, uint64_t capacity, uint64_t* n_segments);
 
 /* ------------------------------------------------------------------ serving
- * A serving loop that keeps tables resident, admits queries by their device
- * memory footprint and batches the queries that arrive while others run
- * (continuous batching over several streams).  Submission is thread-safe. */
+ * A serving loop over tables kept resident on the device (no counterpart in
+ * the paper, which times warm queries one at a time; each query's method is
+ * that of cq_query_run).  A background thread owns the launches:
+ *  - admission: a submitted query is planned at once (plan errors are
+ *    returned by cq_server_submit) and its device footprint -- result
+ *    buffers and its share of the batch control block -- is computed; it is
+ *    admitted to a launch only while the footprints of all queries in flight
+ *    stay within memory_budget_bytes;
+ *  - continuous batching: whenever one of n_streams streams is free, the
+ *    admitted queries are launched together as one batch (cq_batch_run's
+ *    persistent kernel) if the device is idle, max_batch queries are
+ *    waiting, or the oldest has waited max_wait_us; queries arriving while
+ *    earlier batches run go into the next batch on another stream, so their
+ *    work overlaps on the device;
+ *  - completion: launches in flight are polled; a finished query's result
+ *    and latency (submission to observed completion) go to cq_server_wait.
+ * Each query's result equals its cq_query_run result exactly. */
 typedef struct cq_server cq_server;
 
 typedef struct {
-  uint64_t memory_budget_bytes;  /* admission limit on in-flight query scratch; 0 = 1 GiB */
+  uint64_t memory_budget_bytes;  /* admission limit on in-flight query footprints; 0 = 1 GiB */
   uint32_t max_batch;            /* most queries per launch; 0 = 256 */
-  uint32_t n_streams;            /* concurrent launches in flight; 0 = 2 */
+  uint32_t n_streams;            /* concurrent launches in flight (<= 16); 0 = 2 */
   uint32_t max_wait_us;          /* how long a partial batch may wait for company; 0 = 50 */
   uint32_t reserved[3];
 } cq_server_options;
 
+/* Start a serving loop on ctx (which it keeps alive until destroyed). */
 int cq_server_create(cq_ctx* ctx, const cq_server_options* opts, cq_server** out);
 
-/* Submit a query; *ticket identifies it.  The plan and its literals are
- * copied.  CQ_ERR_BUSY when its footprint alone exceeds the budget. */
+/* Submit a query; *ticket identifies it.  Thread-safe.  The plan and its
+ * literals are copied and the table's columns are held, so both handles may
+ * be released after the call.  Errors: those of planning (CQ_ERR_INVALID_ARG,
+ * CQ_ERR_UNSUPPORTED), CQ_ERR_BUSY when the query's footprint alone exceeds
+ * the memory budget. */
 int cq_server_submit(cq_server* srv, cq_table* table, const cq_plan* plan, uint64_t* ticket);
 
-/* Wait up to timeout_us for query `ticket`; on success *res receives its
- * result handle (owned by the caller) and *latency_us the time from
- * submission to completion observed by the serving loop. */
+/* Wait up to timeout_us (UINT64_MAX = forever) for query `ticket`.  On
+ * success *res receives its result handle (owned by the caller, already
+ * complete) and *latency_us the time from submission to completion seen by
+ * the loop.  CQ_ERR_NOT_READY on timeout (the ticket stays valid); a launch
+ * error of the query's batch is returned once and ends the ticket.  Each
+ * ticket is collected at most once. */
 int cq_server_wait(cq_server* srv, uint64_t ticket, uint64_t timeout_us,
                    cq_result** res, double* latency_us);
 
 /* Launches issued and queries completed so far. */
 int cq_server_stats(cq_server* srv, uint64_t* launches, uint64_t* completed);
 
+/* Finish every submitted query, stop the loop, free uncollected results. */
 int cq_server_destroy(cq_server* srv);
 
 #ifdef __cplusplus

@@ -359,6 +359,41 @@ def cq_query_run(table, plan, stream=None, opts: Optional[cq_exec_options] = Non
 cq_query_run_ex = cq_query_run
 
 
+# ---------------------------------------------------------------- serving loop
+def server_options(memory_budget_bytes=0, max_batch=0, n_streams=0, max_wait_us=0) -> cq_server_options:
+    o = cq_server_options()
+    o.memory_budget_bytes, o.max_batch, o.n_streams, o.max_wait_us = memory_budget_bytes, max_batch, n_streams, \
+        max_wait_us
+    return o
+
+
+def cq_server_create(ctx, opts: Optional[cq_server_options] = None) -> Handle:
+    out = C.c_void_p()
+    _check(lib.cq_server_create(ctx.ptr, C.byref(opts) if opts is not None else None, C.byref(out)))
+    return Handle(out.value, lib.cq_server_destroy, [ctx])
+
+
+def cq_server_submit(srv, table, plan) -> int:
+    ps = plan if isinstance(plan, PlanStruct) else PlanStruct(plan)
+    t = C.c_uint64()
+    _check(lib.cq_server_submit(srv.ptr, table.ptr, C.byref(ps.s), C.byref(t)))
+    return t.value
+
+
+def cq_server_wait(srv, ticket: int, timeout_us: int = 2**64 - 1):
+    """Returns (result handle, latency in microseconds)."""
+    out = C.c_void_p()
+    lat = C.c_double()
+    _check(lib.cq_server_wait(srv.ptr, ticket, timeout_us, C.byref(out), C.byref(lat)))
+    return Handle(out.value, lib.cq_result_destroy, [srv]), lat.value
+
+
+def cq_server_stats(srv):
+    a, b = C.c_uint64(), C.c_uint64()
+    _check(lib.cq_server_stats(srv.ptr, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
 def cq_result_wait(res, timeout_us: int = 2**64 - 1) -> int:
     return _check(lib.cq_result_wait(res.ptr, timeout_us))
 

@@ -9,9 +9,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <memory>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "cq_internal.h"
@@ -184,18 +189,29 @@ static uint64_t batch_key(uint32_t n, cq_table* const* tables, const cq_plan* pl
 }
 
 // ------------------------------------------------------------------ one batch
-static int run_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, uint32_t tile_rows,
-                     uint32_t items_per_cta, cudaStream_t s, cq_result** results) {
+// Device bytes a planned query holds while it runs: its result block plus
+// its share of the control block (admission control of the serving loop).
+static uint64_t query_footprint(const Planned& P) {
+  return al256(query_block_layout(P, false).total) + sizeof(QueryDesc) + 4 * P.aux.size() + 64;
+}
+
+static int plan_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, uint32_t tile_rows,
+                      std::vector<Planned>* P) {
   cq_ctx* ctx = tables[0]->ctx;
-  // ---- plan every query for the batch kernel's shape
-  std::vector<Planned> P(n);
+  P->resize(n);
   for (uint32_t i = 0; i < n; ++i) {
-    const int rc = plan_batch_query(tables[i], &plans[i], tile_rows, ctx->batch_smem, &P[i]);
+    const int rc = plan_batch_query(tables[i], &plans[i], tile_rows, ctx->batch_smem, &(*P)[i]);
     if (rc != CQ_OK) {
       const std::string msg = cq_last_error();
       return set_error(rc, "batch query %u: %s", i, msg.c_str());
     }
   }
+  return CQ_OK;
+}
+
+// Launch n planned queries as one batch on stream s (see cq_batch_run).
+static int launch_planned_batch(cq_ctx* ctx, uint32_t n, cq_table* const* tables, std::vector<Planned>& P,
+                                uint32_t items_per_cta, cudaStream_t s, cq_result** results) {
   // ---- work items: C tiles at most, about items_per_cta per CTA, larger first
   const unsigned grid = (unsigned)ctx->num_sms;
   uint64_t total_tiles = 0;
@@ -303,6 +319,14 @@ static int run_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, 
     results[i] = r;
   }
   return CQ_OK;
+}
+
+static int run_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, uint32_t tile_rows,
+                     uint32_t items_per_cta, cudaStream_t s, cq_result** results) {
+  std::vector<Planned> P;
+  const int rc = plan_batch(n, tables, plans, tile_rows, &P);
+  if (rc != CQ_OK) return rc;
+  return launch_planned_batch(tables[0]->ctx, n, tables, P, items_per_cta, s, results);
 }
 
 static int check_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, cq_result** results,
@@ -435,23 +459,335 @@ extern "C" int cq_batch_tune(uint32_t n, cq_table* const* tables, const cq_plan*
 }
 
 // ---------------------------------------------------------------- serving loop
+namespace cq {
+
+// A plan with every array and literal it points to copied.
+struct PlanCopy {
+  std::vector<cq_predicate> preds;
+  std::vector<std::vector<int64_t>> ints;
+  std::vector<std::vector<std::string>> strs;
+  std::vector<std::vector<const char*>> str_ptrs;
+  std::vector<std::vector<uint32_t>> str_lens;
+  std::vector<uint32_t> group_by;
+  std::vector<cq_aggregate> aggs;
+  cq_plan plan;
+
+  explicit PlanCopy(const cq_plan& p) {
+    preds.assign(p.preds, p.preds + (p.preds ? p.n_preds : 0));
+    ints.resize(preds.size());
+    strs.resize(preds.size());
+    str_ptrs.resize(preds.size());
+    str_lens.resize(preds.size());
+    for (size_t i = 0; i < preds.size(); ++i) {
+      cq_predicate& d = preds[i];
+      if (d.in_ints && d.n_in) ints[i].assign(d.in_ints, d.in_ints + d.n_in);
+      if (d.strs && d.n_strs) {
+        for (uint32_t k = 0; k < d.n_strs; ++k) {
+          const size_t len = d.str_lens ? d.str_lens[k] : (d.strs[k] ? strlen(d.strs[k]) : 0);
+          strs[i].emplace_back(d.strs[k] ? std::string(d.strs[k], len) : std::string());
+        }
+      }
+      for (const std::string& x : strs[i]) {
+        str_ptrs[i].push_back(x.data());
+        str_lens[i].push_back((uint32_t)x.size());
+      }
+      d.in_ints = ints[i].empty() ? nullptr : ints[i].data();
+      d.strs = str_ptrs[i].empty() ? nullptr : str_ptrs[i].data();
+      d.str_lens = str_lens[i].empty() ? nullptr : str_lens[i].data();
+    }
+    group_by.assign(p.group_by, p.group_by + (p.group_by ? p.n_group_by : 0));
+    aggs.assign(p.aggs, p.aggs + (p.aggs ? p.n_aggs : 0));
+    plan.preds = preds.empty() ? nullptr : preds.data();
+    plan.n_preds = (uint32_t)preds.size();
+    plan.group_by = group_by.empty() ? nullptr : group_by.data();
+    plan.n_group_by = (uint32_t)group_by.size();
+    plan.aggs = aggs.empty() ? nullptr : aggs.data();
+    plan.n_aggs = (uint32_t)aggs.size();
+  }
+};
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket = 0;
+  cq_table* table = nullptr;
+  Planned planned;
+  uint64_t footprint = 0;
+  Clock::time_point submitted;
+  // completion
+  bool done = false;
+  int status = CQ_OK;
+  std::string error;
+  cq_result* result = nullptr;
+  double latency_us = 0;
+};
+
+struct InFlight {
+  std::vector<std::shared_ptr<Request>> reqs;
+  cudaEvent_t done = nullptr;
+  uint64_t footprint = 0;
+  int stream = 0;
+};
+
+}  // namespace cq
+
+struct cq_server {
+  cq_ctx* ctx = nullptr;
+  cq_server_options opt;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> stream_busy;             // launches in flight per stream
+  std::vector<cudaEvent_t> free_events;
+  std::mutex mu;
+  std::condition_variable cv_submit, cv_done;
+  std::deque<std::shared_ptr<cq::Request>> pending;
+  std::unordered_map<uint64_t, std::shared_ptr<cq::Request>> by_ticket;
+  std::vector<cq::InFlight> inflight;
+  uint64_t next_ticket = 1;
+  uint64_t used_bytes = 0;
+  uint64_t launches = 0, completed = 0;
+  bool stop = false;
+  std::thread loop;
+};
+
+namespace cq {
+
+// Take admitted requests for the next launch: oldest first, while the batch
+// has room and their footprints fit the budget beside what is in flight.
+static std::vector<std::shared_ptr<Request>> take_batch(cq_server* srv) {
+  std::vector<std::shared_ptr<Request>> b;
+  uint64_t used = srv->used_bytes;
+  while (!srv->pending.empty() && b.size() < srv->opt.max_batch) {
+    const std::shared_ptr<Request>& r = srv->pending.front();
+    if (used + r->footprint > srv->opt.memory_budget_bytes && !(b.empty() && srv->inflight.empty())) break;
+    used += r->footprint;
+    b.push_back(r);
+    srv->pending.pop_front();
+  }
+  srv->used_bytes = used;
+  return b;
+}
+
+static void finish(cq_server* srv, Request& r, int status, const std::string& err) {
+  r.done = true;
+  r.status = status;
+  r.error = err;
+  r.latency_us = std::chrono::duration<double, std::micro>(Clock::now() - r.submitted).count();
+  srv->completed++;
+}
+
+// The serving loop: launch batches while streams and memory allow, poll the
+// launches in flight, hand finished results to their waiters.
+static void serve(cq_server* srv) {
+  cudaSetDevice(srv->ctx->device);
+  const auto max_wait = std::chrono::microseconds(srv->opt.max_wait_us);
+  std::unique_lock<std::mutex> lk(srv->mu);
+  while (true) {
+    // ---- completions
+    bool any_done = false;
+    for (size_t i = 0; i < srv->inflight.size();) {
+      InFlight& f = srv->inflight[i];
+      if (cudaEventQuery(f.done) != cudaSuccess) {
+        (void)cudaGetLastError();   // not ready is not an error
+        ++i;
+        continue;
+      }
+      for (auto& r : f.reqs) {
+        // the result is complete: later frees may go to the context's stream,
+        // so results outlive the server's own streams
+        if (r->result) {
+          r->result->stream = srv->ctx->stream;
+          if (r->result->batch_keepalive)
+            static_cast<BatchShared*>(r->result->batch_keepalive.get())->stream = srv->ctx->stream;
+        }
+        finish(srv, *r, CQ_OK, std::string());
+      }
+      srv->used_bytes -= f.footprint;
+      srv->stream_busy[f.stream]--;
+      srv->free_events.push_back(f.done);
+      srv->inflight[i] = std::move(srv->inflight.back());
+      srv->inflight.pop_back();
+      any_done = true;
+    }
+    if (any_done) srv->cv_done.notify_all();
+    if (srv->stop && srv->pending.empty() && srv->inflight.empty()) break;
+    // ---- launches: a free stream, and either an idle device, a full batch
+    // or a request that has waited long enough for company
+    int sidx = -1;
+    for (size_t k = 0; k < srv->streams.size(); ++k)
+      if (srv->stream_busy[k] == 0) { sidx = (int)k; break; }
+    bool go = false;
+    if (sidx >= 0 && !srv->pending.empty()) {
+      go = srv->inflight.empty() || srv->pending.size() >= srv->opt.max_batch || srv->stop ||
+           Clock::now() - srv->pending.front()->submitted >= max_wait;
+    }
+    if (go) {
+      std::vector<std::shared_ptr<Request>> b = take_batch(srv);
+      if (!b.empty()) {
+        uint64_t fp = 0;
+        for (auto& r : b) fp += r->footprint;
+        lk.unlock();
+        std::vector<cq_table*> tables;
+        std::vector<Planned> P;
+        for (auto& r : b) {
+          tables.push_back(r->table);
+          P.push_back(r->planned);
+        }
+        std::vector<cq_result*> res(b.size(), nullptr);
+        const int rc = launch_planned_batch(srv->ctx, (uint32_t)b.size(), tables.data(), P, 0,
+                                            srv->streams[sidx], res.data());
+        const std::string err = rc == CQ_OK ? std::string() : std::string(cq_last_error());
+        cudaEvent_t ev = nullptr;
+        lk.lock();
+        if (rc == CQ_OK) {
+          if (!srv->free_events.empty()) {
+            ev = srv->free_events.back();
+            srv->free_events.pop_back();
+          } else {
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+          }
+          cudaEventRecord(ev, srv->streams[sidx]);
+          for (size_t k = 0; k < b.size(); ++k) b[k]->result = res[k];
+          InFlight f;
+          f.reqs = std::move(b);
+          f.done = ev;
+          f.footprint = fp;
+          f.stream = sidx;
+          srv->stream_busy[sidx]++;
+          srv->inflight.push_back(std::move(f));
+          srv->launches++;
+        } else {
+          for (auto& r : b) finish(srv, *r, rc, err);
+          srv->used_bytes -= fp;
+          srv->cv_done.notify_all();
+        }
+        continue;
+      }
+    }
+    // ---- wait: for a submission, or briefly while launches are in flight
+    if (srv->inflight.empty() && srv->pending.empty()) {
+      srv->cv_submit.wait(lk);
+    } else {
+      srv->cv_submit.wait_for(lk, std::chrono::microseconds(20));
+    }
+  }
+}
+
+}  // namespace cq
+
 extern "C" int cq_server_create(cq_ctx* ctx, const cq_server_options* opts, cq_server** out) {
-  (void)ctx; (void)opts; (void)out;
-  return set_error(CQ_ERR_UNSUPPORTED, "the serving loop is not built yet");
+  clear_error();
+  if (!ctx || !out) return set_error(CQ_ERR_INVALID_ARG, "NULL context or out");
+  *out = nullptr;
+  std::unique_ptr<cq_server> srv(new cq_server);
+  srv->ctx = ctx;
+  memset(&srv->opt, 0, sizeof(srv->opt));
+  if (opts) srv->opt = *opts;
+  if (!srv->opt.memory_budget_bytes) srv->opt.memory_budget_bytes = 1ull << 30;
+  if (!srv->opt.max_batch) srv->opt.max_batch = 256;
+  if (!srv->opt.n_streams) srv->opt.n_streams = 2;
+  if (!srv->opt.max_wait_us) srv->opt.max_wait_us = 50;
+  if (srv->opt.n_streams > 16) return set_error(CQ_ERR_INVALID_ARG, "at most 16 streams");
+  CQ_CUDA(cudaSetDevice(ctx->device));
+  {
+    std::lock_guard<std::mutex> lk(ctx->batch_mu);
+    const int rc = ensure_batch_kernel(ctx);
+    if (rc != CQ_OK) return rc;
+  }
+  for (uint32_t i = 0; i < srv->opt.n_streams; ++i) {
+    cudaStream_t st = nullptr;
+    CQ_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    srv->streams.push_back(st);
+    srv->stream_busy.push_back(0);
+  }
+  ctx->refs++;   // the server keeps its context alive
+  cq_server* s = srv.release();
+  s->loop = std::thread(serve, s);
+  *out = s;
+  return CQ_OK;
 }
+
 extern "C" int cq_server_submit(cq_server* srv, cq_table* table, const cq_plan* plan, uint64_t* ticket) {
-  (void)srv; (void)table; (void)plan; (void)ticket;
-  return set_error(CQ_ERR_UNSUPPORTED, "the serving loop is not built yet");
+  clear_error();
+  if (!srv || !table || !plan || !ticket) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  if (table->ctx != srv->ctx) return set_error(CQ_ERR_INVALID_ARG, "table of another context");
+  std::shared_ptr<Request> r(new Request);
+  r->submitted = Clock::now();
+  {
+    PlanCopy pc(*plan);   // literals resolved at planning; the copy lives until then
+    const int rc = plan_batch_query(table, &pc.plan, 0, srv->ctx->batch_smem, &r->planned);
+    if (rc != CQ_OK) return rc;
+  }
+  r->footprint = query_footprint(r->planned);
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (srv->stop) return set_error(CQ_ERR_INVALID_ARG, "server is shutting down");
+  if (r->footprint > srv->opt.memory_budget_bytes)
+    return set_error(CQ_ERR_BUSY, "query needs %llu device bytes, the budget is %llu",
+                     (unsigned long long)r->footprint, (unsigned long long)srv->opt.memory_budget_bytes);
+  r->ticket = srv->next_ticket++;
+  // a private binding of the table's columns: the caller may destroy its
+  // table handle before the query has run
+  r->table = new cq_table(*table);
+  for (cq_column* c : table->cols) c->refs++;
+  srv->by_ticket[r->ticket] = r;
+  srv->pending.push_back(r);
+  *ticket = r->ticket;
+  srv->cv_submit.notify_one();
+  return CQ_OK;
 }
-extern "C" int cq_server_wait(cq_server* srv, uint64_t ticket, uint64_t timeout_us, cq_result** res, double* latency_us) {
-  (void)srv; (void)ticket; (void)timeout_us; (void)res; (void)latency_us;
-  return set_error(CQ_ERR_UNSUPPORTED, "the serving loop is not built yet");
+
+extern "C" int cq_server_wait(cq_server* srv, uint64_t ticket, uint64_t timeout_us, cq_result** res,
+                              double* latency_us) {
+  clear_error();
+  if (!srv || !res) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  *res = nullptr;
+  std::unique_lock<std::mutex> lk(srv->mu);
+  auto it = srv->by_ticket.find(ticket);
+  if (it == srv->by_ticket.end()) return set_error(CQ_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+  std::shared_ptr<Request> r = it->second;
+  auto ready = [&] { return r->done; };
+  if (timeout_us == UINT64_MAX) srv->cv_done.wait(lk, ready);
+  else if (!srv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready))
+    return set_error(CQ_ERR_NOT_READY, "query %llu still running", (unsigned long long)ticket);
+  srv->by_ticket.erase(it);
+  lk.unlock();
+  cq_table_destroy(r->table);
+  r->table = nullptr;
+  if (latency_us) *latency_us = r->latency_us;
+  if (r->status != CQ_OK) return set_error(r->status, "%s", r->error.c_str());
+  *res = r->result;
+  r->result = nullptr;
+  return CQ_OK;
 }
+
 extern "C" int cq_server_stats(cq_server* srv, uint64_t* launches, uint64_t* completed) {
-  (void)srv; (void)launches; (void)completed;
-  return set_error(CQ_ERR_UNSUPPORTED, "the serving loop is not built yet");
+  if (!srv) return set_error(CQ_ERR_INVALID_ARG, "NULL server");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (launches) *launches = srv->launches;
+  if (completed) *completed = srv->completed;
+  return CQ_OK;
 }
+
 extern "C" int cq_server_destroy(cq_server* srv) {
-  (void)srv;
+  clear_error();
+  if (!srv) return CQ_OK;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv_submit.notify_all();
+  if (srv->loop.joinable()) srv->loop.join();
+  cudaSetDevice(srv->ctx->device);
+  for (auto& kv : srv->by_ticket) {   // results nobody collected
+    if (kv.second->result) cq_result_destroy(kv.second->result);
+    cq_table_destroy(kv.second->table);
+  }
+  for (cudaEvent_t e : srv->free_events) cudaEventDestroy(e);
+  for (cudaStream_t st : srv->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  cq_ctx* ctx = srv->ctx;
+  delete srv;
+  ctx_release(ctx);
   return CQ_OK;
 }

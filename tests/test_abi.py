@@ -43,9 +43,7 @@ def test_binding_uses_the_c_names(libpath):
     for n in declared():
         if n != "cq_last_error" and n not in ("cq_result_column_kind", "cq_column_encoding", "cq_table_num_rows",
                                               "cq_result_destroy", "cq_column_destroy", "cq_table_destroy",
-                                              "cq_ctx_destroy", "cq_server_create", "cq_server_submit",
-                                              "cq_server_wait", "cq_server_stats", "cq_server_destroy",
-                                              "cq_batch_run"):
+                                              "cq_ctx_destroy", "cq_server_destroy"):
             assert hasattr(cq, n), n
 
 
