@@ -1110,6 +1110,25 @@ void free_result(cq_result* r) {
   delete r;
 }
 
+// Launch one planned query with the one-query kernels (the serving loop's
+// path for a batch of one); the result holds the table's columns.
+int launch_solo(cq_table* table, Planned& P, cudaStream_t s, cq_result** out) {
+  cq_ctx* ctx = table->ctx;
+  cq_result* r = new_result(ctx, s, true);
+  cudaEventRecord(r->ev_start, s);
+  const int rc = launch_planned(ctx, P, s, r);
+  if (rc != CQ_OK) {
+    free_result(r);
+    return rc;
+  }
+  for (int kc : P.out_key_col) r->key_cols.push_back(kc >= 0 ? table->cols[kc] : nullptr);
+  for (cq_column* c : table->cols) c->refs++;
+  r->held_cols = table->cols;
+  cudaEventRecord(r->ev_done, s);
+  *out = r;
+  return CQ_OK;
+}
+
 // Plan one query of a batch (see plan_query): the shared kernel shape, tiles
 // of `tile_rows` rows (0 = the mode's default), shared memory within
 // `smem_limit` bytes.

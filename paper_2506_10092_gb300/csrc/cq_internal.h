@@ -309,6 +309,7 @@ QueryBlock query_block_layout(const Planned& P, bool with_aux);
 void bind_query_block(Planned& P, uint8_t* base, const QueryBlock& L, const uint32_t* aux_dev);
 void attach_outputs(cq_result* r, const Planned& P);
 cq_result* new_result(cq_ctx* ctx, cudaStream_t s, bool own_events);
+int launch_solo(cq_table* table, Planned& P, cudaStream_t s, cq_result** out);
 void free_result(cq_result* r);
 
 }  // namespace cq

@@ -633,8 +633,11 @@ static void serve(cq_server* srv) {
           P.push_back(r->planned);
         }
         std::vector<cq_result*> res(b.size(), nullptr);
-        const int rc = launch_planned_batch(srv->ctx, (uint32_t)b.size(), tables.data(), P, 0,
-                                            srv->streams[sidx], res.data());
+        // a batch of one runs the one-query kernels (no per-item table
+        // resets and flushes, no control-block upload)
+        const int rc = b.size() == 1 ? launch_solo(tables[0], P[0], srv->streams[sidx], &res[0])
+                                     : launch_planned_batch(srv->ctx, (uint32_t)b.size(), tables.data(), P, 0,
+                                                            srv->streams[sidx], res.data());
         const std::string err = rc == CQ_OK ? std::string() : std::string(cq_last_error());
         cudaEvent_t ev = nullptr;
         lk.lock();
