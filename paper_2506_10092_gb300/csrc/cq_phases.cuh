@@ -15,11 +15,12 @@
 namespace cq {
 
 constexpr uint32_t kWin = 128;                           // prefetched run ends / positions per column and tile
+constexpr uint32_t kWinBufs = 3;                         // row mode: windows of tiles t, t+1, t+2
 constexpr uint32_t kAuxSmemWords = 4096;                 // aux tables up to 16 KB live in shared memory
 
 // ------------------------------------------------------------------ shared-memory layout
 struct SmemLayout {
-  uint32_t stage, mbar, tkeys, tacc, tacc32, bm, pre, tcur, win, ubm, upre, seg, clist, aux, flags, misc, total;
+  uint32_t stage, mbar, tkeys, tacc, tacc32, bm, pre, tcur, win, wcnt, ubm, upre, seg, clist, aux, flags, misc, total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -54,8 +55,12 @@ __host__ __device__ inline SmemLayout smem_layout(const QueryDesc& q) {
   off = align_up(off, 8);
   L.tcur = off;
   off += 8u * kMaxBitmapCols * nbuf;
+  // row mode: per window buffer and bitmap column, kWin run ends / positions
+  // followed by the kWin values of the same runs / listed rows
   L.win = off;
-  off += q.seg_mode ? 0u : 8u * kWin * nb * 2;
+  off += q.seg_mode ? 0u : 16u * kWin * nb * kWinBufs;
+  L.wcnt = off;
+  off += 4u * kMaxBitmapCols * kWinBufs;
   L.ubm = off;
   off += q.seg_mode ? 4u * nwords : 0u;
   L.upre = off;
@@ -87,6 +92,7 @@ struct Smem {
   uint32_t* pre;
   unsigned long long* tcur;
   uint8_t* win;
+  uint32_t* wcnt;  // entries held by each window [buffer][column] (segment mode: zeros)
   uint32_t* ubm;
   uint32_t* upre;
   uint16_t* seg;
@@ -110,6 +116,7 @@ __device__ __forceinline__ Smem carve(const QueryDesc& q) {
   s.pre = reinterpret_cast<uint32_t*>(g_smem + L.pre);
   s.tcur = reinterpret_cast<unsigned long long*>(g_smem + L.tcur);
   s.win = g_smem + L.win;
+  s.wcnt = reinterpret_cast<uint32_t*>(g_smem + L.wcnt);
   s.ubm = reinterpret_cast<uint32_t*>(g_smem + L.ubm);
   s.upre = reinterpret_cast<uint32_t*>(g_smem + L.upre);
   s.seg = reinterpret_cast<uint16_t*>(g_smem + L.seg);
@@ -125,6 +132,8 @@ struct TileView {
   const uint32_t* bm;                // bitmaps of this tile [n_bitmaps][nwords]
   const uint32_t* pre;               // word prefix popcounts [n_bitmaps][nwords + 1]
   const unsigned long long* cur;     // first run / position of each bitmap column in this tile
+  const uint8_t* win;                // window set of this tile (row mode), see win_value
+  const uint32_t* wn;                // entries in each column's window (0: none)
   const uint8_t* stage;              // staged row-level columns of this tile
   const uint32_t* aux;               // predicate / key tables (shared or global memory)
   uint32_t nwords;
@@ -179,6 +188,17 @@ __device__ __forceinline__ void dispatch_test(const PredDesc& p, F&& f) {
 }
 
 // ------------------------------------------------------------------ column readers
+// Value of the tile's k-th run (RLE) or listed row (index) of column c: from
+// the shared-memory window the helper warp prefetched for this tile when it
+// holds entry k, else from global memory.
+__device__ __forceinline__ long long win_value(const ColDesc& c, const TileView& t, uint32_t k) {
+  if (k < t.wn[c.bslot]) {
+    const uint8_t* v = t.win + (size_t)c.bslot * kWin * 16 + kWin * 8;
+    return c.v64 ? reinterpret_cast<const long long*>(v)[k] : (long long)reinterpret_cast<const int*>(v)[k];
+  }
+  return ldg_val(c.vals, t.cur[c.bslot] + k, c.v64);
+}
+
 // Raw value of column c at tile row o (the logical value for RLE / index /
 // plain columns; the unsigned field for dictionary codes and, when
 // raw_is_offset, bit-packed offsets).
@@ -193,13 +213,13 @@ __device__ __forceinline__ long long col_raw(const ColDesc& c, const TileView& t
   } else if constexpr (ENC == ENC_RLE) {
     const uint32_t* B = t.bm + c.bslot * t.nwords;
     const uint32_t* P = t.pre + c.bslot * (t.nwords + 1);
-    return ldg_val(c.vals, t.cur[c.bslot] + rank_incl(B, P, o), c.v64);
+    return win_value(c, t, rank_incl(B, P, o));
   } else {  // ENC_INDEX
     const uint32_t* B = t.bm + c.bslot * t.nwords;
     const uint32_t wv = B[o >> 5];
     if (!((wv >> (o & 31)) & 1u)) return c.base;
     const uint32_t* P = t.pre + c.bslot * (t.nwords + 1);
-    return ldg_val(c.vals, t.cur[c.bslot] + P[o >> 5] + __popc(wv & ((1u << (o & 31)) - 1u)), c.v64);
+    return win_value(c, t, P[o >> 5] + __popc(wv & ((1u << (o & 31)) - 1u)));
   }
 }
 
@@ -217,14 +237,13 @@ __device__ __forceinline__ int col_raw32(const ColDesc& c, const TileView& t, ui
   } else if constexpr (ENC == ENC_RLE) {
     const uint32_t* B = t.bm + c.bslot * t.nwords;
     const uint32_t* P = t.pre + c.bslot * (t.nwords + 1);
-    return __ldg(reinterpret_cast<const int*>(c.vals) + t.cur[c.bslot] + rank_incl(B, P, o));
+    return (int)win_value(c, t, rank_incl(B, P, o));
   } else {
     const uint32_t* B = t.bm + c.bslot * t.nwords;
     const uint32_t wv = B[o >> 5];
     if (!((wv >> (o & 31)) & 1u)) return (int)c.base;
     const uint32_t* P = t.pre + c.bslot * (t.nwords + 1);
-    return __ldg(reinterpret_cast<const int*>(c.vals) + t.cur[c.bslot] + P[o >> 5] +
-                 __popc(wv & ((1u << (o & 31)) - 1u)));
+    return (int)win_value(c, t, P[o >> 5] + __popc(wv & ((1u << (o & 31)) - 1u)));
   }
 }
 
@@ -244,7 +263,7 @@ __device__ __forceinline__ bool index_lookup(const ColDesc& c, const TileView& t
   const uint32_t wv = B[o >> 5];
   if (!((wv >> (o & 31)) & 1u)) return false;
   const uint32_t* P = t.pre + c.bslot * (t.nwords + 1);
-  *v = ldg_val(c.vals, t.cur[c.bslot] + P[o >> 5] + __popc(wv & ((1u << (o & 31)) - 1u)), c.v64);
+  *v = win_value(c, t, P[o >> 5] + __popc(wv & ((1u << (o & 31)) - 1u)));
   return true;
 }
 

@@ -30,24 +30,33 @@ __device__ __forceinline__ const ColDesc& bitmap_col(const QueryDesc& q, int j) 
   return q.cols[idx];
 }
 
-__device__ __forceinline__ uint8_t* window(const QueryDesc& q, const Smem& sm, int buf, int j) {
-  return sm.win + ((size_t)buf * q.n_bitmaps + j) * kWin * 8;
+// Window set `wb`: per bitmap column kWin run ends / positions, then the
+// values of the same runs / listed rows.
+__device__ __forceinline__ uint8_t* window_set(const QueryDesc& q, const Smem& sm, int wb) {
+  return sm.win + (size_t)wb * q.n_bitmaps * kWin * 16;
+}
+__device__ __forceinline__ uint8_t* window(const QueryDesc& q, const Smem& sm, int wb, int j) {
+  return window_set(q, sm, wb) + (size_t)j * kWin * 16;
 }
 
-// Prefetch kWin run ends / positions of every bitmap column, from the helper
-// cursor on, into window buffer `buf` (helper warp).
-__device__ inline void prefetch_windows(const QueryDesc& q, const Smem& sm, int buf) {
+// Prefetch kWin run ends / positions and their values of every bitmap
+// column, from the helper cursor on, into window set `wb` (helper warp).
+__device__ inline void prefetch_windows(const QueryDesc& q, const Smem& sm, int wb) {
   const int lane = threadIdx.x & 31;
   const unsigned long long* hcur = helper_cursor(sm);
   for (int j = 0; j < q.n_bitmaps; ++j) {
     const ColDesc& cd = bitmap_col(q, j);
     const unsigned long long cur = hcur[j];
     const uint32_t avail = cur < cd.n ? (uint32_t)((cd.n - cur) < kWin ? (cd.n - cur) : kWin) : 0u;
-    uint8_t* dst = window(q, sm, buf, j);
+    uint8_t* dst = window(q, sm, wb, j);
+    uint8_t* vdst = dst + kWin * 8;
     for (uint32_t i = lane; i < avail; i += 32) {
       if (cd.e64) cp_async8(dst + 8 * i, reinterpret_cast<const long long*>(cd.ends) + cur + i);
       else cp_async4(dst + 4 * i, reinterpret_cast<const int*>(cd.ends) + cur + i);
+      if (cd.v64) cp_async8(vdst + 8 * i, reinterpret_cast<const long long*>(cd.vals) + cur + i);
+      else cp_async4(vdst + 4 * i, reinterpret_cast<const int*>(cd.vals) + cur + i);
     }
+    if (lane == 0) sm.wcnt[wb * kMaxBitmapCols + j] = avail;
   }
   cp_async_commit();
 }
@@ -55,8 +64,8 @@ __device__ inline void prefetch_windows(const QueryDesc& q, const Smem& sm, int 
 // Build the bitmaps of tile [s, e) into buffer `buf` from the prefetched
 // windows (falling back to global loads past a window), record the tile's
 // start cursors and advance the helper cursors (helper warp).
-__device__ inline void helper_build(const QueryDesc& q, const Smem& sm, int buf, unsigned long long s, unsigned long long e,
-                             uint32_t nwords) {
+__device__ inline void helper_build(const QueryDesc& q, const Smem& sm, int buf, int wb, unsigned long long s,
+                                    unsigned long long e, uint32_t nwords) {
   const int lane = threadIdx.x & 31;
   const int nb = q.n_bitmaps;
   unsigned long long* hcur = helper_cursor(sm);
@@ -71,7 +80,7 @@ __device__ inline void helper_build(const QueryDesc& q, const Smem& sm, int buf,
     __syncwarp();
     const unsigned long long cur = hcur[j];
     const uint32_t avail = cur < cd.n ? (uint32_t)((cd.n - cur) < kWin ? (cd.n - cur) : kWin) : 0u;
-    const uint8_t* win = window(q, sm, buf, j);
+    const uint8_t* win = window(q, sm, wb, j);
     unsigned long long cnt = 0;
     int eq = 0;
     for (unsigned long long base = 0;; base += 32) {
@@ -195,8 +204,12 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
     if (lane == 0)
       for (unsigned long long u = t_begin; u < t_end && u < t_begin + q.stages; ++u) issue(u);
     if (nb) {
+      // window set (u - t_begin) % kWinBufs serves tile u: prefetched two
+      // tiles ahead, turned into bitmaps one tile ahead, read by the compute
+      // warps (values) while the tile is processed
       prefetch_windows(q, sm, 0);
-      helper_build(q, sm, 0, t_begin * T, ((t_begin + 1) * T < q.n_rows) ? (t_begin + 1) * T : q.n_rows, nwords);
+      helper_build(q, sm, 0, 0, t_begin * T, ((t_begin + 1) * T < q.n_rows) ? (t_begin + 1) * T : q.n_rows,
+                   nwords);
       if (t_begin + 1 < t_end) prefetch_windows(q, sm, 1);
     }
   }
@@ -218,6 +231,9 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
       tv.bm = sm.bm + (size_t)buf * nb * nwords;
       tv.pre = sm.pre + (size_t)buf * nb * (nwords + 1);
       tv.cur = sm.tcur + buf * kMaxBitmapCols;
+      const int wb = (int)((t - t_begin) % kWinBufs);
+      tv.win = window_set(q, sm, wb);
+      tv.wn = sm.wcnt + wb * kMaxBitmapCols;
       tv.stage = sm.stage + (size_t)st * q.stage_bytes;
       tv.aux = aux_smem ? sm.aux : q.aux;
       tv.nwords = nwords;
@@ -225,8 +241,9 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
       const uint32_t n_pass = compact<GPW>(pm, wbase, gstride, mylist);
       phase_aggregate<false, 2>(q, sm, tv, nullptr, mylist, n_pass, s);
     } else if (nb && t + 1 < t_end) {
-      helper_build(q, sm, buf ^ 1, e, (e + T < q.n_rows) ? e + T : q.n_rows, nwords);
-      if (t + 2 < t_end) prefetch_windows(q, sm, buf);
+      helper_build(q, sm, buf ^ 1, (int)((t + 1 - t_begin) % kWinBufs), e, (e + T < q.n_rows) ? e + T : q.n_rows,
+                   nwords);
+      if (t + 2 < t_end) prefetch_windows(q, sm, (int)((t + 2 - t_begin) % kWinBufs));
     }
     // one barrier per tile; thread 0 decides the flush from the occupancy it
     // sees (an early or late flush is harmless: a full table falls back to

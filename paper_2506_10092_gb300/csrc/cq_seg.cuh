@@ -182,6 +182,7 @@ __device__ __forceinline__ void seg_range(const QueryDesc& q, const Smem& sm, un
   for (uint32_t sl = threadIdx.x; sl < q.table_slots; sl += blockDim.x) reset_slot(q, sm, sl);
   if (threadIdx.x < 8) sm.misc[threadIdx.x] = 0;
   if (threadIdx.x < 2 * kMaxBitmapCols) sm.flags[threadIdx.x] = 0;
+  if (threadIdx.x < kMaxBitmapCols) sm.wcnt[threadIdx.x] = 0;
   const bool aux_smem = q.aux_words <= kAuxSmemWords;
   if (aux_smem)
     for (uint32_t i = threadIdx.x; i < q.aux_words; i += blockDim.x) sm.aux[i] = __ldg(q.aux + i);
@@ -199,6 +200,8 @@ __device__ __forceinline__ void seg_range(const QueryDesc& q, const Smem& sm, un
   tv.bm = sm.bm;
   tv.pre = sm.pre;
   tv.cur = sm.tcur;
+  tv.win = nullptr;
+  tv.wn = sm.wcnt;   // zero: no windows in segment mode
   tv.stage = nullptr;
   tv.aux = aux_smem ? sm.aux : q.aux;
   tv.nwords = nwords;
