@@ -722,18 +722,22 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     }
   }
   // ---- 32-bit evaluation where the column's raw values fit int32
+  // a column whose raw values the kernel may read in 32 bits
+  auto narrow_col = [&](const ColDesc& cd, const PlanCol& pc) {
+    switch (cd.enc) {
+      case ENC_PLAIN: return !cd.v64;
+      case ENC_PACKED: return cd.raw_is_offset && cd.bw <= 31;
+      case ENC_DICT: return cd.bw <= 31;
+      case ENC_RLE: return !cd.v64;
+      case ENC_INDEX: return !cd.v64 && pc.base >= INT_MIN && pc.base <= INT_MAX;
+    }
+    return false;
+  };
   for (uint32_t i = 0; i < plan->n_preds; ++i) {
     PredDesc& d = q.preds[i];
     const ColDesc& cd = q.cols[d.col];
     const PlanCol& pc = tcols[plan->preds[i].col];
-    bool narrow = false;
-    switch (cd.enc) {
-      case ENC_PLAIN: narrow = !cd.v64; break;
-      case ENC_PACKED: narrow = cd.raw_is_offset && cd.bw <= 31; break;
-      case ENC_DICT: narrow = cd.bw <= 31; break;
-      case ENC_RLE: narrow = !cd.v64; break;
-      case ENC_INDEX: narrow = !cd.v64 && pc.base >= INT_MIN && pc.base <= INT_MAX; break;
-    }
+    const bool narrow = narrow_col(cd, pc);
     d.n32 = 0;
     if (!narrow) continue;
     if (d.kind == PK_RANGE) {
@@ -814,6 +818,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       kd.card = (uint32_t)card;
     }
     if (kd.card == 0) kd.card = 1;
+    kd.n32 = (narrow_col(cd, pc) && kd.kmin >= -(1ll << 30) && kd.kmin <= (1ll << 30)) ? 1 : 0;
     groups *= kd.card;
     if (groups > (i128)kDenseMaxGroups)
       return set_error(CQ_ERR_UNSUPPORTED, "the group-by key domain exceeds 2^24 groups");
@@ -826,6 +831,23 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   q.n_groups = (uint64_t)groups;
   // ---- table shape and flush period
   q.flush_rows = 1u << 20;
+  // a SUM whose values are small enough for a 32-bit shared word over a
+  // flush period of at least 2^18 rows shortens the period to fit it
+  for (uint32_t i = 0; i < plan->n_aggs; ++i) {
+    const cq_aggregate& a = plan->aggs[i];
+    if (a.op != CQ_SUM && a.op != CQ_AVG) continue;
+    const PlanCol& pc = tcols[a.col];
+    if (pc.enc == ENC_INDEX) continue;
+    const ColDesc& cd = q.cols[slot[a.col]];
+    i128 lo, hi;
+    if (cd.raw_is_offset) { lo = pc.stats.min_raw; hi = pc.stats.max_raw; }
+    else { lo = pc.stats.min_val; hi = pc.stats.max_val; }
+    const i128 bound = std::max<i128>(hi < 0 ? -hi : hi, lo < 0 ? -lo : lo) + 1;
+    const i128 limit = lo >= 0 ? ((i128)1 << 32) : ((i128)1 << 31);
+    uint32_t f = 1u << 20;
+    while (f > (1u << 18) && bound * (i128)f >= limit) f >>= 1;
+    if (bound * (i128)f < limit && f < q.flush_rows) q.flush_rows = f;
+  }
   if (q.flush_rows < tile) q.flush_rows = tile;
   // ---- aggregates
   q.n_aggs = (uint8_t)plan->n_aggs;
@@ -866,8 +888,19 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       else { rlo = pc.stats.min_val; rhi = pc.stats.max_val; }
       // a warp reduces up to 128 values (4 per lane) in 32 bits
       d.red32 = (!idx && !d.wide && rlo > -((i128)1 << 24) && rhi < ((i128)1 << 24)) ? 1 : 0;
-      d.sw = (uint8_t)sw;
-      sw += d.wide ? 2 : 1;
+      d.n32 = (d.red32 && narrow_col(cd, pc)) ? 1 : 0;
+      {
+        const i128 b = std::max<i128>(rhi < 0 ? -rhi : rhi, rlo < 0 ? -rlo : rlo) + 1;
+        const i128 limit = rlo >= 0 ? ((i128)1 << 32) : ((i128)1 << 31);
+        d.s32 = (!idx && b * (i128)q.flush_rows < limit) ? (rlo >= 0 ? 1 : 2) : 0;
+      }
+      if (d.s32) {
+        d.sw32 = (uint8_t)sw32;
+        sw32 += 1;
+      } else {
+        d.sw = (uint8_t)sw;
+        sw += d.wide ? 2 : 1;
+      }
       d.gw = gw;
       gw += 3;
     } else {  // MIN / MAX
@@ -875,6 +908,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       if (idx || cd.raw_is_offset) { rlo = pc.stats.min_raw; rhi = pc.stats.max_raw; }
       else { rlo = pc.stats.min_val; rhi = pc.stats.max_val; }
       d.w32 = (rlo >= (i128)INT_MIN && rhi <= (i128)INT_MAX) ? 1 : 0;
+      d.n32 = (d.w32 && !idx && narrow_col(cd, pc)) ? 1 : 0;
       // value: a 32-bit word when it fits, else a 64-bit one; index
       // columns add a 32-bit listed count
       d.sw = (uint8_t)sw;

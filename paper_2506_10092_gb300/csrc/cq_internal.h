@@ -81,7 +81,8 @@ struct PredDesc {
 struct KeyDesc {
   uint8_t col;
   uint8_t remap;     // 1: digit = rank of raw in a bitmap (IN-list) -- aux bitmap + prefix
-  uint16_t pad0;
+  uint8_t n32;       // raw values read in 32 bits and |kmin| <= 2^30: digits in 32-bit arithmetic
+  uint8_t pad0;
   uint32_t aux_off;  // bitmap words (remap)
   uint32_t aux_len;  // bitmap words (remap)
   uint32_t card;     // number of digit values
@@ -102,6 +103,9 @@ struct AggDesc {
   uint8_t out_kind;  // 0 int64, 1 uint64, 2 double
   uint8_t red32;     // SUM: |raw| < 2^24 -> a warp batch (<= 128 values) is reduced in 32 bits
   uint8_t w32;       // MIN/MAX: raw values fit int32 -> 32-bit shared accumulator, warp-reduced
+  uint8_t n32;       // values read in 32 bits (narrow column and red32 / w32)
+  uint8_t s32;       // SUM: shared accumulator is one 32-bit word (sw32): 1 unsigned, 2 signed;
+                     // the flush period keeps it from wrapping
   int64_t base;      // value added back at finalize (packed base or index default)
 };
 

@@ -318,6 +318,22 @@ __device__ __forceinline__ bool key_digit(const KeyDesc& k, const uint32_t* aux,
   return true;
 }
 
+// key_digit for a key whose raw values are read in 32 bits and whose kmin
+// lies within +-2^30 (so v - kmin cannot wrap into the digit range).
+__device__ __forceinline__ bool key_digit32(const KeyDesc& k, const uint32_t* aux, int v, uint32_t* digit) {
+  const uint32_t d = (uint32_t)v - (uint32_t)(int)k.kmin;
+  if (!k.remap) {
+    if (d >= k.card) return false;
+    *digit = d;
+    return true;
+  }
+  if (d >= 32u * k.aux_len) return false;
+  const uint32_t w = aux[k.aux_off + (d >> 5)];
+  if (!((w >> (d & 31)) & 1u)) return false;
+  *digit = aux[k.prefix_off + (d >> 5)] + __popc(w & ((1u << (d & 31)) - 1u));
+  return true;
+}
+
 // First device error wins; its detail (what, where, value) is kept for the host.
 __device__ __forceinline__ void report(const QueryDesc& q, int code, unsigned long long what,
                                        unsigned long long where, unsigned long long value) {
@@ -406,7 +422,8 @@ __device__ __forceinline__ void smem_add64(unsigned long long* w, long long x) {
 __device__ __forceinline__ void sum_add(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot, uint32_t gid,
                                         I128 x) {
   if (slot >= 0) {
-    if (!a.wide) smem_add64(sword(q, sm, a.sw, slot), (long long)x.lo);
+    if (a.s32) atomicAdd(reinterpret_cast<unsigned*>(sword32(q, sm, a.sw32, slot)), (unsigned)x.lo);
+    else if (!a.wide) smem_add64(sword(q, sm, a.sw, slot), (long long)x.lo);
     else atomic_add_i128(sword(q, sm, a.sw, slot), sword(q, sm, a.sw + 1, slot), x);
   } else {
     global_add_limbs(gword(q, a.gw, gid), gword(q, a.gw + 1, gid), gword(q, a.gw + 2, gid), x);
@@ -416,12 +433,22 @@ __device__ __forceinline__ void sum_add(const QueryDesc& q, const Smem& sm, cons
 __device__ __forceinline__ void minmax_add(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot,
                                            uint32_t gid, long long v, bool is_min) {
   if (slot >= 0) {
+    // read first: most values do not improve the extreme, and a plain read
+    // is cheaper than an atomic (a stale read only costs an extra atomic)
     if (a.w32) {
-      if (is_min) atomicMin(sword32(q, sm, a.sw32, slot), (int)v);
-      else atomicMax(sword32(q, sm, a.sw32, slot), (int)v);
+      int* p = sword32(q, sm, a.sw32, slot);
+      const int cur = *reinterpret_cast<volatile int*>(p);
+      if (is_min ? (int)v < cur : (int)v > cur) {
+        if (is_min) atomicMin(p, (int)v);
+        else atomicMax(p, (int)v);
+      }
     } else {
-      if (is_min) atomicMin(reinterpret_cast<long long*>(sword(q, sm, a.sw, slot)), v);
-      else atomicMax(reinterpret_cast<long long*>(sword(q, sm, a.sw, slot)), v);
+      long long* p = reinterpret_cast<long long*>(sword(q, sm, a.sw, slot));
+      const long long cur = *reinterpret_cast<volatile long long*>(p);
+      if (is_min ? v < cur : v > cur) {
+        if (is_min) atomicMin(p, v);
+        else atomicMax(p, v);
+      }
     }
   } else {
     if (is_min) atomicMin(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
@@ -436,8 +463,12 @@ __device__ __forceinline__ void reset_slot(const QueryDesc& q, const Smem& sm, u
     switch (a.kind) {
       case AK_SUM:
       case AK_ISUM:
-        *sword(q, sm, a.sw, s) = 0;
-        if (a.wide) *sword(q, sm, a.sw + 1, s) = 0;
+        if (a.s32) {
+          *sword32(q, sm, a.sw32, s) = 0;
+        } else {
+          *sword(q, sm, a.sw, s) = 0;
+          if (a.wide) *sword(q, sm, a.sw + 1, s) = 0;
+        }
         break;
       case AK_MIN:
       case AK_IMIN:
@@ -473,7 +504,11 @@ __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
         case AK_SUM:
         case AK_ISUM: {
           I128 x;
-          if (a.wide) {
+          if (a.s32 == 1) {
+            x = sext((long long)(unsigned)*sword32(q, sm, a.sw32, s));
+          } else if (a.s32 == 2) {
+            x = sext((long long)*sword32(q, sm, a.sw32, s));
+          } else if (a.wide) {
             x.lo = *sword(q, sm, a.sw, s);
             x.hi = (long long)*sword(q, sm, a.sw + 1, s);
           } else {
@@ -626,6 +661,21 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
       const ColDesc& c = q.cols[k.col];
       dispatch_col<SEG>(c.enc, [&](auto et) {
         constexpr int E = decltype(et)::value;
+        if (k.n32) {
+#pragma unroll
+          for (int m = 0; m < MI; ++m) {
+            const int v = col_raw32<E>(c, t, o[m]);
+            uint32_t d;
+            if (key_digit32(k, t.aux, v, &d)) {
+              gid[m] += d * (uint32_t)k.stride;
+            } else if (act[m]) {
+              act[m] = false;
+              report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)ki << 8), tile_row0 + o[m],
+                     (unsigned long long)(long long)v);
+            }
+          }
+          return;
+        }
 #pragma unroll
         for (int m = 0; m < MI; ++m) {
           const long long v = col_raw<E>(c, t, o[m]);
@@ -687,8 +737,13 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
       if (a.col != last_col) {
         dispatch_col<SEG>(c.enc, [&](auto et) {
           constexpr int E = decltype(et)::value;
+          if (a.n32) {
 #pragma unroll
-          for (int m = 0; m < MI; ++m) val[m] = col_raw<E>(c, t, o[m]);
+            for (int m = 0; m < MI; ++m) val[m] = (long long)col_raw32<E>(c, t, o[m]);
+          } else {
+#pragma unroll
+            for (int m = 0; m < MI; ++m) val[m] = col_raw<E>(c, t, o[m]);
+          }
         });
         last_col = a.col;
       }
@@ -700,7 +755,10 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
 #pragma unroll
           for (int m = 0; m < MI; ++m) x += act[m] ? (int)val[m] : 0;
           r = __reduce_add_sync(0xFFFFFFFFu, x);
-          if (lane == 0) smem_add64(sword(q, sm, a.sw, 0), (long long)r);
+          if (lane == 0) {
+            if (a.s32) atomicAdd(reinterpret_cast<unsigned*>(sword32(q, sm, a.sw32, 0)), (unsigned)r);
+            else smem_add64(sword(q, sm, a.sw, 0), (long long)r);
+          }
         } else {
           const bool mn = a.kind == AK_MIN;
           int x = mn ? INT_MAX : INT_MIN;
