@@ -617,9 +617,11 @@ __device__ __forceinline__ uint32_t compact(uint32_t pm, uint32_t wbase, uint32_
 }
 
 // One aggregate's update for one item (slot >= 0: shared table; else global).
+// Row mode items are single rows (len 1); segment items weigh by length.
+template <bool SEG>
 __device__ __forceinline__ void agg_item(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot,
                                          uint32_t gid, long long v, uint32_t len) {
-  if (a.kind == AK_SUM) sum_add(q, sm, a, slot, gid, len == 1 ? sext(v) : mul_s64(v, (long long)len));
+  if (a.kind == AK_SUM) sum_add(q, sm, a, slot, gid, SEG ? mul_s64(v, (long long)len) : sext(v));
   else minmax_add(q, sm, a, slot, gid, v, a.kind == AK_MIN);
 }
 
@@ -775,7 +777,7 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
       }
 #pragma unroll
       for (int m = 0; m < MI; ++m)
-        if (act[m]) agg_item(q, sm, a, slot[m], gid[m], val[m], len[m]);
+        if (act[m]) agg_item<SEG>(q, sm, a, slot[m], gid[m], val[m], len[m]);
     }
   }
 }
