@@ -968,7 +968,10 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     }
     q.smem_bytes = (uint32_t)query_kernel_smem(q);
   }
+  // ncw 8 marks the two-CTA row shape; segment mode runs two CTAs per SM
+  // whenever its shared memory fits half an SM (ncw 16 with limit smem_two)
   P->ctas_per_sm = (!q.seg_mode && ncw == 8) ? 2 : 1;
+  if (q.seg_mode && smem_limit <= ctx->smem_two) P->ctas_per_sm = 2;
   P->grid_ctas = opts ? opts->grid_ctas : 0u;
   // ---- outputs
   q.n_out = plan->n_group_by + plan->n_aggs;
@@ -1026,6 +1029,8 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
     // row mode), one CTA per SM, shared memory within the batch kernel's limit
     add(16, seg ? 4096u : 8192u, batch_limit);
   } else if (seg) {
+    // two CTAs per SM when the tile fits half the shared memory, else one
+    if (want_ctas != 1) add(16, 4096, ctx->smem_two);
     add(16, 4096, ctx->smem_optin);
   } else if (want_ctas == 2) {
     add(8, 4096, ctx->smem_two);

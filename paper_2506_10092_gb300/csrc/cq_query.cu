@@ -26,8 +26,8 @@ size_t query_kernel_smem(const QueryDesc& q) { return smem_layout(q).total; }
 // ------------------------------------------------------------------ segment-mode kernel
 // GPW: groups of 32 segments per warp per tile (tile_rows / kThreads).  Each
 // CTA walks one contiguous range of tiles.
-template <int GPW>
-__global__ void __launch_bounds__(kThreads, 1) seg_query_kernel(const __grid_constant__ QueryDesc q) {
+template <int GPW, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) seg_query_kernel(const __grid_constant__ QueryDesc q) {
   const unsigned long long t_begin = (unsigned long long)blockIdx.x * q.n_tiles / gridDim.x;
   const unsigned long long t_end = (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;
   if (t_begin >= t_end) return;
@@ -310,10 +310,11 @@ cudaError_t launch_row_kernel(const QueryDesc& q, unsigned grid, cudaStream_t s)
 cudaError_t query_kernel_set_smem(size_t bytes) {
   cudaError_t e;
   const int b = (int)bytes;
-  if ((e = cudaFuncSetAttribute(seg_query_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-  if ((e = cudaFuncSetAttribute(seg_query_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-  if ((e = cudaFuncSetAttribute(seg_query_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-  if ((e = cudaFuncSetAttribute(seg_query_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+#define CQ_SEG_SET(G, M)                                                                                  \
+  if ((e = cudaFuncSetAttribute(seg_query_kernel<G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+  CQ_SEG_SET(2, 1) CQ_SEG_SET(4, 1) CQ_SEG_SET(8, 1) CQ_SEG_SET(16, 1)
+  CQ_SEG_SET(2, 2) CQ_SEG_SET(4, 2) CQ_SEG_SET(8, 2) CQ_SEG_SET(16, 2)
+#undef CQ_SEG_SET
   return row_kernel_set_smem(b);
 }
 
@@ -331,10 +332,23 @@ cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ct
   if (grid == 0) return cudaSuccess;
   if (!q.seg_mode) return launch_row_kernel(q, grid, s);
   switch (q.tile_rows / kThreads) {
-    case 2: seg_query_kernel<2><<<grid, kThreads, q.smem_bytes, s>>>(q); break;
-    case 4: seg_query_kernel<4><<<grid, kThreads, q.smem_bytes, s>>>(q); break;
-    case 8: seg_query_kernel<8><<<grid, kThreads, q.smem_bytes, s>>>(q); break;
-    default: seg_query_kernel<16><<<grid, kThreads, q.smem_bytes, s>>>(q); break;
+    // two CTAs per SM overlap one CTA's barrier-separated phases with the other's
+    case 2:
+      if (ctas_per_sm == 2) seg_query_kernel<2, 2><<<grid, kThreads, q.smem_bytes, s>>>(q);
+      else seg_query_kernel<2, 1><<<grid, kThreads, q.smem_bytes, s>>>(q);
+      break;
+    case 4:
+      if (ctas_per_sm == 2) seg_query_kernel<4, 2><<<grid, kThreads, q.smem_bytes, s>>>(q);
+      else seg_query_kernel<4, 1><<<grid, kThreads, q.smem_bytes, s>>>(q);
+      break;
+    case 8:
+      if (ctas_per_sm == 2) seg_query_kernel<8, 2><<<grid, kThreads, q.smem_bytes, s>>>(q);
+      else seg_query_kernel<8, 1><<<grid, kThreads, q.smem_bytes, s>>>(q);
+      break;
+    default:
+      if (ctas_per_sm == 2) seg_query_kernel<16, 2><<<grid, kThreads, q.smem_bytes, s>>>(q);
+      else seg_query_kernel<16, 1><<<grid, kThreads, q.smem_bytes, s>>>(q);
+      break;
   }
   return cudaGetLastError();
 }
