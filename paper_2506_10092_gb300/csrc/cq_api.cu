@@ -1018,9 +1018,8 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   struct Shape { int ncw; uint32_t tile; size_t limit; };
   std::vector<Shape> shapes;
   auto add = [&](int ncw, uint32_t first, size_t limit) {
-    // a tile is 16 compute warps * 32 * GPW rows with GPW in {2, 4, 8, 16};
-    // the two-CTA shape (marked ncw == 8) stops at GPW 8
-    const uint32_t max_tile = ncw == 8 ? 4096u : 8192u;
+    // a tile is 16 compute warps * 32 * GPW rows with GPW in {2, 4, 8, 16}
+    const uint32_t max_tile = 8192u;
     for (uint32_t t = want_tile ? want_tile : first; t >= 1024; t /= 2)
       if (t <= max_tile) shapes.push_back({ncw, t, limit});
   };
@@ -1033,8 +1032,11 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
     if (want_ctas != 1) add(16, 4096, ctx->smem_two);
     add(16, 4096, ctx->smem_optin);
   } else if (want_ctas == 2) {
-    add(8, 4096, ctx->smem_two);
+    add(8, 8192, ctx->smem_two);
   } else {
+    // two CTAs per SM (ncw 8 marks the shape) when a full 8192-row tile fits
+    // half an SM -- more warps hide more latency -- else one CTA
+    if (want_ctas == 0 && (want_tile == 0 || want_tile == 8192)) shapes.push_back({8, 8192u, ctx->smem_two});
     add(16, 8192, ctx->smem_optin);
   }
   int rc = CQ_ERR_UNSUPPORTED;

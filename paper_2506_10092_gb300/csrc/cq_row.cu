@@ -27,7 +27,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) row_query_kernel(const _
 }
 
 
-#define CQ_ROW_SHAPES(X) X(16, 2, 1) X(16, 4, 1) X(16, 8, 1) X(16, 16, 1) X(16, 2, 2) X(16, 4, 2) X(16, 8, 2)
+#define CQ_ROW_SHAPES(X) X(16, 2, 1) X(16, 4, 1) X(16, 8, 1) X(16, 16, 1) X(16, 2, 2) X(16, 4, 2) X(16, 8, 2) X(16, 16, 2)
 
 cudaError_t row_kernel_set_smem(int bytes) {
   cudaError_t e = cudaSuccess;
