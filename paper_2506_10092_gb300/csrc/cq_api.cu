@@ -1034,9 +1034,14 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   } else if (want_ctas == 2) {
     add(8, 8192, ctx->smem_two);
   } else {
-    // two CTAs per SM (ncw 8 marks the shape) when a full 8192-row tile fits
-    // half an SM -- more warps hide more latency -- else one CTA
-    if (want_ctas == 0 && (want_tile == 0 || want_tile == 8192)) shapes.push_back({8, 8192u, ctx->smem_two});
+    // more warps hide more latency: two CTAs of 16 compute warps per SM (ncw 8
+    // marks the shape) when a full 8192-row tile fits half an SM, else one CTA
+    // of 24 compute warps with 6144-row tiles, else one of 16 with tiles down
+    // to 1024 rows
+    if (want_ctas == 0 && want_tile == 0) {
+      shapes.push_back({8, 8192u, ctx->smem_two});
+      shapes.push_back({24, 6144u, ctx->smem_optin});
+    }
     add(16, 8192, ctx->smem_optin);
   }
   int rc = CQ_ERR_UNSUPPORTED;

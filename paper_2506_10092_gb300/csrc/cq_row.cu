@@ -27,7 +27,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) row_query_kernel(const _
 }
 
 
-#define CQ_ROW_SHAPES(X) X(16, 2, 1) X(16, 4, 1) X(16, 8, 1) X(16, 16, 1) X(16, 2, 2) X(16, 4, 2) X(16, 8, 2) X(16, 16, 2)
+// (compute warps, 32-row groups per warp per tile, CTAs per SM)
+#define CQ_ROW_SHAPES(X) \
+  X(16, 2, 1) X(16, 4, 1) X(16, 8, 1) X(16, 16, 1) X(16, 2, 2) X(16, 4, 2) X(16, 8, 2) X(16, 16, 2) X(24, 8, 1)
 
 cudaError_t row_kernel_set_smem(int bytes) {
   cudaError_t e = cudaSuccess;
@@ -40,11 +42,13 @@ cudaError_t row_kernel_set_smem(int bytes) {
 }
 
 cudaError_t launch_row_kernel(const QueryDesc& q, unsigned grid, cudaStream_t s) {
-  const int gpw = (int)(q.tile_rows / (16 * 32));
-  const int minb = q.ncw == 8 ? 2 : 1;   // ncw field: 8 marks the two-CTA shape
+  // ncw field: 16 one CTA of 16 compute warps, 8 two such CTAs, 24 one CTA of 24
+  const int ncw = q.ncw == 24 ? 24 : 16;
+  const int gpw = (int)(q.tile_rows / (ncw * 32));
+  const int minb = q.ncw == 8 ? 2 : 1;
   bool launched = false;
 #define CQ_GO(N, G, M)                                                                \
-  if (!launched && gpw == G && minb == M) {                                           \
+  if (!launched && ncw == N && gpw == G && minb == M) {                               \
     row_query_kernel<N, G, M><<<grid, (N + 1) * 32, q.smem_bytes, s>>>(q);            \
     launched = true;                                                                  \
   }
