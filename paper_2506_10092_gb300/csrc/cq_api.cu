@@ -1040,6 +1040,7 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
     // to 1024 rows
     if (want_ctas == 0 && want_tile == 0) {
       shapes.push_back({8, 8192u, ctx->smem_two});
+      shapes.push_back({28, 7168u, ctx->smem_optin});
       shapes.push_back({24, 6144u, ctx->smem_optin});
     }
     add(16, 8192, ctx->smem_optin);

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB) row_query_kernel(const _
 
 // (compute warps, 32-row groups per warp per tile, CTAs per SM)
 #define CQ_ROW_SHAPES(X) \
-  X(16, 2, 1) X(16, 4, 1) X(16, 8, 1) X(16, 16, 1) X(16, 2, 2) X(16, 4, 2) X(16, 8, 2) X(16, 16, 2) X(24, 8, 1)
+  X(16, 2, 1) X(16, 4, 1) X(16, 8, 1) X(16, 16, 1) X(16, 2, 2) X(16, 4, 2) X(16, 8, 2) X(16, 16, 2) X(24, 8, 1) X(28, 8, 1)
 
 cudaError_t row_kernel_set_smem(int bytes) {
   cudaError_t e = cudaSuccess;
@@ -43,7 +43,7 @@ cudaError_t row_kernel_set_smem(int bytes) {
 
 cudaError_t launch_row_kernel(const QueryDesc& q, unsigned grid, cudaStream_t s) {
   // ncw field: 16 one CTA of 16 compute warps, 8 two such CTAs, 24 one CTA of 24
-  const int ncw = q.ncw == 24 ? 24 : 16;
+  const int ncw = (q.ncw == 24 || q.ncw == 28) ? q.ncw : 16;
   const int gpw = (int)(q.tile_rows / (ncw * 32));
   const int minb = q.ncw == 8 ? 2 : 1;
   bool launched = false;
