@@ -98,7 +98,7 @@ def kernel_source_hash() -> str:
 def profile_traffic(workload_name: str):
     """dram bytes per launch of the fused kernel from the committed ncu summary,
     when it was taken on the current kernel sources; else None."""
-    p = os.path.join(ROOT, "profiles", "fused_query_kernel_heterogeneous.json")
+    p = os.path.join(ROOT, "profiles", "row_query_kernel_heterogeneous.json")
     if not os.path.exists(p):
         return None
     try:
@@ -166,6 +166,19 @@ def dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's); x itself with one process."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return x
+    dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def exec_opts(cq, args):
@@ -302,10 +315,7 @@ def run_cq(args):
     for r in results:
         cq.cq_result_wait(r)
         r.close()
-    if ws > 1:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+    elapsed_ms = max_over_ranks(elapsed_ms)
     ms_per_step = elapsed_ms / args.steps
     value = n_rows * args.steps * ws / (elapsed_ms / 1000.0)
     k_us = statistics.mean(kernel_us)
@@ -367,11 +377,7 @@ def run_cq(args):
         for _ in range(args.e2e_steps):
             d2h = e2e_step()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            tt = torch.tensor([dt], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": table.n_rows * args.e2e_steps * ws / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h + 16, "steps": args.e2e_steps,
                "note": "columns created from pinned host buffers (library copy + validation), query, result fetch"}
@@ -397,7 +403,8 @@ def run_cq(args):
             "kernel_us": k_us,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "fused_query_kernel", "peak_source": f"{peak_src} hbm_gbs",
+                         "kernel": "row_query_kernel" if dn is not None or args.workload != "tiny"
+                         else "seg_query_kernel", "peak_source": f"{peak_src} hbm_gbs",
                          "algorithmic_bytes_per_launch": alg_bytes},
             "cpu_baseline": cpu,
             "e2e": e2e,
