@@ -55,17 +55,20 @@ static size_t dsize(int t) { return t == CQ_I64 ? 8 : 4; }
 static uint64_t pad16(uint64_t bytes) { return (bytes + 15) / 16 * 16; }
 
 // Allocate library-owned device memory (padded to 16 bytes plus 16 of slack)
-// and fill it from host or device memory.
+// from the context's stream-ordered pool and fill it from host or device
+// memory; only the padding is cleared.  The column's creation synchronises
+// the context's stream before the buffer is used anywhere else.
 static int own_copy(cq_ctx* ctx, const void* src, uint64_t bytes, bool from_device, void** dst) {
   const uint64_t alloc = pad16(bytes) + 16;
   void* p = nullptr;
-  if (cudaMalloc(&p, alloc) != cudaSuccess) return set_error(CQ_ERR_OOM, "cudaMalloc of %llu bytes failed", (unsigned long long)alloc);
-  cudaMemsetAsync(p, 0, alloc, ctx->stream);
+  if (cudaMallocFromPoolAsync(&p, alloc, ctx->pool, ctx->stream) != cudaSuccess)
+    return set_error(CQ_ERR_OOM, "device allocation of %llu bytes failed", (unsigned long long)alloc);
+  cudaMemsetAsync(reinterpret_cast<uint8_t*>(p) + bytes, 0, alloc - bytes, ctx->stream);
   if (bytes) {
     cudaError_t e = cudaMemcpyAsync(p, src, bytes, from_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     ctx->stream);
     if (e != cudaSuccess) {
-      cudaFree(p);
+      cudaFreeAsync(p, ctx->stream);
       return set_error(CQ_ERR_CUDA, "copy of column buffer failed: %s", cudaGetErrorString(e));
     }
   }
@@ -83,15 +86,15 @@ static int check_borrow(const void* p, const char* what) {
 static int finish_column(cq_column* c) {
   cq_ctx* ctx = c->ctx;
   void* d = nullptr;
-  CQ_CUDA(cudaMalloc(&d, 64));
+  CQ_CUDA(cudaMallocFromPoolAsync(&d, 64, ctx->pool, ctx->stream));
   struct {
     int err, pad;
     long long mn, mx;
   } h{};
   cudaError_t e = run_column_check(c, d, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(d, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  cudaFree(d);
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "column check failed: %s", cudaGetErrorString(e));
   if (h.err) {
     const char* why = h.err == CQ_ERR_UNSORTED ? "run ends / positions are not strictly increasing"
@@ -216,10 +219,12 @@ static int new_column(cq_ctx* ctx, uint8_t enc, uint64_t n_rows, cq_column** out
   return CQ_OK;
 }
 
+// Owned buffers go back to the context's pool (every query that used them
+// has finished: results hold their columns until their stream is drained).
 static void release_buffers(cq_column* c) {
   if (c->owned) {
-    if (c->vals) cudaFree(c->vals);
-    if (c->ends) cudaFree(c->ends);
+    if (c->vals) cudaFreeAsync(c->vals, c->ctx->stream);
+    if (c->ends) cudaFreeAsync(c->ends, c->ctx->stream);
   }
   c->vals = c->ends = nullptr;
 }

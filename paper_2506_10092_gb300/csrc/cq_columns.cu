@@ -79,29 +79,56 @@ __global__ void check_index_kernel(const void* vals, bool v64, const void* pos, 
 
 // Packed / dictionary codes: range of the unsigned fields (signed view for
 // 64-bit fields); codes must be below n_entries.
+// One thread per 32-bit word of the stream: it decodes the fields that start
+// in its word (consecutive threads read consecutive words).
 __global__ void check_packed_kernel(const uint32_t* words, unsigned long long n_words, uint32_t bw,
                                     unsigned long long n_rows, unsigned long long limit, CheckOut* out) {
   long long lmin = LLONG_MAX, lmax = LLONG_MIN;
-  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < n_rows;
-       r += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long bit = r * bw;
-    const unsigned long long q = bit >> 5;
-    const uint32_t sh = (uint32_t)(bit & 31);
-    const uint32_t w0 = __ldg(words + q), w1 = q + 1 < n_words ? __ldg(words + q + 1) : 0u;
-    uint64_t f = __funnelshift_r(w0, w1, sh);
-    if (bw > 32) f |= (uint64_t)__funnelshift_r(w1, q + 2 < n_words ? __ldg(words + q + 2) : 0u, sh) << 32;
-    if (bw < 64) f &= (1ull << bw) - 1ull;
-    if (limit && f >= limit) atomicCAS(&out->err, 0, (int)CQ_ERR_INVALID_ARG);
-    lmin = min(lmin, (long long)f);
-    lmax = max(lmax, (long long)f);
+  const unsigned long long used = (n_rows * bw + 31) / 32;   // words holding a field start
+  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < used;
+       j += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long b0 = j * 32;
+    const unsigned long long f0 = (b0 + bw - 1) / bw;
+    unsigned long long f1 = (b0 + 32 + bw - 1) / bw;
+    if (f1 > n_rows) f1 = n_rows;
+    const uint32_t w0 = __ldg(words + j), w1 = j + 1 < n_words ? __ldg(words + j + 1) : 0u;
+    const uint32_t w2 = (bw > 32 && j + 2 < n_words) ? __ldg(words + j + 2) : 0u;
+    for (unsigned long long f = f0; f < f1; ++f) {
+      const uint32_t sh = (uint32_t)(f * bw - b0);
+      uint64_t v = __funnelshift_r(w0, w1, sh);
+      if (bw > 32) v |= (uint64_t)__funnelshift_r(w1, w2, sh) << 32;
+      if (bw < 64) v &= (1ull << bw) - 1ull;
+      if (limit && v >= limit) atomicCAS(&out->err, 0, (int)CQ_ERR_INVALID_ARG);
+      lmin = min(lmin, (long long)v);
+      lmax = max(lmax, (long long)v);
+    }
   }
   block_minmax(lmin, lmax, out);
 }
 
+// Buffers are 16-byte aligned: whole 16-byte vectors first, then the tail.
 __global__ void check_plain_kernel(const void* vals, bool v64, unsigned long long n, CheckOut* out) {
   long long lmin = LLONG_MAX, lmax = LLONG_MIN;
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long t0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  const unsigned long long per = v64 ? 2 : 4;
+  const unsigned long long nv = n / per;
+  const int4* vec = reinterpret_cast<const int4*>(vals);
+  for (unsigned long long i = t0; i < nv; i += stride) {
+    const int4 x = __ldg(vec + i);
+    long long a, b, c, d;
+    if (v64) {
+      a = (long long)(((unsigned long long)(uint32_t)x.y << 32) | (uint32_t)x.x);
+      b = (long long)(((unsigned long long)(uint32_t)x.w << 32) | (uint32_t)x.z);
+      c = a;
+      d = b;
+    } else {
+      a = x.x; b = x.y; c = x.z; d = x.w;
+    }
+    lmin = min(lmin, min(min(a, b), min(c, d)));
+    lmax = max(lmax, max(max(a, b), max(c, d)));
+  }
+  for (unsigned long long i = nv * per + t0; i < n; i += stride) {
     const long long v = ldg_val(vals, i, v64);
     lmin = min(lmin, v);
     lmax = max(lmax, v);
@@ -117,7 +144,7 @@ cudaError_t run_column_check(const cq_column* c, void* d_out_raw, cudaStream_t s
   const unsigned threads = 256;
   auto blocks_for = [](unsigned long long n) {
     unsigned long long b = (n + 255) / 256;
-    return (unsigned)(b < 4096 ? (b ? b : 1) : 4096);
+    return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
   };
   switch (c->enc) {
     case ENC_RLE:
