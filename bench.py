@@ -87,10 +87,14 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
+# the sources the row kernel is compiled from (its code and its descriptor)
+ROW_KERNEL_SOURCES = ("cq_row.cu", "cq_rowpath.cuh", "cq_phases.cuh", "cq_device.cuh", "cq_internal.h")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2506_10092_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for name in ROW_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_10092_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
