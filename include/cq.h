@@ -338,6 +338,16 @@ int cq_align_segments_static(uint32_t k, const void* const* run_ends, const uint
                              const uint64_t* n_runs, uint64_t n_rows, void* cuda_stream,
                              int64_t* seg_ends, int64_t* ridx, uint64_t capacity, uint64_t* n_segments);
 
+/* ------------------------------------------------------------------ self-test
+ * No counterpart in the paper: checks the failure path of the fused kernels'
+ * device waits.  One device thread waits on a barrier that nothing will
+ * complete, with the same bounded wait the kernels use on their bulk-copy
+ * stages, limited to limit_us microseconds (1 us .. 5 s); *device_status
+ * receives the status the wait left (CQ_ERR_TIMEOUT when it gave up, as it
+ * must).  The context stays usable afterwards.  Synchronous on the
+ * context's stream. */
+int cq_selftest_bounded_wait(cq_ctx* ctx, uint32_t limit_us, int32_t* device_status);
+
 /* ------------------------------------------------------------------ serving
  * A serving loop over tables kept resident on the device (no counterpart in
  * the paper, which times warm queries one at a time; each query's method is

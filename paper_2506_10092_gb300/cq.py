@@ -108,6 +108,7 @@ _SIGS = {
     "cq_server_wait": [_VP, C.c_uint64, C.c_uint64, C.POINTER(_VP), C.POINTER(C.c_double)],
     "cq_server_stats": [_VP, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
     "cq_server_destroy": [_VP],
+    "cq_selftest_bounded_wait": [_VP, C.c_uint32, C.POINTER(C.c_int32)],
 }
 
 
@@ -357,6 +358,13 @@ def cq_query_run(table, plan, stream=None, opts: Optional[cq_exec_options] = Non
 
 
 cq_query_run_ex = cq_query_run
+
+
+def cq_selftest_bounded_wait(ctx, limit_us: int) -> int:
+    """Device status left by a bounded wait on a barrier nothing completes."""
+    st = C.c_int32()
+    _check(lib.cq_selftest_bounded_wait(ctx.ptr, limit_us, C.byref(st)))
+    return st.value
 
 
 # ---------------------------------------------------------------- serving loop

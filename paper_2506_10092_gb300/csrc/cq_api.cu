@@ -761,6 +761,30 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       d.n32 = 1;
     }
   }
+  // ---- evaluation order and per-run evaluation (Appendix D: predicates on
+  // run-length columns are tested first, once per run value).  Row mode:
+  // each RLE / index predicate gets a tile pass bitmap the helper warp fills
+  // from the run (listed-row) values; segment mode evaluates per segment.
+  {
+    // order: predicates with a pass bitmap, other RLE / index predicates, the rest
+    q.n_pbm = 0;
+    for (uint32_t i = 0; i < plan->n_preds; ++i) {
+      PredDesc& d = q.preds[i];
+      const uint8_t enc = q.cols[d.col].enc;
+      d.pbm = 0xFF;
+      if ((enc == ENC_RLE || enc == ENC_INDEX) && !q.seg_mode && d.kind != PK_TRUE && d.kind != PK_FALSE &&
+          q.n_pbm < kMaxPassBitmaps)
+        d.pbm = q.n_pbm++;
+    }
+    uint32_t k = 0;
+    for (int pass = 0; pass < 3; ++pass)
+      for (uint32_t i = 0; i < plan->n_preds; ++i) {
+        const PredDesc& d = q.preds[i];
+        const uint8_t enc = q.cols[d.col].enc;
+        const int cls = d.pbm != 0xFF ? 0 : (enc == ENC_RLE || enc == ENC_INDEX) ? 1 : 2;
+        if (cls == pass) q.pred_order[k++] = (uint8_t)i;
+      }
+  }
   // ---- group keys (dense mixed radix, first key most significant)
   q.n_keys = (uint8_t)plan->n_group_by;
   i128 groups = 1;
@@ -1432,5 +1456,27 @@ extern "C" int cq_align_segments(cq_ctx* ctx, cq_column* const* cols, uint32_t k
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "alignment failed: %s", cudaGetErrorString(e));
   *n_segments = ns;
   if (ns > capacity) return set_error(CQ_ERR_SIZE_MISMATCH, "%llu segments, capacity %llu", ns, (unsigned long long)capacity);
+  return CQ_OK;
+}
+
+// ====================================================================== self-test
+namespace cq {
+cudaError_t launch_bounded_wait_selftest(uint64_t limit_ns, int* status, cudaStream_t s);   // cq_columns.cu
+}
+
+extern "C" int cq_selftest_bounded_wait(cq_ctx* ctx, uint32_t limit_us, int32_t* device_status) {
+  clear_error();
+  if (!ctx || !device_status) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
+  if (limit_us == 0 || limit_us > 5000000u) return set_error(CQ_ERR_INVALID_ARG, "limit must be 1 us .. 5 s");
+  CQ_CUDA(cudaSetDevice(ctx->device));
+  void* d = nullptr;
+  CQ_CUDA(cudaMallocFromPoolAsync(&d, 16, ctx->pool, ctx->stream));
+  cudaError_t e = launch_bounded_wait_selftest(1000ull * limit_us, reinterpret_cast<int*>(d), ctx->stream);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(d, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "self-test failed: %s", cudaGetErrorString(e));
+  *device_status = h;
   return CQ_OK;
 }

@@ -415,4 +415,21 @@ cudaError_t align_launch_write_raw(const void* const* ends, const uint8_t* e64, 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ bounded-wait self-test
+// One thread waits on an mbarrier that nothing will complete, with the
+// bounded wait the fused kernels use, and records the status it ends with.
+__global__ void bounded_wait_selftest_kernel(uint64_t limit_ns, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_barrier_init();
+  *status = 0;
+  mbar_wait_bounded(&bar, 0, status, limit_ns);
+}
+
+cudaError_t launch_bounded_wait_selftest(uint64_t limit_ns, int* status, cudaStream_t s) {
+  bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(limit_ns, status);
+  return cudaGetLastError();
+}
+
 }  // namespace cq

@@ -79,12 +79,13 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 // Bounded wait: gives up after ~2 s of wall time, records CQ_ERR_TIMEOUT and
 // returns false; the caller carries on (results are then flagged invalid).
 // Waiting threads sleep inside try_wait instead of spinning.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err,
+                                                  uint64_t limit_ns = 2000000000ull) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   for (;;) {
     if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
-    if (global_timer_ns() - t0 > 2000000000ull) {
+    if (global_timer_ns() - t0 > limit_ns) {
       atomicCAS(err, 0, (int)CQ_ERR_TIMEOUT);
       return false;
     }

@@ -23,6 +23,7 @@ constexpr int kMaxPreds = 16;
 constexpr int kMaxKeys = 8;
 constexpr int kMaxAggs = 16;
 constexpr int kMaxBitmapCols = 8; // RLE / index columns per query
+constexpr int kMaxPassBitmaps = 4; // row-mode predicates evaluated once per run
 constexpr uint64_t kDenseMaxGroups = 1ull << 24;
 
 enum Enc : uint8_t { ENC_RLE = 1, ENC_DICT = 2, ENC_INDEX = 3, ENC_PACKED = 4, ENC_PLAIN = 5 };
@@ -71,7 +72,8 @@ struct PredDesc {
   uint8_t col;       // index into QueryDesc::cols
   uint8_t kind;
   uint8_t n32;       // raw values and bounds fit int32: evaluate in 32 bits (lo32 / hi32)
-  uint8_t pad0;
+  uint8_t pbm;       // row mode, RLE / index column: slot of the tile pass bitmap the helper
+                     // warp fills once per run / listed row (0xFF: evaluated per row)
   uint32_t aux_off;  // 32-bit words into the aux area (bitmap or list of int64 as word pairs)
   uint32_t aux_len;  // bitmap words / list entries
   int32_t lo32, hi32;
@@ -127,6 +129,8 @@ struct QueryDesc {
   uint8_t n_sw32;          // 32-bit shared accumulator words per slot (word 0 = COUNT)
   uint8_t n_gw;            // global accumulator words per group (word 0 = COUNT)
   uint8_t has_index_agg;
+  uint8_t n_pbm;           // tile pass bitmaps (row mode predicates on RLE / index columns)
+  uint8_t pred_order[kMaxPreds];  // evaluation order: RLE / index predicates first
   uint32_t flush_rows;     // flush the shared table at least this often (rows)
   uint64_t n_groups;       // dense global domain
   uint8_t row_cols[kMaxCols];   // ColDesc indices of staged columns

@@ -20,7 +20,7 @@ constexpr uint32_t kAuxSmemWords = 4096;                 // aux tables up to 16 
 
 // ------------------------------------------------------------------ shared-memory layout
 struct SmemLayout {
-  uint32_t stage, mbar, tkeys, tacc, tacc32, bm, pre, tcur, win, wcnt, ubm, upre, seg, clist, aux, flags, misc, total;
+  uint32_t stage, mbar, tkeys, tacc, tacc32, bm, pre, pbm, tcur, win, wcnt, ubm, upre, seg, clist, aux, flags, misc, total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -52,6 +52,8 @@ __host__ __device__ inline SmemLayout smem_layout(const QueryDesc& q) {
   off += 4u * nwords * nb * nbuf;
   L.pre = off;
   off += 4u * (nwords + 1) * nb * nbuf;
+  L.pbm = off;
+  off += 4u * nwords * q.n_pbm * nbuf;
   off = align_up(off, 8);
   L.tcur = off;
   off += 8u * kMaxBitmapCols * nbuf;
@@ -90,6 +92,7 @@ struct Smem {
   unsigned* tacc32;
   uint32_t* bm;
   uint32_t* pre;
+  uint32_t* pbm;   // row mode: tile pass bitmaps [buffer][slot][nwords]
   unsigned long long* tcur;
   uint8_t* win;
   uint32_t* wcnt;  // entries held by each window [buffer][column] (segment mode: zeros)
@@ -114,6 +117,7 @@ __device__ __forceinline__ Smem carve(const QueryDesc& q) {
   s.tacc32 = reinterpret_cast<unsigned*>(g_smem + L.tacc32);
   s.bm = reinterpret_cast<uint32_t*>(g_smem + L.bm);
   s.pre = reinterpret_cast<uint32_t*>(g_smem + L.pre);
+  s.pbm = reinterpret_cast<uint32_t*>(g_smem + L.pbm);
   s.tcur = reinterpret_cast<unsigned long long*>(g_smem + L.tcur);
   s.win = g_smem + L.win;
   s.wcnt = reinterpret_cast<uint32_t*>(g_smem + L.wcnt);
@@ -133,6 +137,7 @@ struct TileView {
   const uint32_t* pre;               // word prefix popcounts [n_bitmaps][nwords + 1]
   const unsigned long long* cur;     // first run / position of each bitmap column in this tile
   const uint8_t* win;                // window set of this tile (row mode), see win_value
+  const uint32_t* pbm;               // pass bitmaps of this tile (row mode) [slot][nwords]
   const uint32_t* wn;                // entries in each column's window (0: none)
   const uint8_t* stage;              // staged row-level columns of this tile
   const uint32_t* aux;               // predicate / key tables (shared or global memory)
@@ -316,6 +321,18 @@ __device__ __forceinline__ bool key_digit(const KeyDesc& k, const uint32_t* aux,
   if (!((w >> (d & 31)) & 1u)) return false;
   *digit = aux[k.prefix_off + (uint32_t)(d >> 5)] + __popc(w & ((1u << (d & 31)) - 1u));
   return true;
+}
+
+// A predicate on one raw value (the helper's once-per-run evaluation).
+__device__ __forceinline__ bool pred_eval(const PredDesc& p, const uint32_t* aux, long long v) {
+  switch (p.kind) {
+    case PK_RANGE: return pred_test<PT_RANGE>(p, aux, v);
+    case PK_NE: return pred_test<PT_NE>(p, aux, v);
+    case PK_BITMAP: return pred_test<PT_BITMAP>(p, aux, v);
+    case PK_LIST: return pred_test<PT_LIST>(p, aux, v);
+    case PK_FALSE: return false;
+    default: return true;
+  }
 }
 
 // key_digit for a key whose raw values are read in 32 bits and whose kmin
@@ -557,9 +574,20 @@ __device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileV
 #pragma unroll
   for (int g = 0; g < GPW; ++g) valid |= (wbase + g * gstride + lane < n_items ? 1u : 0u) << g;
   uint32_t pm = valid;
-  for (int pi = 0; pi < q.n_preds; ++pi) {
+  int first = 0;
+  if constexpr (!SEG) {
+    // the first n_pbm predicates were evaluated once per run by the helper
+    // warp: one bit per row
+    for (; first < q.n_pbm; ++first) {
+      const uint32_t* PB = t.pbm + (size_t)q.preds[q.pred_order[first]].pbm * t.nwords;
+#pragma unroll 4
+      for (int g = 0; g < GPW; ++g)
+        if (!((PB[(wbase + g * gstride) >> 5] >> lane) & 1u)) pm &= ~(1u << g);
+    }
+  }
+  for (int oi = first; oi < q.n_preds; ++oi) {
     if (!__any_sync(0xFFFFFFFFu, pm != 0)) break;
-    const PredDesc& p = q.preds[pi];
+    const PredDesc& p = q.preds[q.pred_order[oi]];
     if (p.kind == PK_TRUE) continue;
     if (p.kind == PK_FALSE) {
       pm = 0;

@@ -143,6 +143,82 @@ __device__ inline void helper_build(const QueryDesc& q, const Smem& sm, int buf,
 // tile holds NCW * GPW * 32 rows.  MINB CTAs share an SM (registers are
 // capped so that MINB CTAs fit).
 
+// Set bits [a, b) of a tile bitmap (this lane's run; its interior words are
+// its own, its end words may be shared with neighbouring runs).
+__device__ __forceinline__ void fill_bits(uint32_t* B, uint32_t a, uint32_t b) {
+  if (a >= b) return;
+  const uint32_t wa = a >> 5, wz = (b - 1) >> 5;
+  const uint32_t ma = ~0u << (a & 31), mz = ~0u >> (31 - ((b - 1) & 31));
+  if (wa == wz) {
+    atomicOr(&B[wa], ma & mz);
+    return;
+  }
+  atomicOr(&B[wa], ma);
+  for (uint32_t w = wa + 1; w < wz; ++w) B[w] = ~0u;
+  atomicOr(&B[wz], mz);
+}
+
+// Fill the pass bitmaps of tile [s, e) in buffer `buf` from the window set
+// `wb` (helper warp, after helper_build of the same tile): each predicate on
+// an RLE column is evaluated once per run of the tile and sets the run's
+// rows; one on an index column is evaluated once for the default and once
+// per listed row.
+__device__ inline void helper_pass_bitmaps(const QueryDesc& q, const Smem& sm, const uint32_t* aux, int buf, int wb,
+                                           unsigned long long s, unsigned long long e, uint32_t nwords) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t rows = (uint32_t)(e - s);
+  const int nb = q.n_bitmaps;
+  for (int pi = 0; pi < q.n_preds; ++pi) {
+    const PredDesc& p = q.preds[pi];
+    if (p.pbm == 0xFF) continue;
+    const ColDesc& c = q.cols[p.col];
+    const int j = c.bslot;
+    uint32_t* PB = sm.pbm + ((size_t)buf * q.n_pbm + p.pbm) * nwords;
+    const uint32_t nset = sm.pre[((size_t)buf * nb + j) * (nwords + 1) + nwords];
+    const unsigned long long cur = sm.tcur[buf * kMaxBitmapCols + j];
+    const uint8_t* win = window(q, sm, wb, j);
+    const uint32_t avail = sm.wcnt[wb * kMaxBitmapCols + j];
+    auto end_at = [&](uint32_t k) -> unsigned long long {
+      if (k < avail) return c.e64 ? (unsigned long long)reinterpret_cast<const long long*>(win)[k]
+                                  : (unsigned long long)reinterpret_cast<const int*>(win)[k];
+      return (unsigned long long)ldg_val(c.ends, cur + k, c.e64);
+    };
+    auto val_at = [&](uint32_t k) -> long long {
+      if (k < avail) {
+        const uint8_t* v = win + kWin * 8;
+        return c.v64 ? reinterpret_cast<const long long*>(v)[k] : (long long)reinterpret_cast<const int*>(v)[k];
+      }
+      return ldg_val(c.vals, cur + k, c.v64);
+    };
+    if (c.enc == ENC_RLE) {
+      for (uint32_t w = lane; w < nwords; w += 32) PB[w] = 0u;
+      __syncwarp();
+      // nset boundaries inside the tile: nset + 1 runs, the last one clipped
+      for (uint32_t k = lane; k <= nset; k += 32) {
+        const uint32_t a = k == 0 ? 0u : (uint32_t)(end_at(k - 1) - s);
+        const unsigned long long x = end_at(k);
+        const uint32_t b = x - s < rows ? (uint32_t)(x - s) : rows;
+        if (pred_eval(p, aux, val_at(k))) fill_bits(PB, a, b);
+      }
+    } else {
+      const bool base_pass = pred_eval(p, aux, c.base);
+      for (uint32_t w = lane; w < nwords; w += 32) {
+        const uint32_t lo = w * 32;
+        uint32_t m = base_pass ? ~0u : 0u;
+        if (lo >= rows) m = 0u;
+        else if (rows - lo < 32) m &= (1u << (rows - lo)) - 1u;
+        PB[w] = m;
+      }
+      __syncwarp();
+      for (uint32_t k = lane; k < nset; k += 32) {
+        const uint32_t o = (uint32_t)(end_at(k) - s);
+        if (pred_eval(p, aux, val_at(k)) != base_pass) atomicXor(&PB[o >> 5], 1u << (o & 31));
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Walk tiles [t_begin, t_end) of one row-mode query with NCW compute warps
 // and one helper warp (warp NCW): reset the group table, start the bulk-copy
 // pipeline, then per tile filter and aggregate (compute warps) while the
@@ -208,8 +284,9 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
       // tiles ahead, turned into bitmaps one tile ahead, read by the compute
       // warps (values) while the tile is processed
       prefetch_windows(q, sm, 0);
-      helper_build(q, sm, 0, 0, t_begin * T, ((t_begin + 1) * T < q.n_rows) ? (t_begin + 1) * T : q.n_rows,
-                   nwords);
+      const unsigned long long e0 = ((t_begin + 1) * T < q.n_rows) ? (t_begin + 1) * T : q.n_rows;
+      helper_build(q, sm, 0, 0, t_begin * T, e0, nwords);
+      if (q.n_pbm) helper_pass_bitmaps(q, sm, aux_smem ? sm.aux : q.aux, 0, 0, t_begin * T, e0, nwords);
       if (t_begin + 1 < t_end) prefetch_windows(q, sm, 1);
     }
   }
@@ -233,6 +310,7 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
       tv.cur = sm.tcur + buf * kMaxBitmapCols;
       const int wb = (int)((t - t_begin) % kWinBufs);
       tv.win = window_set(q, sm, wb);
+      tv.pbm = sm.pbm + (size_t)buf * q.n_pbm * nwords;
       tv.wn = sm.wcnt + wb * kMaxBitmapCols;
       tv.stage = sm.stage + (size_t)st * q.stage_bytes;
       tv.aux = aux_smem ? sm.aux : q.aux;
@@ -241,8 +319,10 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
       const uint32_t n_pass = compact<GPW>(pm, wbase, gstride, mylist);
       phase_aggregate<false, 2>(q, sm, tv, nullptr, mylist, n_pass, s);
     } else if (nb && t + 1 < t_end) {
-      helper_build(q, sm, buf ^ 1, (int)((t + 1 - t_begin) % kWinBufs), e, (e + T < q.n_rows) ? e + T : q.n_rows,
-                   nwords);
+      const int wb1 = (int)((t + 1 - t_begin) % kWinBufs);
+      const unsigned long long e1 = (e + T < q.n_rows) ? e + T : q.n_rows;
+      helper_build(q, sm, buf ^ 1, wb1, e, e1, nwords);
+      if (q.n_pbm) helper_pass_bitmaps(q, sm, aux_smem ? sm.aux : q.aux, buf ^ 1, wb1, e, e1, nwords);
       if (t + 2 < t_end) prefetch_windows(q, sm, (int)((t + 2 - t_begin) % kWinBufs));
     }
     // one barrier per tile; thread 0 decides the flush from the occupancy it

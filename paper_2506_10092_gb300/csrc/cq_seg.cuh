@@ -201,6 +201,7 @@ __device__ __forceinline__ void seg_range(const QueryDesc& q, const Smem& sm, un
   tv.pre = sm.pre;
   tv.cur = sm.tcur;
   tv.win = nullptr;
+  tv.pbm = nullptr;
   tv.wn = sm.wcnt;   // zero: no windows in segment mode
   tv.stage = nullptr;
   tv.aux = aux_smem ? sm.aux : q.aux;
