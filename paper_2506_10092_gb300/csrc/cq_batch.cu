@@ -3,7 +3,7 @@
 // Many queries, over tables (or partitions) of very different sizes, run in
 // one launch.  The host cuts every query's tiles into work items (query, tile
 // range), orders them larger first, and uploads them with the queries'
-// descriptors.  Each CTA of a one-CTA-per-SM grid repeatedly takes the next
+// descriptors.  Each CTA of a one- (or two-) CTA-per-SM grid repeatedly takes the next
 // item from a global counter, copies that query's descriptor into shared
 // memory, lays out the dynamic shared memory for it, and walks the item's
 // tiles with the one-query steps: segment mode (cq_seg.cuh) or row mode with
@@ -22,7 +22,10 @@ namespace cq {
 constexpr int kBatchThreads = (kWarps + 1) * 32;
 static_assert(sizeof(QueryDesc) % 8 == 0, "descriptor is copied in 8-byte words");
 
-__global__ void __launch_bounds__(kBatchThreads, 1) batch_query_kernel(BatchCtl* ctl) {
+// MINB CTAs per SM: 1, or 2 when every query of the batch was planned within
+// half an SM's shared memory (more resident warps hide more latency).
+template <int MINB>
+__global__ void __launch_bounds__(kBatchThreads, MINB) batch_query_kernel(BatchCtl* ctl) {
   __shared__ __align__(16) QueryDesc qs;
   __shared__ unsigned long long item_id;
   const uint32_t n_items = ctl->n_items;
@@ -61,24 +64,29 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_query_kernel(BatchCtl*
   }
 }
 
-cudaError_t batch_kernel_static_smem(size_t* bytes) {
+cudaError_t batch_kernel_static_smem(int minb, size_t* bytes) {
   cudaFuncAttributes a;
-  const cudaError_t e = cudaFuncGetAttributes(&a, batch_query_kernel);
+  const cudaError_t e = minb == 2 ? cudaFuncGetAttributes(&a, batch_query_kernel<2>)
+                                  : cudaFuncGetAttributes(&a, batch_query_kernel<1>);
   if (e == cudaSuccess) *bytes = a.sharedSizeBytes;
   return e;
 }
 
-cudaError_t batch_kernel_set_smem(size_t bytes) {
-  return cudaFuncSetAttribute(batch_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t batch_kernel_set_smem(int minb, size_t bytes) {
+  return minb == 2
+             ? cudaFuncSetAttribute(batch_query_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)
+             : cudaFuncSetAttribute(batch_query_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 cudaError_t launch_batch_init(const BatchCtl* ctl, cudaStream_t s, unsigned grid);       // cq_query.cu
 cudaError_t launch_batch_finalize(const BatchCtl* ctl, cudaStream_t s, unsigned grid);   // cq_query.cu
 
-cudaError_t launch_batch(BatchCtl* ctl_dev, cudaStream_t s, unsigned grid, size_t dyn_smem, unsigned aux_grid) {
+cudaError_t launch_batch(BatchCtl* ctl_dev, cudaStream_t s, unsigned grid, int minb, size_t dyn_smem,
+                         unsigned aux_grid) {
   cudaError_t e = launch_batch_init(ctl_dev, s, aux_grid);
   if (e != cudaSuccess) return e;
-  batch_query_kernel<<<grid, kBatchThreads, dyn_smem, s>>>(ctl_dev);
+  if (minb == 2) batch_query_kernel<2><<<grid, kBatchThreads, dyn_smem, s>>>(ctl_dev);
+  else batch_query_kernel<1><<<grid, kBatchThreads, dyn_smem, s>>>(ctl_dev);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return launch_batch_finalize(ctl_dev, s, aux_grid);
 }

@@ -223,7 +223,8 @@ struct cq_ctx {
   std::mutex batch_mu;
   std::vector<cq::BatchGraph*> graphs;   // owned; freed by the destructor (cq_serve.cu)
   std::vector<cq::TunedShape> tuned;
-  size_t batch_smem = 0;     // dynamic shared memory of the batch kernel
+  size_t batch_smem = 0;     // dynamic shared memory of the batch kernel (one CTA per SM)
+  size_t batch_smem_two = 0; // ... and with two CTAs per SM
   ~cq_ctx();
 };
 
@@ -308,9 +309,10 @@ cudaError_t query_kernel_set_smem(size_t bytes);
 
 // batches (cq_batch.cu): the persistent kernel's static shared memory, its
 // dynamic-size attribute, and the launch of init -> items -> finalize
-cudaError_t batch_kernel_static_smem(size_t* bytes);
-cudaError_t batch_kernel_set_smem(size_t bytes);
-cudaError_t launch_batch(BatchCtl* ctl_dev, cudaStream_t s, unsigned grid, size_t dyn_smem, unsigned aux_grid);
+cudaError_t batch_kernel_static_smem(int minb, size_t* bytes);
+cudaError_t batch_kernel_set_smem(int minb, size_t bytes);
+cudaError_t launch_batch(BatchCtl* ctl_dev, cudaStream_t s, unsigned grid, int minb, size_t dyn_smem,
+                         unsigned aux_grid);
 
 // planner / results (cq_api.cu)
 int plan_batch_query(cq_table* table, const cq_plan* plan, uint32_t tile_rows, size_t smem_limit, Planned* P);

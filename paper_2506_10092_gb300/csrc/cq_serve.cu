@@ -33,6 +33,7 @@ struct BatchGraph {
   int device = 0;
   size_t cap = 0;                 // control-block bytes
   unsigned grid = 0;              // persistent CTAs
+  int minb = 1;                   // CTAs per SM
   uint8_t* host = nullptr;        // pinned staging
   uint8_t* dev = nullptr;         // control block (device)
   cudaGraph_t graph = nullptr;
@@ -72,13 +73,17 @@ static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 // the kernel's static shared memory (its descriptor copy).
 static int ensure_batch_kernel(cq_ctx* ctx) {
   if (ctx->batch_smem) return CQ_OK;
-  size_t st = 0;
-  cudaError_t e = batch_kernel_static_smem(&st);
-  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "batch kernel attributes: %s", cudaGetErrorString(e));
-  const size_t dyn = (ctx->smem_optin - st) / 128 * 128;
-  e = batch_kernel_set_smem(dyn);
-  if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "batch kernel shared memory: %s", cudaGetErrorString(e));
-  ctx->batch_smem = dyn;
+  for (int minb = 1; minb <= 2; ++minb) {
+    size_t st = 0;
+    cudaError_t e = batch_kernel_static_smem(minb, &st);
+    if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "batch kernel attributes: %s", cudaGetErrorString(e));
+    const size_t limit = minb == 2 ? ctx->smem_two : ctx->smem_optin;
+    const size_t dyn = (limit - st) / 128 * 128;
+    e = batch_kernel_set_smem(minb, dyn);
+    if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "batch kernel shared memory: %s", cudaGetErrorString(e));
+    if (minb == 2) ctx->batch_smem_two = dyn;
+    else ctx->batch_smem = dyn;
+  }
   return CQ_OK;
 }
 
@@ -88,7 +93,8 @@ static int capture_graph(cq_ctx* ctx, BatchGraph* g) {
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->dev, g->host, g->cap, cudaMemcpyHostToDevice, cs);
   if (e == cudaSuccess)
-    e = launch_batch(reinterpret_cast<BatchCtl*>(g->dev), cs, g->grid, ctx->batch_smem, (unsigned)ctx->num_sms * 2);
+    e = launch_batch(reinterpret_cast<BatchCtl*>(g->dev), cs, g->grid, g->minb,
+                     g->minb == 2 ? ctx->batch_smem_two : ctx->batch_smem, (unsigned)ctx->num_sms * 2);
   cudaGraph_t graph = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
   if (e == cudaSuccess) e = e2;
@@ -113,7 +119,8 @@ static int capture_graph(cq_ctx* ctx, BatchGraph* g) {
 }
 
 // A launch graph whose control block holds `bytes`, marked as being filled.
-static int acquire_graph(cq_ctx* ctx, size_t bytes, unsigned grid, BatchGraph** out) {
+static int acquire_graph(cq_ctx* ctx, size_t bytes, int minb, BatchGraph** out) {
+  const unsigned grid = (unsigned)ctx->num_sms * (unsigned)minb;
   std::unique_lock<std::mutex> lk(ctx->batch_mu);
   for (int pass = 0; pass < 2; ++pass) {
     for (auto& g : ctx->graphs) {
@@ -138,6 +145,7 @@ static int acquire_graph(cq_ctx* ctx, size_t bytes, unsigned grid, BatchGraph** 
   g->cap = 256 * 1024;
   while (g->cap < bytes) g->cap *= 2;
   g->grid = grid;
+  g->minb = minb;
   CQ_CUDA(cudaMalloc(&g->dev, g->cap));
   CQ_CUDA(cudaMallocHost(&g->host, g->cap));
   CQ_CUDA(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming));
@@ -195,12 +203,12 @@ static uint64_t query_footprint(const Planned& P) {
   return al256(query_block_layout(P, false).total) + sizeof(QueryDesc) + 4 * P.aux.size() + 64;
 }
 
+// Plan every query of a batch within `smem_limit` bytes of shared memory.
 static int plan_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, uint32_t tile_rows,
-                      std::vector<Planned>* P) {
-  cq_ctx* ctx = tables[0]->ctx;
+                      size_t smem_limit, std::vector<Planned>* P) {
   P->resize(n);
   for (uint32_t i = 0; i < n; ++i) {
-    const int rc = plan_batch_query(tables[i], &plans[i], tile_rows, ctx->batch_smem, &(*P)[i]);
+    const int rc = plan_batch_query(tables[i], &plans[i], tile_rows, smem_limit, &(*P)[i]);
     if (rc != CQ_OK) {
       const std::string msg = cq_last_error();
       return set_error(rc, "batch query %u: %s", i, msg.c_str());
@@ -211,9 +219,9 @@ static int plan_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans,
 
 // Launch n planned queries as one batch on stream s (see cq_batch_run).
 static int launch_planned_batch(cq_ctx* ctx, uint32_t n, cq_table* const* tables, std::vector<Planned>& P,
-                                uint32_t items_per_cta, cudaStream_t s, cq_result** results) {
+                                uint32_t items_per_cta, int minb, cudaStream_t s, cq_result** results) {
   // ---- work items: C tiles at most, about items_per_cta per CTA, larger first
-  const unsigned grid = (unsigned)ctx->num_sms;
+  const unsigned grid = (unsigned)ctx->num_sms * (unsigned)minb;
   uint64_t total_tiles = 0;
   for (const Planned& p : P) total_tiles += p.q.n_tiles;
   const uint64_t target = (uint64_t)grid * (items_per_cta ? items_per_cta : 4u);
@@ -265,7 +273,7 @@ static int launch_planned_batch(cq_ctx* ctx, uint32_t n, cq_table* const* tables
   CQ_CUDA(cudaEventCreate(&sh->ev_done));
   // ---- fill the staging copy of a launch graph's control block
   BatchGraph* g = nullptr;
-  int rc = acquire_graph(ctx, bytes, grid, &g);
+  int rc = acquire_graph(ctx, bytes, minb, &g);
   if (rc != CQ_OK) return rc;
   uint8_t* h = g->host;
   uint8_t* d = g->dev;
@@ -323,10 +331,25 @@ static int launch_planned_batch(cq_ctx* ctx, uint32_t n, cq_table* const* tables
 
 static int run_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, uint32_t tile_rows,
                      uint32_t items_per_cta, cudaStream_t s, cq_result** results) {
+  // two CTAs per SM when every query fits half an SM's shared memory at its
+  // preferred tile, else one
+  cq_ctx* ctx = tables[0]->ctx;
   std::vector<Planned> P;
-  const int rc = plan_batch(n, tables, plans, tile_rows, &P);
-  if (rc != CQ_OK) return rc;
-  return launch_planned_batch(tables[0]->ctx, n, tables, P, items_per_cta, s, results);
+  int minb = 2;
+  int rc = plan_batch(n, tables, plans, tile_rows, ctx->batch_smem_two, &P);
+  if (rc == CQ_OK) {
+    for (const Planned& p : P) {
+      const uint32_t want = tile_rows ? tile_rows : (p.q.seg_mode ? 4096u : 8192u);
+      if (p.q.tile_rows < want) minb = 1;
+    }
+  }
+  if (rc != CQ_OK || minb == 1) {
+    minb = 1;
+    clear_error();
+    rc = plan_batch(n, tables, plans, tile_rows, ctx->batch_smem, &P);
+    if (rc != CQ_OK) return rc;
+  }
+  return launch_planned_batch(ctx, n, tables, P, items_per_cta, minb, s, results);
 }
 
 static int check_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, cq_result** results,
@@ -636,7 +659,7 @@ static void serve(cq_server* srv) {
         // a batch of one runs the one-query kernels (no per-item table
         // resets and flushes, no control-block upload)
         const int rc = b.size() == 1 ? launch_solo(tables[0], P[0], srv->streams[sidx], &res[0])
-                                     : launch_planned_batch(srv->ctx, (uint32_t)b.size(), tables.data(), P, 0,
+                                     : launch_planned_batch(srv->ctx, (uint32_t)b.size(), tables.data(), P, 0, 1,
                                                             srv->streams[sidx], res.data());
         const std::string err = rc == CQ_OK ? std::string() : std::string(cq_last_error());
         cudaEvent_t ev = nullptr;
