@@ -761,30 +761,6 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       d.n32 = 1;
     }
   }
-  // ---- evaluation order and per-run evaluation (Appendix D: predicates on
-  // run-length columns are tested first, once per run value).  Row mode:
-  // each RLE / index predicate gets a tile pass bitmap the helper warp fills
-  // from the run (listed-row) values; segment mode evaluates per segment.
-  {
-    // order: predicates with a pass bitmap, other RLE / index predicates, the rest
-    q.n_pbm = 0;
-    for (uint32_t i = 0; i < plan->n_preds; ++i) {
-      PredDesc& d = q.preds[i];
-      const uint8_t enc = q.cols[d.col].enc;
-      d.pbm = 0xFF;
-      if ((enc == ENC_RLE || enc == ENC_INDEX) && !q.seg_mode && d.kind != PK_TRUE && d.kind != PK_FALSE &&
-          q.n_pbm < kMaxPassBitmaps)
-        d.pbm = q.n_pbm++;
-    }
-    uint32_t k = 0;
-    for (int pass = 0; pass < 3; ++pass)
-      for (uint32_t i = 0; i < plan->n_preds; ++i) {
-        const PredDesc& d = q.preds[i];
-        const uint8_t enc = q.cols[d.col].enc;
-        const int cls = d.pbm != 0xFF ? 0 : (enc == ENC_RLE || enc == ENC_INDEX) ? 1 : 2;
-        if (cls == pass) q.pred_order[k++] = (uint8_t)i;
-      }
-  }
   // ---- group keys (dense mixed radix, first key most significant)
   q.n_keys = (uint8_t)plan->n_group_by;
   i128 groups = 1;
@@ -858,6 +834,32 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     stride *= q.keys[k].card;
   }
   q.n_groups = (uint64_t)groups;
+  // ---- evaluation order and per-run evaluation (Appendix D: predicates on
+  // run-length columns are tested first, once per run value).  Row mode:
+  // up to kMaxPassBitmaps RLE / index predicates get a tile pass bitmap the
+  // helper warp fills from the run (listed-row) values; segment mode
+  // evaluates per segment.  The descriptors are reordered in place (the keys
+  // above copied what they needed): pass-bitmap predicates, other RLE /
+  // index predicates, the rest.
+  {
+    q.n_pbm = 0;
+    int cls[kMaxPreds];
+    for (uint32_t i = 0; i < plan->n_preds; ++i) {
+      PredDesc& d = q.preds[i];
+      const uint8_t enc = q.cols[d.col].enc;
+      const bool run_col = enc == ENC_RLE || enc == ENC_INDEX;
+      d.pbm = 0xFF;
+      if (run_col && !q.seg_mode && d.kind != PK_TRUE && d.kind != PK_FALSE && q.n_pbm < kMaxPassBitmaps)
+        d.pbm = q.n_pbm++;
+      cls[i] = d.pbm != 0xFF ? 0 : run_col ? 1 : 2;
+    }
+    PredDesc sorted[kMaxPreds];
+    uint32_t k = 0;
+    for (int c = 0; c < 3; ++c)
+      for (uint32_t i = 0; i < plan->n_preds; ++i)
+        if (cls[i] == c) sorted[k++] = q.preds[i];
+    for (uint32_t i = 0; i < k; ++i) q.preds[i] = sorted[i];
+  }
   // ---- table shape and flush period
   q.flush_rows = 1u << 20;
   // a SUM whose values are small enough for a 32-bit shared word over a

@@ -129,8 +129,7 @@ struct QueryDesc {
   uint8_t n_sw32;          // 32-bit shared accumulator words per slot (word 0 = COUNT)
   uint8_t n_gw;            // global accumulator words per group (word 0 = COUNT)
   uint8_t has_index_agg;
-  uint8_t n_pbm;           // tile pass bitmaps (row mode predicates on RLE / index columns)
-  uint8_t pred_order[kMaxPreds];  // evaluation order: RLE / index predicates first
+  uint8_t n_pbm;           // tile pass bitmaps: predicates 0 .. n_pbm-1 (row mode, RLE / index columns)
   uint32_t flush_rows;     // flush the shared table at least this often (rows)
   uint64_t n_groups;       // dense global domain
   uint8_t row_cols[kMaxCols];   // ColDesc indices of staged columns

@@ -579,7 +579,7 @@ __device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileV
     // the first n_pbm predicates were evaluated once per run by the helper
     // warp: one bit per row
     for (; first < q.n_pbm; ++first) {
-      const uint32_t* PB = t.pbm + (size_t)q.preds[q.pred_order[first]].pbm * t.nwords;
+      const uint32_t* PB = t.pbm + (size_t)q.preds[first].pbm * t.nwords;
 #pragma unroll 4
       for (int g = 0; g < GPW; ++g)
         if (!((PB[(wbase + g * gstride) >> 5] >> lane) & 1u)) pm &= ~(1u << g);
@@ -587,7 +587,7 @@ __device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileV
   }
   for (int oi = first; oi < q.n_preds; ++oi) {
     if (!__any_sync(0xFFFFFFFFu, pm != 0)) break;
-    const PredDesc& p = q.preds[q.pred_order[oi]];
+    const PredDesc& p = q.preds[oi];
     if (p.kind == PK_TRUE) continue;
     if (p.kind == PK_FALSE) {
       pm = 0;
