@@ -202,7 +202,8 @@ typedef struct {
   int32_t mode;          /* cq_exec_mode */
   uint32_t tile_rows;    /* rows per tile (multiple of 1024, <= 16384); 0 = default */
   uint32_t ctas_per_sm;  /* 0 = default */
-  uint32_t stages;       /* bulk-copy pipeline depth (2..8); 0 = default */
+  uint32_t stages;       /* bulk-copy pipeline depth (1..8); 0 = default (4, fewer if shared
+                            memory is short, never below 2) */
   uint32_t table_slots;  /* shared-memory group-table slots per CTA (power of 2); 0 = default */
   uint32_t grid_ctas;    /* CTAs of the fused kernel; 0 = SMs x ctas_per_sm */
   uint32_t items_per_cta;  /* batches: work items per CTA the tiles are cut into

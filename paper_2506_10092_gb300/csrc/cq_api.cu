@@ -645,7 +645,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   q.stage_bytes = stage_off;
   q.stages = (uint8_t)(opts && opts->stages ? opts->stages : 4);
   q.ncw = (uint8_t)ncw;
-  if (q.stages < 2 || q.stages > 8) return set_error(CQ_ERR_INVALID_ARG, "stages must be in 2..8");
+  if (q.stages < 1 || q.stages > 8) return set_error(CQ_ERR_INVALID_ARG, "stages must be in 1..8");
   auto& aux = P->aux;
   // ---- predicates
   q.n_preds = (uint8_t)plan->n_preds;
