@@ -201,7 +201,7 @@ typedef enum {
 typedef struct {
   int32_t mode;          /* cq_exec_mode */
   uint32_t tile_rows;    /* rows per tile (multiple of 1024, <= 16384); 0 = default */
-  uint32_t ctas_per_sm;  /* 0 = default */
+  uint32_t ctas_per_sm;  /* 0 = default (the planner picks); 1, 2, or 3 (segment mode only) */
   uint32_t stages;       /* bulk-copy pipeline depth (1..8); 0 = default (4, fewer if shared
                             memory is short, never below 2) */
   uint32_t table_slots;  /* shared-memory group-table slots per CTA (power of 2); 0 = default */

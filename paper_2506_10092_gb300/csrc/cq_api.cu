@@ -156,6 +156,7 @@ extern "C" int cq_ctx_create(int device, void* cuda_stream, cq_ctx** out) {
   CQ_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
   CQ_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
   c->smem_two = (size_t)(per_sm / 2 - reserved);
+  c->smem_three = (size_t)(per_sm / 3 - reserved) / 128 * 128;
   cudaMemPoolProps props{};
   props.allocType = cudaMemAllocationTypePinned;
   props.location.type = cudaMemLocationTypeDevice;
@@ -1002,7 +1003,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   // ncw 8 marks the two-CTA row shape; segment mode runs two CTAs per SM
   // whenever its shared memory fits half an SM (ncw 16 with limit smem_two)
   P->ctas_per_sm = (!q.seg_mode && ncw == 8) ? 2 : 1;
-  if (q.seg_mode && smem_limit <= ctx->smem_two) P->ctas_per_sm = 2;
+  if (q.seg_mode && smem_limit <= ctx->smem_two) P->ctas_per_sm = smem_limit <= ctx->smem_three ? 3 : 2;
   P->grid_ctas = opts ? opts->grid_ctas : 0u;
   // ---- outputs
   q.n_out = plan->n_group_by + plan->n_aggs;
@@ -1036,7 +1037,7 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   const uint32_t want_ctas = opts ? opts->ctas_per_sm : 0;
   if (want_tile && (want_tile < 1024 || want_tile > 8192 || (want_tile & (want_tile - 1))))
     return set_error(CQ_ERR_INVALID_ARG, "tile_rows must be 1024, 2048, 4096 or 8192");
-  if (want_ctas > 2) return set_error(CQ_ERR_INVALID_ARG, "ctas_per_sm must be 0, 1 or 2");
+  if (want_ctas > 3) return set_error(CQ_ERR_INVALID_ARG, "ctas_per_sm must be 0, 1, 2 or 3 (3: segment mode)");
   // segment mode when every referenced column is RLE or index-encoded
   bool seg = true;
   auto look = [&](uint32_t c) {
@@ -1059,7 +1060,9 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
     // row mode), one CTA per SM, shared memory within the batch kernel's limit
     add(16, seg ? 4096u : 8192u, batch_limit);
   } else if (seg) {
-    // two CTAs per SM when the tile fits half the shared memory, else one
+    // three CTAs per SM when the tile fits a third of the shared memory, two
+    // when it fits half, else one
+    if (want_ctas == 0 || want_ctas == 3) add(16, 4096, ctx->smem_three);
     if (want_ctas != 1) add(16, 4096, ctx->smem_two);
     add(16, 4096, ctx->smem_optin);
   } else if (want_ctas == 2) {

@@ -217,6 +217,7 @@ struct cq_ctx {
   int num_sms = 0;
   size_t smem_optin = 0;     // max dynamic shared memory of one CTA
   size_t smem_two = 0;       // max dynamic shared memory per CTA with two CTAs per SM
+  size_t smem_three = 0;     // ... with three CTAs per SM (segment mode)
   std::mutex mu;
   // batches: cached launch graphs and autotuned shapes
   std::mutex batch_mu;

@@ -314,6 +314,7 @@ cudaError_t query_kernel_set_smem(size_t bytes) {
   if ((e = cudaFuncSetAttribute(seg_query_kernel<G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
   CQ_SEG_SET(2, 1) CQ_SEG_SET(4, 1) CQ_SEG_SET(8, 1) CQ_SEG_SET(16, 1)
   CQ_SEG_SET(2, 2) CQ_SEG_SET(4, 2) CQ_SEG_SET(8, 2) CQ_SEG_SET(16, 2)
+  CQ_SEG_SET(2, 3) CQ_SEG_SET(4, 3) CQ_SEG_SET(8, 3) CQ_SEG_SET(16, 3)
 #undef CQ_SEG_SET
   return row_kernel_set_smem(b);
 }
@@ -332,21 +333,19 @@ cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ct
   if (grid == 0) return cudaSuccess;
   if (!q.seg_mode) return launch_row_kernel(q, grid, s);
   switch (q.tile_rows / kThreads) {
-    // two CTAs per SM overlap one CTA's barrier-separated phases with the other's
-    case 2:
-      if (ctas_per_sm == 2) seg_query_kernel<2, 2><<<grid, kThreads, q.smem_bytes, s>>>(q);
-      else seg_query_kernel<2, 1><<<grid, kThreads, q.smem_bytes, s>>>(q);
-      break;
-    case 4:
-      if (ctas_per_sm == 2) seg_query_kernel<4, 2><<<grid, kThreads, q.smem_bytes, s>>>(q);
-      else seg_query_kernel<4, 1><<<grid, kThreads, q.smem_bytes, s>>>(q);
-      break;
-    case 8:
-      if (ctas_per_sm == 2) seg_query_kernel<8, 2><<<grid, kThreads, q.smem_bytes, s>>>(q);
-      else seg_query_kernel<8, 1><<<grid, kThreads, q.smem_bytes, s>>>(q);
-      break;
+    // two or three CTAs per SM overlap one CTA's barrier-separated phases with
+    // the others'
+#define CQ_SEG_GO(G)                                                                      \
+  case G:                                                                                 \
+    if (ctas_per_sm == 3) seg_query_kernel<G, 3><<<grid, kThreads, q.smem_bytes, s>>>(q); \
+    else if (ctas_per_sm == 2) seg_query_kernel<G, 2><<<grid, kThreads, q.smem_bytes, s>>>(q); \
+    else seg_query_kernel<G, 1><<<grid, kThreads, q.smem_bytes, s>>>(q);                  \
+    break;
+    CQ_SEG_GO(2) CQ_SEG_GO(4) CQ_SEG_GO(8)
+#undef CQ_SEG_GO
     default:
-      if (ctas_per_sm == 2) seg_query_kernel<16, 2><<<grid, kThreads, q.smem_bytes, s>>>(q);
+      if (ctas_per_sm == 3) seg_query_kernel<16, 3><<<grid, kThreads, q.smem_bytes, s>>>(q);
+      else if (ctas_per_sm == 2) seg_query_kernel<16, 2><<<grid, kThreads, q.smem_bytes, s>>>(q);
       else seg_query_kernel<16, 1><<<grid, kThreads, q.smem_bytes, s>>>(q);
       break;
   }

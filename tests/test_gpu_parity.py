@@ -77,7 +77,7 @@ def test_random_tables(cq, ctx, oracle_mod, seed):
     plan = random_plan(rng, table)
     ref = oracle_mod.query(table, plan)
     tile = int(rng.choice([1024, 2048, 4096, 8192]))
-    opts = cq.exec_options(tile_rows=tile, stages=int(rng.choice([2, 3, 4])),
+    opts = cq.exec_options(tile_rows=tile, stages=int(rng.choice([1, 2, 3, 4])),
                            table_slots=int(rng.choice([128, 1024])))
     check(run(cq, ctx, table, plan, device=bool(seed % 2), opts=opts), ref, f"seed {seed} tile {tile}")
 
