@@ -79,29 +79,23 @@ __global__ void check_index_kernel(const void* vals, bool v64, const void* pos, 
 
 // Packed / dictionary codes: range of the unsigned fields (signed view for
 // 64-bit fields); codes must be below n_entries.
-// One thread per 32-bit word of the stream: it decodes the fields that start
-// in its word (consecutive threads read consecutive words).
+// One thread per row: the row's field (codes of a dictionary column must lie
+// below its size), folded into the column's min / max.
 __global__ void check_packed_kernel(const uint32_t* words, unsigned long long n_words, uint32_t bw,
                                     unsigned long long n_rows, unsigned long long limit, CheckOut* out) {
   long long lmin = LLONG_MAX, lmax = LLONG_MIN;
-  const unsigned long long used = (n_rows * bw + 31) / 32;   // words holding a field start
-  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < used;
-       j += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long b0 = j * 32;
-    const unsigned long long f0 = (b0 + bw - 1) / bw;
-    unsigned long long f1 = (b0 + 32 + bw - 1) / bw;
-    if (f1 > n_rows) f1 = n_rows;
-    const uint32_t w0 = __ldg(words + j), w1 = j + 1 < n_words ? __ldg(words + j + 1) : 0u;
-    const uint32_t w2 = (bw > 32 && j + 2 < n_words) ? __ldg(words + j + 2) : 0u;
-    for (unsigned long long f = f0; f < f1; ++f) {
-      const uint32_t sh = (uint32_t)(f * bw - b0);
-      uint64_t v = __funnelshift_r(w0, w1, sh);
-      if (bw > 32) v |= (uint64_t)__funnelshift_r(w1, w2, sh) << 32;
-      if (bw < 64) v &= (1ull << bw) - 1ull;
-      if (limit && v >= limit) atomicCAS(&out->err, 0, (int)CQ_ERR_INVALID_ARG);
-      lmin = min(lmin, (long long)v);
-      lmax = max(lmax, (long long)v);
-    }
+  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < n_rows;
+       r += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long bit = r * bw;
+    const unsigned long long q = bit >> 5;
+    const uint32_t sh = (uint32_t)(bit & 31);
+    const uint32_t w0 = __ldg(words + q), w1 = q + 1 < n_words ? __ldg(words + q + 1) : 0u;
+    uint64_t f = __funnelshift_r(w0, w1, sh);
+    if (bw > 32) f |= (uint64_t)__funnelshift_r(w1, q + 2 < n_words ? __ldg(words + q + 2) : 0u, sh) << 32;
+    if (bw < 64) f &= (1ull << bw) - 1ull;
+    if (limit && f >= limit) atomicCAS(&out->err, 0, (int)CQ_ERR_INVALID_ARG);
+    lmin = min(lmin, (long long)f);
+    lmax = max(lmax, (long long)f);
   }
   block_minmax(lmin, lmax, out);
 }
