@@ -244,7 +244,7 @@ int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_exec_options*
  * replayed for every later batch that fits it; only the upload size changes.
  * opts: mode must be CQ_EXEC_FUSED; tile_rows and items_per_cta select the
  * shape (0 = the autotuned shape of cq_batch_tune for this kind of batch,
- * else tile 4096 rows for all-RLE/index queries and 8192 otherwise, 4 items
+ * else tiles of 8192 rows, 4 items
  * per CTA); ctas_per_sm, stages and grid_ctas are ignored.
  * Asynchronous like cq_query_run; results[i] is owned by the caller (the
  * device buffers of the batch are freed when its last result is destroyed).

@@ -1025,11 +1025,9 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
 }
 
 // Plan the query, trying kernel shapes in order of preference until one fits
-// in shared memory.  Row mode runs one CTA of 16 compute warps per SM with
-// 8192-row tiles (two CTAs of 8 compute warps with 4096-row tiles when asked);
-// tiles halve down to 1024 rows.  Segment mode runs one 512-thread CTA per SM.
-// Options pin the tile size (smaller ones are tried when it does not fit)
-// and / or the CTAs per SM.
+// in shared memory (the order is given where the shapes are listed below);
+// tiles halve down to 1024 rows.  Options pin the tile size (smaller ones are
+// tried when it does not fit) and / or the CTAs per SM.
 static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
                       const cq_exec_options* opts, const cq_ctx* ctx, Planned* P, size_t batch_limit = 0) {
   if (!plan) return set_error(CQ_ERR_INVALID_ARG, "plan is NULL");
@@ -1058,13 +1056,13 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   if (batch_limit) {
     // a batch shares one kernel shape: 16 compute warps (+ the helper warp in
     // row mode), one CTA per SM, shared memory within the batch kernel's limit
-    add(16, seg ? 4096u : 8192u, batch_limit);
+    add(16, 8192u, batch_limit);
   } else if (seg) {
     // three CTAs per SM when the tile fits a third of the shared memory, two
     // when it fits half, else one
-    if (want_ctas == 0 || want_ctas == 3) add(16, 4096, ctx->smem_three);
-    if (want_ctas != 1) add(16, 4096, ctx->smem_two);
-    add(16, 4096, ctx->smem_optin);
+    if (want_ctas == 0 || want_ctas == 3) add(16, 8192, ctx->smem_three);
+    if (want_ctas != 1) add(16, 8192, ctx->smem_two);
+    add(16, 8192, ctx->smem_optin);
   } else if (want_ctas == 2) {
     add(8, 8192, ctx->smem_two);
   } else {

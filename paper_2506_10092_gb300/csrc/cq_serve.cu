@@ -339,7 +339,7 @@ static int run_batch(uint32_t n, cq_table* const* tables, const cq_plan* plans, 
   int rc = plan_batch(n, tables, plans, tile_rows, ctx->batch_smem_two, &P);
   if (rc == CQ_OK) {
     for (const Planned& p : P) {
-      const uint32_t want = tile_rows ? tile_rows : (p.q.seg_mode ? 4096u : 8192u);
+      const uint32_t want = tile_rows ? tile_rows : 8192u;
       if (p.q.tile_rows < want) minb = 1;
     }
   }
