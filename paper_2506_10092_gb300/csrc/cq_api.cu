@@ -1000,8 +1000,8 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     }
     q.smem_bytes = (uint32_t)query_kernel_smem(q);
   }
-  // ncw 8 marks the two-CTA row shape; segment mode runs two CTAs per SM
-  // whenever its shared memory fits half an SM (ncw 16 with limit smem_two)
+  // ncw 8 marks the two-CTA row shape; segment mode runs three (two) CTAs per
+  // SM whenever its shared memory fits a third (half) of an SM
   P->ctas_per_sm = (!q.seg_mode && ncw == 8) ? 2 : 1;
   if (q.seg_mode && smem_limit <= ctx->smem_two) P->ctas_per_sm = smem_limit <= ctx->smem_three ? 3 : 2;
   P->grid_ctas = opts ? opts->grid_ctas : 0u;
@@ -1049,6 +1049,7 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   std::vector<Shape> shapes;
   auto add = [&](int ncw, uint32_t first, size_t limit) {
     // a tile is 16 compute warps * 32 * GPW rows with GPW in {2, 4, 8, 16}
+    // (the 24- and 28-warp shapes are listed with their own tile sizes)
     const uint32_t max_tile = 8192u;
     for (uint32_t t = want_tile ? want_tile : first; t >= 1024; t /= 2)
       if (t <= max_tile) shapes.push_back({ncw, t, limit});

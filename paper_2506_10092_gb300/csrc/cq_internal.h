@@ -121,7 +121,7 @@ struct QueryDesc {
   uint8_t n_row_cols;      // columns staged per tile (row mode)
   uint8_t stages;
   uint8_t ncw;             // row mode shape: 16 = one CTA of 16 compute warps per SM, 8 = two such CTAs,
-                           // 24 = one CTA of 24 compute warps (6144-row tiles)
+                           // 24 / 28 = one CTA of 24 / 28 compute warps (6144 / 7168-row tiles)
   uint32_t stage_bytes;    // bytes of one stage (all row-level columns)
   uint32_t table_slots;    // shared-memory group-table slots (power of two)
   uint8_t table_dense;     // 1: slot = gid (gid domain fits the table)

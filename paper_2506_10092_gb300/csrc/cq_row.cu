@@ -4,10 +4,11 @@
 //
 // Each CTA (one or two per SM) walks a contiguous range of tiles with a
 // software pipeline:
-//  * 8 or 16 compute warps filter and aggregate tile t;
-//  * one helper warp builds the run-end / position bitmaps of tile t+1 from
-//    windows it prefetched with cp.async during tile t-1, and prefetches the
-//    windows of tile t+2;
+//  * 16, 24 or 28 compute warps filter and aggregate tile t;
+//  * one helper warp builds the run-end / position bitmaps (and the pass
+//    bitmaps of run-length predicates) of tile t+1 from windows it
+//    prefetched with cp.async during tile t-1, and prefetches the windows
+//    of tile t+2;
 //  * the helper's lane 0 keeps `stages` tiles of the row-level columns in
 //    flight with 1-D bulk copies (TMA engine) completing on mbarriers.
 // One CTA barrier separates tiles; the group table is flushed to the global
@@ -42,7 +43,8 @@ cudaError_t row_kernel_set_smem(int bytes) {
 }
 
 cudaError_t launch_row_kernel(const QueryDesc& q, unsigned grid, cudaStream_t s) {
-  // ncw field: 16 one CTA of 16 compute warps, 8 two such CTAs, 24 one CTA of 24
+  // ncw field: 16 one CTA of 16 compute warps, 8 two such CTAs, 24 / 28 one
+  // CTA of 24 / 28
   const int ncw = (q.ncw == 24 || q.ncw == 28) ? q.ncw : 16;
   const int gpw = (int)(q.tile_rows / (ncw * 32));
   const int minb = q.ncw == 8 ? 2 : 1;
