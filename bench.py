@@ -91,11 +91,23 @@ def measured_peak():
 ROW_KERNEL_SOURCES = ("cq_row.cu", "cq_rowpath.cuh", "cq_phases.cuh", "cq_device.cuh", "cq_internal.h")
 
 
-def kernel_source_hash() -> str:
+def _code_only(text: str) -> str:
+    """Source text without comments and whitespace (comment edits keep the hash)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return re.sub(r"\s+", "", text)
+
+
+def kernel_source_hash(read=None) -> str:
     h = hashlib.sha256()
     for name in ROW_KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2506_10092_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_2506_10092_gb300", "csrc", name)) as fh:
+                text = fh.read()
+        else:
+            text = read(name)
+        h.update(_code_only(text).encode())
     return h.hexdigest()[:16]
 
 
