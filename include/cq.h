@@ -242,7 +242,8 @@ int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_exec_options*
  * The launch (upload of descriptors and work list, init, persistent kernel,
  * finalize) is a CUDA graph instantiated once per control-block capacity and
  * replayed for every later batch that fits it; only the upload size changes.
- * opts: mode must be CQ_EXEC_FUSED; tile_rows and items_per_cta select the
+ * opts: mode must be CQ_EXEC_FUSED; tile_rows (0, 4096 or 8192; a query whose
+ * shared memory does not fit 8192-row tiles gets 4096) and items_per_cta select the
  * shape (0 = the autotuned shape of cq_batch_tune for this kind of batch,
  * else tiles of 8192 rows, 4 items
  * per CTA); ctas_per_sm, stages and grid_ctas are ignored.
@@ -255,7 +256,7 @@ int cq_batch_run(uint32_t n, cq_table* const* tables, const cq_plan* plans,
                  const cq_exec_options* opts, void* cuda_stream, cq_result** results);
 
 /* Autotuner for batches: run the batch once per candidate shape (tile rows
- * 1024..8192 and mode default, 1 to 8 items per CTA), time each launch with
+ * 4096 or 8192, 1 to 8 items per CTA), time each launch with
  * CUDA events (best of two runs after a warm-up), and remember the fastest
  * for batches of the same kind -- keyed by the number of queries and total
  * rows (powers of two) and the share of all-RLE/index queries -- so that

@@ -1056,8 +1056,12 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   };
   if (batch_limit) {
     // a batch shares one kernel shape: 16 compute warps (+ the helper warp in
-    // row mode), one CTA per SM, shared memory within the batch kernel's limit
-    add(16, 8192u, batch_limit);
+    // row mode), shared memory within the batch kernel's limit, 8192- or
+    // 4096-row tiles
+    if (want_tile && want_tile < 4096)
+      return set_error(CQ_ERR_INVALID_ARG, "batches use 4096- or 8192-row tiles");
+    if (!want_tile || want_tile == 8192) shapes.push_back({16, 8192u, batch_limit});
+    shapes.push_back({16, 4096u, batch_limit});
   } else if (seg) {
     // three CTAs per SM when the tile fits a third of the shared memory, two
     // when it fits half, else one

@@ -46,20 +46,14 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_query_kernel(BatchC
     const Smem sm = carve(qs);
     const unsigned long long t0 = item.t_begin, t1 = item.t_begin + item.n_tiles;
     const uint32_t gpw = qs.tile_rows / (kWarps * 32);
+    // batches plan 4096- or 8192-row tiles only: two tile walks per mode keep
+    // the kernel's code small enough for the instruction cache
     if (qs.seg_mode) {
-      switch (gpw) {
-        case 2: seg_range<2>(qs, sm, t0, t1); break;
-        case 4: seg_range<4>(qs, sm, t0, t1); break;
-        case 8: seg_range<8>(qs, sm, t0, t1); break;
-        default: seg_range<16>(qs, sm, t0, t1); break;
-      }
+      if (gpw == 8) seg_range<8>(qs, sm, t0, t1);
+      else seg_range<16>(qs, sm, t0, t1);
     } else {
-      switch (gpw) {
-        case 2: row_range<kWarps, 2>(qs, sm, t0, t1); break;
-        case 4: row_range<kWarps, 4>(qs, sm, t0, t1); break;
-        case 8: row_range<kWarps, 8>(qs, sm, t0, t1); break;
-        default: row_range<kWarps, 16>(qs, sm, t0, t1); break;
-      }
+      if (gpw == 8) row_range<kWarps, 8>(qs, sm, t0, t1);
+      else row_range<kWarps, 16>(qs, sm, t0, t1);
     }
   }
 }

@@ -422,7 +422,7 @@ extern "C" int cq_batch_tune(uint32_t n, cq_table* const* tables, const cq_plan*
   int rc = check_batch(n, tables, plans, nullptr, &ctx);
   if (rc != CQ_OK) return rc;
   cudaStream_t s = cuda_stream ? reinterpret_cast<cudaStream_t>(cuda_stream) : ctx->stream;
-  static const uint32_t kTiles[] = {0, 1024, 2048, 4096, 8192};
+  static const uint32_t kTiles[] = {4096, 8192};
   static const uint32_t kIpc[] = {1, 2, 4, 8};
   std::vector<cq_result*> res(n, nullptr);
   double best_t = 1e300;

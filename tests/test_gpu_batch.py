@@ -60,7 +60,7 @@ def workload(rng, pool, n_queries):
     return tabs, handles, plans
 
 
-@pytest.mark.parametrize("tile,ipc", [(0, 0), (1024, 1), (2048, 8), (4096, 2), (8192, 4)])
+@pytest.mark.parametrize("tile,ipc", [(0, 0), (4096, 1), (8192, 8), (4096, 2), (8192, 4)])
 def test_batch_equals_solo_and_oracle(cq, ctx, pool, oracle_mod, tile, ipc):
     rng = np.random.default_rng(11 + tile + ipc)
     tabs, handles, plans = workload(rng, pool, 40)
@@ -129,7 +129,7 @@ def test_autotuner_choice_is_used_and_exact(cq, ctx, pool, oracle_mod):
     tabs, handles, plans = workload(rng, pool, 64)
     best, us = cq.cq_batch_tune(handles, plans)
     assert us > 0
-    assert best.tile_rows in (0, 1024, 2048, 4096, 8192) and best.items_per_cta in (1, 2, 4, 8)
+    assert best.tile_rows in (4096, 8192) and best.items_per_cta in (1, 2, 4, 8)
     res = cq.cq_batch_run(handles, plans)     # no options: the tuned shape
     for i, r in enumerate(res):
         check(cq.fetch_all(r), oracle_mod.query(tabs[i], plans[i]), f"query {i}")
@@ -146,3 +146,11 @@ def test_repeated_mixed_batches_are_exact(cq, ctx, pool, oracle_mod):
     for rep in range(20):
         for i, r in enumerate(cq.cq_batch_run(handles, plans, opts=opts)):
             check(cq.fetch_all(r), refs[i], f"replay {rep} query {i}")
+
+
+def test_batch_rejects_small_tiles(cq, ctx, pool):
+    rng = np.random.default_rng(12)
+    tabs, handles, plans = workload(rng, pool, 4)
+    with pytest.raises(cq.CQError) as e:
+        cq.cq_batch_run(handles, plans, opts=cq.exec_options(tile_rows=2048))
+    assert e.value.status == cq.CQ_ERR_INVALID_ARG
