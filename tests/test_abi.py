@@ -65,3 +65,23 @@ def test_oracle_is_not_reachable_from_the_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"(import\s+oracle|from\s+oracle|liboracle|cq_oracle)", text), f
+
+
+def test_every_exported_definition_is_declared():
+    """No entry point is defined in the sources without a declaration in the
+    public header (and so without its documentation)."""
+    import glob
+    src = ""
+    for f in glob.glob(os.path.join(ROOT, "paper_2506_10092_gb300", "csrc", "*.cu")):
+        src += open(f).read()
+    defined = set(re.findall(r'extern "C"[^(]*?\b(cq_[a-z0-9_]+)\s*\(', src))
+    assert defined and defined <= set(declared()), sorted(defined - set(declared()))
+
+
+def test_generator_library_exports_its_header(libpath):
+    gen_h = os.path.join(ROOT, "include", "cq_gen.h")
+    names = sorted(set(re.findall(r"\b(cqgen_[a-z0-9_]+)\s*\(", re.sub(r"/\*.*?\*/", "", open(gen_h).read(),
+                                                                         flags=re.S))))
+    assert names == ["cqgen_hash_fields", "cqgen_nested_codes4"]
+    lib = ctypes.CDLL(os.path.join(os.path.dirname(libpath), "libcqgen.so"))
+    assert all(hasattr(lib, n) for n in names)
