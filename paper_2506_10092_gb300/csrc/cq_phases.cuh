@@ -1,7 +1,8 @@
-// cq_phases.cuh -- device building blocks shared by the two fused query
-// kernels (segment mode in cq_query.cu, row mode in cq_row.cu): shared-memory
-// layouts, column readers, predicate tests, the shared-memory group table and
-// the filter / aggregate phases of one tile.
+// cq_phases.cuh -- device building blocks shared by the fused query kernels
+// (segment mode in cq_query.cu, row mode in cq_row.cu, both in the batch
+// kernel of cq_batch.cu): shared-memory layouts, column readers, predicate
+// tests, the shared-memory group table and the filter / aggregate phases of
+// one tile.
 #pragma once
 
 #include <cuda_runtime.h>
