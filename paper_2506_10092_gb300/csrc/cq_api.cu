@@ -42,6 +42,19 @@ cudaError_t expand_column(const cq_column* c, long long* out, cudaStream_t s, in
 // ------------------------------------------------------------------ helpers
 typedef __int128 i128;
 
+cudaError_t pool_alloc(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t s) {
+  static const long long fail_at = [] {
+    const char* v = getenv("CQ_FAULT_INJECT");
+    return (v && strncmp(v, "alloc:", 6) == 0) ? atoll(v + 6) : 0ll;
+  }();
+  static std::atomic<long long> calls{0};
+  if (fail_at > 0 && ++calls == fail_at) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 static int cmp_bytes(const char* a, size_t la, const char* b, size_t lb) {
   const size_t m = la < lb ? la : lb;
   const int c = m ? memcmp(a, b, m) : 0;
@@ -61,7 +74,7 @@ static uint64_t pad16(uint64_t bytes) { return (bytes + 15) / 16 * 16; }
 static int own_copy(cq_ctx* ctx, const void* src, uint64_t bytes, bool from_device, void** dst) {
   const uint64_t alloc = pad16(bytes) + 16;
   void* p = nullptr;
-  if (cudaMallocFromPoolAsync(&p, alloc, ctx->pool, ctx->stream) != cudaSuccess)
+  if (pool_alloc((void**)&p, alloc, ctx->pool, ctx->stream) != cudaSuccess)
     return set_error(CQ_ERR_OOM, "device allocation of %llu bytes failed", (unsigned long long)alloc);
   cudaMemsetAsync(reinterpret_cast<uint8_t*>(p) + bytes, 0, alloc - bytes, ctx->stream);
   if (bytes) {
@@ -86,7 +99,7 @@ static int check_borrow(const void* p, const char* what) {
 static int finish_column(cq_column* c) {
   cq_ctx* ctx = c->ctx;
   void* d = nullptr;
-  CQ_CUDA(cudaMallocFromPoolAsync(&d, 64, ctx->pool, ctx->stream));
+  CQ_CUDA(pool_alloc((void**)&d, 64, ctx->pool, ctx->stream));
   struct {
     int err, pad;
     long long mn, mx;
@@ -1141,7 +1154,7 @@ static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r)
   clear_stale_error("a query launch");
   const QueryBlock L = query_block_layout(P, true);
   void* base = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync(&base, L.total, ctx->pool, s);
+  cudaError_t e = pool_alloc((void**)&base, L.total, ctx->pool, s);
   if (e != cudaSuccess) return set_error(CQ_ERR_OOM, "device pool allocation of %llu bytes failed: %s", (unsigned long long)L.total, cudaGetErrorString(e));
   r->dev_block = base;
   r->dev_bytes = L.total;
@@ -1257,7 +1270,7 @@ extern "C" int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_ex
     for (size_t i = 0; i < cols.size(); ++i) {
       if (!used[i]) continue;
       void* flat = nullptr;
-      cudaError_t e = cudaMallocFromPoolAsync(&flat, pad16(table->n_rows * 8) + 16, ctx->pool, s);
+      cudaError_t e = pool_alloc((void**)&flat, pad16(table->n_rows * 8) + 16, ctx->pool, s);
       if (e != cudaSuccess) {
         free_result(r);
         return set_error(CQ_ERR_OOM, "flat column allocation failed: %s", cudaGetErrorString(e));
@@ -1454,7 +1467,7 @@ extern "C" int cq_align_segments(cq_ctx* ctx, cq_column* const* cols, uint32_t k
   *n_segments = 0;
   if (n_tiles == 0) return CQ_OK;
   void* scratch = nullptr;
-  CQ_CUDA(cudaMallocFromPoolAsync(&scratch, 8 * n_tiles, ctx->pool, s));
+  CQ_CUDA(pool_alloc((void**)&scratch, 8 * n_tiles, ctx->pool, s));
   std::vector<unsigned long long> host(n_tiles);
   unsigned long long ns = 0;
   cudaError_t e = align_segments(cols, k, s, scratch, n_tiles, n_rows, reinterpret_cast<long long*>(seg_ends),
@@ -1478,7 +1491,7 @@ extern "C" int cq_selftest_bounded_wait(cq_ctx* ctx, uint32_t limit_us, int32_t*
   if (limit_us == 0 || limit_us > 5000000u) return set_error(CQ_ERR_INVALID_ARG, "limit must be 1 us .. 5 s");
   CQ_CUDA(cudaSetDevice(ctx->device));
   void* d = nullptr;
-  CQ_CUDA(cudaMallocFromPoolAsync(&d, 16, ctx->pool, ctx->stream));
+  CQ_CUDA(pool_alloc((void**)&d, 16, ctx->pool, ctx->stream));
   cudaError_t e = launch_bounded_wait_selftest(1000ull * limit_us, reinterpret_cast<int*>(d), ctx->stream);
   int h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);

@@ -297,8 +297,15 @@ void clear_error();
   do {                                                                                          \
     cudaError_t _e = (call);                                                                    \
     if (_e != cudaSuccess)                                                                      \
-      return set_error(CQ_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(_e));            \
+      return set_error(_e == cudaErrorMemoryAllocation ? CQ_ERR_OOM : CQ_ERR_CUDA, "%s failed: %s", \
+                       #call, cudaGetErrorString(_e));                                          \
   } while (0)
+
+// Stream-ordered allocation from a context's pool.  Host-side fault
+// injection for tests: with CQ_FAULT_INJECT=alloc:N in the environment the
+// N-th call of the process (counting from 1) fails with
+// cudaErrorMemoryAllocation without calling CUDA.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t s);
 
 // kernels / launchers (cq_query.cu)
 cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ctas_per_sm, uint32_t grid_ctas);

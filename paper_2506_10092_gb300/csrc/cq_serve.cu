@@ -263,7 +263,7 @@ static int launch_planned_batch(cq_ctx* ctx, uint32_t n, cq_table* const* tables
   std::shared_ptr<BatchShared> sh(new BatchShared);
   sh->device = ctx->device;
   sh->stream = s;
-  cudaError_t e = cudaMallocFromPoolAsync(&sh->block, blk_bytes, ctx->pool, s);
+  cudaError_t e = pool_alloc(&sh->block, blk_bytes, ctx->pool, s);
   if (e != cudaSuccess) {
     sh->block = nullptr;
     return set_error(CQ_ERR_OOM, "device pool allocation of %llu bytes failed: %s", (unsigned long long)blk_bytes,

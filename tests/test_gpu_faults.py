@@ -29,3 +29,44 @@ def test_self_test_rejects_bad_limits():
         with pytest.raises(cq.CQError) as e:
             cq.cq_selftest_bounded_wait(ctx, bad)
         assert e.value.status == cq.CQ_ERR_INVALID_ARG
+
+
+_ALLOC_CHILD = r'''
+import json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2506_10092_gb300 import cq, datagen as dg
+from oracle import oracle
+ctx = cq.cq_ctx_create(0)
+table, plan = dg.tiny_two_rle(20000, seed=2)
+fails, got = [], None
+for _ in range(3):
+    try:
+        t, cols = cq.table_from(ctx, table)
+        got = cq.fetch_all(cq.cq_query_run(t, plan))
+        break
+    except cq.CQError as e:
+        fails.append(e.status)
+ref = oracle.query(table, plan)
+ok = got is not None and all((g == w).all() for g, w in zip(got, ref.keys + ref.aggs))
+print(json.dumps({"fails": fails, "ok": bool(ok)}))
+'''
+
+
+@pytest.mark.parametrize("k", [1, 3, 6, 7])
+def test_injected_allocation_failure_is_reported_and_recovered(k):
+    """Host-side fault injection: the k-th device allocation of a process
+    fails (column copies, validation scratch, the query's block).  The call
+    that hit it returns CQ_ERR_OOM, nothing leaks into later calls, and the
+    retry gives the oracle's result."""
+    import json
+    import os
+    import subprocess
+    import sys
+    from paper_2506_10092_gb300 import cq
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CQ_FAULT_INJECT=f"alloc:{k}")
+    out = subprocess.run([sys.executable, "-c", _ALLOC_CHILD, root], env=env, capture_output=True, text=True,
+                         timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["ok"] and d["fails"] == [cq.CQ_ERR_OOM], d
