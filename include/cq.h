@@ -200,7 +200,9 @@ typedef enum {
 
 typedef struct {
   int32_t mode;          /* cq_exec_mode */
-  uint32_t tile_rows;    /* rows per tile (multiple of 1024, <= 16384); 0 = default */
+  uint32_t tile_rows;    /* rows per tile: 1024, 2048, 4096 or 8192 (smaller ones are tried when
+                            shared memory is short); 0 = the planner's choice, which may also be
+                            6144 or 7168 rows for its 24- / 28-warp row shapes */
   uint32_t ctas_per_sm;  /* 0 = default (the planner picks); 1, 2, or 3 (segment mode only) */
   uint32_t stages;       /* bulk-copy pipeline depth (1..8); 0 = default (4, fewer if shared
                             memory is short, never below 2) */
