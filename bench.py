@@ -224,6 +224,11 @@ def run_reference(args):
     ws, rank, _ = dist()
     if rank != 0:
         return
+    if args.workload in ("batched", "serving"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single queries (heterogeneous, "
+                                                             "tiny, nested); it has no batched or serving form"}),
+              flush=True)
+        return
     name, table, plan = workload(args)
     if table is None:
         # the nested table has no host copy at full size: time a same-shape sample
