@@ -210,7 +210,10 @@ typedef struct {
   uint32_t grid_ctas;    /* CTAs of the fused kernel; 0 = SMs x ctas_per_sm */
   uint32_t items_per_cta;  /* batches: work items per CTA the tiles are cut into
                               (load balance vs per-item overhead); 0 = default */
-  uint32_t reserved;
+  uint32_t kernel;       /* row-mode one-query launches: 0 = a kernel specialised to the query's
+                            shape, compiled at run time on first use and cached by the process
+                            (the environment variable CQ_JIT=0 turns this off); 1 = the generic
+                            ahead-of-time kernel, which reads the shape from the descriptor */
 } cq_exec_options;
 
 /* ------------------------------------------------------------------ queries */
@@ -330,8 +333,9 @@ int cq_align_segments(cq_ctx* ctx, cq_column* const* cols, uint32_t k, void* cud
  * fixed device array of CQ_STATIC_ALIGN_MAX_TILES + 8 64-bit words (512 KB)
  * inside the library, held by every GPU that loads it until the process
  * exits; n_rows above CQ_STATIC_ALIGN_MAX_TILES * 4096 is rejected with
- * CQ_ERR_INVALID_ARG.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress, with the device current); make that
+ * CQ_ERR_INVALID_ARG.  The first call in each device context (again after
+ * cudaDeviceReset) looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current) and caches it; make that
  * first call before capturing any stream.  All calls share the array and it
  * keeps the last call's contents (the call clears what must start at zero),
  * so calls that overlap on the GPU -- from several host threads or streams --
@@ -351,6 +355,20 @@ int cq_align_segments_static(uint32_t k, const void* const* run_ends, const uint
  * must).  The context stays usable afterwards.  Synchronous on the
  * context's stream. */
 int cq_selftest_bounded_wait(cq_ctx* ctx, uint32_t limit_us, int32_t* device_status);
+
+/* Row-mode kernels specialised to a query's shape (cq_exec_options.kernel)
+ * are compiled at run time, once per shape and process.  *compiles receives
+ * how many this process compiled so far, *seconds the compile time they
+ * took (either may be NULL).  No counterpart in the paper.  Always CQ_OK. */
+int cq_jit_stats(uint64_t* compiles, double* seconds);
+
+/* Compile, without loading, one of two built-in shapes (variant 0 or 1) that
+ * between them exercise every encoding, predicate kind, key mapping and
+ * aggregate layout of the specialised row kernel: a check of the run-time
+ * compiler that needs no GPU.  *seconds (may be NULL) receives the compile
+ * time.  CQ_ERR_INVALID_ARG for another variant, CQ_ERR_CUDA (with the
+ * compiler's log in cq_last_error) when compilation fails. */
+int cq_jit_check(uint32_t variant, double* seconds);
 
 /* ------------------------------------------------------------------ serving
  * A serving loop over tables kept resident on the device (no counterpart in

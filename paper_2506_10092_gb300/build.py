@@ -42,12 +42,49 @@ GEN = os.path.join(HERE, "gen")
 GEN_LIB = os.path.join(HERE, "libcqgen.so")
 
 
+# Device headers compiled again at run time for shape-specialised kernels
+# (cq_jit.cu): (name as included, path).
+JIT_HEADERS = [
+    ("cq_fast.cuh", os.path.join(CSRC, "cq_fast.cuh")),
+    ("cq_rowpath.cuh", os.path.join(CSRC, "cq_rowpath.cuh")),
+    ("cq_phases.cuh", os.path.join(CSRC, "cq_phases.cuh")),
+    ("cq_device.cuh", os.path.join(CSRC, "cq_device.cuh")),
+    ("cq_desc.h", os.path.join(CSRC, "cq_desc.h")),
+    ("../../include/cq.h", os.path.join(HERE, "..", "include", "cq.h")),
+]
+JIT_INC = os.path.join(BUILD, "cq_jit_headers.inc")
+
+
+def _write_jit_headers() -> None:
+    """Embed the device headers' text in a C++ include for cq_jit.cu."""
+    parts = ["static const JitHeader kJitHeaders[] = {"]
+    for name, path in JIT_HEADERS:
+        text = open(path).read()
+        if ")cqjit\"" in text:
+            raise RuntimeError(f"{path}: contains the raw-string delimiter")
+        parts.append(f'  {{"{name}", R"cqjit({text})cqjit"}},')
+    parts.append("};")
+    parts.append(f"static const int kNumJitHeaders = {len(JIT_HEADERS)};")
+    out = "\n".join(parts) + "\n"
+    if not os.path.exists(JIT_INC) or open(JIT_INC).read() != out:
+        with open(JIT_INC + ".tmp", "w") as f:
+            f.write(out)
+        os.replace(JIT_INC + ".tmp", JIT_INC)
+
+
+def _cuda_lib_dir(nvcc: str) -> str:
+    import shutil
+    path = nvcc if os.path.sep in nvcc else (shutil.which(nvcc) or "/usr/local/cuda/bin/nvcc")
+    return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(path))), "lib64")
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     """Build libcq.so (the query library) and libcqgen.so (the device-side
     input generator); returns the path of libcq.so."""
     os.makedirs(BUILD, exist_ok=True)
+    _write_jit_headers()
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        [os.path.join(HERE, "..", "include", "cq.h")]
+        [os.path.join(HERE, "..", "include", "cq.h"), JIT_INC]
     gen_headers = [os.path.join(HERE, "..", "include", "cq_gen.h")]
     nvcc = _nvcc()
     jobs = []
@@ -57,7 +94,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            cmd = [nvcc] + ARCH + NVFLAGS + list(extra_flags) + ["-c", src, "-o", obj]
+            cmd = [nvcc] + ARCH + NVFLAGS + list(extra_flags) + ["-I", BUILD, "-c", src, "-o", obj]
             jobs.append(cmd)
     for src in sorted(glob.glob(os.path.join(GEN, "*.cu"))):
         obj = os.path.join(BUILD, "gen_" + os.path.basename(src)[:-3] + ".o")
@@ -77,10 +114,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for out in ex.map(run, jobs):
             if verbose and out.strip():
                 print(out)
-    for lib, lib_objs in ((LIB, objs), (GEN_LIB, gen_objs)):
+    cuda_lib = _cuda_lib_dir(nvcc)
+    for lib, lib_objs, libs in ((LIB, objs, ["-L" + cuda_lib, "-lnvrtc", "-Xlinker", "-rpath=" + cuda_lib]),
+                                (GEN_LIB, gen_objs, [])):
         if force or _stale(lib, lib_objs):
             tmp = lib + f".tmp{os.getpid()}"
-            run([nvcc] + ARCH + ["-shared", "-o", tmp] + lib_objs + ["-lpthread"])
+            run([nvcc] + ARCH + ["-shared", "-o", tmp] + lib_objs + libs + ["-lpthread"])
             os.replace(tmp, lib)
     return LIB
 

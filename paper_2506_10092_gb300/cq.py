@@ -58,7 +58,7 @@ class cq_plan(C.Structure):
 class cq_exec_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile_rows", C.c_uint32), ("ctas_per_sm", C.c_uint32),
                 ("stages", C.c_uint32), ("table_slots", C.c_uint32), ("grid_ctas", C.c_uint32),
-                ("items_per_cta", C.c_uint32), ("reserved", C.c_uint32)]
+                ("items_per_cta", C.c_uint32), ("kernel", C.c_uint32)]
 
 
 class cq_server_options(C.Structure):
@@ -109,6 +109,8 @@ _SIGS = {
     "cq_server_stats": [_VP, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)],
     "cq_server_destroy": [_VP],
     "cq_selftest_bounded_wait": [_VP, C.c_uint32, C.POINTER(C.c_int32)],
+    "cq_jit_stats": [C.POINTER(C.c_uint64), C.POINTER(C.c_double)],
+    "cq_jit_check": [C.c_uint32, C.POINTER(C.c_double)],
 }
 
 
@@ -306,12 +308,29 @@ class PlanStruct:
         self.plan = plan
 
 
+KERNEL_SPECIALISED, KERNEL_GENERIC = 0, 1
+
+
 def exec_options(mode=CQ_EXEC_FUSED, tile_rows=0, ctas_per_sm=0, stages=0, table_slots=0,
-                 grid_ctas=0, items_per_cta=0) -> cq_exec_options:
+                 grid_ctas=0, items_per_cta=0, kernel=KERNEL_SPECIALISED) -> cq_exec_options:
     o = cq_exec_options()
     o.mode, o.tile_rows, o.ctas_per_sm, o.stages, o.table_slots = mode, tile_rows, ctas_per_sm, stages, table_slots
-    o.grid_ctas, o.items_per_cta = grid_ctas, items_per_cta
+    o.grid_ctas, o.items_per_cta, o.kernel = grid_ctas, items_per_cta, kernel
     return o
+
+
+def cq_jit_check(variant: int) -> float:
+    """Compile (no GPU needed) one of the built-in check shapes; returns seconds."""
+    sec = C.c_double()
+    _check(lib.cq_jit_check(variant, C.byref(sec)))
+    return sec.value
+
+
+def cq_jit_stats():
+    """(kernels compiled at run time by this process, seconds spent compiling)."""
+    n, sec = C.c_uint64(), C.c_double()
+    _check(lib.cq_jit_stats(C.byref(n), C.byref(sec)))
+    return n.value, sec.value
 
 
 class _Batch:

@@ -42,11 +42,14 @@ cudaError_t expand_column(const cq_column* c, long long* out, cudaStream_t s, in
 // ------------------------------------------------------------------ helpers
 typedef __int128 i128;
 
+long long fault_inject_at(const char* kind) {
+  const char* v = getenv("CQ_FAULT_INJECT");
+  const size_t n = strlen(kind);
+  return (v && strncmp(v, kind, n) == 0 && v[n] == ':') ? atoll(v + n + 1) : 0ll;
+}
+
 cudaError_t pool_alloc(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t s) {
-  static const long long fail_at = [] {
-    const char* v = getenv("CQ_FAULT_INJECT");
-    return (v && strncmp(v, "alloc:", 6) == 0) ? atoll(v + 6) : 0ll;
-  }();
+  static const long long fail_at = fault_inject_at("alloc");
   static std::atomic<long long> calls{0};
   if (fail_at > 0 && ++calls == fail_at) {
     *p = nullptr;
@@ -1018,6 +1021,8 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   P->ctas_per_sm = (!q.seg_mode && ncw == 8) ? 2 : 1;
   if (q.seg_mode && smem_limit <= ctx->smem_two) P->ctas_per_sm = smem_limit <= ctx->smem_three ? 3 : 2;
   P->grid_ctas = opts ? opts->grid_ctas : 0u;
+  P->generic = opts && opts->kernel == 1;
+  P->row_fn = nullptr;
   // ---- outputs
   q.n_out = plan->n_group_by + plan->n_aggs;
   P->out_kind.clear();
@@ -1049,6 +1054,7 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   if (want_tile && (want_tile < 1024 || want_tile > 8192 || (want_tile & (want_tile - 1))))
     return set_error(CQ_ERR_INVALID_ARG, "tile_rows must be 1024, 2048, 4096 or 8192");
   if (want_ctas > 3) return set_error(CQ_ERR_INVALID_ARG, "ctas_per_sm must be 0, 1, 2 or 3 (3: segment mode)");
+  if (opts && opts->kernel > 1) return set_error(CQ_ERR_INVALID_ARG, "kernel must be 0 (specialised) or 1 (generic)");
   // segment mode when every referenced column is RLE or index-encoded
   bool seg = true;
   auto look = [&](uint32_t c) {
@@ -1151,6 +1157,13 @@ void attach_outputs(cq_result* r, const Planned& P) {
 // init -> fused kernel -> finalize on `s`.
 static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r) {
   QueryDesc& q = P.q;
+  if (!q.seg_mode && !P.generic && !P.row_fn && jit_enabled()) {
+    // row mode: the kernel specialised to this query's shape (compiled on first use)
+    int ncw, gpw, minb;
+    row_shape(q, &ncw, &gpw, &minb);
+    const int rc = jit_row_kernel(q, ncw, gpw, minb, ctx->device, ctx->smem_optin, &P.row_fn);
+    if (rc != CQ_OK) return rc;
+  }
   clear_stale_error("a query launch");
   const QueryBlock L = query_block_layout(P, true);
   void* base = nullptr;
@@ -1169,7 +1182,7 @@ static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r)
   e = launch_init_global(q, s);
   if (e == cudaSuccess && (step = "event", true)) e = cudaEventRecord(r->ev_k0, s);
   if (e == cudaSuccess && (step = "fused kernel", true))
-    e = launch_query(q, s, ctx->num_sms, P.ctas_per_sm, P.grid_ctas);
+    e = launch_query(q, s, ctx->num_sms, P.ctas_per_sm, P.grid_ctas, P.row_fn);
   if (e == cudaSuccess && (step = "event", true)) e = cudaEventRecord(r->ev_k1, s);
   if (e == cudaSuccess && (step = "finalize", true)) e = launch_finalize(q, s);
   if (e != cudaSuccess)

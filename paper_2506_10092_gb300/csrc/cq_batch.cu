@@ -14,6 +14,7 @@
 // joins the block barriers.
 #include <cuda_runtime.h>
 
+#include "cq_internal.h"
 #include "cq_rowpath.cuh"
 #include "cq_seg.cuh"
 

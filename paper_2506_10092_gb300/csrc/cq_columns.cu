@@ -167,7 +167,6 @@ cudaError_t run_column_check(const cq_column* c, void* d_out_raw, cudaStream_t s
 // fall in (s, e] are set in per-column bitmaps (bit o <-> end s + o + 1); the
 // union gives the segment ends of the tile; the run of column j covering
 // the segment that ends at x is the number of column-j ends below x.
-constexpr uint32_t kAlignTile = 4096;
 constexpr uint32_t kAlignWords = kAlignTile / 32;
 constexpr int kAlignThreads = 256;
 

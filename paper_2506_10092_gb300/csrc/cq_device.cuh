@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "cq_internal.h"
+#include "cq_desc.h"
 
 namespace cq {
 

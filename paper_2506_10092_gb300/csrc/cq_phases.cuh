@@ -11,7 +11,6 @@
 #include <type_traits>
 
 #include "cq_device.cuh"
-#include "cq_internal.h"
 
 namespace cq {
 

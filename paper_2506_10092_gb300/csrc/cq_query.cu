@@ -17,6 +17,7 @@
 #include <climits>
 #include <cstdio>
 
+#include "cq_internal.h"
 #include "cq_seg.cuh"
 
 namespace cq {
@@ -326,12 +327,18 @@ cudaError_t launch_init_global(const QueryDesc& q, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ctas_per_sm, uint32_t grid_ctas) {
+cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ctas_per_sm, uint32_t grid_ctas,
+                         const void* row_fn) {
   const unsigned long long want =
       grid_ctas ? (unsigned long long)grid_ctas : (unsigned long long)num_sms * (unsigned long long)ctas_per_sm;
   const unsigned grid = (unsigned)(q.n_tiles < want ? q.n_tiles : want);
   if (grid == 0) return cudaSuccess;
-  if (!q.seg_mode) return launch_row_kernel(q, grid, s);
+  if (!q.seg_mode) {
+    if (!row_fn) return launch_row_kernel(q, grid, s);
+    int ncw, gpw, minb;
+    row_shape(q, &ncw, &gpw, &minb);
+    return launch_row_jit(row_fn, q, grid, ncw, s);
+  }
   switch (q.tile_rows / kThreads) {
     // two or three CTAs per SM overlap one CTA's barrier-separated phases with
     // the others'

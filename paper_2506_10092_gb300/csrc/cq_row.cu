@@ -15,6 +15,7 @@
 // accumulators when it fills.
 #include <cuda_runtime.h>
 
+#include "cq_internal.h"
 #include "cq_rowpath.cuh"
 
 namespace cq {
@@ -42,12 +43,17 @@ cudaError_t row_kernel_set_smem(int bytes) {
   return e;
 }
 
+// ncw field: 16 one CTA of 16 compute warps, 8 two such CTAs, 24 / 28 one
+// CTA of 24 / 28
+void row_shape(const QueryDesc& q, int* ncw, int* gpw, int* minb) {
+  *ncw = (q.ncw == 24 || q.ncw == 28) ? q.ncw : 16;
+  *gpw = (int)(q.tile_rows / (*ncw * 32));
+  *minb = q.ncw == 8 ? 2 : 1;
+}
+
 cudaError_t launch_row_kernel(const QueryDesc& q, unsigned grid, cudaStream_t s) {
-  // ncw field: 16 one CTA of 16 compute warps, 8 two such CTAs, 24 / 28 one
-  // CTA of 24 / 28
-  const int ncw = (q.ncw == 24 || q.ncw == 28) ? q.ncw : 16;
-  const int gpw = (int)(q.tile_rows / (ncw * 32));
-  const int minb = q.ncw == 8 ? 2 : 1;
+  int ncw, gpw, minb;
+  row_shape(q, &ncw, &gpw, &minb);
   bool launched = false;
 #define CQ_GO(N, G, M)                                                                \
   if (!launched && ncw == N && gpw == G && minb == M) {                               \

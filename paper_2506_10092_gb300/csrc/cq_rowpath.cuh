@@ -224,7 +224,22 @@ __device__ inline void helper_pass_bitmaps(const QueryDesc& q, const Smem& sm, c
 // pipeline, then per tile filter and aggregate (compute warps) while the
 // helper builds the next tile's bitmaps; flush the table when it fills and
 // after the last tile.  Every issued stage is consumed before returning.
-template <int NCW, int GPW>
+// The compute warps' work on one tile -- filter its rows, compact the passing
+// ones, aggregate them -- is Body::tile; GenericBody reads every shape
+// property of the query from its descriptor at run time (FastBody in
+// cq_fast.cuh has them as compile-time constants).
+struct GenericBody {
+  template <int NCW, int GPW>
+  __device__ static __forceinline__ void tile(const QueryDesc& q, const Smem& sm, const TileView& tv, uint32_t wbase,
+                                              uint32_t rows, uint16_t* list, unsigned long long row0) {
+    const uint32_t gstride = NCW * 32;
+    const uint32_t pm = phase_filter<false, GPW>(q, tv, nullptr, wbase, gstride, rows);
+    const uint32_t n_pass = compact<GPW>(pm, wbase, gstride, list);
+    phase_aggregate<false, 2>(q, sm, tv, nullptr, list, n_pass, row0);
+  }
+};
+
+template <int NCW, int GPW, class Body = GenericBody>
 __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, unsigned long long t_begin,
                                           unsigned long long t_end) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -294,7 +309,7 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
 
   uint32_t rows_since_flush = 0;
   uint16_t* mylist = sm.clist + (helper ? 0 : warp) * (GPW * 32);
-  const uint32_t wbase = warp * 32, gstride = NCW * 32;
+  const uint32_t wbase = warp * 32;
 
   for (unsigned long long t = t_begin; t < t_end; ++t) {
     const unsigned long long s = t * T;
@@ -315,9 +330,7 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
       tv.stage = sm.stage + (size_t)st * q.stage_bytes;
       tv.aux = aux_smem ? sm.aux : q.aux;
       tv.nwords = nwords;
-      const uint32_t pm = phase_filter<false, GPW>(q, tv, nullptr, wbase, gstride, rows);
-      const uint32_t n_pass = compact<GPW>(pm, wbase, gstride, mylist);
-      phase_aggregate<false, 2>(q, sm, tv, nullptr, mylist, n_pass, s);
+      Body::template tile<NCW, GPW>(q, sm, tv, wbase, rows, mylist, s);
     } else if (nb && t + 1 < t_end) {
       const int wb1 = (int)((t + 1 - t_begin) % kWinBufs);
       const unsigned long long e1 = (e + T < q.n_rows) ? e + T : q.n_rows;

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -598,6 +599,19 @@ static void finish(cq_server* srv, Request& r, int status, const std::string& er
   srv->completed++;
 }
 
+// State of a launch in flight: cudaSuccess (done), cudaErrorNotReady, or
+// the error the launch met.  With CQ_FAULT_INJECT=event:N the N-th poll of
+// the process reports a launch failure without asking CUDA (tests of the
+// error path).
+static cudaError_t poll_launch(cudaEvent_t ev) {
+  static const long long fail_at = fault_inject_at("event");
+  static std::atomic<long long> polls{0};
+  if (fail_at > 0 && ++polls == fail_at) return cudaErrorLaunchFailure;
+  const cudaError_t e = cudaEventQuery(ev);
+  if (e == cudaErrorNotReady) (void)cudaGetLastError();   // not ready is not an error
+  return e;
+}
+
 // The serving loop: launch batches while streams and memory allow, poll the
 // launches in flight, hand finished results to their waiters.
 static void serve(cq_server* srv) {
@@ -609,9 +623,34 @@ static void serve(cq_server* srv) {
     bool any_done = false;
     for (size_t i = 0; i < srv->inflight.size();) {
       InFlight& f = srv->inflight[i];
-      if (cudaEventQuery(f.done) != cudaSuccess) {
-        (void)cudaGetLastError();   // not ready is not an error
+      const cudaError_t st = poll_launch(f.done);
+      if (st == cudaErrorNotReady) {
         ++i;
+        continue;
+      }
+      if (st != cudaSuccess) {
+        // the launch failed: its requests end with the error and their
+        // results are released once the stream has drained
+        const std::string msg = std::string("the launch of this query's batch failed: ") + cudaGetErrorString(st);
+        (void)cudaGetLastError();
+        cudaStreamSynchronize(srv->streams[f.stream]);
+        (void)cudaGetLastError();
+        for (auto& r : f.reqs) {
+          if (r->result) {
+            r->result->stream = srv->ctx->stream;
+            if (r->result->batch_keepalive)
+              static_cast<BatchShared*>(r->result->batch_keepalive.get())->stream = srv->ctx->stream;
+            cq_result_destroy(r->result);
+            r->result = nullptr;
+          }
+          finish(srv, *r, CQ_ERR_CUDA, msg);
+        }
+        srv->used_bytes -= f.footprint;
+        srv->stream_busy[f.stream]--;
+        cudaEventDestroy(f.done);
+        srv->inflight[i] = std::move(srv->inflight.back());
+        srv->inflight.pop_back();
+        any_done = true;
         continue;
       }
       for (auto& r : f.reqs) {
@@ -664,14 +703,35 @@ static void serve(cq_server* srv) {
         const std::string err = rc == CQ_OK ? std::string() : std::string(cq_last_error());
         cudaEvent_t ev = nullptr;
         lk.lock();
+        int rc2 = rc;
+        std::string err2 = err;
         if (rc == CQ_OK) {
+          cudaError_t ee = cudaSuccess;
           if (!srv->free_events.empty()) {
             ev = srv->free_events.back();
             srv->free_events.pop_back();
           } else {
-            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            ee = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
           }
-          cudaEventRecord(ev, srv->streams[sidx]);
+          if (ee == cudaSuccess) ee = cudaEventRecord(ev, srv->streams[sidx]);
+          if (ee != cudaSuccess) {
+            // without a completion event the launch cannot be tracked: wait
+            // for it here and fail its requests
+            rc2 = CQ_ERR_CUDA;
+            err2 = std::string("completion event of a launch: ") + cudaGetErrorString(ee);
+            (void)cudaGetLastError();
+            if (ev) cudaEventDestroy(ev);
+            cudaStreamSynchronize(srv->streams[sidx]);
+            (void)cudaGetLastError();
+            for (cq_result* x : res)
+              if (x) {
+                x->stream = srv->ctx->stream;
+                if (x->batch_keepalive) static_cast<BatchShared*>(x->batch_keepalive.get())->stream = srv->ctx->stream;
+                cq_result_destroy(x);
+              }
+          }
+        }
+        if (rc2 == CQ_OK) {
           for (size_t k = 0; k < b.size(); ++k) b[k]->result = res[k];
           InFlight f;
           f.reqs = std::move(b);
@@ -682,7 +742,7 @@ static void serve(cq_server* srv) {
           srv->inflight.push_back(std::move(f));
           srv->launches++;
         } else {
-          for (auto& r : b) finish(srv, *r, rc, err);
+          for (auto& r : b) finish(srv, *r, rc2, err2);
           srv->used_bytes -= fp;
           srv->cv_done.notify_all();
         }

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <vector>
 
 #include "cq_device.cuh"
 #include "cq_internal.h"
@@ -18,7 +19,8 @@
 namespace cq {
 
 constexpr unsigned long long kStaticTiles = CQ_STATIC_ALIGN_MAX_TILES;
-constexpr unsigned long long kStaticTileRows = 4096;   // rows per tile of the alignment kernels
+constexpr unsigned long long kStaticTileRows = kAlignTile;   // rows per tile of the alignment kernels
+static_assert(kStaticTileRows == 4096, "the header states the row limit as CQ_STATIC_ALIGN_MAX_TILES * 4096");
 
 // [0, kStaticTiles): per-tile counts, then their exclusive prefix sums;
 // [kStaticTiles]: total segments; [kStaticTiles + 1]: input status (0 ok)
@@ -83,21 +85,55 @@ __global__ void static_scan_kernel(unsigned long long* counts, unsigned long lon
   if (threadIdx.x == 0) counts[kStaticTiles] = carry;
 }
 
-// Device address of the static scratch, looked up once per device (with that
-// device current) and cached.
+// The CUDA context current on this thread (driver entry point looked up
+// through the runtime, so the library needs no link against the driver).
+static void* current_context() {
+  typedef int (*GetCurrent)(void**);
+  static GetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<GetCurrent>(f);
+  }();
+  void* c = nullptr;
+  if (fn && fn(&c) != 0) c = nullptr;
+  return c;
+}
+
+// Device address of the static scratch: looked up (with the device current)
+// at the first call in each device context and cached for that context, so a
+// context torn down and created again (cudaDeviceReset) gets its own lookup.
 static int static_scratch(int device, unsigned long long** out) {
+  struct Entry {
+    int device;
+    void* context;
+    unsigned long long* addr;
+  };
   static std::mutex mu;
-  static unsigned long long* addr[64] = {nullptr};
-  if (device < 0 || device >= 64) return set_error(CQ_ERR_INVALID_ARG, "device %d out of range", device);
+  static std::vector<Entry> cache;
+  void* context = current_context();
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess)
-      return set_error(CQ_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-    addr[device] = reinterpret_cast<unsigned long long*>(p);
-  }
-  *out = addr[device];
+  for (const Entry& e : cache)
+    if (e.device == device && e.context == context && context) {
+      *out = e.addr;
+      return CQ_OK;
+    }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess)
+    return set_error(CQ_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+  *out = reinterpret_cast<unsigned long long*>(p);
+  // a context created after cudaDeviceReset may reuse the old handle value:
+  // the entry for this device is replaced, never kept beside it
+  for (Entry& x : cache)
+    if (x.device == device) {
+      x.context = context;
+      x.addr = *out;
+      return CQ_OK;
+    }
+  cache.push_back({device, context, *out});
   return CQ_OK;
 }
 
@@ -113,11 +149,12 @@ extern "C" int cq_align_segments_static(uint32_t k, const void* const* run_ends,
   if (!run_ends || !end_is_i64 || !n_runs || !n_segments) return set_error(CQ_ERR_INVALID_ARG, "NULL argument");
   if (k == 0 || k > (uint32_t)kMaxBitmapCols) return set_error(CQ_ERR_INVALID_ARG, "k must be in 1..%d", kMaxBitmapCols);
   if (capacity && (!seg_ends || !ridx)) return set_error(CQ_ERR_INVALID_ARG, "NULL output buffer");
-  const unsigned long long n_tiles = (n_rows + kStaticTileRows - 1) / kStaticTileRows;
-  if (n_tiles > kStaticTiles)
+  // compared before the tile count is formed, which would wrap near 2^64
+  if (n_rows > kStaticTiles * kStaticTileRows)
     return set_error(CQ_ERR_INVALID_ARG,
                      "%llu rows exceed the static alignment limit of %llu rows (%llu tiles of %llu rows)",
                      (unsigned long long)n_rows, kStaticTiles * kStaticTileRows, kStaticTiles, kStaticTileRows);
+  const unsigned long long n_tiles = n_rows / kStaticTileRows + (n_rows % kStaticTileRows != 0 ? 1 : 0);
   uint8_t e64[kMaxBitmapCols];
   unsigned long long n[kMaxBitmapCols];
   for (uint32_t j = 0; j < k; ++j) {

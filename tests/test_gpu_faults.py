@@ -70,3 +70,49 @@ def test_injected_allocation_failure_is_reported_and_recovered(k):
     assert out.returncode == 0, out.stderr[-2000:]
     d = json.loads(out.stdout.strip().splitlines()[-1])
     assert d["ok"] and d["fails"] == [cq.CQ_ERR_OOM], d
+
+
+_EVENT_CHILD = r'''
+import json, sys, threading
+sys.path.insert(0, sys.argv[1])
+from paper_2506_10092_gb300 import cq, datagen as dg
+from oracle import oracle
+ctx = cq.cq_ctx_create(0)
+table, plan = dg.tiny_two_rle(20000, seed=3)
+t, cols = cq.table_from(ctx, table)
+srv = cq.cq_server_create(ctx)
+statuses = []
+for _ in range(2):
+    tk = cq.cq_server_submit(srv, t, plan)
+    try:
+        res, _lat = cq.cq_server_wait(srv, tk, timeout_us=30_000_000)
+        got = cq.fetch_all(res)
+        statuses.append(0)
+    except cq.CQError as e:
+        statuses.append(e.status)
+ref = oracle.query(table, plan)
+ok = all((g == w).all() for g, w in zip(got, ref.keys + ref.aggs))
+done = threading.Event()
+threading.Thread(target=lambda: (srv.close(), done.set()), daemon=True).start()
+print(json.dumps({"statuses": statuses, "ok": bool(ok), "destroyed": done.wait(60)}))
+'''
+
+
+def test_serving_loop_fails_a_launch_whose_completion_reports_an_error():
+    """Host-side fault injection (no GPU fault): the serving loop's first poll
+    of a launch in flight reports a launch failure.  That query ends with
+    CQ_ERR_CUDA instead of waiting forever, the next query gets the oracle's
+    result, and the server shuts down."""
+    import json
+    import os
+    import subprocess
+    import sys
+    from paper_2506_10092_gb300 import cq
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CQ_FAULT_INJECT="event:1")
+    out = subprocess.run([sys.executable, "-c", _EVENT_CHILD, root], env=env, capture_output=True, text=True,
+                         timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["statuses"] == [cq.CQ_ERR_CUDA, 0], d
+    assert d["ok"] and d["destroyed"], d

@@ -46,3 +46,39 @@ def test_static_alignment_matches_the_allocating_entry_point():
     with pytest.raises(cq.CQError) as e:
         cq.cq_align_segments_static(ends, 65536 * 4096 + 1)
     assert e.value.status == cq.CQ_ERR_INVALID_ARG
+
+
+def test_static_alignment_rejects_malformed_inputs():
+    """Unsorted run ends, a last end other than n_rows, a capacity below the
+    segment count and a row count near 2^64 (a negative size through the
+    binding) are refused with their status; a good call still works after."""
+    import torch
+
+    from paper_2506_10092_gb300 import cq
+
+    cq.cq_ctx_create(0)
+    seg = torch.empty(64, dtype=torch.int64, device="cuda")
+    ridx = torch.empty(128, dtype=torch.int64, device="cuda")
+
+    def call(ends, n_rows, capacity=64):
+        return cq.cq_align_segments_static(ends, n_rows, seg, ridx, capacity)
+
+    good = [torch.tensor([3, 7, 10], dtype=torch.int64, device="cuda"),
+            torch.tensor([5, 10], dtype=torch.int32, device="cuda")]
+    with pytest.raises(cq.CQError) as e:
+        call([torch.tensor([3, 2, 10], dtype=torch.int64, device="cuda")], 10)
+    assert e.value.status == cq.CQ_ERR_UNSORTED
+    with pytest.raises(cq.CQError) as e:
+        call([torch.tensor([3, 7, 9], dtype=torch.int64, device="cuda")], 10)
+    assert e.value.status == cq.CQ_ERR_SIZE_MISMATCH and "n_rows" in str(e.value)
+    with pytest.raises(cq.CQError) as e:
+        call(good, 10, capacity=3)          # segments end at 3, 5, 7, 10
+    assert e.value.status == cq.CQ_ERR_SIZE_MISMATCH
+    with pytest.raises(cq.CQError) as e:
+        call(good, -1)
+    assert e.value.status == cq.CQ_ERR_INVALID_ARG
+    assert call(good, 10) == 4
+    torch.cuda.synchronize()
+    assert seg[:4].tolist() == [3, 5, 7, 10]
+    assert ridx[:4].tolist() == [0, 1, 1, 2]          # ridx[j * capacity + s]
+    assert ridx[64:68].tolist() == [0, 0, 1, 1]
