@@ -11,9 +11,14 @@
 // (range bounds, IN tables, key minima and strides, bases) stay in the
 // descriptor, so queries that differ only in their literals share a kernel.
 //
-// S provides (all constexpr): tile_rows, n_preds, n_pbm, n_keys, n_aggs,
-// one_group, table_dense; per column c: enc, v64, bw, bslot, raw_off,
-// stage_off; per predicate i (evaluation order): pcol, pkind, pn32, ppbm;
+// The helper warp's steps (bulk-copy issue, window prefetch, bitmap and
+// pass-bitmap building) are specialised the same way.
+//
+// S provides (all constexpr): tile_rows, n_cols, n_bitmaps, n_row_cols,
+// stage_bytes, n_preds, n_pbm, n_keys, n_aggs, one_group, table_dense; per
+// column c: enc, v64, e64, bw, bslot, raw_off, stage_off; bcol(j), the
+// column of bitmap slot j; row_col(i), the i-th staged column; per predicate
+// i (evaluation order): pcol, pkind, pn32, ppbm;
 // per key k: kcol, kremap, kn32; per aggregate i: akind, acol, asw, awide,
 // asw32, agw, ared32, aw32, an32, as32, asrc (the first aggregate reading the
 // same column value, whose read is reused).
@@ -387,6 +392,25 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
   }
 }
 
+// ------------------------------------------------------------------ helper warp
+// Bits per row of a staged column.
+template <class S, int C>
+__device__ __forceinline__ constexpr uint32_t col_bits() {
+  return S::enc(C) == ENC_PLAIN ? (S::v64(C) ? 64u : 32u) : (uint32_t)S::bw(C);
+}
+
+// A predicate on one run / listed value (the helper's once-per-value test).
+template <class S, int I>
+__device__ __forceinline__ bool fast_pred_value(const QueryDesc& q, const uint32_t* aux, long long v) {
+  constexpr int kind = S::pkind(I);
+  const PredDesc& p = q.preds[I];
+  if constexpr (kind == PK_RANGE) return pred_test<PT_RANGE>(p, aux, v);
+  else if constexpr (kind == PK_NE) return pred_test<PT_NE>(p, aux, v);
+  else if constexpr (kind == PK_BITMAP) return pred_test<PT_BITMAP>(p, aux, v);
+  else if constexpr (kind == PK_LIST) return pred_test<PT_LIST>(p, aux, v);
+  else return kind == PK_TRUE;
+}
+
 template <class S>
 struct FastBody {
   template <int NCW, int GPW>
@@ -396,6 +420,205 @@ struct FastBody {
     const uint32_t pm = fast_filter<S, GS, GPW>(q, tv, wbase, rows);
     const uint32_t n_pass = compact<GPW>(pm, wbase, GS, list);
     fast_aggregate<S>(q, sm, tv, list, n_pass, row0);
+  }
+
+  // Bulk copies of tile u's row-level columns into stage st (a full tile's
+  // byte counts are constants).
+  __device__ static __forceinline__ void issue(const QueryDesc& q, const Smem& sm, unsigned long long u, uint32_t st) {
+    constexpr uint32_t T = S::tile_rows;
+    uint8_t* dst = sm.stage + (size_t)st * S::stage_bytes;
+    const unsigned long long r0 = u * T;
+    const bool full = q.n_rows - r0 >= T;
+    const uint32_t rows = full ? T : (uint32_t)(q.n_rows - r0);
+    uint32_t total = 0;
+    static_for<S::n_row_cols>([&](auto I) {
+      constexpr int c = S::row_col(decltype(I)::value);
+      constexpr uint32_t bits = col_bits<S, c>();
+      constexpr uint32_t full_bytes = ((T * bits + 7) / 8 + 15) / 16 * 16;
+      total += full ? full_bytes : ((rows * bits + 7) / 8 + 15) / 16 * 16;
+    });
+    mbar_arrive_expect_tx(&sm.mbar[st], total);
+    static_for<S::n_row_cols>([&](auto I) {
+      constexpr int c = S::row_col(decltype(I)::value);
+      constexpr uint32_t bits = col_bits<S, c>();
+      constexpr uint32_t full_bytes = ((T * bits + 7) / 8 + 15) / 16 * 16;
+      const uint32_t bytes = full ? full_bytes : ((rows * bits + 7) / 8 + 15) / 16 * 16;
+      bulk_g2s(dst + S::stage_off(c), reinterpret_cast<const uint8_t*>(q.cols[c].vals) + r0 * bits / 8, bytes,
+               &sm.mbar[st]);
+    });
+  }
+
+  // Windows of kWin run ends / positions and their values per bitmap column,
+  // from the helper cursors on, into window set wb.
+  __device__ static __forceinline__ void prefetch(const QueryDesc& q, const Smem& sm, int wb) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long* hcur = helper_cursor(sm);
+    static_for<S::n_bitmaps>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr int c = S::bcol(j);
+      const ColDesc& cd = q.cols[c];
+      const unsigned long long cur = hcur[j];
+      const uint32_t avail = cur < cd.n ? (uint32_t)((cd.n - cur) < kWin ? (cd.n - cur) : kWin) : 0u;
+      uint8_t* dst = sm.win + ((size_t)wb * S::n_bitmaps + j) * kWin * 16;
+      uint8_t* vdst = dst + kWin * 8;
+      for (uint32_t i = lane; i < avail; i += 32) {
+        if constexpr (S::e64(c)) cp_async8(dst + 8 * i, reinterpret_cast<const long long*>(cd.ends) + cur + i);
+        else cp_async4(dst + 4 * i, reinterpret_cast<const int*>(cd.ends) + cur + i);
+        if constexpr (S::v64(c)) cp_async8(vdst + 8 * i, reinterpret_cast<const long long*>(cd.vals) + cur + i);
+        else cp_async4(vdst + 4 * i, reinterpret_cast<const int*>(cd.vals) + cur + i);
+      }
+      if (lane == 0) sm.wcnt[wb * kMaxBitmapCols + j] = avail;
+    });
+    cp_async_commit();
+  }
+
+  // Bitmaps (bit o: a run of the column ends at tile row o / row o is listed)
+  // with word prefix popcounts, start cursors, and the pass bitmaps of the
+  // run-column predicates, for tile [s, e) into buffer buf.
+  __device__ static __forceinline__ void build(const QueryDesc& q, const Smem& sm, const uint32_t* aux, int buf, int wb,
+                                               unsigned long long s, unsigned long long e) {
+    constexpr uint32_t nwords = S::tile_rows / 32;
+    constexpr uint32_t per = nwords / 32;
+    constexpr int nb = S::n_bitmaps;
+    const int lane = threadIdx.x & 31;
+    unsigned long long* hcur = helper_cursor(sm);
+    cp_async_wait_all();
+    __syncwarp();
+    static_for<nb>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr int c = S::bcol(j);
+      constexpr bool is_rle = S::enc(c) == ENC_RLE;
+      constexpr bool e64 = S::e64(c);
+      const ColDesc& cd = q.cols[c];
+      uint32_t* B = sm.bm + ((size_t)buf * nb + j) * nwords;
+      uint32_t* P = sm.pre + ((size_t)buf * nb + j) * (nwords + 1);
+#pragma unroll
+      for (uint32_t k = 0; k < per; ++k) B[k * 32 + lane] = 0;
+      __syncwarp();
+      const unsigned long long cur = hcur[j];
+      const uint32_t avail = sm.wcnt[wb * kMaxBitmapCols + j];
+      const uint8_t* win = sm.win + ((size_t)wb * nb + j) * kWin * 16;
+      unsigned long long cnt = 0;
+      int eq = 0;
+      for (unsigned long long base = 0;; base += 32) {
+        const unsigned long long idx = cur + base + lane;
+        long long x = 0;
+        bool have = true;
+        if (base + lane < avail) {
+          if constexpr (e64) x = reinterpret_cast<const long long*>(win)[base + lane];
+          else x = reinterpret_cast<const int*>(win)[base + lane];
+        } else if (idx < cd.n) {
+          x = ldg_val(cd.ends, idx, e64);
+        } else {
+          have = false;
+        }
+        const bool in_tile = have && (unsigned long long)x < e;
+        if (in_tile) {
+          // a boundary before the tile would mean a corrupt cursor: flag it, never write
+          if ((unsigned long long)x < s || (is_rle && (unsigned long long)x == s)) {
+            report(q, CQ_ERR_INVALID_ARG, 2ull + ((unsigned long long)j << 8), s, (unsigned long long)x);
+          } else {
+            const uint32_t o = (uint32_t)((unsigned long long)x - s);
+            atomicOr(&B[o >> 5], 1u << (o & 31));
+          }
+        }
+        const uint32_t stop = __ballot_sync(0xFFFFFFFFu, !in_tile);
+        if (stop) {
+          const int f = __ffs(stop) - 1;
+          cnt = base + f;
+          const long long xf = __shfl_sync(0xFFFFFFFFu, x, f);
+          const bool hf = __shfl_sync(0xFFFFFFFFu, have, f);
+          eq = (is_rle && hf && (unsigned long long)xf == e) ? 1 : 0;
+          break;
+        }
+      }
+      __syncwarp();
+      // word prefix popcounts: lane owns words [lane * per, lane * per + per)
+      uint32_t wv[per];
+      uint32_t local = 0;
+#pragma unroll
+      for (uint32_t k = 0; k < per; ++k) {
+        wv[k] = B[lane * per + k];
+        local += __popc(wv[k]);
+      }
+      uint32_t incl = local;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      uint32_t run = incl - local;
+#pragma unroll
+      for (uint32_t k = 0; k < per; ++k) {
+        P[lane * per + k] = run;
+        run += __popc(wv[k]);
+      }
+      if (lane == 31) P[nwords] = incl;
+      if (lane == 0) {
+        sm.tcur[buf * kMaxBitmapCols + j] = cur;
+        hcur[j] = cur + cnt + (unsigned long long)eq;
+      }
+      __syncwarp();
+    });
+    // pass bitmaps: predicates 0 .. n_pbm-1, on RLE / index columns, evaluated
+    // once per run / listed row
+    const uint32_t rows = (uint32_t)(e - s);
+    static_for<S::n_pbm>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int c = S::pcol(i);
+      constexpr int j = S::bslot(c);
+      constexpr bool e64 = S::e64(c), v64 = S::v64(c);
+      const ColDesc& cd = q.cols[c];
+      uint32_t* PB = sm.pbm + ((size_t)buf * S::n_pbm + S::ppbm(i)) * nwords;
+      const uint32_t nset = sm.pre[((size_t)buf * nb + j) * (nwords + 1) + nwords];
+      const unsigned long long cur = sm.tcur[buf * kMaxBitmapCols + j];
+      const uint8_t* win = sm.win + ((size_t)wb * nb + j) * kWin * 16;
+      const uint32_t avail = sm.wcnt[wb * kMaxBitmapCols + j];
+      auto end_at = [&](uint32_t k) -> unsigned long long {
+        if (k < avail) {
+          if constexpr (e64) return (unsigned long long)reinterpret_cast<const long long*>(win)[k];
+          else return (unsigned long long)reinterpret_cast<const int*>(win)[k];
+        }
+        return (unsigned long long)ldg_val(cd.ends, cur + k, e64);
+      };
+      auto val_at = [&](uint32_t k) -> long long {
+        if (k < avail) {
+          const uint8_t* v = win + kWin * 8;
+          if constexpr (v64) return reinterpret_cast<const long long*>(v)[k];
+          else return (long long)reinterpret_cast<const int*>(v)[k];
+        }
+        return ldg_val(cd.vals, cur + k, v64);
+      };
+      if constexpr (S::enc(c) == ENC_RLE) {
+#pragma unroll
+        for (uint32_t k = 0; k < per; ++k) PB[k * 32 + lane] = 0u;
+        __syncwarp();
+        // nset boundaries inside the tile: nset + 1 runs, the last one clipped
+        for (uint32_t k = lane; k <= nset; k += 32) {
+          const uint32_t a = k == 0 ? 0u : (uint32_t)(end_at(k - 1) - s);
+          const unsigned long long x = end_at(k);
+          const uint32_t b = x - s < rows ? (uint32_t)(x - s) : rows;
+          if (fast_pred_value<S, i>(q, aux, val_at(k))) fill_bits(PB, a, b);
+        }
+      } else {
+        const bool base_pass = fast_pred_value<S, i>(q, aux, cd.base);
+#pragma unroll
+        for (uint32_t k = 0; k < per; ++k) {
+          const uint32_t w = k * 32 + lane;
+          const uint32_t lo = w * 32;
+          uint32_t m = base_pass ? ~0u : 0u;
+          if (lo >= rows) m = 0u;
+          else if (rows - lo < 32) m &= (1u << (rows - lo)) - 1u;
+          PB[w] = m;
+        }
+        __syncwarp();
+        for (uint32_t k = lane; k < nset; k += 32) {
+          const uint32_t o = (uint32_t)(end_at(k) - s);
+          if (fast_pred_value<S, i>(q, aux, val_at(k)) != base_pass) atomicXor(&PB[o >> 5], 1u << (o & 31));
+        }
+      }
+      __syncwarp();
+    });
   }
 };
 

@@ -79,22 +79,29 @@ static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) 
   s += "#include \"cq_fast.cuh\"\nnamespace cq {\nstruct JitShape {\n";
   snprintf(buf, sizeof(buf),
            "  static constexpr int tile_rows = %u, n_preds = %u, n_pbm = %u, n_keys = %u, n_aggs = %u;\n"
+           "  static constexpr int n_cols = %u, n_bitmaps = %u, n_row_cols = %u, stage_bytes = %u;\n"
            "  static constexpr bool one_group = %s, table_dense = %s;\n",
-           q.tile_rows, q.n_preds, q.n_pbm, q.n_keys, q.n_aggs, q.n_groups == 1 ? "true" : "false",
-           q.table_dense ? "true" : "false");
+           q.tile_rows, q.n_preds, q.n_pbm, q.n_keys, q.n_aggs, q.n_cols, q.n_bitmaps, q.n_row_cols, q.stage_bytes,
+           q.n_groups == 1 ? "true" : "false", q.table_dense ? "true" : "false");
   s += buf;
-  std::vector<long long> enc, v64, bw, bslot, roff, soff;
+  std::vector<long long> enc, v64, e64, bw, bslot, roff, soff, bcol(q.n_bitmaps, 0), rcol;
   for (int c = 0; c < q.n_cols; ++c) {
     const ColDesc& d = q.cols[c];
     enc.push_back(d.enc);
     v64.push_back(d.v64);
+    e64.push_back(d.e64);
     bw.push_back(d.bw);
     bslot.push_back(d.bslot);
     roff.push_back(d.raw_is_offset);
     soff.push_back(d.stage_off);
+    if (d.bslot != 0xFF && d.bslot < q.n_bitmaps) bcol[d.bslot] = c;
   }
+  for (int i = 0; i < q.n_row_cols; ++i) rcol.push_back(q.row_cols[i]);
   emit_fn(s, "enc", enc);
   emit_fn(s, "v64", v64);
+  emit_fn(s, "e64", e64);
+  emit_fn(s, "bcol", bcol);
+  emit_fn(s, "row_col", rcol);
   emit_fn(s, "bw", bw);
   emit_fn(s, "bslot", bslot);
   emit_fn(s, "raw_off", roff);

@@ -228,6 +228,9 @@ __device__ inline void helper_pass_bitmaps(const QueryDesc& q, const Smem& sm, c
 // ones, aggregate them -- is Body::tile; GenericBody reads every shape
 // property of the query from its descriptor at run time (FastBody in
 // cq_fast.cuh has them as compile-time constants).
+// The helper warp's steps go through the body too: issue (lane 0: the bulk
+// copies of tile u into stage st), prefetch (windows of run ends / positions
+// into window set wb) and build (bitmaps and pass bitmaps of tile [s, e)).
 struct GenericBody {
   template <int NCW, int GPW>
   __device__ static __forceinline__ void tile(const QueryDesc& q, const Smem& sm, const TileView& tv, uint32_t wbase,
@@ -236,6 +239,37 @@ struct GenericBody {
     const uint32_t pm = phase_filter<false, GPW>(q, tv, nullptr, wbase, gstride, rows);
     const uint32_t n_pass = compact<GPW>(pm, wbase, gstride, list);
     phase_aggregate<false, 2>(q, sm, tv, nullptr, list, n_pass, row0);
+  }
+
+  __device__ static __forceinline__ void issue(const QueryDesc& q, const Smem& sm, unsigned long long u, uint32_t st) {
+    const uint32_t T = q.tile_rows;
+    uint8_t* dst = sm.stage + (size_t)st * q.stage_bytes;
+    const unsigned long long r0 = u * T;
+    const unsigned long long rows = (q.n_rows - r0) < (unsigned long long)T ? (q.n_rows - r0) : (unsigned long long)T;
+    uint32_t total = 0;
+    for (int i = 0; i < q.n_row_cols; ++i) {
+      const ColDesc& c = q.cols[q.row_cols[i]];
+      const uint32_t bits = c.enc == ENC_PLAIN ? (c.v64 ? 64u : 32u) : (uint32_t)c.bw;
+      total += (uint32_t)(((rows * bits + 7) / 8 + 15) / 16 * 16);
+    }
+    mbar_arrive_expect_tx(&sm.mbar[st], total);
+    for (int i = 0; i < q.n_row_cols; ++i) {
+      const ColDesc& c = q.cols[q.row_cols[i]];
+      const uint32_t bits = c.enc == ENC_PLAIN ? (c.v64 ? 64u : 32u) : (uint32_t)c.bw;
+      const uint32_t bytes = (uint32_t)(((rows * bits + 7) / 8 + 15) / 16 * 16);
+      bulk_g2s(dst + c.stage_off, reinterpret_cast<const uint8_t*>(c.vals) + r0 * bits / 8, bytes, &sm.mbar[st]);
+    }
+  }
+
+  __device__ static __forceinline__ void prefetch(const QueryDesc& q, const Smem& sm, int wb) {
+    prefetch_windows(q, sm, wb);
+  }
+
+  __device__ static __forceinline__ void build(const QueryDesc& q, const Smem& sm, const uint32_t* aux, int buf, int wb,
+                                               unsigned long long s, unsigned long long e) {
+    const uint32_t nwords = q.tile_rows / 32;
+    helper_build(q, sm, buf, wb, s, e, nwords);
+    if (q.n_pbm) helper_pass_bitmaps(q, sm, aux, buf, wb, s, e, nwords);
   }
 };
 
@@ -269,40 +303,21 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
   }
   __syncthreads();
 
-  // ---- bulk-copy producer (helper lane 0): tile u -> stage (u - t_begin) % stages
-  auto issue = [&](unsigned long long u) {
-    const uint32_t st = (uint32_t)((u - t_begin) % q.stages);
-    uint8_t* dst = sm.stage + (size_t)st * q.stage_bytes;
-    const unsigned long long r0 = u * T;
-    const unsigned long long rows = (q.n_rows - r0) < (unsigned long long)T ? (q.n_rows - r0) : (unsigned long long)T;
-    uint32_t total = 0;
-    for (int i = 0; i < q.n_row_cols; ++i) {
-      const ColDesc& c = q.cols[q.row_cols[i]];
-      const uint32_t bits = c.enc == ENC_PLAIN ? (c.v64 ? 64u : 32u) : (uint32_t)c.bw;
-      total += (uint32_t)(((rows * bits + 7) / 8 + 15) / 16 * 16);
-    }
-    mbar_arrive_expect_tx(&sm.mbar[st], total);
-    for (int i = 0; i < q.n_row_cols; ++i) {
-      const ColDesc& c = q.cols[q.row_cols[i]];
-      const uint32_t bits = c.enc == ENC_PLAIN ? (c.v64 ? 64u : 32u) : (uint32_t)c.bw;
-      const uint32_t bytes = (uint32_t)(((rows * bits + 7) / 8 + 15) / 16 * 16);
-      bulk_g2s(dst + c.stage_off, reinterpret_cast<const uint8_t*>(c.vals) + r0 * bits / 8, bytes, &sm.mbar[st]);
-    }
-  };
-
+  // ---- bulk-copy producer (helper lane 0): stage st holds tile u; stage and
+  // barrier parity advance with the tile (no division per tile)
   // ---- prologue: first tile's bitmaps, windows of the second, the first stages
   if (helper) {
     if (lane == 0)
-      for (unsigned long long u = t_begin; u < t_end && u < t_begin + q.stages; ++u) issue(u);
+      for (unsigned long long u = t_begin; u < t_end && u < t_begin + q.stages; ++u)
+        Body::issue(q, sm, u, (uint32_t)(u - t_begin));
     if (nb) {
       // window set (u - t_begin) % kWinBufs serves tile u: prefetched two
       // tiles ahead, turned into bitmaps one tile ahead, read by the compute
       // warps (values) while the tile is processed
-      prefetch_windows(q, sm, 0);
+      Body::prefetch(q, sm, 0);
       const unsigned long long e0 = ((t_begin + 1) * T < q.n_rows) ? (t_begin + 1) * T : q.n_rows;
-      helper_build(q, sm, 0, 0, t_begin * T, e0, nwords);
-      if (q.n_pbm) helper_pass_bitmaps(q, sm, aux_smem ? sm.aux : q.aux, 0, 0, t_begin * T, e0, nwords);
-      if (t_begin + 1 < t_end) prefetch_windows(q, sm, 1);
+      Body::build(q, sm, aux_smem ? sm.aux : q.aux, 0, 0, t_begin * T, e0);
+      if (t_begin + 1 < t_end) Body::prefetch(q, sm, 1);
     }
   }
   __syncthreads();
@@ -310,6 +325,8 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
   uint32_t rows_since_flush = 0;
   uint16_t* mylist = sm.clist + (helper ? 0 : warp) * (GPW * 32);
   const uint32_t wbase = warp * 32;
+  uint32_t st = 0, ph = 0;   // stage of tile t and the parity of its barrier phase
+  uint32_t wbi = 0;          // window set of tile t: (t - t_begin) % kWinBufs
 
   for (unsigned long long t = t_begin; t < t_end; ++t) {
     const unsigned long long s = t * T;
@@ -317,13 +334,12 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
     const uint32_t rows = (uint32_t)(e - s);
     const int buf = (int)((t - t_begin) & 1ull);
     if (!helper) {
-      const uint32_t st = (uint32_t)((t - t_begin) % q.stages);
-      mbar_wait_bounded(&sm.mbar[st], (uint32_t)(((t - t_begin) / q.stages) & 1ull), q.err);
+      mbar_wait_bounded(&sm.mbar[st], ph, q.err);
       TileView tv;
       tv.bm = sm.bm + (size_t)buf * nb * nwords;
       tv.pre = sm.pre + (size_t)buf * nb * (nwords + 1);
       tv.cur = sm.tcur + buf * kMaxBitmapCols;
-      const int wb = (int)((t - t_begin) % kWinBufs);
+      const int wb = (int)wbi;
       tv.win = window_set(q, sm, wb);
       tv.pbm = sm.pbm + (size_t)buf * q.n_pbm * nwords;
       tv.wn = sm.wcnt + wb * kMaxBitmapCols;
@@ -332,11 +348,10 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
       tv.nwords = nwords;
       Body::template tile<NCW, GPW>(q, sm, tv, wbase, rows, mylist, s);
     } else if (nb && t + 1 < t_end) {
-      const int wb1 = (int)((t + 1 - t_begin) % kWinBufs);
+      const int wb1 = (int)(wbi + 1 == kWinBufs ? 0 : wbi + 1);
       const unsigned long long e1 = (e + T < q.n_rows) ? e + T : q.n_rows;
-      helper_build(q, sm, buf ^ 1, wb1, e, e1, nwords);
-      if (q.n_pbm) helper_pass_bitmaps(q, sm, aux_smem ? sm.aux : q.aux, buf ^ 1, wb1, e, e1, nwords);
-      if (t + 2 < t_end) prefetch_windows(q, sm, (int)((t + 2 - t_begin) % kWinBufs));
+      Body::build(q, sm, aux_smem ? sm.aux : q.aux, buf ^ 1, wb1, e, e1);
+      if (t + 2 < t_end) Body::prefetch(q, sm, (int)(wbi == 0 ? 2 : wbi - 1));
     }
     // one barrier per tile; thread 0 decides the flush from the occupancy it
     // sees (an early or late flush is harmless: a full table falls back to
@@ -347,13 +362,18 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
                                       (last || (!q.table_dense && sm.misc[0] * 2 > (int)q.table_slots) ||
                                        rows_since_flush + T > q.flush_rows));
     // tile t's stage is free: refill it with tile t + stages
-    if (helper && lane == 0 && t + q.stages < t_end) issue(t + q.stages);
+    if (helper && lane == 0 && t + q.stages < t_end) Body::issue(q, sm, t + q.stages, st);
     if (need) {
       flush_table(q, sm);
       if (threadIdx.x == 0) sm.misc[0] = 0;
       __syncthreads();
       rows_since_flush = 0;
     }
+    if (++st == q.stages) {
+      st = 0;
+      ph ^= 1u;
+    }
+    wbi = wbi + 1 == kWinBufs ? 0 : wbi + 1;
   }
   // the stage barriers are dead: invalidate them so the batch kernel may
   // reuse their words for another query's layout
