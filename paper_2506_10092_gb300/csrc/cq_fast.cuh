@@ -450,12 +450,14 @@ struct FastBody {
 
   // Windows of kWin run ends / positions and their values per bitmap column,
   // from the helper cursors on, into window set wb.
-  __device__ static __forceinline__ void prefetch(const QueryDesc& q, const Smem& sm, int wb) {
+  // (helper warp hw of nh takes the columns j with j % nh == hw)
+  __device__ static __forceinline__ void prefetch(const QueryDesc& q, const Smem& sm, int wb, int hw, int nh) {
     const int lane = threadIdx.x & 31;
     const unsigned long long* hcur = helper_cursor(sm);
     static_for<S::n_bitmaps>([&](auto J) {
       constexpr int j = decltype(J)::value;
       constexpr int c = S::bcol(j);
+      if (j % nh != hw) return;
       const ColDesc& cd = q.cols[c];
       const unsigned long long cur = hcur[j];
       const uint32_t avail = cur < cd.n ? (uint32_t)((cd.n - cur) < kWin ? (cd.n - cur) : kWin) : 0u;
@@ -476,7 +478,7 @@ struct FastBody {
   // with word prefix popcounts, start cursors, and the pass bitmaps of the
   // run-column predicates, for tile [s, e) into buffer buf.
   __device__ static __forceinline__ void build(const QueryDesc& q, const Smem& sm, const uint32_t* aux, int buf, int wb,
-                                               unsigned long long s, unsigned long long e) {
+                                               unsigned long long s, unsigned long long e, int hw, int nh) {
     constexpr uint32_t nwords = S::tile_rows / 32;
     constexpr uint32_t per = nwords / 32;
     constexpr int nb = S::n_bitmaps;
@@ -489,6 +491,7 @@ struct FastBody {
       constexpr int c = S::bcol(j);
       constexpr bool is_rle = S::enc(c) == ENC_RLE;
       constexpr bool e64 = S::e64(c);
+      if (j % nh != hw) return;
       const ColDesc& cd = q.cols[c];
       uint32_t* B = sm.bm + ((size_t)buf * nb + j) * nwords;
       uint32_t* P = sm.pre + ((size_t)buf * nb + j) * (nwords + 1);
@@ -568,6 +571,7 @@ struct FastBody {
       constexpr int c = S::pcol(i);
       constexpr int j = S::bslot(c);
       constexpr bool e64 = S::e64(c), v64 = S::v64(c);
+      if (j % nh != hw) return;
       const ColDesc& cd = q.cols[c];
       uint32_t* PB = sm.pbm + ((size_t)buf * S::n_pbm + S::ppbm(i)) * nwords;
       const uint32_t nset = sm.pre[((size_t)buf * nb + j) * (nwords + 1) + nwords];

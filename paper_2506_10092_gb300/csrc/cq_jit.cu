@@ -71,6 +71,9 @@ static void emit_fn(std::string& s, const char* name, const std::vector<long lon
   s += "0; }\n";
 }
 
+// Helper warps of the specialised kernel: one per bitmap column, at most two.
+int jit_helpers(const QueryDesc& q) { return q.n_bitmaps >= 2 ? 2 : 1; }
+
 // Source of the shape class and kernel for descriptor q run with ncw compute
 // warps, gpw 32-row groups per warp and minb CTAs per SM.
 static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) {
@@ -163,15 +166,17 @@ static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) 
   emit_fn(s, "as32", as32);
   emit_fn(s, "asrc", asrc);
   s += "};\n}  // namespace cq\n";
+  const int nh = jit_helpers(q);
   snprintf(buf, sizeof(buf),
            "extern \"C\" __global__ void __launch_bounds__(%d, %d) cq_row_jit(const __grid_constant__ cq::QueryDesc q) {\n",
-           (ncw + 1) * 32, minb);
+           (ncw + nh) * 32, minb);
   s += buf;
   s += "  const unsigned long long t_begin = (unsigned long long)blockIdx.x * q.n_tiles / gridDim.x;\n"
        "  const unsigned long long t_end = (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;\n"
        "  if (t_begin >= t_end) return;\n";
-  snprintf(buf, sizeof(buf), "  cq::row_range<%d, %d, cq::FastBody<cq::JitShape>>(q, cq::carve(q), t_begin, t_end);\n}\n",
-           ncw, gpw);
+  snprintf(buf, sizeof(buf),
+           "  cq::row_range<%d, %d, cq::FastBody<cq::JitShape>, %d>(q, cq::carve(q), t_begin, t_end);\n}\n", ncw, gpw,
+           nh);
   s += buf;
   return s;
 }
@@ -273,7 +278,7 @@ int jit_row_kernel(const QueryDesc& q, int ncw, int gpw, int minb, int device, s
 
 cudaError_t launch_row_jit(const void* fn, const QueryDesc& q, unsigned grid, int ncw, cudaStream_t s) {
   void* args[] = {const_cast<QueryDesc*>(&q)};
-  return cudaLaunchKernel(fn, dim3(grid), dim3((ncw + 1) * 32), args, q.smem_bytes, s);
+  return cudaLaunchKernel(fn, dim3(grid), dim3((ncw + jit_helpers(q)) * 32), args, q.smem_bytes, s);
 }
 
 }  // namespace cq

@@ -261,25 +261,30 @@ struct GenericBody {
     }
   }
 
-  __device__ static __forceinline__ void prefetch(const QueryDesc& q, const Smem& sm, int wb) {
+  // (one helper warp: hw = 0, nh = 1)
+  __device__ static __forceinline__ void prefetch(const QueryDesc& q, const Smem& sm, int wb, int hw, int nh) {
     prefetch_windows(q, sm, wb);
   }
 
   __device__ static __forceinline__ void build(const QueryDesc& q, const Smem& sm, const uint32_t* aux, int buf, int wb,
-                                               unsigned long long s, unsigned long long e) {
+                                               unsigned long long s, unsigned long long e, int hw, int nh) {
     const uint32_t nwords = q.tile_rows / 32;
     helper_build(q, sm, buf, wb, s, e, nwords);
     if (q.n_pbm) helper_pass_bitmaps(q, sm, aux, buf, wb, s, e, nwords);
   }
 };
 
-template <int NCW, int GPW, class Body = GenericBody>
+// NH helper warps (warps NCW .. NCW + NH - 1) share the bitmap columns:
+// helper hw builds and prefetches columns j with j % NH == hw; helper 0 also
+// issues the bulk copies.
+template <int NCW, int GPW, class Body = GenericBody, int NH = 1>
 __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, unsigned long long t_begin,
                                           unsigned long long t_end) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t T = q.tile_rows;
   const uint32_t nwords = T / 32;
-  const bool helper = warp == NCW;
+  const bool helper = warp >= NCW;
+  const int hw = warp - NCW;
   const int nb = q.n_bitmaps;
 
   // ---- init: group table, aux tables, barriers, helper cursors
@@ -293,7 +298,7 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
     fence_barrier_init();
   }
   if (helper) {
-    for (int j = 0; j < nb; ++j) {
+    for (int j = hw; j < nb; j += NH) {
       const ColDesc& cd = bitmap_col(q, j);
       // RLE: first run whose exclusive end exceeds the first row; index: first position >= it
       const unsigned long long c0 =
@@ -307,17 +312,17 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
   // barrier parity advance with the tile (no division per tile)
   // ---- prologue: first tile's bitmaps, windows of the second, the first stages
   if (helper) {
-    if (lane == 0)
+    if (hw == 0 && lane == 0)
       for (unsigned long long u = t_begin; u < t_end && u < t_begin + q.stages; ++u)
         Body::issue(q, sm, u, (uint32_t)(u - t_begin));
     if (nb) {
       // window set (u - t_begin) % kWinBufs serves tile u: prefetched two
       // tiles ahead, turned into bitmaps one tile ahead, read by the compute
       // warps (values) while the tile is processed
-      Body::prefetch(q, sm, 0);
+      Body::prefetch(q, sm, 0, hw, NH);
       const unsigned long long e0 = ((t_begin + 1) * T < q.n_rows) ? (t_begin + 1) * T : q.n_rows;
-      Body::build(q, sm, aux_smem ? sm.aux : q.aux, 0, 0, t_begin * T, e0);
-      if (t_begin + 1 < t_end) Body::prefetch(q, sm, 1);
+      Body::build(q, sm, aux_smem ? sm.aux : q.aux, 0, 0, t_begin * T, e0, hw, NH);
+      if (t_begin + 1 < t_end) Body::prefetch(q, sm, 1, hw, NH);
     }
   }
   __syncthreads();
@@ -350,8 +355,8 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
     } else if (nb && t + 1 < t_end) {
       const int wb1 = (int)(wbi + 1 == kWinBufs ? 0 : wbi + 1);
       const unsigned long long e1 = (e + T < q.n_rows) ? e + T : q.n_rows;
-      Body::build(q, sm, aux_smem ? sm.aux : q.aux, buf ^ 1, wb1, e, e1);
-      if (t + 2 < t_end) Body::prefetch(q, sm, (int)(wbi == 0 ? 2 : wbi - 1));
+      Body::build(q, sm, aux_smem ? sm.aux : q.aux, buf ^ 1, wb1, e, e1, hw, NH);
+      if (t + 2 < t_end) Body::prefetch(q, sm, (int)(wbi == 0 ? 2 : wbi - 1), hw, NH);
     }
     // one barrier per tile; thread 0 decides the flush from the occupancy it
     // sees (an early or late flush is harmless: a full table falls back to
@@ -362,7 +367,7 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
                                       (last || (!q.table_dense && sm.misc[0] * 2 > (int)q.table_slots) ||
                                        rows_since_flush + T > q.flush_rows));
     // tile t's stage is free: refill it with tile t + stages
-    if (helper && lane == 0 && t + q.stages < t_end) Body::issue(q, sm, t + q.stages, st);
+    if (helper && hw == 0 && lane == 0 && t + q.stages < t_end) Body::issue(q, sm, t + q.stages, st);
     if (need) {
       flush_table(q, sm);
       if (threadIdx.x == 0) sm.misc[0] = 0;
