@@ -38,9 +38,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cq", choices=["cq", "reference"])
     ap.add_argument("--workload", default="heterogeneous",
-                    choices=["heterogeneous", "tiny", "nested", "batched", "serving"])
+                    choices=["heterogeneous", "tiny", "nested", "batched", "serving", "runsweep"])
     ap.add_argument("--rates", default="100,500,1000,2000,5000", help="serving: arrival rates (queries/s)")
-    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving: arrivals per rate and mode")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving: measured arrivals per rate and mode")
+    ap.add_argument("--serve-warmup", type=float, default=1.0,
+                    help="serving: seconds of arrivals before the measured ones (latencies not counted)")
     ap.add_argument("--serve-modes", default="batched,one_at_a_time,decompress_then_scan")
     ap.add_argument("--queries", type=int, default=4096, help="batched: queries per batch")
     ap.add_argument("--parts", type=int, default=256, help="batched: partitions in the pool")
@@ -57,6 +59,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="heterogeneous workload: skip the decompress-then-scan comparison and the 20e9-row "
+                         "nested query reported beside the main line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -87,8 +92,9 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-# the sources the row kernel is compiled from (its code and its descriptor)
-ROW_KERNEL_SOURCES = ("cq_row.cu", "cq_rowpath.cuh", "cq_phases.cuh", "cq_device.cuh", "cq_internal.h")
+# the device code of the shape-specialised row kernel (compiled at run time
+# from these headers and the shape class cq_jit.cu writes)
+ROW_KERNEL_SOURCES = ("cq_fast.cuh", "cq_rowpath.cuh", "cq_phases.cuh", "cq_device.cuh", "cq_desc.h", "cq_jit.cu")
 
 
 def _code_only(text: str) -> str:
@@ -424,17 +430,150 @@ def run_cq(args):
             "kernel_us": k_us,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "row_query_kernel" if dn is not None or args.workload != "tiny"
-                         else "seg_query_kernel", "peak_source": f"{peak_src} hbm_gbs",
+                         "kernel": "cq_row_jit (row kernel specialised to the query shape)"
+                         if dn is not None or args.workload != "tiny" else "seg_query_kernel",
+                         "peak_source": f"{peak_src} hbm_gbs",
                          "algorithmic_bytes_per_launch": alg_bytes},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": launches_per_query(n_rows) * args.steps,
         }
+        if args.workload == "heterogeneous" and args.mode == "fused" and not args.no_secondary:
+            line["decompress_then_scan"] = run_dts_comparison(cq, t, ps, stream, n_rows, ms_per_step, torch)
+            del t, cols
+            torch.cuda.synchronize()
+            line["nested_20e9"] = run_nested_secondary(cq, ctx, stream, args, torch, peak)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def launches_per_query(n_rows: int) -> int:
+    """Kernels one fused query launches: init, the fused kernel (one launch per
+    2^31 rows, a SUM fold between two), three finalize kernels."""
+    parts = max(1, -(-n_rows // (1 << 31)))
+    return 1 + parts + (parts - 1) + 3
+
+
+def run_dts_comparison(cq, t, ps, stream, n_rows, fused_ms, torch, steps: int = 3):
+    """The same query on the decompress-then-scan comparison path (expand every
+    referenced column to flat int64 arrays, then scan them), timed on the same
+    GPU; steps after one warm-up."""
+    opts = cq.exec_options(mode=cq.CQ_EXEC_DECOMPRESS_THEN_SCAN)
+    r = cq.cq_query_run(t, ps, stream=stream, opts=opts)
+    cq.cq_result_wait(r)
+    r.close()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    res = [cq.cq_query_run(t, ps, stream=stream, opts=opts) for _ in range(steps)]
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    for r in res:
+        cq.cq_result_wait(r)
+        r.close()
+    return {"ms_per_step": ms, "rows_per_s": n_rows / (ms / 1000.0), "steps": steps,
+            "fused_speedup": ms / fused_ms,
+            "note": "every referenced column expanded to flat int64 on the device, then the row scan"}
+
+
+def run_nested_secondary(cq, ctx, stream, args, torch, peak, steps: int = 3):
+    """The largest single-GPU configuration beside the main line: the 20e9-row
+    nested table (62.4 GB of compressed columns resident), its c3-range query
+    GROUP BY c2, c4; device time of the fused kernel and of the whole query."""
+    from paper_2506_10092_gb300 import datagen as dg
+    from paper_2506_10092_gb300 import devgen
+    try:
+        n_rows = 20_000_000_000
+        t_gen = time.perf_counter()
+        dn = devgen.DeviceNested(cq, ctx, n_rows, seed=args.seed)
+        torch.cuda.synchronize()
+        t_gen = time.perf_counter() - t_gen
+        plan = dg.nested_plan(lean=True)
+        ps = cq.PlanStruct(plan)
+        alg = dn.query_bytes(plan)
+        for _ in range(2):
+            r = cq.cq_query_run(dn.table, ps, stream=stream)
+            cq.cq_result_wait(r)
+            r.close()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        res = [cq.cq_query_run(dn.table, ps, stream=stream) for _ in range(steps)]
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        k_us = statistics.mean(cq.cq_result_kernel_time_us(r) for r in res)
+        groups = cq.cq_result_num_groups(res[-1])
+        for r in res:
+            r.close()
+        del dn
+        torch.cuda.synchronize()
+        return {"workload": f"nested-lean-{n_rows}", "rows": n_rows, "ms_per_step": ms,
+                "rows_per_s": n_rows / (ms / 1000.0), "compressed_bytes": alg, "groups": groups,
+                "kernel_us": k_us, "achieved_gbs": alg / (k_us * 1e-6) / 1e9,
+                "frac_of_measured_hbm": alg / (k_us * 1e-6) / 1e9 / peak, "steps": steps,
+                "table_build_s": t_gen, "launches_per_query": launches_per_query(n_rows)}
+    except Exception as e:   # the main line stands without it
+        return {"workload": "nested-lean-20000000000", "error": str(e)[:300]}
+
+
+# ---------------------------------------------------------------- run-length sweep
+def run_runsweep(args):
+    """Compressed GB/s of pure run-length queries as the runs lengthen: the
+    two-RLE template (A < 50 GROUP BY B) over 100M rows at mean runs 8 / 5,
+    1e3 and 1e5, and a c3-range query GROUP BY c2 over the RLE columns of a
+    1e9-row nested table.  Segment-mode work follows the runs, so the
+    compressed GB/s should not fall as runs lengthen."""
+    import torch
+    from paper_2506_10092_gb300 import cq
+    from paper_2506_10092_gb300 import datagen as dg
+    from paper_2506_10092_gb300 import devgen
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx = cq.cq_ctx_create(0, stream)
+    n = args.rows or 100_000_000
+    rows_out = []
+
+    def timed(t, ps, n_rows, alg, label):
+        for _ in range(max(3, args.warmup)):
+            r = cq.cq_query_run(t, ps, stream=stream)
+            cq.cq_result_wait(r)
+            r.close()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        res = [cq.cq_query_run(t, ps, stream=stream) for _ in range(args.steps)]
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        k_us = statistics.mean(cq.cq_result_kernel_time_us(r) for r in res)
+        for r in res:
+            r.close()
+        rows_out.append({"case": label, "rows": n_rows, "compressed_bytes": alg, "ms_per_step": ms,
+                         "kernel_us": k_us, "rows_per_s": n_rows / (ms / 1e3),
+                         "compressed_gbs_kernel": alg / (k_us * 1e-6) / 1e9})
+        print(json.dumps(rows_out[-1]), file=sys.stderr, flush=True)
+
+    for ma, mb in ((8.0, 5.0), (1e3, 625.0), (1e5, 62500.0)):
+        table, plan = dg.tiny_two_rle(n, seed=args.seed, mean_a=ma, mean_b=mb)
+        t, cols = cq.table_from(ctx, table)
+        timed(t, cq.PlanStruct(plan), n, dg.compressed_bytes(table, dg.plan_columns(plan)),
+              f"two-RLE mean runs {ma:g}/{mb:g}")
+        del t, cols, table
+    dn = devgen.DeviceNested(cq, ctx, 1_000_000_000, seed=args.seed)
+    plan = dg.Plan([dg.Pred(2, "between", 200, 699)], [1], [dg.Agg("count"), dg.Agg("sum", 2), dg.Agg("max", 0)])
+    timed(dn.table, cq.PlanStruct(plan), dn.n_rows, dn.query_bytes(plan), "nested c1..c3 RLE, 1e9 rows")
+    print(json.dumps({"metric": "compressed GB/s of pure run-length queries", "value": None, "unit": "GB/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                      "config": {"workload": "run-length sweep", "parallelism": "replicas1"},
+                      "by_case": rows_out, "gpu_launches": 5 * args.steps * len(rows_out)}), flush=True)
 
 
 # ---------------------------------------------------------------- batched workload
@@ -633,7 +772,14 @@ def run_serving(args):
     def pct(xs, p):
         return float(np.percentile(np.asarray(xs), p)) if xs else None
 
-    def run_mode(mode, rate, reqs, arrivals):
+    # compile the kernels specialised to every query shape of the mix before
+    # any timing (each process compiles a shape once)
+    for tb, ps in ([tiny[0], cq.PlanStruct(dg.tiny_plan(50))],
+                   [het[0], cq.PlanStruct(het_plan)]) + tuple(
+                       [p.table, cq.PlanStruct(dg.nested_plan(200, 699, lean=True))] for p in nest):
+        cq.cq_result_wait(cq.cq_query_run(tb, ps))
+
+    def run_mode(mode, rate, reqs, arrivals, n_warm):
         n = len(reqs)
         lat = [None] * n
         done_t = [0.0] * n
@@ -676,21 +822,26 @@ def run_serving(args):
                 done_t[i] = time.perf_counter()
                 lat[i] = (done_t[i] - arr) * 1e6
                 r.close()
-        span = max(done_t) - t0
-        return {"mode": mode, "rate": rate, "queries": n, "achieved_qps": n / span, "p50_us": pct(lat, 50),
-                "p99_us": pct(lat, 99), "launches": launches}
+        # statistics over the measured arrivals only (after the warm-up ones)
+        meas = lat[n_warm:]
+        t_first = t0 + arrivals[n_warm] if n_warm < n else t0
+        span = max(done_t[n_warm:]) - t_first
+        return {"mode": mode, "rate": rate, "queries": n - n_warm, "warmup_queries": n_warm,
+                "achieved_qps": (n - n_warm) / span, "p50_us": pct(meas, 50), "p99_us": pct(meas, 99),
+                "p99_samples": len(meas), "launches": launches}
 
     rows = []
     modes = [m for m in args.serve_modes.split(",") if m]
     for rate in [float(x) for x in args.rates.split(",")]:
-        n = max(20, int(rate * args.serve_seconds))
+        n_warm = int(rate * args.serve_warmup)
+        n = n_warm + max(20, int(rate * args.serve_seconds))
         r = np.random.default_rng([args.seed, 7, int(rate)])
         arrivals = np.cumsum(r.exponential(1.0 / rate, size=n))
         reqs = [request(r) for _ in range(n)]
         for mode in modes:
             # the comparison path is slow: a bounded prefix of the same arrivals
-            k = n if mode != "decompress_then_scan" else min(n, 1500)
-            rows.append(run_mode(mode, rate, reqs[:k], arrivals[:k]))
+            k = n if mode != "decompress_then_scan" else min(n, n_warm + 1500)
+            rows.append(run_mode(mode, rate, reqs[:k], arrivals[:k], min(n_warm, k - 1)))
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     best = max((x for x in rows if x["mode"] == "batched"), key=lambda x: x["achieved_qps"], default=None)
     line = {
@@ -698,6 +849,7 @@ def run_serving(args):
         "n_gpus": 1, "steps": len(rows), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": "serving-mix-60-30-10", "rates": args.rates, "seconds_per_rate": args.serve_seconds,
+                   "warmup_seconds_per_rate": args.serve_warmup,
                    "tables": "two-RLE 1M, heterogeneous 100M, 16 nested partitions", "parallelism": "replicas1"},
         "p50_us": best["p50_us"] if best else None, "p99_us": best["p99_us"] if best else None,
         "by_rate": rows,
@@ -714,6 +866,8 @@ def main():
         run_serving(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "runsweep":
+        run_runsweep(args)
     else:
         run_cq(args)
 

@@ -214,6 +214,10 @@ typedef struct {
                             shape, compiled at run time on first use and cached by the process
                             (the environment variable CQ_JIT=0 turns this off); 1 = the generic
                             ahead-of-time kernel, which reads the shape from the descriptor */
+  uint32_t hash_slots_log2;  /* key domains above 2^24 groups: initial slots of the global hash
+                                table as a power of two (12..26); 0 = twice the groups that can
+                                exist, 2^12 .. 2^22.  A table that fills is retried by
+                                cq_result_wait with four times the slots, up to 2^26 */
 } cq_exec_options;
 
 /* ------------------------------------------------------------------ queries */
@@ -226,8 +230,14 @@ typedef struct {
  * predicate, in ascending lexicographic key order (dictionary keys by code,
  * i.e. by string); a plan without GROUP BY yields exactly one row (COUNT 0,
  * SUM 0, MIN / MAX / AVG 0 when nothing passes).
+ * Tables of more than 2^31 rows run as several launches of at most 2^31 rows
+ * each, with the exact SUM accumulators normalised in between.
+ * Key domains (the product of the group-by columns' value ranges) up to
+ * 2^24 groups are dense arrays; larger ones, up to 2^62, keep their groups in
+ * an open-addressing hash table in device memory keyed by the packed key, and
+ * finalize sorts the groups by key (Section 7, grouping phase).
  * Errors (synchronous): CQ_ERR_INVALID_ARG for a malformed plan,
- * CQ_ERR_UNSUPPORTED when the dense key domain exceeds 2^24 groups. */
+ * CQ_ERR_UNSUPPORTED when the key domain exceeds 2^62 groups. */
 int cq_query_run(cq_table* table, const cq_plan* plan, void* cuda_stream, cq_result** out);
 int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_exec_options* opts,
                     void* cuda_stream, cq_result** out);
@@ -256,7 +266,8 @@ int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_exec_options*
  * device buffers of the batch are freed when its last result is destroyed).
  * Errors (synchronous, no result is returned): those of cq_query_run for any
  * query (the message names the query), CQ_ERR_INVALID_ARG for n == 0 or
- * tables of different contexts. */
+ * tables of different contexts, CQ_ERR_UNSUPPORTED for a table of more than
+ * 2^31 rows or a key domain above 2^24 groups (run such a query alone). */
 int cq_batch_run(uint32_t n, cq_table* const* tables, const cq_plan* plans,
                  const cq_exec_options* opts, void* cuda_stream, cq_result** results);
 
@@ -362,12 +373,13 @@ int cq_selftest_bounded_wait(cq_ctx* ctx, uint32_t limit_us, int32_t* device_sta
  * took (either may be NULL).  No counterpart in the paper.  Always CQ_OK. */
 int cq_jit_stats(uint64_t* compiles, double* seconds);
 
-/* Compile, without loading, one of two built-in shapes (variant 0 or 1) that
- * between them exercise every encoding, predicate kind, key mapping and
- * aggregate layout of the specialised row kernel: a check of the run-time
- * compiler that needs no GPU.  *seconds (may be NULL) receives the compile
- * time.  CQ_ERR_INVALID_ARG for another variant, CQ_ERR_CUDA (with the
- * compiler's log in cq_last_error) when compilation fails. */
+/* Compile, without loading, one of three built-in shapes (variant 0, 1 or 2)
+ * that between them exercise every encoding, predicate kind, key mapping,
+ * aggregate layout and group domain of the specialised row kernel: a check
+ * of the run-time compiler that needs no GPU.  *seconds (may be NULL)
+ * receives the compile time.  CQ_ERR_INVALID_ARG for another variant,
+ * CQ_ERR_CUDA (with the compiler's log in cq_last_error) when compilation
+ * fails. */
 int cq_jit_check(uint32_t variant, double* seconds);
 
 /* ------------------------------------------------------------------ serving
@@ -379,12 +391,18 @@ int cq_jit_check(uint32_t variant, double* seconds);
  *    buffers and its share of the batch control block -- is computed; it is
  *    admitted to a launch only while the footprints of all queries in flight
  *    stay within memory_budget_bytes;
- *  - continuous batching: whenever one of n_streams streams is free, the
- *    admitted queries are launched together as one batch (cq_batch_run's
- *    persistent kernel) if the device is idle, max_batch queries are
- *    waiting, or the oldest has waited max_wait_us; queries arriving while
- *    earlier batches run go into the next batch on another stream, so their
- *    work overlaps on the device;
+ *  - two lanes (n_streams >= 2): queries over tables of more than
+ *    2^large_rows_log2 rows form the large lane -- planned like cq_query_run,
+ *    launched alone on stream 0 as soon as no other large launch is in
+ *    flight (large scans are bandwidth-bound; two at once only delay both);
+ *  - continuous batching of the small lane: whenever one of the other
+ *    streams (created at the highest stream priority) is free, the admitted
+ *    small queries are launched together as one batch (cq_batch_run's
+ *    persistent kernel) if the lane is idle, max_batch queries are waiting,
+ *    or the oldest has waited max_wait_us; small batches arriving while
+ *    others run go on another stream, so their work overlaps on the device
+ *    and with the large lane's scan (with n_streams == 1 every query is in
+ *    the small lane);
  *  - completion: launches in flight are polled; a finished query's result
  *    and latency (submission to observed completion) go to cq_server_wait.
  * Each query's result equals its cq_query_run result exactly. */
@@ -395,7 +413,8 @@ typedef struct {
   uint32_t max_batch;            /* most queries per launch; 0 = 256 */
   uint32_t n_streams;            /* concurrent launches in flight (<= 16); 0 = 2 */
   uint32_t max_wait_us;          /* how long a partial batch may wait for company; 0 = 50 */
-  uint32_t reserved[3];
+  uint32_t large_rows_log2;      /* tables above 2^this many rows use the large lane; 0 = 22 */
+  uint32_t reserved[2];
 } cq_server_options;
 
 /* Start a serving loop on ctx (which it keeps alive until destroyed). */

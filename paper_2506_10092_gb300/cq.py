@@ -58,12 +58,13 @@ class cq_plan(C.Structure):
 class cq_exec_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile_rows", C.c_uint32), ("ctas_per_sm", C.c_uint32),
                 ("stages", C.c_uint32), ("table_slots", C.c_uint32), ("grid_ctas", C.c_uint32),
-                ("items_per_cta", C.c_uint32), ("kernel", C.c_uint32)]
+                ("items_per_cta", C.c_uint32), ("kernel", C.c_uint32),
+                ("hash_slots_log2", C.c_uint32)]
 
 
 class cq_server_options(C.Structure):
     _fields_ = [("memory_budget_bytes", C.c_uint64), ("max_batch", C.c_uint32), ("n_streams", C.c_uint32),
-                ("max_wait_us", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+                ("max_wait_us", C.c_uint32), ("large_rows_log2", C.c_uint32), ("reserved", C.c_uint32 * 2)]
 
 
 _VP = C.c_void_p
@@ -312,10 +313,10 @@ KERNEL_SPECIALISED, KERNEL_GENERIC = 0, 1
 
 
 def exec_options(mode=CQ_EXEC_FUSED, tile_rows=0, ctas_per_sm=0, stages=0, table_slots=0,
-                 grid_ctas=0, items_per_cta=0, kernel=KERNEL_SPECIALISED) -> cq_exec_options:
+                 grid_ctas=0, items_per_cta=0, kernel=KERNEL_SPECIALISED, hash_slots_log2=0) -> cq_exec_options:
     o = cq_exec_options()
     o.mode, o.tile_rows, o.ctas_per_sm, o.stages, o.table_slots = mode, tile_rows, ctas_per_sm, stages, table_slots
-    o.grid_ctas, o.items_per_cta, o.kernel = grid_ctas, items_per_cta, kernel
+    o.grid_ctas, o.items_per_cta, o.kernel, o.hash_slots_log2 = grid_ctas, items_per_cta, kernel, hash_slots_log2
     return o
 
 
@@ -387,10 +388,12 @@ def cq_selftest_bounded_wait(ctx, limit_us: int) -> int:
 
 
 # ---------------------------------------------------------------- serving loop
-def server_options(memory_budget_bytes=0, max_batch=0, n_streams=0, max_wait_us=0) -> cq_server_options:
+def server_options(memory_budget_bytes=0, max_batch=0, n_streams=0, max_wait_us=0,
+                   large_rows_log2=0) -> cq_server_options:
     o = cq_server_options()
     o.memory_budget_bytes, o.max_batch, o.n_streams, o.max_wait_us = memory_budget_bytes, max_batch, n_streams, \
         max_wait_us
+    o.large_rows_log2 = large_rows_log2
     return o
 
 

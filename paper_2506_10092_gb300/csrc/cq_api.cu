@@ -587,9 +587,17 @@ static void set_members(PredDesc& d, std::vector<int64_t> vals, std::vector<uint
   }
 }
 
+// Capacity of a query's global hash table: 2^lg slots, and the CTAs of its
+// finalize sort (about 4096 slots each, at most 1024).
+static void set_hash_capacity(QueryDesc& q, uint32_t lg) {
+  q.n_groups = 1ull << lg;
+  const uint64_t b = q.n_groups / 4096;
+  q.sort_blocks = (uint32_t)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
+
 static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
                            const cq_exec_options* opts, const cq_ctx* ctx, uint32_t tile, int ncw,
-                           size_t smem_limit, Planned* P, bool* no_fit) {
+                           size_t smem_limit, Planned* P, bool* no_fit, bool batch) {
   *no_fit = false;
   if (!plan) return set_error(CQ_ERR_INVALID_ARG, "plan is NULL");
   if (plan->n_preds > (uint32_t)kMaxPreds || plan->n_group_by > (uint32_t)kMaxKeys || plan->n_aggs > (uint32_t)kMaxAggs)
@@ -833,24 +841,46 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       }
       if (hi < lo) { lo = 0; hi = 0; }
       const i128 card = hi - lo + 1;
-      if (card > (i128)kDenseMaxGroups)
-        return set_error(CQ_ERR_UNSUPPORTED, "group-by column %u spans %.3g values; dense key domains are limited to 2^24",
+      if (card > ((i128)1 << 62))
+        return set_error(CQ_ERR_UNSUPPORTED, "group-by column %u spans %.3g values; key domains are limited to 2^62",
                          plan->group_by[k], (double)card);
       kd.kmin = (int64_t)lo;
-      kd.card = (uint32_t)card;
+      kd.card = (uint64_t)card;
     }
     if (kd.card == 0) kd.card = 1;
-    kd.n32 = (narrow_col(cd, pc) && kd.kmin >= -(1ll << 30) && kd.kmin <= (1ll << 30)) ? 1 : 0;
-    groups *= kd.card;
-    if (groups > (i128)kDenseMaxGroups)
-      return set_error(CQ_ERR_UNSUPPORTED, "the group-by key domain exceeds 2^24 groups");
+    kd.n32 = (narrow_col(cd, pc) && kd.kmin >= -(1ll << 30) && kd.kmin <= (1ll << 30) && kd.card <= (1ull << 32)) ? 1 : 0;
+    groups *= (i128)kd.card;
+    if (groups > ((i128)1 << 62))
+      return set_error(CQ_ERR_UNSUPPORTED, "the group-by key domain exceeds 2^62 groups");
   }
   uint64_t stride = 1;
   for (int k = (int)plan->n_group_by - 1; k >= 0; --k) {
     q.keys[k].stride = stride;
     stride *= q.keys[k].card;
   }
-  q.n_groups = (uint64_t)groups;
+  // Key domains above 2^24 groups keep their groups in a global hash table
+  // of packed 64-bit keys (a single query only; batches keep dense domains)
+  q.ghash = groups > (i128)kDenseMaxGroups ? 1 : 0;
+  if (q.ghash) {
+    if (batch)
+      return set_error(CQ_ERR_UNSUPPORTED,
+                       "the group-by key domain (%.3g groups) needs the global hash table, which batched queries "
+                       "do not use; run the query alone",
+                       (double)groups);
+    uint32_t bits = 1;
+    while (bits < 63 && ((i128)1 << bits) < groups) ++bits;
+    q.key_bits = (uint8_t)bits;
+    // initial capacity: twice the groups that can exist (at most one per
+    // row), within 2^12 .. 2^22 slots unless the options name one
+    const i128 est = std::min<i128>(groups, (i128)n_rows > 0 ? (i128)n_rows : 1);
+    uint32_t lg = kHashMinLog2;
+    while (lg < 22 && ((i128)1 << lg) < 2 * est) ++lg;
+    if (opts && opts->hash_slots_log2) lg = opts->hash_slots_log2;
+    set_hash_capacity(q, lg);
+  } else {
+    q.key_bits = 0;
+    q.n_groups = (uint64_t)groups;
+  }
   // ---- evaluation order and per-run evaluation (Appendix D: predicates on
   // run-length columns are tested first, once per run value).  Row mode:
   // up to kMaxPassBitmaps RLE / index predicates get a tile pass bitmap the
@@ -983,7 +1013,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   uint32_t slots = opts && opts->table_slots ? opts->table_slots : 1024;
   if (slots & (slots - 1)) return set_error(CQ_ERR_INVALID_ARG, "table_slots must be a power of two");
   const uint64_t dense_cap = 4096;
-  if (q.n_groups <= dense_cap) {
+  if (q.n_groups <= dense_cap && !q.ghash) {
     q.table_dense = 1;
     q.table_slots = (uint32_t)q.n_groups;
   } else {
@@ -1055,6 +1085,8 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
     return set_error(CQ_ERR_INVALID_ARG, "tile_rows must be 1024, 2048, 4096 or 8192");
   if (want_ctas > 3) return set_error(CQ_ERR_INVALID_ARG, "ctas_per_sm must be 0, 1, 2 or 3 (3: segment mode)");
   if (opts && opts->kernel > 1) return set_error(CQ_ERR_INVALID_ARG, "kernel must be 0 (specialised) or 1 (generic)");
+  if (opts && opts->hash_slots_log2 && (opts->hash_slots_log2 < kHashMinLog2 || opts->hash_slots_log2 > kHashMaxLog2))
+    return set_error(CQ_ERR_INVALID_ARG, "hash_slots_log2 must be 0 or in %u..%u", kHashMinLog2, kHashMaxLog2);
   // segment mode when every referenced column is RLE or index-encoded
   bool seg = true;
   auto look = [&](uint32_t c) {
@@ -1104,7 +1136,7 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   int rc = CQ_ERR_UNSUPPORTED;
   for (const Shape& sh : shapes) {
     bool no_fit = false;
-    rc = plan_query_tile(tcols, n_rows, plan, opts, ctx, sh.tile, sh.ncw, sh.limit, P, &no_fit);
+    rc = plan_query_tile(tcols, n_rows, plan, opts, ctx, sh.tile, sh.ncw, sh.limit, P, &no_fit, batch_limit != 0);
     if (rc == CQ_OK || !no_fit) return rc;
   }
   return rc;
@@ -1119,7 +1151,10 @@ QueryBlock query_block_layout(const Planned& P, bool with_aux) {
   QueryBlock L;
   L.gacc = 0;
   L.out = L.gacc + al(8ull * q.n_gw * G);
-  L.aux = L.out + al(8ull * q.n_out * G);
+  // hash domains: the key table and the finalize sort's buffers
+  L.hkeys = L.out + al(8ull * q.n_out * G);
+  L.hsort = L.hkeys + (q.ghash ? al(8ull * G) : 0);
+  L.aux = L.hsort + (q.ghash ? 2 * al(8ull * G) + 2 * al(4ull * G) + al(4ull * 256 * q.sort_blocks) : 0);
   L.err = L.aux + (with_aux ? al(4ull * (P.aux.size() + 2)) : 0);
   L.cnt = L.err + 256;
   L.blk = L.cnt + 256;
@@ -1134,6 +1169,21 @@ void bind_query_block(Planned& P, uint8_t* b, const QueryBlock& L, const uint32_
   const uint64_t G = q.n_groups;
   q.gacc = reinterpret_cast<unsigned long long*>(b + L.gacc);
   for (uint32_t i = 0; i < q.n_out; ++i) q.out[i] = b + L.out + (uint64_t)i * 8 * G;
+  if (q.ghash) {
+    auto al = [](uint64_t x) { return (x + 255) / 256 * 256; };
+    uint8_t* h = b + L.hsort;
+    q.gkeys = reinterpret_cast<unsigned long long*>(b + L.hkeys);
+    q.skeys[0] = reinterpret_cast<unsigned long long*>(h);
+    q.skeys[1] = reinterpret_cast<unsigned long long*>(h + al(8ull * G));
+    q.svals[0] = reinterpret_cast<uint32_t*>(h + 2 * al(8ull * G));
+    q.svals[1] = reinterpret_cast<uint32_t*>(h + 2 * al(8ull * G) + al(4ull * G));
+    q.shist = reinterpret_cast<uint32_t*>(h + 2 * al(8ull * G) + 2 * al(4ull * G));
+  } else {
+    q.gkeys = nullptr;
+    q.skeys[0] = q.skeys[1] = nullptr;
+    q.svals[0] = q.svals[1] = nullptr;
+    q.shist = nullptr;
+  }
   q.aux = aux_dev;
   q.aux_words = (uint32_t)P.aux.size();
   q.err = reinterpret_cast<int*>(b + L.err);
@@ -1155,15 +1205,20 @@ void attach_outputs(cq_result* r, const Planned& P) {
 
 // Carve one pool allocation into the query's device buffers and enqueue
 // init -> fused kernel -> finalize on `s`.
+// Row mode: resolve the kernel specialised to the query's shape (compiled on
+// first use of the shape in this process).
+int prepare_row_kernel(cq_ctx* ctx, Planned& P) {
+  QueryDesc& q = P.q;
+  if (q.seg_mode || P.generic || P.row_fn || !jit_enabled()) return CQ_OK;
+  int ncw, gpw, minb;
+  row_shape(q, &ncw, &gpw, &minb);
+  return jit_row_kernel(q, ncw, gpw, minb, ctx->device, ctx->smem_optin, &P.row_fn);
+}
+
 static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r) {
   QueryDesc& q = P.q;
-  if (!q.seg_mode && !P.generic && !P.row_fn && jit_enabled()) {
-    // row mode: the kernel specialised to this query's shape (compiled on first use)
-    int ncw, gpw, minb;
-    row_shape(q, &ncw, &gpw, &minb);
-    const int rc = jit_row_kernel(q, ncw, gpw, minb, ctx->device, ctx->smem_optin, &P.row_fn);
-    if (rc != CQ_OK) return rc;
-  }
+  const int prc = prepare_row_kernel(ctx, P);
+  if (prc != CQ_OK) return prc;
   clear_stale_error("a query launch");
   const QueryBlock L = query_block_layout(P, true);
   void* base = nullptr;
@@ -1181,8 +1236,23 @@ static int launch_planned(cq_ctx* ctx, Planned& P, cudaStream_t s, cq_result* r)
   const char* step = "init";
   e = launch_init_global(q, s);
   if (e == cudaSuccess && (step = "event", true)) e = cudaEventRecord(r->ev_k0, s);
-  if (e == cudaSuccess && (step = "fused kernel", true))
-    e = launch_query(q, s, ctx->num_sms, P.ctas_per_sm, P.grid_ctas, P.row_fn);
+  if (e == cudaSuccess && (step = "fused kernel", true)) {
+    // launches of at most kLaunchRows rows, the SUM limbs folded in between
+    // (CQ_LAUNCH_ROWS in the environment lowers the split, for tests)
+    uint64_t rows = kLaunchRows;
+    if (const char* env = getenv("CQ_LAUNCH_ROWS")) {
+      const unsigned long long v = strtoull(env, nullptr, 10);
+      if (v >= q.tile_rows && v < rows) rows = v;
+    }
+    const uint64_t chunk = rows / q.tile_rows;
+    for (uint64_t t0 = 0; t0 < q.n_tiles && e == cudaSuccess; t0 += chunk) {
+      QueryDesc qc = q;
+      qc.tile0 = t0;
+      qc.n_tiles = q.n_tiles - t0 < chunk ? q.n_tiles - t0 : chunk;
+      e = launch_query(qc, s, ctx->num_sms, P.ctas_per_sm, P.grid_ctas, P.row_fn);
+      if (e == cudaSuccess && t0 + chunk < q.n_tiles && (step = "fold", true)) e = launch_fold_sums(q, s);
+    }
+  }
   if (e == cudaSuccess && (step = "event", true)) e = cudaEventRecord(r->ev_k1, s);
   if (e == cudaSuccess && (step = "finalize", true)) e = launch_finalize(q, s);
   if (e != cudaSuccess)
@@ -1239,11 +1309,23 @@ int launch_solo(cq_table* table, Planned& P, cudaStream_t s, cq_result** out) {
   return CQ_OK;
 }
 
+// Plan one query for a launch of its own (cq_query_run's planner).
+int plan_solo_query(cq_table* table, const cq_plan* plan, Planned* P) {
+  if (!table) return set_error(CQ_ERR_INVALID_ARG, "NULL table");
+  std::vector<PlanCol> cols;
+  cols.reserve(table->cols.size());
+  for (cq_column* c : table->cols) cols.push_back(view_of(c));
+  return plan_query(cols, table->n_rows, plan, nullptr, table->ctx, P);
+}
+
 // Plan one query of a batch (see plan_query): the shared kernel shape, tiles
 // of `tile_rows` rows (0 = the mode's default), shared memory within
 // `smem_limit` bytes.
 int plan_batch_query(cq_table* table, const cq_plan* plan, uint32_t tile_rows, size_t smem_limit, Planned* P) {
   if (!table) return set_error(CQ_ERR_INVALID_ARG, "NULL table");
+  if (table->n_rows > kLaunchRows)
+    return set_error(CQ_ERR_UNSUPPORTED, "batched queries take tables of at most 2^31 rows (%llu given); run it alone",
+                     (unsigned long long)table->n_rows);
   std::vector<PlanCol> cols;
   cols.reserve(table->cols.size());
   for (cq_column* c : table->cols) cols.push_back(view_of(c));
@@ -1314,6 +1396,7 @@ extern "C" int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_ex
     free_result(r);
     return rc;
   }
+  if (P.q.ghash) r->retry.reset(new Planned(P));   // cq_result_wait may relaunch it larger
   for (int kc : P.out_key_col) r->key_cols.push_back(kc >= 0 ? table->cols[kc] : nullptr);
   for (cq_column* c : table->cols) c->refs++;   // results keep their columns' dictionaries alive
   r->held_cols = table->cols;
@@ -1336,6 +1419,8 @@ static int report_status(cq_result* r) {
   if (err == CQ_ERR_OVERFLOW)
     return set_error(err, "SUM of aggregate %llu does not fit int64 (dense group %llu)", idx, st[2]);
   if (err == CQ_ERR_TIMEOUT) return set_error(err, "a bounded device wait gave up");
+  if (err == CQ_ERR_TABLE_FULL)
+    return set_error(err, "the global group hash table (%llu slots) is full at key %llu", st[2], st[3]);
   if (err == CQ_ERR_INVALID_ARG && what == 1)
     return set_error(err, "group-by key %llu at row %llu has value %lld outside its recorded domain", idx, st[2],
                      (long long)st[3]);
@@ -1368,7 +1453,26 @@ extern "C" int cq_result_wait(cq_result* r, uint64_t timeout_us) {
   e = cudaMemcpy(st, r->err_dev, sizeof(st), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&cnt, r->count_dev, sizeof(cnt), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "status read-back failed: %s", cudaGetErrorString(e));
-  const int err = (int)(uint32_t)st[0];
+  int err = (int)(uint32_t)st[0];
+  // a full global hash table: launch again with four times the slots
+  while (err == CQ_ERR_TABLE_FULL && r->retry) {
+    Planned& P = *r->retry;
+    uint32_t lg = 0;
+    while ((1ull << lg) < P.q.n_groups) ++lg;
+    if (lg + 2 > kHashMaxLog2) break;
+    cudaFreeAsync(r->dev_block, r->stream);
+    r->dev_block = nullptr;
+    set_hash_capacity(P.q, lg + 2);
+    int rc = launch_planned(r->ctx, P, r->stream, r);
+    if (rc != CQ_OK) return rc;
+    e = cudaEventRecord(r->ev_done, r->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(r->ev_done);
+    if (e == cudaSuccess) e = cudaMemcpy(st, r->err_dev, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&cnt, r->count_dev, sizeof(cnt), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_error(CQ_ERR_CUDA, "query failed: %s", cudaGetErrorString(e));
+    err = (int)(uint32_t)st[0];
+    r->retries++;
+  }
   r->waited = true;
   r->n_groups = cnt;
   r->status = err;

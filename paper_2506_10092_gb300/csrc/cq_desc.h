@@ -17,7 +17,11 @@ constexpr int kMaxKeys = 8;
 constexpr int kMaxAggs = 16;
 constexpr int kMaxBitmapCols = 8; // RLE / index columns per query
 constexpr int kMaxPassBitmaps = 4; // row-mode predicates evaluated once per run
-constexpr uint64_t kDenseMaxGroups = 1ull << 24;
+constexpr uint64_t kDenseMaxGroups = 1ull << 24;   // larger key domains use the global hash table
+constexpr uint32_t kHashMinLog2 = 12;               // global hash table: 2^12 .. 2^26 slots
+constexpr uint32_t kHashMaxLog2 = 26;
+constexpr int kGlobalProbes = 256;                  // probe bound of the global hash table
+constexpr unsigned long long kEmptyGroup = ~0ull;   // empty global (and 64-bit shared) key
 
 enum Enc : uint8_t { ENC_RLE = 1, ENC_DICT = 2, ENC_INDEX = 3, ENC_PACKED = 4, ENC_PLAIN = 5 };
 
@@ -80,8 +84,8 @@ struct KeyDesc {
   uint8_t pad0;
   uint32_t aux_off;  // bitmap words (remap)
   uint32_t aux_len;  // bitmap words (remap)
-  uint32_t card;     // number of digit values
-  uint64_t stride;   // gid = sum digit * stride
+  uint64_t card;     // number of digit values
+  uint64_t stride;   // gid = sum digit * stride (the packed key, ordered like the key tuple)
   int64_t kmin;      // digit = raw - kmin (remap: bitmap covers raw - kmin)
   uint32_t prefix_off; // remap: uint32 prefix popcounts per bitmap word in aux
   uint32_t list_off;   // remap: sorted raw values (int64 word pairs) for decoding ranks
@@ -106,7 +110,8 @@ struct AggDesc {
 
 struct QueryDesc {
   uint64_t n_rows;
-  uint64_t n_tiles;
+  uint64_t n_tiles;        // tiles of this launch: [tile0, tile0 + n_tiles)
+  uint64_t tile0;          // first tile of this launch (launches over 2^31 rows are split)
   uint32_t tile_rows;
   uint8_t n_cols, n_preds, n_keys, n_aggs;
   uint8_t seg_mode;        // 1: every referenced column is RLE/index -> items are segments
@@ -134,6 +139,15 @@ struct QueryDesc {
   uint32_t aux_words;
   uint32_t smem_bytes;     // dynamic shared memory of the fused kernel
   // global state
+  uint8_t ghash;             // 1: groups live in an open-addressing hash table of n_groups
+                             // (a power of two) slots keyed by the packed 64-bit gid; 0: the
+                             // dense domain, gid indexes the accumulators directly
+  uint8_t key_bits;          // bits of the packed key (hash tables: the finalize sort's width)
+  uint32_t sort_blocks;      // hash tables: CTAs of the finalize sort's passes
+  unsigned long long* gkeys; // hash tables: [n_groups] packed keys, kEmptyGroup when free
+  unsigned long long* skeys[2];  // hash tables: finalize sort buffers (keys)
+  uint32_t* svals[2];            // ... and slot indices
+  uint32_t* shist;               // ... per-block digit counts [256][sort_blocks]
   unsigned long long* gacc;  // [n_gw][n_groups]
   int* err;                  // device status word (cq_status, 0 = ok)
   unsigned long long* err_info;  // what / where / value of the first device error

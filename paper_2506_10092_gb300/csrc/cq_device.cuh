@@ -165,7 +165,10 @@ __device__ __forceinline__ void atomic_add_i128(unsigned long long* lo_w, unsign
 
 // Global SUM accumulator: three words, value = w0 + w1 * 2^32 + w2 * 2^64 with
 // w0, w1 receiving 32-bit limbs (unsigned) and w2 the signed top.  Every
-// update is a fire-and-forget atomic add; exact for < 2^32 updates per word.
+// update is a fire-and-forget atomic add; exact for < 2^32 updates per word,
+// which the host guarantees: one launch covers at most 2^31 rows (each row or
+// flushed group adds at most one limb per word), and the limbs are folded
+// into the next word between launches (fold_sums_kernel).
 __device__ __forceinline__ void global_add_limbs(unsigned long long* w0, unsigned long long* w1, unsigned long long* w2,
                                                  I128 x) {
   const unsigned long long l0 = x.lo & 0xFFFFFFFFull;

@@ -15,7 +15,8 @@
 // pass-bitmap building) are specialised the same way.
 //
 // S provides (all constexpr): tile_rows, n_cols, n_bitmaps, n_row_cols,
-// stage_bytes, n_preds, n_pbm, n_keys, n_aggs, one_group, table_dense; per
+// stage_bytes, n_preds, n_pbm, n_keys, n_aggs, one_group, table_dense, ghash
+// (groups in the global hash table, 64-bit packed keys); per
 // column c: enc, v64, e64, bw, bslot, raw_off, stage_off; bcol(j), the
 // column of bitmap slot j; row_col(i), the i-th staged column; per predicate
 // i (evaluation order): pcol, pkind, pn32, ppbm;
@@ -27,6 +28,15 @@
 #include "cq_rowpath.cuh"
 
 namespace cq {
+
+template <bool B, class T, class F>
+struct Pick {
+  typedef T type;
+};
+template <class T, class F>
+struct Pick<false, T, F> {
+  typedef F type;
+};
 
 template <int I, int N, class F>
 __device__ __forceinline__ void static_for_from(F& f) {
@@ -213,8 +223,9 @@ __device__ __forceinline__ uint32_t fast_filter(const QueryDesc& q, const TileVi
 }
 
 // ------------------------------------------------------------------ aggregation
+// Digit of key K at tile row o (64-bit: hash domains pack wide digits).
 template <class S, int K>
-__device__ __forceinline__ bool fast_digit(const QueryDesc& q, const TileView& t, uint32_t o, uint32_t* d,
+__device__ __forceinline__ bool fast_digit(const QueryDesc& q, const TileView& t, uint32_t o, unsigned long long* d,
                                            long long* raw) {
   constexpr int c = S::kcol(K);
   const KeyDesc& k = q.keys[K];
@@ -230,9 +241,9 @@ __device__ __forceinline__ bool fast_digit(const QueryDesc& q, const TileView& t
   } else {
     const long long v = fast_raw<S, c>(q, t, o);
     *raw = v;
-    const unsigned long long dd = (unsigned long long)(v - k.kmin);
+    const unsigned long long dd = (unsigned long long)v - (unsigned long long)k.kmin;
     if constexpr (!S::kremap(K)) {
-      *d = (uint32_t)dd;
+      *d = dd;
       return v >= k.kmin && dd < k.card;
     }
     if (v < k.kmin || dd >= 32ull * k.aux_len) return false;
@@ -249,7 +260,7 @@ __device__ __forceinline__ bool fast_digit(const QueryDesc& q, const TileView& t
 }
 
 // One aggregate's update of shared slot `slot` (or, when the table had no
-// free slot, of group gid's global accumulators).
+// free slot, of the global accumulators at index gid, see gindex).
 template <class S, int I>
 __device__ __forceinline__ void fast_update(const QueryDesc& q, const Smem& sm, int slot, uint32_t gid, long long v) {
   constexpr int kind = S::akind(I);
@@ -317,10 +328,11 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
     const uint32_t j = j0 + lane;
     bool act = j < n_pass;
     const uint32_t o = list[act ? j : j0];
-    uint32_t gid = 0;
+    // the packed key: 64-bit for a hash domain, else the 32-bit dense gid
+    typename Pick<S::ghash, unsigned long long, uint32_t>::type gid = 0;
     static_for<S::n_keys>([&](auto K) {
       constexpr int k = decltype(K)::value;
-      uint32_t d = 0;
+      unsigned long long d = 0;
       long long raw = 0;
       if (!fast_digit<S, k>(q, t, o, &d, &raw)) {
         if (act) {
@@ -329,7 +341,8 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
         }
         d = 0;
       }
-      gid += d * (uint32_t)q.keys[k].stride;
+      if constexpr (S::ghash) gid += d * q.keys[k].stride;
+      else gid += (uint32_t)d * (uint32_t)q.keys[k].stride;
     });
     long long val[S::n_aggs + 1];
     static_for<S::n_aggs>([&](auto A) {
@@ -373,19 +386,26 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
       });
     } else {
       int slot = -1;
+      uint32_t gi = 0;   // global accumulator index, used when the shared table has no slot
       if (act) {
         if constexpr (S::table_dense) slot = (int)gid;
-        else slot = table_slot(q, sm, gid);
-        if (slot >= 0) atomicAdd(scount(q, sm, slot), 1u);
-        else atomicAdd(gword(q, 0, gid), 1ull);
+        else slot = table_slot_t<S::ghash>(q, sm, gid);
+        if (slot >= 0) {
+          atomicAdd(scount(q, sm, slot), 1u);
+        } else {
+          const long long g = gindex_t<S::ghash>(q, gid);
+          if (g < 0) act = false;   // global hash table full: the host retries larger
+          gi = (uint32_t)g;
+          if (act) atomicAdd(gword(q, 0, gi), 1ull);
+        }
       }
       static_for<S::n_aggs>([&](auto A) {
         constexpr int i = decltype(A)::value;
         constexpr int kind = S::akind(i);
         if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
-          if (act) fast_update<S, i>(q, sm, slot, gid, val[i]);
+          if (act) fast_update<S, i>(q, sm, slot, gi, val[i]);
         } else if constexpr (kind != AK_COUNT) {
-          if (act) fast_index_update<S, i>(q, sm, t, slot, gid, o);
+          if (act) fast_index_update<S, i>(q, sm, t, slot, gi, o);
         }
       });
     }

@@ -43,7 +43,7 @@ struct Planned {
 
 // Byte offsets of one query's device buffers inside one allocation.
 struct QueryBlock {
-  uint64_t gacc, out, aux, err, cnt, blk, total;
+  uint64_t gacc, out, hkeys, hsort, aux, err, cnt, blk, total;
 };
 
 struct BatchGraph;   // cq_serve.cu
@@ -124,6 +124,8 @@ struct cq_result {
   std::vector<cq_column*> held_cols; // columns referenced until the result is destroyed
   std::shared_ptr<void> batch_keepalive;  // batch launches: shared device block and events
   bool own_events = true;          // false: the events belong to the batch
+  std::unique_ptr<cq::Planned> retry;  // hash-domain queries: the plan, relaunched when its table fills
+  uint32_t retries = 0;
 };
 
 namespace cq {
@@ -169,6 +171,10 @@ cudaError_t launch_row_jit(const void* fn, const QueryDesc& q, unsigned grid, in
 void row_shape(const QueryDesc& q, int* ncw, int* gpw, int* minb);
 cudaError_t launch_init_global(const QueryDesc& q, cudaStream_t s);
 cudaError_t launch_finalize(const QueryDesc& q, cudaStream_t s);
+cudaError_t launch_fold_sums(const QueryDesc& q, cudaStream_t s);
+// rows of one fused-kernel launch: longer queries are split so that no global
+// SUM limb word receives 2^31 or more additions between two folds
+constexpr uint64_t kLaunchRows = 1ull << 31;
 size_t query_kernel_smem(const QueryDesc& q);
 cudaError_t query_kernel_set_smem(size_t bytes);
 
@@ -181,6 +187,8 @@ cudaError_t launch_batch(BatchCtl* ctl_dev, cudaStream_t s, unsigned grid, int m
 
 // planner / results (cq_api.cu)
 int plan_batch_query(cq_table* table, const cq_plan* plan, uint32_t tile_rows, size_t smem_limit, Planned* P);
+int plan_solo_query(cq_table* table, const cq_plan* plan, Planned* P);
+int prepare_row_kernel(cq_ctx* ctx, Planned& P);
 QueryBlock query_block_layout(const Planned& P, bool with_aux);
 void bind_query_block(Planned& P, uint8_t* base, const QueryBlock& L, const uint32_t* aux_dev);
 void attach_outputs(cq_result* r, const Planned& P);

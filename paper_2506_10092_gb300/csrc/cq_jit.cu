@@ -83,9 +83,10 @@ static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) 
   snprintf(buf, sizeof(buf),
            "  static constexpr int tile_rows = %u, n_preds = %u, n_pbm = %u, n_keys = %u, n_aggs = %u;\n"
            "  static constexpr int n_cols = %u, n_bitmaps = %u, n_row_cols = %u, stage_bytes = %u;\n"
-           "  static constexpr bool one_group = %s, table_dense = %s;\n",
+           "  static constexpr bool one_group = %s, table_dense = %s, ghash = %s;\n",
            q.tile_rows, q.n_preds, q.n_pbm, q.n_keys, q.n_aggs, q.n_cols, q.n_bitmaps, q.n_row_cols, q.stage_bytes,
-           q.n_groups == 1 ? "true" : "false", q.table_dense ? "true" : "false");
+           (q.n_groups == 1 && !q.ghash) ? "true" : "false", q.table_dense ? "true" : "false",
+           q.ghash ? "true" : "false");
   s += buf;
   std::vector<long long> enc, v64, e64, bw, bslot, roff, soff, bcol(q.n_bitmaps, 0), rcol;
   for (int c = 0; c < q.n_cols; ++c) {
@@ -171,8 +172,8 @@ static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) 
            "extern \"C\" __global__ void __launch_bounds__(%d, %d) cq_row_jit(const __grid_constant__ cq::QueryDesc q) {\n",
            (ncw + nh) * 32, minb);
   s += buf;
-  s += "  const unsigned long long t_begin = (unsigned long long)blockIdx.x * q.n_tiles / gridDim.x;\n"
-       "  const unsigned long long t_end = (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;\n"
+  s += "  const unsigned long long t_begin = q.tile0 + (unsigned long long)blockIdx.x * q.n_tiles / gridDim.x;\n"
+       "  const unsigned long long t_end = q.tile0 + (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;\n"
        "  if (t_begin >= t_end) return;\n";
   snprintf(buf, sizeof(buf),
            "  cq::row_range<%d, %d, cq::FastBody<cq::JitShape>, %d>(q, cq::carve(q), t_begin, t_end);\n}\n", ncw, gpw,
@@ -284,8 +285,9 @@ cudaError_t launch_row_jit(const void* fn, const QueryDesc& q, unsigned grid, in
 }  // namespace cq
 
 namespace cq {
-// Two synthetic shapes that between them use every encoding, predicate kind,
-// key mapping and aggregate layout of the specialised body; only compiled.
+// Three synthetic shapes that between them use every encoding, predicate
+// kind, key mapping, aggregate layout and group domain (dense hash table,
+// global hash table, single group) of the specialised body; only compiled.
 static void check_shape(uint32_t variant, QueryDesc* q) {
   memset(q, 0, sizeof(*q));
   q->tile_rows = 8192;
@@ -327,7 +329,11 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
     agg(4, AK_COUNT, 0, 0, 0, 0, 0, 0, 0, 0, 0);
   } else {
     q->n_cols = 5; q->n_preds = 6; q->n_keys = 1; q->n_aggs = 7; q->n_bitmaps = 2; q->n_pbm = 1;
-    q->n_groups = 1; q->table_dense = 1; q->table_slots = 1;
+    if (variant == 1) {
+      q->n_groups = 1u << 20; q->table_dense = 0; q->table_slots = 512; q->ghash = 1;
+    } else {
+      q->n_groups = 1; q->table_dense = 1; q->table_slots = 1;
+    }
     col(0, ENC_RLE, 1, 0, 0, 0, 0);
     col(1, ENC_INDEX, 1, 0, 1, 0, 0);
     col(2, ENC_PLAIN, 1, 0, 0xFF, 0, 0);
@@ -355,7 +361,7 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
 // run-time compilation that needs no GPU.  *seconds receives the compile time.
 extern "C" int cq_jit_check(uint32_t variant, double* seconds) {
   cq::clear_error();
-  if (variant > 1) return cq::set_error(CQ_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (variant > 2) return cq::set_error(CQ_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
   cq::QueryDesc q;
   cq::check_shape(variant, &q);
   cq::JitKernel k;

@@ -41,7 +41,7 @@ __host__ __device__ inline SmemLayout smem_layout(const QueryDesc& q) {
   off += 8u * (q.seg_mode ? 0u : q.stages);
   off = align_up(off, 16);
   L.tkeys = off;
-  off += q.table_dense ? 0u : 4u * q.table_slots;
+  off += q.table_dense ? 0u : (q.ghash ? 8u : 4u) * q.table_slots;
   off = align_up(off, 16);
   L.tacc = off;
   off += 8u * q.n_sw * q.table_slots;
@@ -59,8 +59,8 @@ __host__ __device__ inline SmemLayout smem_layout(const QueryDesc& q) {
   off += 8u * kMaxBitmapCols * nbuf;
   // row mode: per window buffer and bitmap column, kWin run ends / positions
   // followed by the kWin values of the same runs / listed rows
-  L.win = off;
-  off += q.seg_mode ? 0u : 16u * kWin * nb * kWinBufs;
+  L.win = off;   // segment mode: the next boundary of each bitmap column (long-segment test)
+  off += q.seg_mode ? 8u * kMaxBitmapCols : 16u * kWin * nb * kWinBufs;
   L.wcnt = off;
   off += 4u * kMaxBitmapCols * kWinBufs;
   L.ubm = off;
@@ -87,7 +87,8 @@ __host__ __device__ inline SmemLayout smem_layout(const QueryDesc& q) {
 struct Smem {
   uint8_t* stage;
   uint64_t* mbar;
-  uint32_t* tkeys;
+  uint32_t* tkeys;                 // shared-table keys: 32-bit dense gids ...
+  unsigned long long* tkeys64;     // ... or 64-bit packed keys (global hash table), same words
   unsigned long long* tacc;
   unsigned* tacc32;
   uint32_t* bm;
@@ -113,6 +114,7 @@ __device__ __forceinline__ Smem carve(const QueryDesc& q) {
   s.stage = g_smem + L.stage;
   s.mbar = reinterpret_cast<uint64_t*>(g_smem + L.mbar);
   s.tkeys = reinterpret_cast<uint32_t*>(g_smem + L.tkeys);
+  s.tkeys64 = reinterpret_cast<unsigned long long*>(g_smem + L.tkeys);
   s.tacc = reinterpret_cast<unsigned long long*>(g_smem + L.tacc);
   s.tacc32 = reinterpret_cast<unsigned*>(g_smem + L.tacc32);
   s.bm = reinterpret_cast<uint32_t*>(g_smem + L.bm);
@@ -309,11 +311,12 @@ __device__ __forceinline__ bool pred_test32(const PredDesc& p, const uint32_t* a
 }
 
 // digit of key k for raw value v; false when v is outside the key's domain
-__device__ __forceinline__ bool key_digit(const KeyDesc& k, const uint32_t* aux, long long v, uint32_t* digit) {
-  const unsigned long long d = (unsigned long long)(v - k.kmin);
+__device__ __forceinline__ bool key_digit(const KeyDesc& k, const uint32_t* aux, long long v,
+                                          unsigned long long* digit) {
+  const unsigned long long d = (unsigned long long)v - (unsigned long long)k.kmin;
   if (!k.remap) {
     if (v < k.kmin || d >= k.card) return false;
-    *digit = (uint32_t)d;
+    *digit = d;
     return true;
   }
   if (v < k.kmin || d >= 32ull * k.aux_len) return false;
@@ -337,7 +340,7 @@ __device__ __forceinline__ bool pred_eval(const PredDesc& p, const uint32_t* aux
 
 // key_digit for a key whose raw values are read in 32 bits and whose kmin
 // lies within +-2^30 (so v - kmin cannot wrap into the digit range).
-__device__ __forceinline__ bool key_digit32(const KeyDesc& k, const uint32_t* aux, int v, uint32_t* digit) {
+__device__ __forceinline__ bool key_digit32(const KeyDesc& k, const uint32_t* aux, int v, unsigned long long* digit) {
   const uint32_t d = (uint32_t)v - (uint32_t)(int)k.kmin;
   if (!k.remap) {
     if (d >= k.card) return false;
@@ -349,6 +352,14 @@ __device__ __forceinline__ bool key_digit32(const KeyDesc& k, const uint32_t* au
   if (!((w >> (d & 31)) & 1u)) return false;
   *digit = aux[k.prefix_off + (d >> 5)] + __popc(w & ((1u << (d & 31)) - 1u));
   return true;
+}
+
+// The column whose bitmap slot is j.
+__device__ __forceinline__ const ColDesc& bitmap_col(const QueryDesc& q, int j) {
+  int idx = 0;
+  for (int c = 0; c < q.n_cols; ++c)
+    if (q.cols[c].bslot == j) idx = c;
+  return q.cols[idx];
 }
 
 // First device error wins; its detail (what, where, value) is kept for the host.
@@ -372,25 +383,83 @@ __device__ __forceinline__ uint32_t hash_gid(uint32_t g, uint32_t log2_slots) {
 }
 
 // Shared-memory slot of gid, or -1 when the probe limit is hit (caller then
-// updates the global accumulators directly).
-__device__ __forceinline__ int table_slot(const QueryDesc& q, const Smem& sm, uint32_t gid) {
+// updates the global accumulators directly).  Dense domains key the table by
+// the 32-bit gid, hash domains by the 64-bit packed key.
+template <bool GH>
+__device__ __forceinline__ int table_slot_t(const QueryDesc& q, const Smem& sm, unsigned long long gid) {
   if (q.table_dense) return (int)gid;
   const uint32_t mask = q.table_slots - 1;
-  uint32_t h = hash_gid(gid, 31 - __clz(q.table_slots)) & mask;
+  const uint32_t lg = 31 - __clz(q.table_slots);
+  if constexpr (GH) {
+    uint32_t h = (uint32_t)((gid * 0x9E3779B97F4A7C15ull) >> (64 - lg)) & mask;
+    for (int probe = 0; probe < 32; ++probe) {
+      unsigned long long k = sm.tkeys64[h];
+      if (k == gid) return (int)h;
+      if (k == kEmptyGroup) {
+        k = atomicCAS(&sm.tkeys64[h], kEmptyGroup, gid);
+        if (k == kEmptyGroup) {
+          atomicAdd(&sm.misc[0], 1);
+          return (int)h;
+        }
+        if (k == gid) return (int)h;
+      }
+      h = (h + 1) & mask;
+    }
+    return -1;
+  }
+  const uint32_t g = (uint32_t)gid;
+  uint32_t h = hash_gid(g, lg) & mask;
   for (int probe = 0; probe < 32; ++probe) {
     uint32_t k = sm.tkeys[h];
-    if (k == gid) return (int)h;
+    if (k == g) return (int)h;
     if (k == kEmptyKey) {
-      k = atomicCAS(&sm.tkeys[h], kEmptyKey, gid);
+      k = atomicCAS(&sm.tkeys[h], kEmptyKey, g);
       if (k == kEmptyKey) {
         atomicAdd(&sm.misc[0], 1);
         return (int)h;
       }
-      if (k == gid) return (int)h;
+      if (k == g) return (int)h;
     }
     h = (h + 1) & mask;
   }
   return -1;
+}
+
+// Index of group gid in the global accumulators: the gid itself in a dense
+// domain; in a hash domain the slot of its packed key in the open-addressing
+// key table (linear probing from a multiplicative hash, inserting the key;
+// keys are never removed).  After kGlobalProbes occupied slots the query
+// fails with CQ_ERR_TABLE_FULL (the host then retries with a larger table)
+// and -1 is returned: the caller skips the update.
+template <bool GH>
+__device__ __forceinline__ long long gindex_t(const QueryDesc& q, unsigned long long gid) {
+  if constexpr (!GH) return (long long)gid;
+  const unsigned long long mask = q.n_groups - 1;
+  const uint32_t lg = 63 - __clzll((long long)q.n_groups);
+  unsigned long long h = lg ? ((gid * 0x9E3779B97F4A7C15ull) >> (64 - lg)) & mask : 0ull;
+  for (int probe = 0; probe < kGlobalProbes; ++probe) {
+    unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&q.gkeys[h]);
+    if (k == gid) return (long long)h;
+    if (k == kEmptyGroup) {
+      k = atomicCAS(&q.gkeys[h], kEmptyGroup, gid);
+      if (k == kEmptyGroup || k == gid) return (long long)h;
+    }
+    h = (h + 1) & mask;
+  }
+  if (atomicCAS(q.err, 0, (int)CQ_ERR_TABLE_FULL) == 0) {
+    q.err_info[0] = 4;
+    q.err_info[1] = q.n_groups;
+    q.err_info[2] = gid;
+  }
+  return -1;
+}
+
+// (the descriptor's domain kind read at run time)
+__device__ __forceinline__ int table_slot(const QueryDesc& q, const Smem& sm, unsigned long long gid) {
+  return q.ghash ? table_slot_t<true>(q, sm, gid) : table_slot_t<false>(q, sm, gid);
+}
+__device__ __forceinline__ long long gindex(const QueryDesc& q, unsigned long long gid) {
+  return q.ghash ? gindex_t<true>(q, gid) : (long long)gid;
 }
 
 __device__ __forceinline__ unsigned long long* gword(const QueryDesc& q, uint32_t w, uint32_t gid) {
@@ -435,20 +504,20 @@ __device__ __forceinline__ void smem_add64(unsigned long long* w, long long x) {
 }
 
 // Add a 128-bit contribution to a SUM accumulator in shared memory (slot >= 0)
-// or straight into the global limbs.
-__device__ __forceinline__ void sum_add(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot, uint32_t gid,
+// or straight into the global limbs of global index gi (see gindex).
+__device__ __forceinline__ void sum_add(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot, uint32_t gi,
                                         I128 x) {
   if (slot >= 0) {
     if (a.s32) atomicAdd(reinterpret_cast<unsigned*>(sword32(q, sm, a.sw32, slot)), (unsigned)x.lo);
     else if (!a.wide) smem_add64(sword(q, sm, a.sw, slot), (long long)x.lo);
     else atomic_add_i128(sword(q, sm, a.sw, slot), sword(q, sm, a.sw + 1, slot), x);
   } else {
-    global_add_limbs(gword(q, a.gw, gid), gword(q, a.gw + 1, gid), gword(q, a.gw + 2, gid), x);
+    global_add_limbs(gword(q, a.gw, gi), gword(q, a.gw + 1, gi), gword(q, a.gw + 2, gi), x);
   }
 }
 
 __device__ __forceinline__ void minmax_add(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot,
-                                           uint32_t gid, long long v, bool is_min) {
+                                           uint32_t gi, long long v, bool is_min) {
   if (slot >= 0) {
     // read first: most values do not improve the extreme, and a plain read
     // is cheaper than an atomic (a stale read only costs an extra atomic)
@@ -468,8 +537,8 @@ __device__ __forceinline__ void minmax_add(const QueryDesc& q, const Smem& sm, c
       }
     }
   } else {
-    if (is_min) atomicMin(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
-    else atomicMax(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
+    if (is_min) atomicMin(reinterpret_cast<long long*>(gword(q, a.gw, gi)), v);
+    else atomicMax(reinterpret_cast<long long*>(gword(q, a.gw, gi)), v);
   }
 }
 
@@ -501,7 +570,10 @@ __device__ __forceinline__ void reset_slot(const QueryDesc& q, const Smem& sm, u
         break;
     }
   }
-  if (!q.table_dense) sm.tkeys[s] = kEmptyKey;
+  if (!q.table_dense) {
+    if (q.ghash) sm.tkeys64[s] = kEmptyGroup;
+    else sm.tkeys[s] = kEmptyKey;
+  }
 }
 
 // Add every occupied slot into the global accumulators and clear the table.
@@ -510,10 +582,18 @@ __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
   for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
     const unsigned cnt = *scount(q, sm, s);
     if (cnt == 0) {
-      if (!q.table_dense) sm.tkeys[s] = kEmptyKey;
+      if (!q.table_dense) {
+        if (q.ghash) sm.tkeys64[s] = kEmptyGroup;
+        else sm.tkeys[s] = kEmptyKey;
+      }
       continue;
     }
-    const uint32_t gid = q.table_dense ? s : sm.tkeys[s];
+    const long long g = q.table_dense ? (long long)s : (q.ghash ? gindex(q, sm.tkeys64[s]) : (long long)sm.tkeys[s]);
+    if (g < 0) {   // global hash table full: the query fails, the host retries larger
+      reset_slot(q, sm, s);
+      continue;
+    }
+    const uint32_t gid = (uint32_t)g;
     atomicAdd(gword(q, 0, gid), (unsigned long long)cnt);
     for (int i = 0; i < q.n_aggs; ++i) {
       const AggDesc& a = q.aggs[i];
@@ -648,9 +728,9 @@ __device__ __forceinline__ uint32_t compact(uint32_t pm, uint32_t wbase, uint32_
 // Row mode items are single rows (len 1); segment items weigh by length.
 template <bool SEG>
 __device__ __forceinline__ void agg_item(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot,
-                                         uint32_t gid, long long v, uint32_t len) {
-  if (a.kind == AK_SUM) sum_add(q, sm, a, slot, gid, SEG ? mul_s64(v, (long long)len) : sext(v));
-  else minmax_add(q, sm, a, slot, gid, v, a.kind == AK_MIN);
+                                         uint32_t gi, long long v, uint32_t len) {
+  if (a.kind == AK_SUM) sum_add(q, sm, a, slot, gi, SEG ? mul_s64(v, (long long)len) : sext(v));
+  else minmax_add(q, sm, a, slot, gi, v, a.kind == AK_MIN);
 }
 
 // Aggregate: passing items in batches of 32 * MI per warp, MI per lane.  Keys,
@@ -667,7 +747,8 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
   const int lane = threadIdx.x & 31;
   const bool one_group = q.n_groups == 1;
   for (uint32_t j0 = 0; j0 < n_pass; j0 += 32 * MI) {
-    uint32_t o[MI], len[MI], gid[MI];
+    uint32_t o[MI], len[MI], gi[MI];
+    unsigned long long gid[MI];
     int slot[MI];
     bool act[MI];
 #pragma unroll
@@ -683,6 +764,7 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
         len[m] = act[m] ? 1u : 0u;
       }
       gid[m] = 0;
+      gi[m] = 0;
       slot[m] = -1;
     }
     // ---- group ids
@@ -695,9 +777,9 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
 #pragma unroll
           for (int m = 0; m < MI; ++m) {
             const int v = col_raw32<E>(c, t, o[m]);
-            uint32_t d;
+            unsigned long long d;
             if (key_digit32(k, t.aux, v, &d)) {
-              gid[m] += d * (uint32_t)k.stride;
+              gid[m] += d * k.stride;
             } else if (act[m]) {
               act[m] = false;
               report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)ki << 8), tile_row0 + o[m],
@@ -709,9 +791,9 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
 #pragma unroll
         for (int m = 0; m < MI; ++m) {
           const long long v = col_raw<E>(c, t, o[m]);
-          uint32_t d;
+          unsigned long long d;
           if (key_digit(k, t.aux, v, &d)) {
-            gid[m] += d * (uint32_t)k.stride;
+            gid[m] += d * k.stride;
           } else if (act[m]) {
             act[m] = false;
             report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)ki << 8), tile_row0 + o[m], (unsigned long long)v);
@@ -733,8 +815,17 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
       for (int m = 0; m < MI; ++m) {
         if (!act[m]) continue;
         slot[m] = table_slot(q, sm, gid[m]);
-        if (slot[m] >= 0) atomicAdd(scount(q, sm, slot[m]), len[m]);
-        else atomicAdd(gword(q, 0, gid[m]), (unsigned long long)len[m]);
+        if (slot[m] >= 0) {
+          atomicAdd(scount(q, sm, slot[m]), len[m]);
+        } else {
+          const long long g = gindex(q, gid[m]);
+          if (g < 0) {
+            act[m] = false;
+            continue;
+          }
+          gi[m] = (uint32_t)g;
+          atomicAdd(gword(q, 0, gi[m]), (unsigned long long)len[m]);
+        }
       }
     }
     // ---- aggregates
@@ -754,11 +845,11 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
           long long v;
           if (act[m] && index_lookup(c, t, o[m], &v)) {
             if (a.kind == AK_ISUM) {
-              sum_add(q, sm, a, slot[m], gid[m], index_delta(v, a.base));
+              sum_add(q, sm, a, slot[m], gi[m], index_delta(v, a.base));
             } else {
-              minmax_add(q, sm, a, slot[m], gid[m], v, a.kind == AK_IMIN);
+              minmax_add(q, sm, a, slot[m], gi[m], v, a.kind == AK_IMIN);
               if (slot[m] >= 0) atomicAdd(slisted(q, sm, a, slot[m]), 1u);
-              else atomicAdd(gword(q, a.gw + 1, gid[m]), 1ull);
+              else atomicAdd(gword(q, a.gw + 1, gi[m]), 1ull);
             }
           }
         }
@@ -805,7 +896,7 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
       }
 #pragma unroll
       for (int m = 0; m < MI; ++m)
-        if (act[m]) agg_item<SEG>(q, sm, a, slot[m], gid[m], val[m], len[m]);
+        if (act[m]) agg_item<SEG>(q, sm, a, slot[m], gi[m], val[m], len[m]);
     }
   }
 }

@@ -29,8 +29,8 @@ size_t query_kernel_smem(const QueryDesc& q) { return smem_layout(q).total; }
 // CTA walks one contiguous range of tiles.
 template <int GPW, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) seg_query_kernel(const __grid_constant__ QueryDesc q) {
-  const unsigned long long t_begin = (unsigned long long)blockIdx.x * q.n_tiles / gridDim.x;
-  const unsigned long long t_end = (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;
+  const unsigned long long t_begin = q.tile0 + (unsigned long long)blockIdx.x * q.n_tiles / gridDim.x;
+  const unsigned long long t_end = q.tile0 + (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;
   if (t_begin >= t_end) return;
   seg_range<GPW>(q, carve(q), t_begin, t_end);
 }
@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kThreads, MINB) seg_query_kernel(const __grid_
 __device__ __forceinline__ void init_group(const QueryDesc& q, size_t i) {
   const size_t G = q.n_groups;
   q.gacc[i] = 0;
+  if (q.ghash) q.gkeys[i] = kEmptyGroup;
   for (int ai = 0; ai < q.n_aggs; ++ai) {
     const AggDesc& a = q.aggs[ai];
     switch (a.kind) {
@@ -65,6 +66,35 @@ __device__ __forceinline__ void init_group(const QueryDesc& q, size_t i) {
   }
 }
 
+// Carry the upper halves of a SUM's two 32-bit limb words into the next word
+// (w0 + w1 * 2^32 + w2 * 2^64 is unchanged).  Run between the launches of a
+// query split by rows, it keeps every word below 2^63 whatever the row count:
+// each launch adds fewer than 2^31 limbs (each below 2^32) to a word.
+__global__ void fold_sums_kernel(const __grid_constant__ QueryDesc q) {
+  const size_t G = q.n_groups;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < G; i += (size_t)gridDim.x * blockDim.x) {
+    for (int ai = 0; ai < q.n_aggs; ++ai) {
+      const AggDesc& a = q.aggs[ai];
+      if (a.kind != AK_SUM && a.kind != AK_ISUM) continue;
+      unsigned long long* w0 = &q.gacc[(size_t)a.gw * G + i];
+      unsigned long long* w1 = &q.gacc[(size_t)(a.gw + 1) * G + i];
+      unsigned long long* w2 = &q.gacc[(size_t)(a.gw + 2) * G + i];
+      const unsigned long long c0 = *w0 >> 32;
+      *w0 &= 0xFFFFFFFFull;
+      const unsigned long long v1 = *w1 + c0;
+      *w1 = v1 & 0xFFFFFFFFull;
+      *w2 += v1 >> 32;
+    }
+  }
+}
+
+cudaError_t launch_fold_sums(const QueryDesc& q, cudaStream_t s) {
+  const unsigned long long nblk = (q.n_groups + 255) / 256;
+  const unsigned blocks = (unsigned)(nblk < 4096ull ? nblk : 4096ull);
+  fold_sums_kernel<<<blocks ? blocks : 1, 256, 0, s>>>(q);
+  return cudaGetLastError();
+}
+
 __global__ void init_global_kernel(const __grid_constant__ QueryDesc q) {
   const size_t G = q.n_groups;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < G; i += (size_t)gridDim.x * blockDim.x)
@@ -78,6 +108,7 @@ __global__ void init_global_kernel(const __grid_constant__ QueryDesc q) {
 constexpr int kFinBlock = 1024;
 
 __device__ __forceinline__ bool group_present(const QueryDesc& q, size_t g) {
+  if (q.ghash) return q.gkeys[g] != kEmptyGroup;
   return q.gacc[g] != 0 || (q.n_keys == 0 && g == 0);
 }
 
@@ -151,32 +182,15 @@ __device__ __forceinline__ I128 add128(I128 a, I128 b) {
   return r;
 }
 
-__device__ __forceinline__ void fin_write_block(const QueryDesc& q, unsigned blk) {
-  __shared__ unsigned warp_cnt[kFinBlock / 32];
-  const size_t g = blk * (size_t)kFinBlock + threadIdx.x;
-  const bool p = g < q.n_groups && group_present(q, g);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned bal = __ballot_sync(0xFFFFFFFFu, p);
-  if (lane == 0) warp_cnt[warp] = __popc(bal);
-  __syncthreads();
-  if (warp == 0) {
-    const unsigned x = warp_cnt[lane];
-    unsigned incl = x;
-    for (int d = 1; d < 32; d <<= 1) {
-      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-      if (lane >= d) incl += y;
-    }
-    warp_cnt[lane] = incl - x;
-  }
-  __syncthreads();
-  if (!p) return;
-  const size_t row = q.block_counts[blk] + warp_cnt[warp] + __popc(bal & ((1u << lane) - 1u));
+// Result row `row` of the group with packed key `key` whose accumulators sit
+// at index g (dense domains: key == g).
+__device__ __forceinline__ void write_group(const QueryDesc& q, size_t row, unsigned long long key, size_t g) {
   const unsigned long long cnt = q.gacc[g];
   for (uint32_t oc = 0; oc < q.n_out; ++oc) {
     const uint32_t idx = q.out_index[oc];
     if (q.out_is_key[oc]) {
       const KeyDesc& k = q.keys[idx];
-      const uint32_t digit = (uint32_t)((g / k.stride) % k.card);
+      const unsigned long long digit = (key / k.stride) % k.card;
       long long raw;
       if (k.remap) {
         raw = reinterpret_cast<const long long*>(q.aux + k.list_off)[digit];
@@ -232,7 +246,180 @@ __device__ __forceinline__ void fin_write_block(const QueryDesc& q, unsigned blk
   }
 }
 
+
+__device__ __forceinline__ void fin_write_block(const QueryDesc& q, unsigned blk) {
+  __shared__ unsigned warp_cnt[kFinBlock / 32];
+  const size_t g = blk * (size_t)kFinBlock + threadIdx.x;
+  const bool p = g < q.n_groups && group_present(q, g);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned bal = __ballot_sync(0xFFFFFFFFu, p);
+  if (lane == 0) warp_cnt[warp] = __popc(bal);
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned x = warp_cnt[lane];
+    unsigned incl = x;
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    warp_cnt[lane] = incl - x;
+  }
+  __syncthreads();
+  if (!p) return;
+  const size_t row = q.block_counts[blk] + warp_cnt[warp] + __popc(bal & ((1u << lane) - 1u));
+  write_group(q, row, g, g);
+}
+
 __global__ void finalize_write_kernel(const __grid_constant__ QueryDesc q) { fin_write_block(q, blockIdx.x); }
+
+// ------------------------------------------------------------------ hash-domain finalize
+// Groups of a hash domain sit in the slots of an open-addressing table, in no
+// order.  Finalize compacts the occupied slots into (packed key, slot) pairs,
+// sorts them by key with a stable least-significant-digit radix sort (8-bit
+// digits, as many passes as the packed key has bytes; the packed key orders
+// like the key tuple), then writes row r from the r-th pair.
+
+// (key, slot) of the occupied slots of block blk at their compacted rows.
+__global__ void __launch_bounds__(kFinBlock) hfin_compact_kernel(const __grid_constant__ QueryDesc q) {
+  __shared__ unsigned warp_cnt[kFinBlock / 32];
+  const size_t g = blockIdx.x * (size_t)kFinBlock + threadIdx.x;
+  const bool p = g < q.n_groups && q.gkeys[g] != kEmptyGroup;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned bal = __ballot_sync(0xFFFFFFFFu, p);
+  if (lane == 0) warp_cnt[warp] = __popc(bal);
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned x = warp_cnt[lane];
+    unsigned incl = x;
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    warp_cnt[lane] = incl - x;
+  }
+  __syncthreads();
+  if (!p) return;
+  const size_t row = q.block_counts[blockIdx.x] + warp_cnt[warp] + __popc(bal & ((1u << lane) - 1u));
+  q.skeys[0][row] = q.gkeys[g];
+  q.svals[0][row] = (uint32_t)g;
+}
+
+constexpr int kSortThreads = 256;   // one element per thread per tile; 8 warps
+
+// Elements [b0, b1) of sort block b out of n (tiles of kSortThreads).
+__device__ __forceinline__ void sort_chunk(uint32_t n, uint32_t* b0, uint32_t* b1) {
+  const uint32_t nb = gridDim.x;
+  const uint32_t chunk = ((n + nb - 1) / nb + kSortThreads - 1) / kSortThreads * kSortThreads;
+  const unsigned long long lo = (unsigned long long)blockIdx.x * chunk;
+  *b0 = lo < n ? (uint32_t)lo : n;
+  *b1 = lo + chunk < n ? (uint32_t)(lo + chunk) : n;
+}
+
+// Digit counts of this block's chunk: shist[digit * blocks + block].
+__global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const __grid_constant__ QueryDesc q, int pass) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t n = (uint32_t)*q.out_count;
+  uint32_t b0, b1;
+  sort_chunk(n, &b0, &b1);
+  const unsigned long long* k = q.skeys[pass & 1];
+  for (uint32_t i = b0 + threadIdx.x; i < b1; i += kSortThreads) atomicAdd(&h[(k[i] >> (8 * pass)) & 255u], 1u);
+  __syncthreads();
+  q.shist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of a[0, n) in place (one block).
+__global__ void __launch_bounds__(1024) scan_u32_kernel(uint32_t* a, uint32_t n) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t base = 0; base < n; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < n ? a[i] : 0u;
+    uint32_t incl = v;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t x = lane < (int)(blockDim.x / 32) ? warp_tot[lane] : 0u;
+      uint32_t wi = x;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, d);
+        if (lane >= d) wi += y;
+      }
+      warp_tot[lane] = wi - x;
+    }
+    __syncthreads();
+    const uint32_t c0 = carry;
+    if (i < n) a[i] = c0 + warp_tot[warp] + incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = c0 + warp_tot[warp] + incl;
+    __syncthreads();
+  }
+}
+
+// Stable scatter of this block's chunk by digit `pass`: tiles in order,
+// warps of a tile in order, lanes of a warp in order.
+__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const __grid_constant__ QueryDesc q, int pass) {
+  constexpr int kW = kSortThreads / 32;
+  __shared__ uint32_t base[256];
+  __shared__ uint32_t tile_tot[256];
+  __shared__ uint32_t wcnt[kW][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t n = (uint32_t)*q.out_count;
+  uint32_t b0, b1;
+  sort_chunk(n, &b0, &b1);
+  const unsigned long long* kin = q.skeys[pass & 1];
+  const uint32_t* vin = q.svals[pass & 1];
+  unsigned long long* kout = q.skeys[(pass & 1) ^ 1];
+  uint32_t* vout = q.svals[(pass & 1) ^ 1];
+  base[threadIdx.x] = q.shist[threadIdx.x * gridDim.x + blockIdx.x];
+  for (uint32_t i0 = b0; i0 < b1; i0 += kSortThreads) {
+    for (int w = 0; w < kW; ++w) wcnt[w][threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t i = i0 + threadIdx.x;
+    const bool valid = i < b1;
+    const unsigned long long key = valid ? kin[i] : 0ull;
+    const uint32_t val = valid ? vin[i] : 0u;
+    const uint32_t d = valid ? (uint32_t)((key >> (8 * pass)) & 255u) : 256u + (uint32_t)lane;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t run = 0;
+      for (int w = 0; w < kW; ++w) {
+        const uint32_t c = wcnt[w][threadIdx.x];
+        wcnt[w][threadIdx.x] = run;
+        run += c;
+      }
+      tile_tot[threadIdx.x] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = base[d] + wcnt[warp][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    base[threadIdx.x] += tile_tot[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// Row r from the r-th sorted pair (grid-stride).
+__global__ void hfin_write_kernel(const __grid_constant__ QueryDesc q, int buf) {
+  const unsigned long long n = *q.out_count;
+  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < n;
+       r += (unsigned long long)gridDim.x * blockDim.x)
+    write_group(q, (size_t)r, q.skeys[buf][r], (size_t)q.svals[buf][r]);
+}
 
 // ------------------------------------------------------------------ batched init / finalize
 // The same steps over every query of a batch: blocks of all queries are
@@ -363,7 +550,18 @@ cudaError_t launch_finalize(const QueryDesc& q, cudaStream_t s) {
   const unsigned nb = (unsigned)((q.n_groups + kFinBlock - 1) / kFinBlock);
   finalize_count_kernel<<<nb, kFinBlock, 0, s>>>(q);
   finalize_scan_kernel<<<1, 1024, 0, s>>>(q, nb);
-  finalize_write_kernel<<<nb, kFinBlock, 0, s>>>(q);
+  if (!q.ghash) {
+    finalize_write_kernel<<<nb, kFinBlock, 0, s>>>(q);
+    return cudaGetLastError();
+  }
+  hfin_compact_kernel<<<nb, kFinBlock, 0, s>>>(q);
+  const int passes = (q.key_bits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    sort_hist_kernel<<<q.sort_blocks, kSortThreads, 0, s>>>(q, p);
+    scan_u32_kernel<<<1, 1024, 0, s>>>(q.shist, 256u * q.sort_blocks);
+    sort_scatter_kernel<<<q.sort_blocks, kSortThreads, 0, s>>>(q, p);
+  }
+  hfin_write_kernel<<<q.sort_blocks, 256, 0, s>>>(q, passes & 1);
   return cudaGetLastError();
 }
 

@@ -22,8 +22,8 @@ namespace cq {
 
 template <int NCW, int GPW, int MINB>
 __global__ void __launch_bounds__((NCW + 1) * 32, MINB) row_query_kernel(const __grid_constant__ QueryDesc q) {
-  const unsigned long long t_begin = (unsigned long long)blockIdx.x * q.n_tiles / gridDim.x;
-  const unsigned long long t_end = (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;
+  const unsigned long long t_begin = q.tile0 + (unsigned long long)blockIdx.x * q.n_tiles / gridDim.x;
+  const unsigned long long t_end = q.tile0 + (unsigned long long)(blockIdx.x + 1) * q.n_tiles / gridDim.x;
   if (t_begin >= t_end) return;
   row_range<NCW, GPW>(q, carve(q), t_begin, t_end);
 }

@@ -23,13 +23,6 @@ __device__ __forceinline__ unsigned long long* helper_cursor(const Smem& sm) {
   return reinterpret_cast<unsigned long long*>(sm.flags);
 }
 
-__device__ __forceinline__ const ColDesc& bitmap_col(const QueryDesc& q, int j) {
-  int idx = 0;
-  for (int c = 0; c < q.n_cols; ++c)
-    if (q.cols[c].bslot == j) idx = c;
-  return q.cols[idx];
-}
-
 // Window set `wb`: per bitmap column kWin run ends / positions, then the
 // values of the same runs / listed rows.
 __device__ __forceinline__ uint8_t* window_set(const QueryDesc& q, const Smem& sm, int wb) {

@@ -167,6 +167,49 @@ __device__ inline void build_segments(const QueryDesc& q, const Smem& sm, uint32
   __syncthreads();
 }
 
+// One aligned segment of L rows starting at row s over which every column is
+// constant: each RLE column holds the run at its cursor, each index column its
+// default (no listed row inside).  Filter and aggregate it once: COUNT += L,
+// SUM += value x L, MIN / MAX on the value (Section 7; the rows need no
+// bitmaps).  One thread.
+__device__ inline void seg_span_update(const QueryDesc& q, const Smem& sm, const uint32_t* aux, unsigned long long s,
+                                       unsigned long long L) {
+  auto value = [&](const ColDesc& c) -> long long {
+    if (c.enc == ENC_RLE) return ldg_val(c.vals, sm.tcur[c.bslot], c.v64);
+    return c.base;   // index column, unlisted rows
+  };
+  for (int i = 0; i < q.n_preds; ++i)
+    if (!pred_eval(q.preds[i], aux, value(q.cols[q.preds[i].col]))) return;
+  unsigned long long gid = 0;
+  for (int ki = 0; ki < q.n_keys; ++ki) {
+    const KeyDesc& k = q.keys[ki];
+    const long long v = value(q.cols[k.col]);
+    unsigned long long d;
+    if (!key_digit(k, aux, v, &d)) {
+      report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)ki << 8), s, (unsigned long long)v);
+      return;
+    }
+    gid += d * k.stride;
+  }
+  int slot = q.n_groups == 1 && !q.ghash ? 0 : table_slot(q, sm, gid);
+  uint32_t gi = 0;
+  if (slot >= 0) {
+    atomicAdd(scount(q, sm, slot), (unsigned)L);
+  } else {
+    const long long g = gindex(q, gid);
+    if (g < 0) return;
+    gi = (uint32_t)g;
+    atomicAdd(gword(q, 0, gi), L);
+  }
+  for (int ai = 0; ai < q.n_aggs; ++ai) {
+    const AggDesc& a = q.aggs[ai];
+    // index-column aggregates see no listed row here; finalize adds the
+    // default from COUNT
+    if (a.kind == AK_SUM) sum_add(q, sm, a, slot, gi, mul_s64(value(q.cols[a.col]), (long long)L));
+    else if (a.kind == AK_MIN || a.kind == AK_MAX) minmax_add(q, sm, a, slot, gi, value(q.cols[a.col]), a.kind == AK_MIN);
+  }
+}
+
 // Walk tiles [t_begin, t_end) of one segment-mode query: reset the group
 // table, then per tile build the bitmaps and segments, filter, aggregate,
 // and flush the table when it fills and after the last tile.  kWarps warps
@@ -210,8 +253,51 @@ __device__ __forceinline__ void seg_range(const QueryDesc& q, const Smem& sm, un
   uint16_t* mylist = sm.clist + (warp < kWarps ? warp : 0) * (GPW * 32);
   const uint32_t wbase = warp * 32, gstride = kWarps * 32;
 
+  unsigned long long* nextb = reinterpret_cast<unsigned long long*>(sm.win);
+  const unsigned long long end_row = t_end * T < q.n_rows ? t_end * T : q.n_rows;
   for (unsigned long long t = t_begin; t < t_end; ++t) {
     const unsigned long long s = t * T;
+    // ---- long segments: when no column has a boundary before the end of
+    // this tile, the rows up to the first boundary of any column form one
+    // aligned segment.  It is aggregated once and its tiles are skipped, so
+    // the walk costs follow the runs rather than the rows (at most one flush
+    // period per span, so the shared accumulators keep their bounds).
+    if (threadIdx.x < q.n_bitmaps) {
+      const int j = threadIdx.x;
+      const ColDesc& cd = bitmap_col(q, j);
+      const unsigned long long cur = sm.tcur[j];
+      nextb[j] = cur < cd.n ? (unsigned long long)ldg_val(cd.ends, cur, cd.e64) : ~0ull;
+    }
+    __syncthreads();
+    {
+      unsigned long long m = ~0ull;
+      for (int j = 0; j < q.n_bitmaps; ++j) m = nextb[j] < m ? nextb[j] : m;
+      unsigned long long span_end = m < end_row ? m : end_row;
+      const unsigned long long cap = s + (q.flush_rows - rows_since_flush);
+      if (span_end > cap) span_end = cap;
+      if (span_end >= s + T || (span_end == end_row && span_end > s)) {
+        if (span_end != end_row) span_end = span_end / T * T;
+        const unsigned long long L = span_end - s;
+        if (threadIdx.x == 0) seg_span_update(q, sm, tv.aux, s, L);
+        __syncthreads();
+        if (threadIdx.x < q.n_bitmaps) {
+          const int j = threadIdx.x;
+          if (bitmap_col(q, j).enc == ENC_RLE && nextb[j] == span_end) sm.tcur[j] += 1;   // that run ended here
+        }
+        rows_since_flush += (uint32_t)L;
+        t = (span_end + T - 1) / T - 1;   // the loop moves on to the tile holding span_end
+        const bool need = (t + 1 == t_end) || (!q.table_dense && sm.misc[0] * 2 > (int)q.table_slots) ||
+                          rows_since_flush + T > q.flush_rows;
+        __syncthreads();
+        if (need) {
+          flush_table(q, sm);
+          __syncthreads();
+          if (threadIdx.x == 0) sm.misc[0] = 0;
+          rows_since_flush = 0;
+        }
+        continue;
+      }
+    }
     const unsigned long long e = (s + T < q.n_rows) ? s + T : q.n_rows;
     const uint32_t rows = (uint32_t)(e - s);
     build_bitmaps(q, sm, s, e, nwords);

@@ -535,6 +535,7 @@ using Clock = std::chrono::steady_clock;
 struct Request {
   uint64_t ticket = 0;
   cq_table* table = nullptr;
+  bool large = false;      // large lane: launched alone, one large launch in flight at a time
   Planned planned;
   uint64_t footprint = 0;
   Clock::time_point submitted;
@@ -558,12 +559,14 @@ struct InFlight {
 struct cq_server {
   cq_ctx* ctx = nullptr;
   cq_server_options opt;
+  uint64_t large_rows = 0;   // tables above this many rows go to the large lane
   std::vector<cudaStream_t> streams;
   std::vector<int> stream_busy;             // launches in flight per stream
   std::vector<cudaEvent_t> free_events;
   std::mutex mu;
   std::condition_variable cv_submit, cv_done;
-  std::deque<std::shared_ptr<cq::Request>> pending;
+  std::deque<std::shared_ptr<cq::Request>> pending;        // small lane
+  std::deque<std::shared_ptr<cq::Request>> pending_large;  // large lane
   std::unordered_map<uint64_t, std::shared_ptr<cq::Request>> by_ticket;
   std::vector<cq::InFlight> inflight;
   uint64_t next_ticket = 1;
@@ -577,15 +580,16 @@ namespace cq {
 
 // Take admitted requests for the next launch: oldest first, while the batch
 // has room and their footprints fit the budget beside what is in flight.
-static std::vector<std::shared_ptr<Request>> take_batch(cq_server* srv) {
+static std::vector<std::shared_ptr<Request>> take_batch(cq_server* srv, std::deque<std::shared_ptr<Request>>& from,
+                                                         uint32_t max_n) {
   std::vector<std::shared_ptr<Request>> b;
   uint64_t used = srv->used_bytes;
-  while (!srv->pending.empty() && b.size() < srv->opt.max_batch) {
-    const std::shared_ptr<Request>& r = srv->pending.front();
+  while (!from.empty() && b.size() < max_n) {
+    const std::shared_ptr<Request>& r = from.front();
     if (used + r->footprint > srv->opt.memory_budget_bytes && !(b.empty() && srv->inflight.empty())) break;
     used += r->footprint;
     b.push_back(r);
-    srv->pending.pop_front();
+    from.pop_front();
   }
   srv->used_bytes = used;
   return b;
@@ -671,20 +675,34 @@ static void serve(cq_server* srv) {
       any_done = true;
     }
     if (any_done) srv->cv_done.notify_all();
-    if (srv->stop && srv->pending.empty() && srv->inflight.empty()) break;
-    // ---- launches: a free stream, and either an idle device, a full batch
-    // or a request that has waited long enough for company
+    if (srv->stop && srv->pending.empty() && srv->pending_large.empty() && srv->inflight.empty()) break;
+    // ---- launches.  Large lane (stream 0): one large query at a time, alone,
+    // as soon as the lane is free -- large scans are bandwidth-bound, and two
+    // at once only delay both.  Small lane (the other streams, at the highest
+    // stream priority): a free stream takes the waiting small queries as one
+    // batch when the lane is idle, the batch is full, or the oldest has
+    // waited max_wait_us; small batches overlap the large lane's scan.
     int sidx = -1;
-    for (size_t k = 0; k < srv->streams.size(); ++k)
-      if (srv->stream_busy[k] == 0) { sidx = (int)k; break; }
-    bool go = false;
-    if (sidx >= 0 && !srv->pending.empty()) {
-      go = srv->inflight.empty() || srv->pending.size() >= srv->opt.max_batch || srv->stop ||
-           Clock::now() - srv->pending.front()->submitted >= max_wait;
+    std::vector<std::shared_ptr<Request>> b;
+    const bool two_lanes = srv->streams.size() >= 2;
+    if (two_lanes && srv->stream_busy[0] == 0 && !srv->pending_large.empty()) {
+      b = take_batch(srv, srv->pending_large, 1);
+      if (!b.empty()) sidx = 0;
     }
-    if (go) {
-      std::vector<std::shared_ptr<Request>> b = take_batch(srv);
-      if (!b.empty()) {
+    if (b.empty() && !srv->pending.empty()) {
+      int free_s = -1, busy = 0;
+      for (size_t k = two_lanes ? 1 : 0; k < srv->streams.size(); ++k) {
+        if (srv->stream_busy[k] == 0 && free_s < 0) free_s = (int)k;
+        busy += srv->stream_busy[k];
+      }
+      if (free_s >= 0 && (busy == 0 || srv->pending.size() >= srv->opt.max_batch || srv->stop ||
+                          Clock::now() - srv->pending.front()->submitted >= max_wait)) {
+        b = take_batch(srv, srv->pending, srv->opt.max_batch);
+        if (!b.empty()) sidx = free_s;
+      }
+    }
+    if (!b.empty()) {
+      {
         uint64_t fp = 0;
         for (auto& r : b) fp += r->footprint;
         lk.unlock();
@@ -750,7 +768,7 @@ static void serve(cq_server* srv) {
       }
     }
     // ---- wait: for a submission, or briefly while launches are in flight
-    if (srv->inflight.empty() && srv->pending.empty()) {
+    if (srv->inflight.empty() && srv->pending.empty() && srv->pending_large.empty()) {
       srv->cv_submit.wait(lk);
     } else {
       srv->cv_submit.wait_for(lk, std::chrono::microseconds(20));
@@ -772,6 +790,8 @@ extern "C" int cq_server_create(cq_ctx* ctx, const cq_server_options* opts, cq_s
   if (!srv->opt.max_batch) srv->opt.max_batch = 256;
   if (!srv->opt.n_streams) srv->opt.n_streams = 2;
   if (!srv->opt.max_wait_us) srv->opt.max_wait_us = 50;
+  srv->large_rows = srv->opt.large_rows_log2 ? (1ull << (srv->opt.large_rows_log2 < 63 ? srv->opt.large_rows_log2 : 63))
+                                             : (1ull << 22);
   if (srv->opt.n_streams > 16) return set_error(CQ_ERR_INVALID_ARG, "at most 16 streams");
   CQ_CUDA(cudaSetDevice(ctx->device));
   {
@@ -779,9 +799,13 @@ extern "C" int cq_server_create(cq_ctx* ctx, const cq_server_options* opts, cq_s
     const int rc = ensure_batch_kernel(ctx);
     if (rc != CQ_OK) return rc;
   }
+  // stream 0 (the large lane) at the default priority, the others (the small
+  // lane) at the highest
+  int least = 0, greatest = 0;
+  CQ_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
   for (uint32_t i = 0; i < srv->opt.n_streams; ++i) {
     cudaStream_t st = nullptr;
-    CQ_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CQ_CUDA(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, i == 0 ? least : greatest));
     srv->streams.push_back(st);
     srv->stream_busy.push_back(0);
   }
@@ -798,9 +822,17 @@ extern "C" int cq_server_submit(cq_server* srv, cq_table* table, const cq_plan* 
   if (table->ctx != srv->ctx) return set_error(CQ_ERR_INVALID_ARG, "table of another context");
   std::shared_ptr<Request> r(new Request);
   r->submitted = Clock::now();
+  // large-lane queries always run alone: planned (and their kernel compiled)
+  // like cq_query_run's; small ones for a shared batch
+  r->large = srv->opt.n_streams >= 2 && table->n_rows > srv->large_rows;
   {
     PlanCopy pc(*plan);   // literals resolved at planning; the copy lives until then
-    const int rc = plan_batch_query(table, &pc.plan, 0, srv->ctx->batch_smem, &r->planned);
+    const int rc = r->large ? plan_solo_query(table, &pc.plan, &r->planned)
+                            : plan_batch_query(table, &pc.plan, 0, srv->ctx->batch_smem, &r->planned);
+    if (rc != CQ_OK) return rc;
+  }
+  if (r->large) {
+    const int rc = prepare_row_kernel(srv->ctx, r->planned);
     if (rc != CQ_OK) return rc;
   }
   r->footprint = query_footprint(r->planned);
@@ -815,7 +847,8 @@ extern "C" int cq_server_submit(cq_server* srv, cq_table* table, const cq_plan* 
   r->table = new cq_table(*table);
   for (cq_column* c : table->cols) c->refs++;
   srv->by_ticket[r->ticket] = r;
-  srv->pending.push_back(r);
+  if (r->large) srv->pending_large.push_back(r);
+  else srv->pending.push_back(r);
   *ticket = r->ticket;
   srv->cv_submit.notify_one();
   return CQ_OK;

@@ -277,13 +277,13 @@ def make_index(rng, n_rows, nnz, lo, hi, default=0, val_dtype=np.int64, pos_dtyp
 # --------------------------------------------------------------------------
 # the workloads
 # --------------------------------------------------------------------------
-def tiny_two_rle(n_rows: int = 1_000_000, seed: int = DEFAULT_SEED):
+def tiny_two_rle(n_rows: int = 1_000_000, seed: int = DEFAULT_SEED, mean_a: float = 8.0, mean_b: float = 5.0):
     """Two int32 RLE columns.  A: geometric runs (mean 8), values U{0..99};
-    B: geometric runs (mean 5), values U{0..9}.
-    Query: SELECT B, SUM(A), COUNT(*) WHERE A < 50 GROUP BY B."""
+    B: geometric runs (mean 5), values U{0..9} (other means for run-length
+    sweeps).  Query: SELECT B, SUM(A), COUNT(*) WHERE A < 50 GROUP BY B."""
     rng = np.random.default_rng([seed, 1])
-    a = make_rle(rng, n_rows, 8.0, 0, 99)
-    b = make_rle(rng, n_rows, 5.0, 0, 9)
+    a = make_rle(rng, n_rows, mean_a, 0, 99)
+    b = make_rle(rng, n_rows, mean_b, 0, 9)
     table = Table([a, b], n_rows, ["A", "B"])
     plan = Plan([Pred(0, "lt", 50)], [1], [Agg("sum", 0), Agg("count")])
     return table, plan

@@ -90,11 +90,12 @@ def test_generator_library_exports_its_header(libpath):
 def test_specialised_row_kernel_compiles_without_a_gpu(libpath):
     """The run-time compiler builds the shape-specialised row kernel from the
     library's embedded device headers: two check shapes that between them use
-    every encoding, predicate kind, key mapping and aggregate layout."""
+    every encoding, predicate kind, key mapping, aggregate layout and group
+    domain (shared hash table, global hash table, single group)."""
     from paper_2506_10092_gb300 import cq
-    for variant in (0, 1):
+    for variant in (0, 1, 2):
         secs = cq.cq_jit_check(variant)
         assert 0 < secs < 120
     with pytest.raises(cq.CQError) as e:
-        cq.cq_jit_check(2)
+        cq.cq_jit_check(3)
     assert e.value.status == cq.CQ_ERR_INVALID_ARG
