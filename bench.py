@@ -539,23 +539,25 @@ def run_runsweep(args):
     n = args.rows or 100_000_000
     rows_out = []
 
-    def timed(t, ps, n_rows, alg, label):
+    def timed(t, ps, n_rows, alg, label, kernel=0):
+        opts = cq.exec_options(kernel=kernel)
         for _ in range(max(3, args.warmup)):
-            r = cq.cq_query_run(t, ps, stream=stream)
+            r = cq.cq_query_run(t, ps, stream=stream, opts=opts)
             cq.cq_result_wait(r)
             r.close()
         torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        res = [cq.cq_query_run(t, ps, stream=stream) for _ in range(args.steps)]
+        res = [cq.cq_query_run(t, ps, stream=stream, opts=opts) for _ in range(args.steps)]
         ev1.record(stream)
         ev1.synchronize()
         ms = ev0.elapsed_time(ev1) / args.steps
         k_us = statistics.mean(cq.cq_result_kernel_time_us(r) for r in res)
         for r in res:
             r.close()
-        rows_out.append({"case": label, "rows": n_rows, "compressed_bytes": alg, "ms_per_step": ms,
+        walk = {0: "planner's choice", 2: "tiles", 3: "runs"}[kernel]
+        rows_out.append({"case": label, "walk": walk, "rows": n_rows, "compressed_bytes": alg, "ms_per_step": ms,
                          "kernel_us": k_us, "rows_per_s": n_rows / (ms / 1e3),
                          "compressed_gbs_kernel": alg / (k_us * 1e-6) / 1e9})
         print(json.dumps(rows_out[-1]), file=sys.stderr, flush=True)
@@ -563,12 +565,14 @@ def run_runsweep(args):
     for ma, mb in ((8.0, 5.0), (1e3, 625.0), (1e5, 62500.0)):
         table, plan = dg.tiny_two_rle(n, seed=args.seed, mean_a=ma, mean_b=mb)
         t, cols = cq.table_from(ctx, table)
-        timed(t, cq.PlanStruct(plan), n, dg.compressed_bytes(table, dg.plan_columns(plan)),
-              f"two-RLE mean runs {ma:g}/{mb:g}")
+        for kernel in (2, 3, 0):
+            timed(t, cq.PlanStruct(plan), n, dg.compressed_bytes(table, dg.plan_columns(plan)),
+                  f"two-RLE mean runs {ma:g}/{mb:g}", kernel)
         del t, cols, table
     dn = devgen.DeviceNested(cq, ctx, 1_000_000_000, seed=args.seed)
     plan = dg.Plan([dg.Pred(2, "between", 200, 699)], [1], [dg.Agg("count"), dg.Agg("sum", 2), dg.Agg("max", 0)])
-    timed(dn.table, cq.PlanStruct(plan), dn.n_rows, dn.query_bytes(plan), "nested c1..c3 RLE, 1e9 rows")
+    for kernel in (2, 3, 0):
+        timed(dn.table, cq.PlanStruct(plan), dn.n_rows, dn.query_bytes(plan), "nested c1..c3 RLE, 1e9 rows", kernel)
     print(json.dumps({"metric": "compressed GB/s of pure run-length queries", "value": None, "unit": "GB/s",
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -773,11 +777,16 @@ def run_serving(args):
         return float(np.percentile(np.asarray(xs), p)) if xs else None
 
     # compile the kernels specialised to every query shape of the mix before
-    # any timing (each process compiles a shape once)
-    for tb, ps in ([tiny[0], cq.PlanStruct(dg.tiny_plan(50))],
-                   [het[0], cq.PlanStruct(het_plan)]) + tuple(
-                       [p.table, cq.PlanStruct(dg.nested_plan(200, 699, lean=True))] for p in nest):
+    # any timing (each process compiles a shape once): alone and through a
+    # server (whose small lane plans queries for batches)
+    warm = ([tiny[0], cq.PlanStruct(dg.tiny_plan(50))], [het[0], cq.PlanStruct(het_plan)]) + tuple(
+        [p.table, cq.PlanStruct(dg.nested_plan(200, 699, lean=True))] for p in nest)
+    for tb, ps in warm:
         cq.cq_result_wait(cq.cq_query_run(tb, ps))
+    srv = cq.cq_server_create(ctx, cq.server_options(max_batch=256, n_streams=4, max_wait_us=200))
+    for tk in [cq.cq_server_submit(srv, tb, ps) for tb, ps in warm]:
+        cq.cq_server_wait(srv, tk)[0].close()
+    srv.close()
 
     def run_mode(mode, rate, reqs, arrivals, n_warm):
         n = len(reqs)

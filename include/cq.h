@@ -210,10 +210,14 @@ typedef struct {
   uint32_t grid_ctas;    /* CTAs of the fused kernel; 0 = SMs x ctas_per_sm */
   uint32_t items_per_cta;  /* batches: work items per CTA the tiles are cut into
                               (load balance vs per-item overhead); 0 = default */
-  uint32_t kernel;       /* row-mode one-query launches: 0 = a kernel specialised to the query's
-                            shape, compiled at run time on first use and cached by the process
-                            (the environment variable CQ_JIT=0 turns this off); 1 = the generic
-                            ahead-of-time kernel, which reads the shape from the descriptor */
+  uint32_t kernel;       /* 0 = the planner's choice.  Row mode (one-query launches): by default a
+                            kernel specialised to the query's shape, compiled at run time on
+                            first use and cached by the process (the environment variable
+                            CQ_JIT=0 turns this off); 1 = the generic ahead-of-time kernel, which
+                            reads the shape from the descriptor.  Segment mode: by default
+                            tile by tile, or run by run (a k-way merge of the columns'
+                            boundaries, work proportional to the runs) when the columns'
+                            entries average 64 or more rows apart; 2 = tiles, 3 = runs */
   uint32_t hash_slots_log2;  /* key domains above 2^24 groups: initial slots of the global hash
                                 table as a power of two (12..26); 0 = twice the groups that can
                                 exist, 2^12 .. 2^22.  A table that fills is retried by
@@ -373,7 +377,7 @@ int cq_selftest_bounded_wait(cq_ctx* ctx, uint32_t limit_us, int32_t* device_sta
  * took (either may be NULL).  No counterpart in the paper.  Always CQ_OK. */
 int cq_jit_stats(uint64_t* compiles, double* seconds);
 
-/* Compile, without loading, one of three built-in shapes (variant 0, 1 or 2)
+/* Compile, without loading, one of four built-in shapes (variant 0 .. 3)
  * that between them exercise every encoding, predicate kind, key mapping,
  * aggregate layout and group domain of the specialised row kernel: a check
  * of the run-time compiler that needs no GPU.  *seconds (may be NULL)
@@ -392,17 +396,16 @@ int cq_jit_check(uint32_t variant, double* seconds);
  *    admitted to a launch only while the footprints of all queries in flight
  *    stay within memory_budget_bytes;
  *  - two lanes (n_streams >= 2): queries over tables of more than
- *    2^large_rows_log2 rows form the large lane -- planned like cq_query_run,
- *    launched alone on stream 0 as soon as no other large launch is in
- *    flight (large scans are bandwidth-bound; two at once only delay both);
- *  - continuous batching of the small lane: whenever one of the other
- *    streams (created at the highest stream priority) is free, the admitted
- *    small queries are launched together as one batch (cq_batch_run's
- *    persistent kernel) if the lane is idle, max_batch queries are waiting,
- *    or the oldest has waited max_wait_us; small batches arriving while
- *    others run go on another stream, so their work overlaps on the device
- *    and with the large lane's scan (with n_streams == 1 every query is in
- *    the small lane);
+ *    2^large_rows_log2 rows form the large lane -- planned like cq_query_run
+ *    and launched alone; the others are batched.  A fused kernel fills every
+ *    SM (one persistent CTA per SM, most of its shared memory), so launches
+ *    run one after another on one stream, at most two queued: the waiting
+ *    small queries go first, as one batch (cq_batch_run's persistent kernel),
+ *    when nothing runs, max_batch are waiting or the oldest has waited
+ *    max_wait_us; otherwise the oldest large query runs;
+ *  - one lane (n_streams == 1): every query is batched, a batch launched
+ *    when nothing runs, max_batch queries wait or the oldest has waited
+ *    max_wait_us;
  *  - completion: launches in flight are polled; a finished query's result
  *    and latency (submission to observed completion) go to cq_server_wait.
  * Each query's result equals its cq_query_run result exactly. */
@@ -411,7 +414,7 @@ typedef struct cq_server cq_server;
 typedef struct {
   uint64_t memory_budget_bytes;  /* admission limit on in-flight query footprints; 0 = 1 GiB */
   uint32_t max_batch;            /* most queries per launch; 0 = 256 */
-  uint32_t n_streams;            /* concurrent launches in flight (<= 16); 0 = 2 */
+  uint32_t n_streams;            /* 1: one lane (every query batched); >= 2 (<= 16): two lanes; 0 = 2 */
   uint32_t max_wait_us;          /* how long a partial batch may wait for company; 0 = 50 */
   uint32_t large_rows_log2;      /* tables above 2^this many rows use the large lane; 0 = 22 */
   uint32_t reserved[2];

@@ -667,6 +667,25 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   q.n_bitmaps = (uint8_t)nb;
   q.n_row_cols = (uint8_t)nrow;
   q.seg_mode = nrow == 0;
+  // segment mode walks tile by tile (bitmaps of the boundaries) or, when the
+  // segments are long, run by run (a merge of the columns' boundaries whose
+  // work follows the runs): kernel option 2 / 3 pins one
+  q.run_walk = 0;
+  q.run_slot = 0;
+  if (q.seg_mode && nb > 0 && !batch) {
+    uint64_t entries = 0, most = 0;
+    for (int c = 0; c < q.n_cols; ++c) {
+      const ColDesc& d = q.cols[c];
+      if (d.bslot == 0xFF) continue;
+      entries += d.enc == ENC_INDEX ? 2 * d.n : d.n;
+      if (d.n >= most) {
+        most = d.n;
+        q.run_slot = d.bslot;
+      }
+    }
+    const uint32_t k = opts ? opts->kernel : 0;
+    q.run_walk = (k == 3 || (k == 0 && entries * kRunWalkMinSegment <= n_rows)) ? 1 : 0;
+  }
   q.stage_bytes = stage_off;
   q.stages = (uint8_t)(opts && opts->stages ? opts->stages : 4);
   q.ncw = (uint8_t)ncw;
@@ -909,9 +928,11 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   }
   // ---- table shape and flush period
   q.flush_rows = 1u << 20;
+  // a run walk flushes its shared table once, after all of a launch's rows
+  if (q.run_walk) q.flush_rows = (uint32_t)(n_rows < kLaunchRows ? n_rows : kLaunchRows);
   // a SUM whose values are small enough for a 32-bit shared word over a
   // flush period of at least 2^18 rows shortens the period to fit it
-  for (uint32_t i = 0; i < plan->n_aggs; ++i) {
+  for (uint32_t i = 0; i < plan->n_aggs && !q.run_walk; ++i) {
     const cq_aggregate& a = plan->aggs[i];
     if (a.op != CQ_SUM && a.op != CQ_AVG) continue;
     const PlanCol& pc = tcols[a.col];
@@ -1084,7 +1105,9 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   if (want_tile && (want_tile < 1024 || want_tile > 8192 || (want_tile & (want_tile - 1))))
     return set_error(CQ_ERR_INVALID_ARG, "tile_rows must be 1024, 2048, 4096 or 8192");
   if (want_ctas > 3) return set_error(CQ_ERR_INVALID_ARG, "ctas_per_sm must be 0, 1, 2 or 3 (3: segment mode)");
-  if (opts && opts->kernel > 1) return set_error(CQ_ERR_INVALID_ARG, "kernel must be 0 (specialised) or 1 (generic)");
+  if (opts && opts->kernel > 3)
+    return set_error(CQ_ERR_INVALID_ARG, "kernel must be 0 (default), 1 (generic row kernel), 2 (segment mode by "
+                                         "tiles) or 3 (segment mode by runs)");
   if (opts && opts->hash_slots_log2 && (opts->hash_slots_log2 < kHashMinLog2 || opts->hash_slots_log2 > kHashMaxLog2))
     return set_error(CQ_ERR_INVALID_ARG, "hash_slots_log2 must be 0 or in %u..%u", kHashMinLog2, kHashMaxLog2);
   // segment mode when every referenced column is RLE or index-encoded

@@ -115,6 +115,10 @@ struct QueryDesc {
   uint32_t tile_rows;
   uint8_t n_cols, n_preds, n_keys, n_aggs;
   uint8_t seg_mode;        // 1: every referenced column is RLE/index -> items are segments
+  uint8_t run_walk;        // segment mode walked run by run (no tiles): threads take equal shares
+                           // of the entries of bitmap column run_slot and merge every column's
+                           // boundaries over their rows
+  uint8_t run_slot;
   uint8_t n_bitmaps;       // RLE/INDEX columns with a per-tile bitmap
   uint8_t n_row_cols;      // columns staged per tile (row mode)
   uint8_t stages;

@@ -317,6 +317,20 @@ __device__ __forceinline__ void fast_index_update(const QueryDesc& q, const Smem
   }
 }
 
+// Whether every aggregate of the shape can be reduced across a warp in 32-bit
+// arithmetic first (COUNT, SUMs of values below 2^24 in magnitude, MIN / MAX
+// of 32-bit values; index-column aggregates cannot).
+template <class S>
+__device__ constexpr bool seg_reducible() {
+  for (int i = 0; i < S::n_aggs; ++i) {
+    const int k = S::akind(i);
+    if (k == AK_SUM && !S::ared32(i)) return false;
+    if ((k == AK_MIN || k == AK_MAX) && !S::aw32(i)) return false;
+    if (k == AK_ISUM || k == AK_IMIN || k == AK_IMAX) return false;
+  }
+  return true;
+}
+
 // Aggregate the n_pass compacted rows of this warp, 32 at a time (one per
 // lane): group id from the key digits, a shared-table slot, COUNT and every
 // aggregate.  A single-group query reduces across the warp first.
@@ -385,6 +399,61 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
         }
       });
     } else {
+      if constexpr (seg_reducible<S>()) {
+        // Sorted keys (runs of equal groups among consecutive passing rows):
+        // reduce each run of equal gids across the warp first and let its
+        // last lane update the table once -- COUNT = run length, SUM and
+        // MIN / MAX by a segmented shuffle scan.  Taken when the runs average
+        // two or more rows; otherwise every lane updates (below).
+        const auto prev = __shfl_up_sync(0xFFFFFFFFu, gid, 1);
+        const uint32_t actm = __ballot_sync(0xFFFFFFFFu, act);
+        const bool head = act && (lane == 0 || prev != gid);
+        const uint32_t heads = __ballot_sync(0xFFFFFFFFu, head);
+        if (2 * __popc(heads) <= __popc(actm)) {
+          const uint32_t upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+          const int seg0 = 31 - __clz(heads & upto);   // first lane of my run (act lanes)
+          const bool tail = act && (lane == 31 || !((actm >> (lane + 1)) & 1u) || ((heads >> (lane + 1)) & 1u));
+          int red[S::n_aggs + 1];
+          static_for<S::n_aggs>([&](auto A) {
+            constexpr int i = decltype(A)::value;
+            constexpr int kind = S::akind(i);
+            if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+              constexpr bool mn = kind == AK_MIN;
+              int x = act ? (int)val[i] : (kind == AK_SUM ? 0 : (mn ? INT_MAX : INT_MIN));
+#pragma unroll
+              for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+                if (lane - d >= seg0) x = kind == AK_SUM ? x + y : (mn ? min(x, y) : max(x, y));
+              }
+              red[i] = x;
+            }
+          });
+          if (tail) {
+            int slot = -1;
+            uint32_t gi = 0;
+            bool ok = true;
+            const unsigned cnt = (unsigned)(lane - seg0 + 1);
+            if constexpr (S::table_dense) slot = (int)gid;
+            else slot = table_slot_t<S::ghash>(q, sm, gid);
+            if (slot >= 0) {
+              atomicAdd(scount(q, sm, slot), cnt);
+            } else {
+              const long long g = gindex_t<S::ghash>(q, gid);
+              ok = g >= 0;
+              gi = (uint32_t)g;
+              if (ok) atomicAdd(gword(q, 0, gi), (unsigned long long)cnt);
+            }
+            static_for<S::n_aggs>([&](auto A) {
+              constexpr int i = decltype(A)::value;
+              constexpr int kind = S::akind(i);
+              if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+                if (ok) fast_update<S, i>(q, sm, slot, gi, (long long)red[i]);
+              }
+            });
+          }
+          continue;
+        }
+      }
       int slot = -1;
       uint32_t gi = 0;   // global accumulator index, used when the shared table has no slot
       if (act) {

@@ -175,6 +175,9 @@ cudaError_t launch_fold_sums(const QueryDesc& q, cudaStream_t s);
 // rows of one fused-kernel launch: longer queries are split so that no global
 // SUM limb word receives 2^31 or more additions between two folds
 constexpr uint64_t kLaunchRows = 1ull << 31;
+// segment mode walks run by run when the columns' entries (runs, twice the
+// listed rows) average at least this many rows apart
+constexpr uint64_t kRunWalkMinSegment = 64;
 size_t query_kernel_smem(const QueryDesc& q);
 cudaError_t query_kernel_set_smem(size_t bytes);
 

@@ -285,9 +285,10 @@ cudaError_t launch_row_jit(const void* fn, const QueryDesc& q, unsigned grid, in
 }  // namespace cq
 
 namespace cq {
-// Three synthetic shapes that between them use every encoding, predicate
-// kind, key mapping, aggregate layout and group domain (dense hash table,
-// global hash table, single group) of the specialised body; only compiled.
+// Four synthetic shapes that between them use every encoding, predicate
+// kind, key mapping, aggregate layout and group domain (shared hash table,
+// global hash table, single group) of the specialised body, with and without
+// the warp pre-reduction of sorted keys; only compiled.
 static void check_shape(uint32_t variant, QueryDesc* q) {
   memset(q, 0, sizeof(*q));
   q->tile_rows = 8192;
@@ -311,7 +312,7 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
     a.kind = kind; a.col = c; a.sw = sw; a.wide = wide; a.sw32 = sw32; a.gw = gw; a.red32 = red32; a.w32 = w32;
     a.n32 = n32; a.s32 = s32;
   };
-  if (variant == 0) {
+  if (variant == 0 || variant == 3) {
     q->n_cols = 5; q->n_preds = 2; q->n_keys = 2; q->n_aggs = 5; q->n_bitmaps = 2;
     col(0, ENC_RLE, 0, 0, 0, 0, 0);
     col(1, ENC_DICT, 0, 14, 0xFF, 1, 0);
@@ -327,6 +328,7 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
     agg(2, AK_MIN, 4, 2, 0, 2, 7, 0, 1, 1, 0);
     agg(3, AK_MAX, 4, 2, 0, 3, 8, 0, 1, 1, 0);
     agg(4, AK_COUNT, 0, 0, 0, 0, 0, 0, 0, 0, 0);
+    if (variant == 3) agg(0, AK_COUNT, 0, 0, 0, 0, 0, 0, 0, 0, 0);   // reducible across a warp
   } else {
     q->n_cols = 5; q->n_preds = 6; q->n_keys = 1; q->n_aggs = 7; q->n_bitmaps = 2; q->n_pbm = 1;
     if (variant == 1) {
@@ -361,11 +363,11 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
 // run-time compilation that needs no GPU.  *seconds receives the compile time.
 extern "C" int cq_jit_check(uint32_t variant, double* seconds) {
   cq::clear_error();
-  if (variant > 2) return cq::set_error(CQ_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  if (variant > 3) return cq::set_error(CQ_ERR_INVALID_ARG, "variant must be 0 .. 3");
   cq::QueryDesc q;
   cq::check_shape(variant, &q);
   cq::JitKernel k;
-  const int rc = cq::compile(cq::shape_source(q, variant == 0 ? 28 : 16, variant == 0 ? 8 : 16, 1), &k, false);
+  const int rc = cq::compile(cq::shape_source(q, (variant == 0 || variant == 3) ? 28 : 16, (variant == 0 || variant == 3) ? 8 : 16, 1), &k, false);
   if (seconds) *seconds = k.compile_s;
   return rc;
 }

@@ -59,8 +59,10 @@ __host__ __device__ inline SmemLayout smem_layout(const QueryDesc& q) {
   off += 8u * kMaxBitmapCols * nbuf;
   // row mode: per window buffer and bitmap column, kWin run ends / positions
   // followed by the kWin values of the same runs / listed rows
-  L.win = off;   // segment mode: the next boundary of each bitmap column (long-segment test)
-  off += q.seg_mode ? 8u * kMaxBitmapCols : 16u * kWin * nb * kWinBufs;
+  // segment mode: the next boundary of each bitmap column (long-segment
+  // test); walked by runs: each thread's cursor, boundary and value per column
+  L.win = off;
+  off += q.seg_mode ? (q.run_walk ? 24u * nb * kThreads : 8u * kMaxBitmapCols) : 16u * kWin * nb * kWinBufs;
   L.wcnt = off;
   off += 4u * kMaxBitmapCols * kWinBufs;
   L.ubm = off;

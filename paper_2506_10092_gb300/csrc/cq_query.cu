@@ -35,6 +35,25 @@ __global__ void __launch_bounds__(kThreads, MINB) seg_query_kernel(const __grid_
   seg_range<GPW>(q, carve(q), t_begin, t_end);
 }
 
+// Segment mode walked by runs (run_range): every thread merges the columns'
+// boundaries over its share of rows; the block's shared group table is
+// flushed once at the end.
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) run_query_kernel(const __grid_constant__ QueryDesc q) {
+  const Smem sm = carve(q);
+  for (uint32_t sl = threadIdx.x; sl < q.table_slots; sl += blockDim.x) reset_slot(q, sm, sl);
+  if (threadIdx.x < 8) sm.misc[threadIdx.x] = 0;
+  const bool aux_smem = q.aux_words <= kAuxSmemWords;
+  if (aux_smem)
+    for (uint32_t i = threadIdx.x; i < q.aux_words; i += blockDim.x) sm.aux[i] = __ldg(q.aux + i);
+  __syncthreads();
+  const unsigned long long r_lo = q.tile0 * q.tile_rows;
+  const unsigned long long r_end = (q.tile0 + q.n_tiles) * q.tile_rows;
+  run_range(q, sm, aux_smem ? sm.aux : q.aux, r_lo, r_end < q.n_rows ? r_end : q.n_rows);
+  __syncthreads();
+  flush_table(q, sm);
+}
+
 // ------------------------------------------------------------------ init / finalize
 // Identity values of group i's global accumulators.
 __device__ __forceinline__ void init_group(const QueryDesc& q, size_t i) {
@@ -498,6 +517,8 @@ cudaError_t launch_row_kernel(const QueryDesc& q, unsigned grid, cudaStream_t s)
 cudaError_t query_kernel_set_smem(size_t bytes) {
   cudaError_t e;
   const int b = (int)bytes;
+  if ((e = cudaFuncSetAttribute(run_query_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+  if ((e = cudaFuncSetAttribute(run_query_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
 #define CQ_SEG_SET(G, M)                                                                                  \
   if ((e = cudaFuncSetAttribute(seg_query_kernel<G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
   CQ_SEG_SET(2, 1) CQ_SEG_SET(4, 1) CQ_SEG_SET(8, 1) CQ_SEG_SET(16, 1)
@@ -525,6 +546,14 @@ cudaError_t launch_query(const QueryDesc& q, cudaStream_t s, int num_sms, int ct
     int ncw, gpw, minb;
     row_shape(q, &ncw, &gpw, &minb);
     return launch_row_jit(row_fn, q, grid, ncw, s);
+  }
+  if (q.run_walk) {
+    // every thread of a full grid (at most two CTAs per SM resident) takes a
+    // share of the runs
+    const unsigned g = grid_ctas ? grid_ctas : (unsigned)num_sms * (unsigned)(ctas_per_sm < 2 ? ctas_per_sm : 2);
+    if (ctas_per_sm >= 2) run_query_kernel<2><<<g, kThreads, q.smem_bytes, s>>>(q);
+    else run_query_kernel<1><<<g, kThreads, q.smem_bytes, s>>>(q);
+    return cudaGetLastError();
   }
   switch (q.tile_rows / kThreads) {
     // two or three CTAs per SM overlap one CTA's barrier-separated phases with

@@ -167,23 +167,22 @@ __device__ inline void build_segments(const QueryDesc& q, const Smem& sm, uint32
   __syncthreads();
 }
 
-// One aligned segment of L rows starting at row s over which every column is
-// constant: each RLE column holds the run at its cursor, each index column its
-// default (no listed row inside).  Filter and aggregate it once: COUNT += L,
-// SUM += value x L, MIN / MAX on the value (Section 7; the rows need no
-// bitmaps).  One thread.
-__device__ inline void seg_span_update(const QueryDesc& q, const Smem& sm, const uint32_t* aux, unsigned long long s,
-                                       unsigned long long L) {
-  auto value = [&](const ColDesc& c) -> long long {
-    if (c.enc == ENC_RLE) return ldg_val(c.vals, sm.tcur[c.bslot], c.v64);
-    return c.base;   // index column, unlisted rows
-  };
+// Filter and aggregate one aligned segment of L rows starting at row s over
+// which every column is constant: value(c) is column c's value there (an RLE
+// column's run value, an index column's listed value or default), listed(c,
+// &v) tells whether an index column lists the (single) row, with its value.
+// COUNT += L, SUM += value x L, MIN / MAX on the value (Section 7); index
+// aggregates take listed rows only (finalize adds the default from COUNT).
+// One thread per segment.
+template <class Value, class Listed>
+__device__ inline void segment_update(const QueryDesc& q, const Smem& sm, const uint32_t* aux, unsigned long long s,
+                                      unsigned long long L, Value value, Listed listed) {
   for (int i = 0; i < q.n_preds; ++i)
-    if (!pred_eval(q.preds[i], aux, value(q.cols[q.preds[i].col]))) return;
+    if (!pred_eval(q.preds[i], aux, value(q.preds[i].col))) return;
   unsigned long long gid = 0;
   for (int ki = 0; ki < q.n_keys; ++ki) {
     const KeyDesc& k = q.keys[ki];
-    const long long v = value(q.cols[k.col]);
+    const long long v = value(k.col);
     unsigned long long d;
     if (!key_digit(k, aux, v, &d)) {
       report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)ki << 8), s, (unsigned long long)v);
@@ -191,7 +190,7 @@ __device__ inline void seg_span_update(const QueryDesc& q, const Smem& sm, const
     }
     gid += d * k.stride;
   }
-  int slot = q.n_groups == 1 && !q.ghash ? 0 : table_slot(q, sm, gid);
+  const int slot = q.n_groups == 1 && !q.ghash ? 0 : table_slot(q, sm, gid);
   uint32_t gi = 0;
   if (slot >= 0) {
     atomicAdd(scount(q, sm, slot), (unsigned)L);
@@ -203,11 +202,35 @@ __device__ inline void seg_span_update(const QueryDesc& q, const Smem& sm, const
   }
   for (int ai = 0; ai < q.n_aggs; ++ai) {
     const AggDesc& a = q.aggs[ai];
-    // index-column aggregates see no listed row here; finalize adds the
-    // default from COUNT
-    if (a.kind == AK_SUM) sum_add(q, sm, a, slot, gi, mul_s64(value(q.cols[a.col]), (long long)L));
-    else if (a.kind == AK_MIN || a.kind == AK_MAX) minmax_add(q, sm, a, slot, gi, value(q.cols[a.col]), a.kind == AK_MIN);
+    if (a.kind == AK_SUM) {
+      sum_add(q, sm, a, slot, gi, mul_s64(value(a.col), (long long)L));
+    } else if (a.kind == AK_MIN || a.kind == AK_MAX) {
+      minmax_add(q, sm, a, slot, gi, value(a.col), a.kind == AK_MIN);
+    } else if (a.kind != AK_COUNT) {
+      long long v;
+      if (!listed(a.col, &v)) continue;
+      if (a.kind == AK_ISUM) {
+        sum_add(q, sm, a, slot, gi, index_delta(v, a.base));
+      } else {
+        minmax_add(q, sm, a, slot, gi, v, a.kind == AK_IMIN);
+        if (slot >= 0) atomicAdd(slisted(q, sm, a, slot), 1u);
+        else atomicAdd(gword(q, a.gw + 1, gi), 1ull);
+      }
+    }
   }
+}
+
+// A segment of L rows at row s inside which no column has a boundary: each
+// RLE column holds the run at its cursor, each index column its default.
+__device__ inline void seg_span_update(const QueryDesc& q, const Smem& sm, const uint32_t* aux, unsigned long long s,
+                                       unsigned long long L) {
+  auto value = [&](int c) -> long long {
+    const ColDesc& cd = q.cols[c];
+    if (cd.enc == ENC_RLE) return ldg_val(cd.vals, sm.tcur[cd.bslot], cd.v64);
+    return cd.base;
+  };
+  auto listed = [&](int, long long*) { return false; };
+  segment_update(q, sm, aux, s, L, value, listed);
 }
 
 // Walk tiles [t_begin, t_end) of one segment-mode query: reset the group
@@ -324,6 +347,115 @@ __device__ __forceinline__ void seg_range(const QueryDesc& q, const Smem& sm, un
       if (threadIdx.x == 0) sm.misc[0] = 0;
       rows_since_flush = 0;
     }
+  }
+}
+
+}  // namespace cq
+
+namespace cq {
+
+// ------------------------------------------------------------------ walk by runs
+// First index of sorted a[0, n) whose entry exceeds key (upper) or is at
+// least key (lower); a plain binary search by one thread.
+__device__ __forceinline__ unsigned long long thread_bound(const void* a, bool e64, unsigned long long n, long long key,
+                                                          bool upper) {
+  unsigned long long lo = 0, hi = n;
+  while (lo < hi) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    const long long x = ldg_val(a, mid, e64);
+    if (upper ? x <= key : x < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Segment mode without tiles (Section 6 alignment as a k-way merge of the
+// columns' boundaries): thread u of the grid takes the u-th equal share of
+// the entries (runs / listed rows) of the column with the most of them, i.e.
+// the rows from its share's first entry to the next share's, clipped to the
+// launch's rows [r_lo, r_hi).  It finds every column's run / next listed row
+// at its first row by binary search, then walks its rows segment by segment:
+// the segment ends at the nearest boundary of any column (a listed row is a
+// segment of its own), is aggregated once (segment_update) and the columns
+// whose boundary it reached advance.  The work follows the runs, not the
+// rows.  Per-thread cursors live in shared memory (dynamic column index).
+__device__ inline void run_range(const QueryDesc& q, const Smem& sm, const uint32_t* aux, unsigned long long r_lo,
+                                 unsigned long long r_hi) {
+  const int nb = q.n_bitmaps;
+  const unsigned long long U = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const ColDesc& D = bitmap_col(q, q.run_slot);
+  const unsigned long long nD = D.n;
+  unsigned long long r0, r1;
+  if (nD == 0) {   // no entries anywhere: one thread takes every row
+    r0 = u == 0 ? 0ull : q.n_rows;
+    r1 = q.n_rows;
+  } else {
+    const unsigned long long a = u * nD / U, b = (u + 1) * nD / U;
+    auto start_row = [&](unsigned long long i) -> unsigned long long {
+      if (i == 0) return 0ull;
+      if (i >= nD) return q.n_rows;
+      return D.enc == ENC_RLE ? (unsigned long long)ldg_val(D.ends, i - 1, D.e64)
+                              : (unsigned long long)ldg_val(D.ends, i, D.e64);
+    };
+    r0 = start_row(a);
+    r1 = start_row(b);
+  }
+  if (r0 < r_lo) r0 = r_lo;
+  if (r1 > r_hi) r1 = r_hi;
+  if (r0 >= r1) return;
+  // per column j: cursor, next boundary (RLE: end of the current run; index:
+  // next listed row, ~0 past the last), value (RLE: run value; index: listed)
+  unsigned long long* cur = reinterpret_cast<unsigned long long*>(sm.win) + threadIdx.x;
+  long long* bnd = reinterpret_cast<long long*>(sm.win) + (size_t)nb * blockDim.x + threadIdx.x;
+  long long* val = reinterpret_cast<long long*>(sm.win) + (size_t)2 * nb * blockDim.x + threadIdx.x;
+  const size_t S = blockDim.x;
+  auto load = [&](int j) {
+    const ColDesc& c = bitmap_col(q, j);
+    const unsigned long long k = cur[j * S];
+    if (k < c.n) {
+      bnd[j * S] = ldg_val(c.ends, k, c.e64);
+      val[j * S] = ldg_val(c.vals, k, c.v64);
+    } else {
+      bnd[j * S] = c.enc == ENC_RLE ? (long long)q.n_rows : LLONG_MAX;
+      val[j * S] = 0;
+    }
+  };
+  for (int j = 0; j < nb; ++j) {
+    const ColDesc& c = bitmap_col(q, j);
+    cur[j * S] = thread_bound(c.ends, c.e64, c.n, (long long)r0, c.enc == ENC_RLE);
+    load(j);
+  }
+  unsigned long long pos = r0;
+  while (pos < r1) {
+    unsigned long long nxt = r1;
+    for (int j = 0; j < nb; ++j) {
+      const unsigned long long x = (unsigned long long)bnd[j * S];
+      if (bitmap_col(q, j).enc == ENC_INDEX && x == pos) nxt = pos + 1 < nxt ? pos + 1 : nxt;
+      else if (x < nxt) nxt = x;
+    }
+    auto value = [&](int c) -> long long {
+      const ColDesc& cd = q.cols[c];
+      const int j = cd.bslot;
+      if (cd.enc == ENC_RLE) return val[j * S];
+      return (unsigned long long)bnd[j * S] == pos ? val[j * S] : cd.base;
+    };
+    auto listed = [&](int c, long long* v) {
+      const int j = q.cols[c].bslot;
+      if ((unsigned long long)bnd[j * S] != pos) return false;
+      *v = val[j * S];
+      return true;
+    };
+    segment_update(q, sm, aux, pos, nxt - pos, value, listed);
+    for (int j = 0; j < nb; ++j) {
+      const ColDesc& c = bitmap_col(q, j);
+      const unsigned long long x = (unsigned long long)bnd[j * S];
+      if ((c.enc == ENC_RLE && x == nxt) || (c.enc == ENC_INDEX && x == pos)) {
+        cur[j * S] += 1;
+        load(j);
+      }
+    }
+    pos = nxt;
   }
 }
 

@@ -676,29 +676,31 @@ static void serve(cq_server* srv) {
     }
     if (any_done) srv->cv_done.notify_all();
     if (srv->stop && srv->pending.empty() && srv->pending_large.empty() && srv->inflight.empty()) break;
-    // ---- launches.  Large lane (stream 0): one large query at a time, alone,
-    // as soon as the lane is free -- large scans are bandwidth-bound, and two
-    // at once only delay both.  Small lane (the other streams, at the highest
-    // stream priority): a free stream takes the waiting small queries as one
-    // batch when the lane is idle, the batch is full, or the oldest has
-    // waited max_wait_us; small batches overlap the large lane's scan.
+    // ---- launches.  With two lanes, every launch goes to stream 0, at most
+    // two queued: a fused kernel fills every SM (one persistent CTA per SM,
+    // most of its shared memory), so launches on several streams would only
+    // wait for one another.  Waiting small queries go first, as one batch, when
+    // nothing runs, the batch is full or the oldest has waited max_wait_us;
+    // otherwise the oldest large query runs alone.  With one lane
+    // (n_streams == 1) every query is batched.
     int sidx = -1;
     std::vector<std::shared_ptr<Request>> b;
-    const bool two_lanes = srv->streams.size() >= 2;
-    if (two_lanes && srv->stream_busy[0] == 0 && !srv->pending_large.empty()) {
-      b = take_batch(srv, srv->pending_large, 1);
-      if (!b.empty()) sidx = 0;
-    }
-    if (b.empty() && !srv->pending.empty()) {
-      int free_s = -1, busy = 0;
-      for (size_t k = two_lanes ? 1 : 0; k < srv->streams.size(); ++k) {
-        if (srv->stream_busy[k] == 0 && free_s < 0) free_s = (int)k;
-        busy += srv->stream_busy[k];
+    const bool two_lanes = srv->opt.n_streams >= 2;
+    if (two_lanes) {
+      const size_t in_flight = srv->inflight.size();
+      if (in_flight < 2) {
+        const bool small_ready =
+            !srv->pending.empty() && (in_flight == 0 || srv->pending.size() >= srv->opt.max_batch || srv->stop ||
+                                      Clock::now() - srv->pending.front()->submitted >= max_wait);
+        if (small_ready) b = take_batch(srv, srv->pending, srv->opt.max_batch);
+        else if (srv->pending.empty() && !srv->pending_large.empty()) b = take_batch(srv, srv->pending_large, 1);
+        if (!b.empty()) sidx = 0;
       }
-      if (free_s >= 0 && (busy == 0 || srv->pending.size() >= srv->opt.max_batch || srv->stop ||
-                          Clock::now() - srv->pending.front()->submitted >= max_wait)) {
+    } else if (srv->stream_busy[0] == 0 && !srv->pending.empty()) {
+      if (srv->inflight.empty() || srv->pending.size() >= srv->opt.max_batch || srv->stop ||
+          Clock::now() - srv->pending.front()->submitted >= max_wait) {
         b = take_batch(srv, srv->pending, srv->opt.max_batch);
-        if (!b.empty()) sidx = free_s;
+        if (!b.empty()) sidx = 0;
       }
     }
     if (!b.empty()) {
@@ -799,13 +801,10 @@ extern "C" int cq_server_create(cq_ctx* ctx, const cq_server_options* opts, cq_s
     const int rc = ensure_batch_kernel(ctx);
     if (rc != CQ_OK) return rc;
   }
-  // stream 0 (the large lane) at the default priority, the others (the small
-  // lane) at the highest
-  int least = 0, greatest = 0;
-  CQ_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-  for (uint32_t i = 0; i < srv->opt.n_streams; ++i) {
+  // every launch goes to one stream (n_streams >= 2 selects the two lanes)
+  {
     cudaStream_t st = nullptr;
-    CQ_CUDA(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, i == 0 ? least : greatest));
+    CQ_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     srv->streams.push_back(st);
     srv->stream_busy.push_back(0);
   }
@@ -831,7 +830,9 @@ extern "C" int cq_server_submit(cq_server* srv, cq_table* table, const cq_plan* 
                             : plan_batch_query(table, &pc.plan, 0, srv->ctx->batch_smem, &r->planned);
     if (rc != CQ_OK) return rc;
   }
-  if (r->large) {
+  {
+    // the kernel specialised to the query's shape is compiled here, on the
+    // submitting thread, not in the serving loop (a lone query runs it)
     const int rc = prepare_row_kernel(srv->ctx, r->planned);
     if (rc != CQ_OK) return rc;
   }

@@ -93,9 +93,9 @@ def test_specialised_row_kernel_compiles_without_a_gpu(libpath):
     every encoding, predicate kind, key mapping, aggregate layout and group
     domain (shared hash table, global hash table, single group)."""
     from paper_2506_10092_gb300 import cq
-    for variant in (0, 1, 2):
+    for variant in (0, 1, 2, 3):
         secs = cq.cq_jit_check(variant)
         assert 0 < secs < 120
     with pytest.raises(cq.CQError) as e:
-        cq.cq_jit_check(3)
+        cq.cq_jit_check(4)
     assert e.value.status == cq.CQ_ERR_INVALID_ARG

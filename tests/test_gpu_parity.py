@@ -272,3 +272,71 @@ def test_single_group_queries(cq, ctx, oracle_mod, seg):
     else:
         plan = dg.Plan(plan.preds, [], [dg.Agg("sum", 0), dg.Agg("count"), dg.Agg("min", 1), dg.Agg("avg", 0)])
     check(run(cq, ctx, table, plan), oracle_mod.query(table, plan, n_threads=4), f"one group seg={seg}")
+
+
+# ------------------------------------------------------------------ long aligned segments (segment mode)
+@pytest.mark.parametrize("case", ["long_runs", "one_run_each", "ends_on_tile_edges", "sparse_index", "no_keys",
+                                  "mixed_lengths"])
+@pytest.mark.parametrize("tile,kernel", [(4096, 2), (8192, 2), (8192, 3)])
+def test_long_segments(cq, ctx, oracle_mod, case, tile, kernel):
+    """Segment mode aggregates a stretch without boundaries in any column once
+    (value x length) and skips its tiles.  Runs far longer than a tile, runs
+    ending exactly on tile edges, a sparse index column cutting the stretches,
+    a plan without GROUP BY, and long runs mixed with short ones: every result
+    equals the oracle's."""
+    rng = np.random.default_rng(abs(hash(case)) % 10_000 + tile)
+    n = 3_000_017
+    if case == "long_runs":
+        cols = [dg.make_rle(rng, n, 40_000.0, 0, 99, np.int64, np.int64),
+                dg.make_rle(rng, n, 90_000.0, 0, 9, np.int32, np.int32)]
+    elif case == "one_run_each":
+        cols = [_rle([42], [n], n), _rle([3], [n], n)]
+    elif case == "ends_on_tile_edges":
+        e1 = sorted(set(list(range(8192 * 3, n, 8192 * 7)) + [n]))
+        e2 = sorted(set(list(range(4096 * 5, n, 4096 * 11)) + [n]))
+        cols = [_rle(rng.integers(0, 99, len(e1)), e1, n), _rle(rng.integers(0, 9, len(e2)), e2, n)]
+    elif case == "sparse_index":
+        pos = np.sort(rng.choice(n, size=40, replace=False)).astype(np.int64)
+        cols = [dg.make_rle(rng, n, 100_000.0, 0, 99, np.int64, np.int64),
+                dg.Index(rng.integers(-5, 5, size=40).astype(np.int64), pos, 7, n)]
+    elif case == "no_keys":
+        cols = [dg.make_rle(rng, n, 60_000.0, 0, 99, np.int64, np.int64),
+                dg.make_rle(rng, n, 25_000.0, 0, 9, np.int64, np.int64)]
+    else:
+        cols = [dg.make_rle(rng, n, 50_000.0, 0, 99, np.int64, np.int64),
+                dg.make_rle(rng, n, 2.0, 0, 9, np.int64, np.int64)]
+    table = dg.Table(cols, n)
+    gb = [] if case == "no_keys" else [1]
+    plan = dg.Plan([dg.Pred(0, "lt", 60)], gb, [dg.Agg("sum", 0), dg.Agg("count"), dg.Agg("min", 1), dg.Agg("max", 0),
+                                               dg.Agg("avg", 1)])
+    ref = oracle_mod.query(table, plan)
+    check(run(cq, ctx, table, plan, opts=cq.exec_options(tile_rows=tile, kernel=kernel)), ref,
+          f"{case} tile {tile} kernel {kernel}")
+    # and as one query of a batch (the persistent kernel's tile walk)
+    t, _cols = cq.table_from(ctx, table)
+    res = cq.cq_batch_run([t, t], [plan, plan])
+    for r in res:
+        check(cq.fetch_all(r), ref, f"{case} batched")
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_segment_mode_walks_agree(cq, ctx, oracle_mod, seed):
+    """Random all-RLE / index tables (run lengths from 1.5 to 5e4 rows, index
+    columns from empty to dense, int32 and int64) walked tile by tile and run
+    by run: both equal the oracle."""
+    rng = np.random.default_rng(11_000 + seed)
+    n = int(rng.choice([1, 777, 8192, 100_001, 1_000_003]))
+    cols = []
+    for _ in range(int(rng.integers(1, 4))):
+        if rng.random() < 0.7:
+            dt = np.int64 if rng.random() < 0.5 else np.int32
+            cols.append(dg.make_rle(rng, n, float(rng.choice([1.5, 7.0, 300.0, 5e4])), -20, 20, dt, dt))
+        else:
+            nnz = int(rng.choice([0, 1, max(1, n // 1000), n // 3, n]))
+            pos = np.sort(rng.choice(n, size=nnz, replace=False)).astype(np.int64)
+            cols.append(dg.Index(rng.integers(-20, 20, size=nnz).astype(np.int64), pos, int(rng.integers(-3, 3)), n))
+    table = dg.Table(cols, n)
+    plan = random_plan(rng, table)
+    ref = oracle_mod.query(table, plan)
+    for kernel in (2, 3):
+        check(run(cq, ctx, table, plan, opts=cq.exec_options(kernel=kernel)), ref, f"seed {seed} kernel {kernel}")

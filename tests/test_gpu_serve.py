@@ -61,12 +61,17 @@ def check(got, ref, msg):
         np.testing.assert_array_equal(g, w, err_msg=f"{msg} output column {i}")
 
 
-@pytest.mark.parametrize("n_streams,max_batch,budget", [(2, 256, 0), (4, 8, 0), (1, 64, 24 << 20)])
-def test_each_result_is_the_same_alone_and_in_the_mix(cq, ctx, tables, oracle_mod, n_streams, max_batch, budget):
+@pytest.mark.parametrize("n_streams,max_batch,budget,large_log2",
+                         [(2, 256, 0, 0), (4, 8, 0, 18), (2, 32, 0, 16), (1, 64, 24 << 20, 0)])
+def test_each_result_is_the_same_alone_and_in_the_mix(cq, ctx, tables, oracle_mod, n_streams, max_batch, budget,
+                                                     large_log2):
+    """Two lanes (large tables alone, small ones batched; large_log2 moves the
+    heterogeneous and nested tables into the large lane) and one lane."""
     rng = np.random.default_rng(1000 + n_streams * 7 + max_batch)
     qs = mix(rng, tables, 120)
     srv = cq.cq_server_create(ctx, cq.server_options(memory_budget_bytes=budget, max_batch=max_batch,
-                                                     n_streams=n_streams, max_wait_us=100))
+                                                     n_streams=n_streams, max_wait_us=100,
+                                                     large_rows_log2=large_log2))
     tickets = [None] * len(qs)
     delays = rng.exponential(200e-6, size=len(qs))          # Poisson arrivals, ~5000 q/s
 
