@@ -4,9 +4,12 @@
 //   1. decompress every referenced column to flat int64 rows (Section 3
 //      encodings; each decoder below is written from the encoding's
 //      definition, not from any fast path);
-//   2. for every row, evaluate the AND of the predicates (Section 6,
-//      selection; predicates on a dictionary column compare the *bytes* of
-//      the row's string with the literal strings);
+//   2. for every row, evaluate each predicate (Section 6, selection;
+//      predicates on a dictionary column compare the *bytes* of the row's
+//      string with the literal strings), complement it when negated, and
+//      combine the truths with the logical operators of Section 5: the
+//      filter program's AND / OR / NOT when the query has one, else the AND
+//      of the conjuncts (an OR group is one conjunct);
 //   3. for a passing row, look its group-by key tuple up in an ordered map
 //      and update SUM (128-bit), COUNT, MIN, MAX (Section 7 aggregating
 //      phase; App. A.2 worked example);
@@ -155,6 +158,8 @@ struct Query {
   uint32_t n_cols;
   const orc_pred* preds;
   uint32_t n_preds;
+  const orc_node* filter;
+  uint32_t n_filter;
   const uint32_t* gb;
   uint32_t n_gb;
   const orc_agg* aggs;
@@ -162,6 +167,7 @@ struct Query {
   std::vector<uint32_t> used;                 // referenced columns
   std::vector<int> slot;                      // column -> position in `used`
   std::vector<std::vector<uint8_t>> str_pass; // per predicate on a DICT column: result per code
+  std::vector<uint32_t> groups;               // distinct nonzero OR groups
 };
 
 bool eval_int(const orc_pred& p, int64_t v) {
@@ -197,6 +203,52 @@ bool eval_str(const orc_pred& p, const uint8_t* s, uint64_t ls) {
       return false;
   }
   return false;
+}
+
+// Truth of predicate i on the row, complemented when it is negated
+// (Section 5.3, NOT of a mask).
+bool atom(const Query& q, uint32_t i, const std::vector<int64_t>& row) {
+  const orc_pred& p = q.preds[i];
+  const int64_t v = row[q.slot[p.col]];
+  const bool t = q.cols[p.col].enc == ORC_DICT ? q.str_pass[i][v] != 0 : eval_int(p, v);
+  return p.negate ? !t : t;
+}
+
+// Whether the row passes the filter: the postfix program over the
+// predicates' truths (Sections 5.1-5.3: AND, OR, NOT of masks) when there is
+// one, else the conjunction of the or_group-0 predicates and, for each
+// group g > 0, the disjunction of its predicates.
+bool row_passes(const Query& q, const std::vector<int64_t>& row, std::vector<uint8_t>& stack) {
+  if (q.n_filter) {
+    stack.clear();
+    for (uint32_t k = 0; k < q.n_filter; ++k) {
+      const orc_node& nd = q.filter[k];
+      if (nd.kind == ORC_NODE_PRED) {
+        stack.push_back(atom(q, nd.arg, row) ? 1 : 0);
+      } else if (nd.kind == ORC_NODE_NOT) {
+        stack.back() = stack.back() ? 0 : 1;
+      } else {
+        const bool is_and = nd.kind == ORC_NODE_AND;
+        bool r = is_and;
+        for (uint32_t j = 0; j < nd.arg; ++j) {
+          const bool x = stack.back() != 0;
+          stack.pop_back();
+          r = is_and ? (r && x) : (r || x);
+        }
+        stack.push_back(r ? 1 : 0);
+      }
+    }
+    return stack.back() != 0;
+  }
+  for (uint32_t i = 0; i < q.n_preds; ++i)
+    if (q.preds[i].or_group == 0 && !atom(q, i, row)) return false;
+  for (uint32_t g : q.groups) {
+    bool any = false;
+    for (uint32_t i = 0; i < q.n_preds && !any; ++i)
+      if (q.preds[i].or_group == g) any = atom(q, i, row);
+    if (!any) return false;
+  }
+  return true;
 }
 
 typedef std::map<std::vector<int64_t>, Acc> GroupMap;
@@ -271,16 +323,10 @@ int scan_chunk(const Query& q, uint64_t rb, uint64_t re, GroupMap& groups) {
   }
   std::vector<int64_t> row(q.used.size());
   std::vector<int64_t> key(q.n_gb);
+  std::vector<uint8_t> stack;
   for (uint64_t r = 0; r < n; ++r) {
     for (size_t u = 0; u < q.used.size(); ++u) row[u] = flat[u][r];
-    bool pass = true;
-    for (uint32_t i = 0; i < q.n_preds && pass; ++i) {
-      const orc_pred& p = q.preds[i];
-      int64_t v = row[q.slot[p.col]];
-      if (q.cols[p.col].enc == ORC_DICT) pass = q.str_pass[i][v] != 0;
-      else pass = eval_int(p, v);
-    }
-    if (!pass) continue;
+    if (!row_passes(q, row, stack)) continue;
     for (uint32_t k = 0; k < q.n_gb; ++k) key[k] = row[q.slot[q.gb[k]]];
     update(q, groups[key], row);
   }
@@ -291,12 +337,39 @@ int scan_chunk(const Query& q, uint64_t rb, uint64_t re, GroupMap& groups) {
 
 extern "C" int orc_query(const orc_column* cols, uint32_t n_cols, uint64_t n_rows,
                          const orc_pred* preds, uint32_t n_preds,
+                         const orc_node* filter, uint32_t n_filter,
                          const uint32_t* group_by, uint32_t n_group_by,
                          const orc_agg* aggs, uint32_t n_aggs,
                          const uint64_t* row_ranges, uint32_t n_ranges,
                          uint32_t n_threads, orc_result** out) {
   *out = nullptr;
-  Query q{cols, n_cols, preds, n_preds, group_by, n_group_by, aggs, n_aggs, {}, {}, {}};
+  Query q{cols, n_cols, preds, n_preds, filter, n_filter, group_by, n_group_by, aggs, n_aggs, {}, {}, {}, {}};
+  // the filter program must be well formed: every operand present, one
+  // value left; OR groups are not combined with a program
+  if (n_filter && !filter) return ORC_ERR_ARG;
+  {
+    uint32_t depth = 0;
+    for (uint32_t k = 0; k < n_filter; ++k) {
+      const orc_node& nd = filter[k];
+      if (nd.kind == ORC_NODE_PRED) {
+        if (nd.arg >= n_preds) return ORC_ERR_ARG;
+        ++depth;
+      } else if (nd.kind == ORC_NODE_NOT) {
+        if (depth < 1) return ORC_ERR_ARG;
+      } else if (nd.kind == ORC_NODE_AND || nd.kind == ORC_NODE_OR) {
+        if (nd.arg < 1 || nd.arg > depth) return ORC_ERR_ARG;
+        depth -= nd.arg - 1;
+      } else {
+        return ORC_ERR_ARG;
+      }
+    }
+    if (n_filter && depth != 1) return ORC_ERR_ARG;
+  }
+  for (uint32_t i = 0; i < n_preds; ++i) {
+    const uint32_t g = preds[i].or_group;
+    if (g && n_filter) return ORC_ERR_ARG;
+    if (g && std::find(q.groups.begin(), q.groups.end(), g) == q.groups.end()) q.groups.push_back(g);
+  }
   q.slot.assign(n_cols, -1);
   auto use = [&](uint32_t c) {
     if (c >= n_cols) return false;

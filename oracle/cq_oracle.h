@@ -66,7 +66,21 @@ typedef struct {
   const uint8_t* const* strs;     /* string literals on a DICT column */
   const uint32_t* str_lens;
   uint32_t n_strs;
+  uint32_t or_group;              /* 0: a conjunct of its own; g > 0: OR-ed with every other
+                                     predicate of group g, the group being one conjunct */
+  uint32_t negate;                /* nonzero: the predicate is replaced by its complement (NOT) */
 } orc_pred;
+
+/* A boolean filter over the predicates as a postfix program (Section 5:
+ * logical AND, OR, NOT of mask columns).  PRED pushes predicate `arg`'s
+ * truth (its negate flag applied); AND / OR pop `arg` >= 1 values and push
+ * their conjunction / disjunction; NOT replaces the top value by its
+ * complement.  The program must leave exactly one value. */
+enum { ORC_NODE_PRED = 0, ORC_NODE_AND = 1, ORC_NODE_OR = 2, ORC_NODE_NOT = 3 };
+typedef struct {
+  int32_t kind;
+  uint32_t arg;
+} orc_node;
 
 typedef struct {
   int32_t op;
@@ -78,11 +92,16 @@ typedef struct orc_result orc_result;
 /* Decode rows [row_begin, row_end) of one column to int64 (DICT: codes). */
 int orc_decode(const orc_column* c, uint64_t row_begin, uint64_t row_end, int64_t* out);
 
-/* Evaluate the query.  row_ranges (optional, n_ranges pairs [b,e) in row
- * order) restricts the scan to those rows; n_threads >= 1 splits the scan
- * into fixed 1M-row chunks whose per-chunk maps are merged exactly. */
+/* Evaluate the query.  Without a filter program (n_filter == 0) a row
+ * passes when every conjunct holds: each predicate with or_group 0, and for
+ * every group g > 0 at least one of its predicates.  With one, a row passes
+ * when the program yields true (or_group must then be 0 everywhere).
+ * row_ranges (optional, n_ranges pairs [b,e) in row order) restricts the
+ * scan to those rows; n_threads >= 1 splits the scan into fixed 1M-row
+ * chunks whose per-chunk maps are merged exactly. */
 int orc_query(const orc_column* cols, uint32_t n_cols, uint64_t n_rows,
               const orc_pred* preds, uint32_t n_preds,
+              const orc_node* filter, uint32_t n_filter,
               const uint32_t* group_by, uint32_t n_group_by,
               const orc_agg* aggs, uint32_t n_aggs,
               const uint64_t* row_ranges, uint32_t n_ranges,

@@ -39,7 +39,15 @@ class _Pred(C.Structure):
         ("col", C.c_uint32), ("op", C.c_int32), ("lo", C.c_int64), ("hi", C.c_int64),
         ("in_ints", C.c_void_p), ("n_in", C.c_uint32),
         ("strs", C.c_void_p), ("str_lens", C.c_void_p), ("n_strs", C.c_uint32),
+        ("or_group", C.c_uint32), ("negate", C.c_uint32),
     ]
+
+
+class _Node(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("arg", C.c_uint32)]
+
+
+_NODES = {"pred": 0, "and": 1, "or": 2, "not": 3}
 
 
 class _Agg(C.Structure):
@@ -58,7 +66,7 @@ def lib():
             L = C.CDLL(path)
             L.orc_decode.argtypes = [C.POINTER(_Col), C.c_uint64, C.c_uint64, C.c_void_p]
             L.orc_query.argtypes = [C.POINTER(_Col), C.c_uint32, C.c_uint64, C.POINTER(_Pred), C.c_uint32,
-                                    C.c_void_p, C.c_uint32, C.POINTER(_Agg), C.c_uint32,
+                                    C.POINTER(_Node), C.c_uint32, C.c_void_p, C.c_uint32, C.POINTER(_Agg), C.c_uint32,
                                     C.c_void_p, C.c_uint32, C.c_uint32, C.POINTER(C.c_void_p)]
             L.orc_result_status.argtypes = [C.c_void_p]
             L.orc_result_num_groups.argtypes = [C.c_void_p]
@@ -118,6 +126,7 @@ class _Marshal:
     def pred(self, p) -> _Pred:
         s = _Pred()
         s.col, s.op, s.lo, s.hi = int(p.col), _OPS[p.op], int(p.lo), int(p.hi)
+        s.or_group, s.negate = int(getattr(p, "group", 0)), 1 if getattr(p, "neg", False) else 0
         if p.ints is not None:
             a = self.k(_i64(list(p.ints)))
             s.in_ints, s.n_in = _p(a), int(a.shape[0])
@@ -147,6 +156,8 @@ def query(table, plan, row_ranges=None, n_threads: int = 1) -> OracleResult:
     cols = (_Col * len(table.columns))(*[m.column(c) for c in table.columns])
     preds = (_Pred * max(1, len(plan.preds)))(*[m.pred(p) for p in plan.preds])
     aggs = (_Agg * max(1, len(plan.aggs)))(*[_Agg(_AGGS[a.op], int(a.col)) for a in plan.aggs])
+    prog = list(getattr(plan, "filter", None) or [])
+    nodes = (_Node * max(1, len(prog)))(*[_Node(_NODES[k], int(a)) for k, a in prog])
     gb = m.k(np.array(list(plan.group_by) or [0], dtype=np.uint32))
     rr = None
     nr = 0
@@ -154,7 +165,7 @@ def query(table, plan, row_ranges=None, n_threads: int = 1) -> OracleResult:
         rr = m.k(np.ascontiguousarray(np.asarray(row_ranges, dtype=np.uint64).reshape(-1)))
         nr = rr.shape[0] // 2
     out = C.c_void_p()
-    rc = L.orc_query(cols, len(table.columns), int(table.n_rows), preds, len(plan.preds),
+    rc = L.orc_query(cols, len(table.columns), int(table.n_rows), preds, len(plan.preds), nodes, len(prog),
                      gb.ctypes.data, len(plan.group_by), aggs, len(plan.aggs),
                      None if rr is None else rr.ctypes.data, nr, int(n_threads), C.byref(out))
     if rc != 0:

@@ -26,7 +26,7 @@ vector, which is the padding the C-ABI asks of borrowed device buffers.
 from __future__ import annotations
 
 import dataclasses
-from typing import List, Optional, Sequence
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -111,6 +111,8 @@ class Pred:
     hi: int = 0
     ints: Optional[Sequence[int]] = None      # IN list on integer columns
     strs: Optional[Sequence[bytes]] = None    # literals on dictionary columns
+    group: int = 0                  # 0: a conjunct of its own; g > 0: OR-ed with group g's others
+    neg: bool = False               # the predicate's complement (NOT)
 
 
 @dataclasses.dataclass
@@ -124,6 +126,13 @@ class Plan:
     preds: List[Pred]
     group_by: List[int]
     aggs: List[Agg]
+    # optional boolean filter over the predicates, postfix: ("pred", i),
+    # ("and", k), ("or", k) (pop k >= 1 values), ("not", 0); None = the AND
+    # of the conjuncts
+    filter: Optional[List[Tuple[str, int]]] = None
+
+
+FILTER_NODES = {"pred": 0, "and": 1, "or": 2, "not": 3}
 
 
 # --------------------------------------------------------------------------

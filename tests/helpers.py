@@ -1,6 +1,8 @@
 """Small table builders shared by the tests (no query arithmetic here)."""
 from __future__ import annotations
 
+import dataclasses
+
 import numpy as np
 
 from paper_2506_10092_gb300 import datagen as dg
@@ -87,3 +89,38 @@ def random_plan(rng, table, n_preds=None, n_gb=None, allow=("sum", "count", "min
             ops = [o for o in ops if o in ("min", "max")] or ["count"]
         aggs.append(dg.Agg(str(rng.choice(ops)), c))
     return dg.Plan(preds, gb, aggs)
+
+
+def random_tree(rng, n_preds, max_depth=3):
+    """A random boolean expression over predicates 0..n_preds-1 as a postfix
+    program of ("pred", i), ("not", 0), ("and", k), ("or", k) nodes."""
+    out = []
+
+    def build(d):
+        r = rng.random()
+        if d == 0 or r < 0.3:
+            out.append(("pred", int(rng.integers(0, n_preds))))
+            if rng.random() < 0.3:
+                out.append(("not", 0))
+        elif r < 0.4:
+            build(d - 1)
+            out.append(("not", 0))
+        else:
+            k = int(rng.integers(1, 4))
+            for _ in range(k):
+                build(d - 1)
+            out.append((str(rng.choice(["and", "or"])), k))
+
+    build(max_depth)
+    return out
+
+
+def random_or_groups(rng, preds):
+    """The predicates with random OR groups (0 = a conjunct of its own) and
+    random negation."""
+    out = []
+    for p in preds:
+        g = int(rng.integers(0, 3))
+        out.append(dataclasses.replace(p, group=g, neg=bool(rng.random() < 0.35)))
+    return out
+

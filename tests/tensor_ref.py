@@ -63,15 +63,48 @@ def _pred_mask(col, vals, p) -> np.ndarray:
     return np.array([ops[p.op](int(v)) for v in vals], dtype=bool)
 
 
+def filter_mask(plan, masks, n) -> np.ndarray:
+    """Combine Plain masks with the logical operators of Section 5 (``&``,
+    ``|``, ``~``): each predicate's mask is complemented when negated; a
+    filter program is run on a stack of masks, else the masks of or_group 0
+    and the OR of each group's masks are AND-ed."""
+    masks = [~m if getattr(p, "neg", False) else m for p, m in zip(plan.preds, masks)]
+    prog = getattr(plan, "filter", None)
+    if prog:
+        st = []
+        for kind, arg in prog:
+            if kind == "pred":
+                st.append(masks[arg])
+            elif kind == "not":
+                st.append(~st.pop())
+            else:
+                top = [st.pop() for _ in range(arg)]
+                acc = top[0]
+                for m in top[1:]:
+                    acc = (acc & m) if kind == "and" else (acc | m)
+                st.append(acc)
+        assert len(st) == 1
+        return st[0]
+    out = np.ones(n, dtype=bool)
+    groups = {}
+    for p, m in zip(plan.preds, masks):
+        g = getattr(p, "group", 0)
+        if g == 0:
+            out &= m
+        else:
+            groups[g] = groups[g] | m if g in groups else m
+    for m in groups.values():
+        out &= m
+    return out
+
+
 def query(table, plan):
     """Returns (keys: list of int arrays, aggs: list of arrays, overflow: bool)."""
     n = table.n_rows
     flat = {}
     for i in set([p.col for p in plan.preds] + list(plan.group_by) + [a.col for a in plan.aggs if a.op != "count"]):
         flat[i] = decode(table.columns[i])
-    mask = np.ones(n, dtype=bool)
-    for p in plan.preds:
-        mask &= _pred_mask(table.columns[p.col], flat[p.col], p)
+    mask = filter_mask(plan, [_pred_mask(table.columns[p.col], flat[p.col], p) for p in plan.preds], n)
     rows = np.flatnonzero(mask)
     if plan.group_by:
         if len(rows):
