@@ -156,11 +156,28 @@ int cq_table_destroy(cq_table* table);
 int cq_table_num_rows(const cq_table* table, uint64_t* n_rows);
 
 /* ------------------------------------------------------------------ plans
- * A plan is the conjunction (AND) of predicates, each on one column, then
- * GROUP BY the listed columns and the listed aggregates (Sections 6-7).
- * Predicates on a dictionary column take string literals (strs); predicates
- * on every other column take integer literals compared with the row's
- * logical value.  Literals absent from a dictionary simply match nothing. */
+ * A plan is a filter over predicates, each on one column, then GROUP BY the
+ * listed columns and the listed aggregates (Sections 6-7).  Predicates on a
+ * dictionary column take string literals (strs); predicates on every other
+ * column take integer literals compared with the row's logical value.
+ * Literals absent from a dictionary simply match nothing.
+ *
+ * The filter combines the predicates with the logical operators of
+ * Section 5 (AND, OR, NOT of masks) in one of two forms:
+ *  - conjunctive (filter == NULL): a row passes when every conjunct holds.
+ *    A predicate with or_group 0 is a conjunct of its own; the predicates
+ *    sharing an or_group g > 0 form one conjunct, their OR.  A predicate
+ *    with negate != 0 stands for its complement (NOT), taken before the OR.
+ *    All predicates with or_group 0 and negate 0 is the plain AND.
+ *  - a program (n_filter > 0): an expression tree over the predicates in
+ *    postfix order (below); or_group must then be 0 on every predicate,
+ *    negate still complements a predicate where it appears.  The library
+ *    rewrites it to the conjunctive form (NOT moved to the predicates by
+ *    De Morgan's laws, AND distributed over OR, repeated literals, clauses
+ *    that always hold and clauses that contain another clause dropped);
+ *    predicates the program does not name play no part.
+ * The kernels evaluate at most 16 predicate occurrences in conjunctive
+ * form; a program that needs more fails with CQ_ERR_UNSUPPORTED. */
 typedef enum {
   CQ_LT = 0, CQ_LE = 1, CQ_GT = 2, CQ_GE = 3, CQ_EQ = 4, CQ_NE = 5,
   CQ_BETWEEN = 6,  /* lo <= v <= hi (strings: strs[0] <= s <= strs[1]) */
@@ -176,7 +193,21 @@ typedef struct {
   const char* const* strs;      /* string literals on a dictionary column (host) */
   const uint32_t* str_lens;     /* byte length of each literal; NULL = NUL-terminated */
   uint32_t n_strs;
+  uint32_t or_group;            /* conjunctive form: 0 = a conjunct of its own; g > 0 = OR-ed
+                                   with the plan's other predicates of group g */
+  uint32_t negate;              /* nonzero: the predicate's complement (NOT) */
 } cq_predicate;
+
+/* One node of a filter program, in postfix order: PRED pushes predicate
+ * `arg`'s truth for the row; AND / OR pop `arg` >= 1 values and push their
+ * conjunction / disjunction; NOT complements the top value.  The program
+ * must leave exactly one value; at most 64 nodes. */
+typedef enum { CQ_NODE_PRED = 0, CQ_NODE_AND = 1, CQ_NODE_OR = 2, CQ_NODE_NOT = 3 } cq_node_kind;
+
+typedef struct {
+  int32_t kind;                 /* cq_node_kind */
+  uint32_t arg;                 /* PRED: predicate index; AND / OR: operand count; NOT: unused */
+} cq_filter_node;
 
 typedef enum { CQ_SUM = 0, CQ_COUNT = 1, CQ_MIN = 2, CQ_MAX = 3, CQ_AVG = 4 } cq_agg_op;
 
@@ -189,6 +220,8 @@ typedef struct {
   const cq_predicate* preds;  uint32_t n_preds;     /* <= 16 */
   const uint32_t* group_by;   uint32_t n_group_by;  /* <= 8 */
   const cq_aggregate* aggs;   uint32_t n_aggs;      /* <= 16 */
+  const cq_filter_node* filter; uint32_t n_filter;  /* optional filter program (host); 0 = the
+                                                       conjunctive form */
 } cq_plan;
 
 /* Execution choices; zero-initialise for the defaults. */
@@ -225,6 +258,17 @@ typedef struct {
 } cq_exec_options;
 
 /* ------------------------------------------------------------------ queries */
+
+/* The conjunctive form the kernels evaluate for a plan's filter, computed on
+ * the host (no device work): the predicate occurrences with or_group and
+ * negate set, copied to out[0 .. *n_out).  The copies' literal pointers
+ * (in_ints, strs, str_lens) still point into the caller's plan.  A plan
+ * without a filter program comes back as given.  *n_out is set whenever the
+ * program is valid, also when it exceeds cap (then CQ_ERR_INVALID_ARG).
+ * Errors: CQ_ERR_INVALID_ARG (malformed program, or_group set beside a
+ * program), CQ_ERR_UNSUPPORTED (more than 16 occurrences, or an expansion
+ * beyond the work limit). */
+int cq_filter_conjunctive(const cq_plan* plan, cq_predicate* out, uint32_t cap, uint32_t* n_out);
 
 /* Plan the query on `table` and enqueue its kernels on `cuda_stream`
  * (NULL: the context's stream).  Asynchronous: returns once the work is
@@ -406,6 +450,8 @@ int cq_jit_check(uint32_t variant, double* seconds);
  *  - one lane (n_streams == 1): every query is batched, a batch launched
  *    when nothing runs, max_batch queries wait or the oldest has waited
  *    max_wait_us;
+ *  - a query a batch cannot take (a key domain above 2^24 groups, a table
+ *    above 2^31 rows) joins the large lane with either setting;
  *  - completion: launches in flight are polled; a finished query's result
  *    and latency (submission to observed completion) go to cq_server_wait.
  * Each query's result equals its cq_query_run result exactly. */

@@ -42,7 +42,16 @@ class CQError(RuntimeError):
 class cq_predicate(C.Structure):
     _fields_ = [("col", C.c_uint32), ("op", C.c_int32), ("lo", C.c_int64), ("hi", C.c_int64),
                 ("in_ints", C.c_void_p), ("n_in", C.c_uint32),
-                ("strs", C.c_void_p), ("str_lens", C.c_void_p), ("n_strs", C.c_uint32)]
+                ("strs", C.c_void_p), ("str_lens", C.c_void_p), ("n_strs", C.c_uint32),
+                ("or_group", C.c_uint32), ("negate", C.c_uint32)]
+
+
+class cq_filter_node(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("arg", C.c_uint32)]
+
+
+CQ_NODE_PRED, CQ_NODE_AND, CQ_NODE_OR, CQ_NODE_NOT = 0, 1, 2, 3
+NODES = {"pred": CQ_NODE_PRED, "and": CQ_NODE_AND, "or": CQ_NODE_OR, "not": CQ_NODE_NOT}
 
 
 class cq_aggregate(C.Structure):
@@ -52,7 +61,8 @@ class cq_aggregate(C.Structure):
 class cq_plan(C.Structure):
     _fields_ = [("preds", C.c_void_p), ("n_preds", C.c_uint32),
                 ("group_by", C.c_void_p), ("n_group_by", C.c_uint32),
-                ("aggs", C.c_void_p), ("n_aggs", C.c_uint32)]
+                ("aggs", C.c_void_p), ("n_aggs", C.c_uint32),
+                ("filter", C.c_void_p), ("n_filter", C.c_uint32)]
 
 
 class cq_exec_options(C.Structure):
@@ -87,6 +97,7 @@ _SIGS = {
     "cq_table_bind": [_VP, _VP, C.c_uint32, C.POINTER(_VP)],
     "cq_table_destroy": [_VP],
     "cq_table_num_rows": [_VP, C.POINTER(C.c_uint64)],
+    "cq_filter_conjunctive": [C.POINTER(cq_plan), _VP, C.c_uint32, C.POINTER(C.c_uint32)],
     "cq_query_run": [_VP, C.POINTER(cq_plan), _VP, C.POINTER(_VP)],
     "cq_query_run_ex": [_VP, C.POINTER(cq_plan), C.POINTER(cq_exec_options), _VP, C.POINTER(_VP)],
     "cq_batch_run": [C.c_uint32, _VP, _VP, C.POINTER(cq_exec_options), _VP, _VP],
@@ -291,6 +302,7 @@ class PlanStruct:
         for i, p in enumerate(plan.preds):
             s = preds[i]
             s.col, s.op, s.lo, s.hi = int(p.col), OPS[p.op], int(p.lo), int(p.hi)
+            s.or_group, s.negate = int(getattr(p, "group", 0)), 1 if getattr(p, "neg", False) else 0
             if p.ints is not None:
                 a = np.ascontiguousarray(np.asarray(list(p.ints), dtype=np.int64))
                 self.keep.append(a)
@@ -303,9 +315,11 @@ class PlanStruct:
                 s.strs, s.str_lens, s.n_strs = C.addressof(ptrs), lens.ctypes.data, len(bufs)
         gb = np.array(list(plan.group_by) or [0], dtype=np.uint32)
         aggs = (cq_aggregate * max(1, len(plan.aggs)))(*[cq_aggregate(AGGS[a.op], int(a.col)) for a in plan.aggs])
-        self.keep += [preds, gb, aggs]
+        prog = list(getattr(plan, "filter", None) or [])
+        nodes = (cq_filter_node * max(1, len(prog)))(*[cq_filter_node(NODES[k], int(a)) for k, a in prog])
+        self.keep += [preds, gb, aggs, nodes]
         self.s = cq_plan(C.addressof(preds), len(plan.preds), gb.ctypes.data, len(plan.group_by),
-                         C.addressof(aggs), len(plan.aggs))
+                         C.addressof(aggs), len(plan.aggs), C.addressof(nodes) if prog else None, len(prog))
         self.plan = plan
 
 
@@ -318,6 +332,26 @@ def exec_options(mode=CQ_EXEC_FUSED, tile_rows=0, ctas_per_sm=0, stages=0, table
     o.mode, o.tile_rows, o.ctas_per_sm, o.stages, o.table_slots = mode, tile_rows, ctas_per_sm, stages, table_slots
     o.grid_ctas, o.items_per_cta, o.kernel, o.hash_slots_log2 = grid_ctas, items_per_cta, kernel, hash_slots_log2
     return o
+
+
+def cq_filter_conjunctive(plan: dg.Plan):
+    """The conjunctive form of a plan's filter (host only): a list of
+    (index of the plan predicate it copies, or_group, negate); the copies
+    are matched to the plan's predicates by identity of their fields."""
+    ps = PlanStruct(plan)
+    cap = 16
+    out = (cq_predicate * cap)()
+    n = C.c_uint32()
+    _check(lib.cq_filter_conjunctive(C.byref(ps.s), C.addressof(out), cap, C.byref(n)))
+    src = (cq_predicate * max(1, len(plan.preds))).from_address(ps.s.preds)
+    res = []
+    for i in range(n.value):
+        o = out[i]
+        idx = next(j for j in range(len(plan.preds))
+                   if (src[j].col, src[j].op, src[j].lo, src[j].hi, src[j].in_ints, src[j].strs)
+                   == (o.col, o.op, o.lo, o.hi, o.in_ints, o.strs))
+        res.append((idx, int(o.or_group), int(o.negate)))
+    return res
 
 
 def cq_jit_check(variant: int) -> float:

@@ -692,7 +692,28 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   if (q.stages < 1 || q.stages > 8) return set_error(CQ_ERR_INVALID_ARG, "stages must be in 1..8");
   auto& aux = P->aux;
   // ---- predicates
+  // Clauses of the conjunctive form (Section 5 AND / OR / NOT): a predicate
+  // with or_group 0 is a clause alone, the predicates of one nonzero group
+  // share a clause.  Only a plain conjunct (a clause of one predicate, not
+  // negated) restricts every passing row, so only such predicates narrow a
+  // key's domain or remap its digits below.
   q.n_preds = (uint8_t)plan->n_preds;
+  std::vector<int> clause_of(plan->n_preds, -1), clause_size;
+  for (uint32_t i = 0; i < plan->n_preds; ++i) {
+    const uint32_t g = plan->preds[i].or_group;
+    if (g)
+      for (uint32_t j = 0; j < i; ++j)
+        if (plan->preds[j].or_group == g) {
+          clause_of[i] = clause_of[j];
+          break;
+        }
+    if (clause_of[i] < 0) {
+      clause_of[i] = (int)clause_size.size();
+      clause_size.push_back(0);
+    }
+    clause_size[clause_of[i]]++;
+  }
+  auto plain_conjunct = [&](uint32_t i) { return clause_size[clause_of[i]] == 1 && !plan->preds[i].negate; };
   std::vector<int> in_pred_of_col(q.n_cols, -1);
   std::vector<int> in_count(q.n_cols, 0);
   for (uint32_t i = 0; i < plan->n_preds; ++i) {
@@ -702,6 +723,8 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     const ColDesc& cd = q.cols[ci];
     PredDesc& d = q.preds[i];
     d.col = (uint8_t)ci;
+    d.neg = p.negate ? 1 : 0;
+    d.clause = 0;
     if (p.op < CQ_LT || p.op > CQ_IN) return set_error(CQ_ERR_INVALID_ARG, "predicate %u: bad op %d", i, p.op);
     if (is_dict(pc)) {
       const cq_column* dc = pc.src;
@@ -734,8 +757,10 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
             if (a < b) codes.push_back(a);
           }
           set_members(d, codes, aux);
-          in_pred_of_col[ci] = (int)i;
-          in_count[ci]++;
+          if (plain_conjunct(i)) {
+            in_pred_of_col[ci] = (int)i;
+            in_count[ci]++;
+          }
           break;
         }
       }
@@ -764,8 +789,10 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
           if (r >= m.rmin && r <= m.rmax) vals.push_back((int64_t)r);
         }
         set_members(d, vals, aux);
-        in_pred_of_col[ci] = (int)i;
-        in_count[ci]++;
+        if (plain_conjunct(i)) {
+          in_pred_of_col[ci] = (int)i;
+          in_count[ci]++;
+        }
         break;
       }
     }
@@ -803,6 +830,14 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       d.lo32 = (int32_t)d.lo;
       d.hi32 = (int32_t)d.hi;
       d.n32 = 1;
+    }
+  }
+  // a complemented constant is the other constant
+  for (uint32_t i = 0; i < plan->n_preds; ++i) {
+    PredDesc& d = q.preds[i];
+    if (d.neg && (d.kind == PK_TRUE || d.kind == PK_FALSE)) {
+      d.kind = d.kind == PK_TRUE ? PK_FALSE : PK_TRUE;
+      d.neg = 0;
     }
   }
   // ---- group keys (dense mixed radix, first key most significant)
@@ -854,7 +889,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       // a range predicate on the key column narrows its domain
       for (uint32_t i = 0; i < plan->n_preds; ++i) {
         const PredDesc& pd = q.preds[i];
-        if (pd.col != ci) continue;
+        if (pd.col != ci || !plain_conjunct(i)) continue;
         if (pd.kind == PK_RANGE) { lo = std::max(lo, (i128)pd.lo); hi = std::min(hi, (i128)pd.hi); }
         if (pd.kind == PK_BITMAP) { lo = std::max(lo, (i128)pd.lo); hi = std::min(hi, (i128)pd.hi); }
       }
@@ -907,6 +942,9 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   // evaluates per segment.  The descriptors are reordered in place (the keys
   // above copied what they needed): pass-bitmap predicates, other RLE /
   // index predicates, the rest.
+  // A clause's predicates stay adjacent, the clause ordered by its cheapest
+  // member, and its last member marked: the filter ORs a clause's members,
+  // then ANDs the clause in.
   {
     q.n_pbm = 0;
     int cls[kMaxPreds];
@@ -919,11 +957,20 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
         d.pbm = q.n_pbm++;
       cls[i] = d.pbm != 0xFF ? 0 : run_col ? 1 : 2;
     }
+    std::vector<int> ccls(clause_size.size(), 3);
+    for (uint32_t i = 0; i < plan->n_preds; ++i) ccls[clause_of[i]] = std::min(ccls[clause_of[i]], cls[i]);
     PredDesc sorted[kMaxPreds];
     uint32_t k = 0;
     for (int c = 0; c < 3; ++c)
-      for (uint32_t i = 0; i < plan->n_preds; ++i)
-        if (cls[i] == c) sorted[k++] = q.preds[i];
+      for (size_t cl = 0; cl < clause_size.size(); ++cl) {
+        if (ccls[cl] != c) continue;
+        const uint32_t first = k;
+        for (int m = 0; m < 3; ++m)
+          for (uint32_t i = 0; i < plan->n_preds; ++i)
+            if (clause_of[i] == (int)cl && cls[i] == m) sorted[k++] = q.preds[i];
+        for (uint32_t j = first; j < k; ++j)
+          sorted[j].clause = k - first == 1 ? PC_ALONE : (j + 1 == k ? PC_LAST : PC_MEMBER);
+      }
     for (uint32_t i = 0; i < k; ++i) q.preds[i] = sorted[i];
   }
   // ---- table shape and flush period
@@ -1097,9 +1144,14 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
 // in shared memory (the order is given where the shapes are listed below);
 // tiles halve down to 1024 rows.  Options pin the tile size (smaller ones are
 // tried when it does not fit) and / or the CTAs per SM.
-static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan,
+static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const cq_plan* plan_in,
                       const cq_exec_options* opts, const cq_ctx* ctx, Planned* P, size_t batch_limit = 0) {
-  if (!plan) return set_error(CQ_ERR_INVALID_ARG, "plan is NULL");
+  if (!plan_in) return set_error(CQ_ERR_INVALID_ARG, "plan is NULL");
+  // a filter program becomes its conjunctive form (cq_filter.cu)
+  NormFilter nf;
+  const int nrc = normalize_filter(plan_in, &nf);
+  if (nrc != CQ_OK) return nrc;
+  const cq_plan* plan = &nf.plan;
   const uint32_t want_tile = opts ? opts->tile_rows : 0;
   const uint32_t want_ctas = opts ? opts->ctas_per_sm : 0;
   if (want_tile && (want_tile < 1024 || want_tile > 8192 || (want_tile & (want_tile - 1))))
@@ -1324,6 +1376,7 @@ int launch_solo(cq_table* table, Planned& P, cudaStream_t s, cq_result** out) {
     free_result(r);
     return rc;
   }
+  if (P.q.ghash) r->retry.reset(new Planned(P));   // cq_result_wait may relaunch it larger
   for (int kc : P.out_key_col) r->key_cols.push_back(kc >= 0 ? table->cols[kc] : nullptr);
   for (cq_column* c : table->cols) c->refs++;
   r->held_cols = table->cols;

@@ -65,12 +65,20 @@ struct ColDesc {
   uint64_t n;        // RLE n_runs | INDEX nnz | PACKED/DICT n_words | PLAIN n_rows
 };
 
+// A predicate's place in its clause of the conjunctive filter: a clause of
+// its own (AND-ed in directly), or a member OR-ed into the clause, the last
+// member then AND-ing the clause in.
+enum { PC_ALONE = 0, PC_MEMBER = 1, PC_LAST = 2 };
+
 struct PredDesc {
   uint8_t col;       // index into QueryDesc::cols
   uint8_t kind;
   uint8_t n32;       // raw values and bounds fit int32: evaluate in 32 bits (lo32 / hi32)
   uint8_t pbm;       // row mode, RLE / index column: slot of the tile pass bitmap the helper
                      // warp fills once per run / listed row (0xFF: evaluated per row)
+  uint8_t neg;       // the complement of the test (NOT); pass bitmaps hold the complement
+  uint8_t clause;    // PC_ALONE / PC_MEMBER / PC_LAST
+  uint8_t pad_[2];
   uint32_t aux_off;  // 32-bit words into the aux area (bitmap or list of int64 as word pairs)
   uint32_t aux_len;  // bitmap words / list entries
   int32_t lo32, hi32;

@@ -19,7 +19,8 @@
 // (groups in the global hash table, 64-bit packed keys); per
 // column c: enc, v64, e64, bw, bslot, raw_off, stage_off; bcol(j), the
 // column of bitmap slot j; row_col(i), the i-th staged column; per predicate
-// i (evaluation order): pcol, pkind, pn32, ppbm;
+// i (evaluation order): pcol, pkind, pn32, ppbm, pneg (complemented), pcl
+// (PC_ALONE / PC_MEMBER / PC_LAST: its place in its clause);
 // per key k: kcol, kremap, kn32; per aggregate i: akind, acol, asw, awide,
 // asw32, agw, ared32, aw32, an32, as32, asrc (the first aggregate reading the
 // same column value, whose read is reused).
@@ -142,27 +143,42 @@ struct GroupReader {
 };
 
 // ------------------------------------------------------------------ filter
-// Bit g of the result: row wbase + g * GS + lane passes every predicate.
+// Bit g of the result: row wbase + g * GS + lane passes the filter, the
+// conjunction of clauses (Section 5: AND, OR, NOT).  A predicate alone in
+// its clause ANDs its result into the mask directly; a clause's members OR
+// theirs into `acc`, which the last member ANDs in.  A complemented
+// predicate's test is inverted here; its pass bitmap already holds the
+// complement.
 template <class S, uint32_t GS, int GPW>
 __device__ __forceinline__ uint32_t fast_filter(const QueryDesc& q, const TileView& t, uint32_t wbase, uint32_t rows) {
   const int lane = threadIdx.x & 31;
   uint32_t valid = 0;
 #pragma unroll
   for (int g = 0; g < GPW; ++g) valid |= (wbase + g * GS + lane < rows ? 1u : 0u) << g;
-  uint32_t pm = valid;
+  uint32_t pm = valid, acc = 0;
   static_for<S::n_preds>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int kind = S::pkind(i);
     constexpr int c = S::pcol(i);
     constexpr int E = S::enc(c);
+    constexpr int cl = S::pcl(i);
+    constexpr bool ng = S::pneg(i);
+    // row group g's result for this predicate (`ok` before any complement)
+    auto put = [&](int g, bool ok, bool complement) {
+      if (complement) ok = !ok;
+      if constexpr (cl == PC_ALONE) pm &= ok ? ~0u : ~(1u << g);
+      else acc |= (ok ? 1u : 0u) << g;
+    };
     if constexpr (S::ppbm(i) != 0xFF) {
       // evaluated once per run / listed row by the helper warp: one bit per row
       const uint32_t* PB = t.pbm + (size_t)S::ppbm(i) * (S::tile_rows / 32);
 #pragma unroll
-      for (int g = 0; g < GPW; ++g) pm &= ((PB[(wbase + g * GS) >> 5] >> lane) & 1u) ? ~0u : ~(1u << g);
+      for (int g = 0; g < GPW; ++g) put(g, (PB[(wbase + g * GS) >> 5] >> lane) & 1u, false);
     } else if constexpr (kind == PK_FALSE) {
-      pm = 0;
-    } else if constexpr (kind != PK_TRUE) {
+      if constexpr (cl == PC_ALONE) pm = 0;
+    } else if constexpr (kind == PK_TRUE) {
+      if constexpr (cl != PC_ALONE) acc = ~0u;
+    } else {
       if (!__any_sync(0xFFFFFFFFu, pm != 0)) return;
       const PredDesc& p = q.preds[i];
       if constexpr (E == ENC_RLE || E == ENC_INDEX) {
@@ -183,7 +199,7 @@ __device__ __forceinline__ uint32_t fast_filter(const QueryDesc& q, const TileVi
             else if constexpr (kind == PK_BITMAP) ok = pred_test<PT_BITMAP>(p, t.aux, v);
             else ok = pred_test<PT_LIST>(p, t.aux, v);
           }
-          pm &= ok ? ~0u : ~(1u << g);
+          put(g, ok, ng);
         }
       } else {
         const GroupReader<S, c, GS> rd(t, wbase);
@@ -202,7 +218,7 @@ __device__ __forceinline__ uint32_t fast_filter(const QueryDesc& q, const TileVi
               const uint32_t d = v - lo;
               ok = d <= span && ((bm[d >> 5] >> (d & 31)) & 1u);
             }
-            pm &= ok ? ~0u : ~(1u << g);
+            put(g, ok, ng);
           }
         } else {
 #pragma unroll 4
@@ -213,10 +229,14 @@ __device__ __forceinline__ uint32_t fast_filter(const QueryDesc& q, const TileVi
             else if constexpr (kind == PK_NE) ok = pred_test<PT_NE>(p, t.aux, v);
             else if constexpr (kind == PK_BITMAP) ok = pred_test<PT_BITMAP>(p, t.aux, v);
             else ok = pred_test<PT_LIST>(p, t.aux, v);
-            pm &= ok ? ~0u : ~(1u << g);
+            put(g, ok, ng);
           }
         }
       }
+    }
+    if constexpr (cl == PC_LAST) {
+      pm &= acc;
+      acc = 0;
     }
   });
   return pm & valid;
@@ -488,16 +508,19 @@ __device__ __forceinline__ constexpr uint32_t col_bits() {
   return S::enc(C) == ENC_PLAIN ? (S::v64(C) ? 64u : 32u) : (uint32_t)S::bw(C);
 }
 
-// A predicate on one run / listed value (the helper's once-per-value test).
+// A predicate on one run / listed value (the helper's once-per-value test),
+// complemented when the predicate is negated.
 template <class S, int I>
 __device__ __forceinline__ bool fast_pred_value(const QueryDesc& q, const uint32_t* aux, long long v) {
   constexpr int kind = S::pkind(I);
   const PredDesc& p = q.preds[I];
-  if constexpr (kind == PK_RANGE) return pred_test<PT_RANGE>(p, aux, v);
-  else if constexpr (kind == PK_NE) return pred_test<PT_NE>(p, aux, v);
-  else if constexpr (kind == PK_BITMAP) return pred_test<PT_BITMAP>(p, aux, v);
-  else if constexpr (kind == PK_LIST) return pred_test<PT_LIST>(p, aux, v);
-  else return kind == PK_TRUE;
+  bool r;
+  if constexpr (kind == PK_RANGE) r = pred_test<PT_RANGE>(p, aux, v);
+  else if constexpr (kind == PK_NE) r = pred_test<PT_NE>(p, aux, v);
+  else if constexpr (kind == PK_BITMAP) r = pred_test<PT_BITMAP>(p, aux, v);
+  else if constexpr (kind == PK_LIST) r = pred_test<PT_LIST>(p, aux, v);
+  else r = kind == PK_TRUE;
+  return r != S::pneg(I);
 }
 
 template <class S>
@@ -652,65 +675,67 @@ struct FastBody {
       }
       __syncwarp();
     });
-    // pass bitmaps: predicates 0 .. n_pbm-1, on RLE / index columns, evaluated
-    // once per run / listed row
+    // pass bitmaps: predicates with a pass-bitmap slot (on RLE / index
+    // columns), evaluated once per run / listed row
     const uint32_t rows = (uint32_t)(e - s);
-    static_for<S::n_pbm>([&](auto I) {
+    static_for<S::n_preds>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      constexpr int c = S::pcol(i);
-      constexpr int j = S::bslot(c);
-      constexpr bool e64 = S::e64(c), v64 = S::v64(c);
-      if (j % nh != hw) return;
-      const ColDesc& cd = q.cols[c];
-      uint32_t* PB = sm.pbm + ((size_t)buf * S::n_pbm + S::ppbm(i)) * nwords;
-      const uint32_t nset = sm.pre[((size_t)buf * nb + j) * (nwords + 1) + nwords];
-      const unsigned long long cur = sm.tcur[buf * kMaxBitmapCols + j];
-      const uint8_t* win = sm.win + ((size_t)wb * nb + j) * kWin * 16;
-      const uint32_t avail = sm.wcnt[wb * kMaxBitmapCols + j];
-      auto end_at = [&](uint32_t k) -> unsigned long long {
-        if (k < avail) {
-          if constexpr (e64) return (unsigned long long)reinterpret_cast<const long long*>(win)[k];
-          else return (unsigned long long)reinterpret_cast<const int*>(win)[k];
-        }
-        return (unsigned long long)ldg_val(cd.ends, cur + k, e64);
-      };
-      auto val_at = [&](uint32_t k) -> long long {
-        if (k < avail) {
-          const uint8_t* v = win + kWin * 8;
-          if constexpr (v64) return reinterpret_cast<const long long*>(v)[k];
-          else return (long long)reinterpret_cast<const int*>(v)[k];
-        }
-        return ldg_val(cd.vals, cur + k, v64);
-      };
-      if constexpr (S::enc(c) == ENC_RLE) {
+      if constexpr (S::ppbm(i) != 0xFF) {
+        constexpr int c = S::pcol(i);
+        constexpr int j = S::bslot(c);
+        constexpr bool e64 = S::e64(c), v64 = S::v64(c);
+        if (j % nh != hw) return;
+        const ColDesc& cd = q.cols[c];
+        uint32_t* PB = sm.pbm + ((size_t)buf * S::n_pbm + S::ppbm(i)) * nwords;
+        const uint32_t nset = sm.pre[((size_t)buf * nb + j) * (nwords + 1) + nwords];
+        const unsigned long long cur = sm.tcur[buf * kMaxBitmapCols + j];
+        const uint8_t* win = sm.win + ((size_t)wb * nb + j) * kWin * 16;
+        const uint32_t avail = sm.wcnt[wb * kMaxBitmapCols + j];
+        auto end_at = [&](uint32_t k) -> unsigned long long {
+          if (k < avail) {
+            if constexpr (e64) return (unsigned long long)reinterpret_cast<const long long*>(win)[k];
+            else return (unsigned long long)reinterpret_cast<const int*>(win)[k];
+          }
+          return (unsigned long long)ldg_val(cd.ends, cur + k, e64);
+        };
+        auto val_at = [&](uint32_t k) -> long long {
+          if (k < avail) {
+            const uint8_t* v = win + kWin * 8;
+            if constexpr (v64) return reinterpret_cast<const long long*>(v)[k];
+            else return (long long)reinterpret_cast<const int*>(v)[k];
+          }
+          return ldg_val(cd.vals, cur + k, v64);
+        };
+        if constexpr (S::enc(c) == ENC_RLE) {
 #pragma unroll
-        for (uint32_t k = 0; k < per; ++k) PB[k * 32 + lane] = 0u;
-        __syncwarp();
-        // nset boundaries inside the tile: nset + 1 runs, the last one clipped
-        for (uint32_t k = lane; k <= nset; k += 32) {
-          const uint32_t a = k == 0 ? 0u : (uint32_t)(end_at(k - 1) - s);
-          const unsigned long long x = end_at(k);
-          const uint32_t b = x - s < rows ? (uint32_t)(x - s) : rows;
-          if (fast_pred_value<S, i>(q, aux, val_at(k))) fill_bits(PB, a, b);
-        }
-      } else {
-        const bool base_pass = fast_pred_value<S, i>(q, aux, cd.base);
+          for (uint32_t k = 0; k < per; ++k) PB[k * 32 + lane] = 0u;
+          __syncwarp();
+          // nset boundaries inside the tile: nset + 1 runs, the last one clipped
+          for (uint32_t k = lane; k <= nset; k += 32) {
+            const uint32_t a = k == 0 ? 0u : (uint32_t)(end_at(k - 1) - s);
+            const unsigned long long x = end_at(k);
+            const uint32_t b = x - s < rows ? (uint32_t)(x - s) : rows;
+            if (fast_pred_value<S, i>(q, aux, val_at(k))) fill_bits(PB, a, b);
+          }
+        } else {
+          const bool base_pass = fast_pred_value<S, i>(q, aux, cd.base);
 #pragma unroll
-        for (uint32_t k = 0; k < per; ++k) {
-          const uint32_t w = k * 32 + lane;
-          const uint32_t lo = w * 32;
-          uint32_t m = base_pass ? ~0u : 0u;
-          if (lo >= rows) m = 0u;
-          else if (rows - lo < 32) m &= (1u << (rows - lo)) - 1u;
-          PB[w] = m;
+          for (uint32_t k = 0; k < per; ++k) {
+            const uint32_t w = k * 32 + lane;
+            const uint32_t lo = w * 32;
+            uint32_t m = base_pass ? ~0u : 0u;
+            if (lo >= rows) m = 0u;
+            else if (rows - lo < 32) m &= (1u << (rows - lo)) - 1u;
+            PB[w] = m;
+          }
+          __syncwarp();
+          for (uint32_t k = lane; k < nset; k += 32) {
+            const uint32_t o = (uint32_t)(end_at(k) - s);
+            if (fast_pred_value<S, i>(q, aux, val_at(k)) != base_pass) atomicXor(&PB[o >> 5], 1u << (o & 31));
+          }
         }
         __syncwarp();
-        for (uint32_t k = lane; k < nset; k += 32) {
-          const uint32_t o = (uint32_t)(end_at(k) - s);
-          if (fast_pred_value<S, i>(q, aux, val_at(k)) != base_pass) atomicXor(&PB[o >> 5], 1u << (o & 31));
-        }
       }
-      __syncwarp();
     });
   }
 };

@@ -199,4 +199,13 @@ cq_result* new_result(cq_ctx* ctx, cudaStream_t s, bool own_events);
 int launch_solo(cq_table* table, Planned& P, cudaStream_t s, cq_result** out);
 void free_result(cq_result* r);
 
+// A plan whose filter is in conjunctive form (cq_filter.cu): `plan` is the
+// input with a filter program replaced by `preds`, one entry per predicate
+// occurrence with or_group / negate set; without a program, the input itself.
+struct NormFilter {
+  std::vector<cq_predicate> preds;
+  cq_plan plan;
+};
+int normalize_filter(const cq_plan* in, NormFilter* out);
+
 }  // namespace cq

@@ -110,17 +110,21 @@ static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) 
   emit_fn(s, "bslot", bslot);
   emit_fn(s, "raw_off", roff);
   emit_fn(s, "stage_off", soff);
-  std::vector<long long> pcol, pkind, pn32, ppbm;
+  std::vector<long long> pcol, pkind, pn32, ppbm, pneg, pcl;
   for (int i = 0; i < q.n_preds; ++i) {
     pcol.push_back(q.preds[i].col);
     pkind.push_back(q.preds[i].kind);
     pn32.push_back(q.preds[i].n32);
     ppbm.push_back(q.preds[i].pbm);
+    pneg.push_back(q.preds[i].neg);
+    pcl.push_back(q.preds[i].clause);
   }
   emit_fn(s, "pcol", pcol);
   emit_fn(s, "pkind", pkind);
   emit_fn(s, "pn32", pn32);
   emit_fn(s, "ppbm", ppbm);
+  emit_fn(s, "pneg", pneg);
+  emit_fn(s, "pcl", pcl);
   std::vector<long long> kcol, kremap, kn32;
   for (int k = 0; k < q.n_keys; ++k) {
     kcol.push_back(q.keys[k].col);
@@ -347,6 +351,13 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
     pred(3, 3, PK_BITMAP, 0, 0xFF);
     pred(4, 4, PK_LIST, 0, 0xFF);
     pred(5, 0, PK_TRUE, 0, 0xFF);
+    // OR clauses and complements: (NOT p1 OR p2) AND (p4 OR TRUE), p0 negated
+    q->preds[0].neg = 1;
+    q->preds[1].neg = 1;
+    q->preds[1].clause = PC_MEMBER;
+    q->preds[2].clause = PC_LAST;
+    q->preds[4].clause = PC_MEMBER;
+    q->preds[5].clause = PC_LAST;
     key(0, 3, 0, 0);
     agg(0, AK_SUM, 2, 0, 1, 0, 1, 0, 0, 0, 0);
     agg(1, AK_MIN, 3, 2, 0, 0, 4, 0, 0, 0, 0);

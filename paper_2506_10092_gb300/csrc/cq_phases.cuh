@@ -328,16 +328,19 @@ __device__ __forceinline__ bool key_digit(const KeyDesc& k, const uint32_t* aux,
   return true;
 }
 
-// A predicate on one raw value (the helper's once-per-run evaluation).
+// A predicate on one raw value (the helper's once-per-run evaluation),
+// complemented when the predicate is negated.
 __device__ __forceinline__ bool pred_eval(const PredDesc& p, const uint32_t* aux, long long v) {
+  bool r;
   switch (p.kind) {
-    case PK_RANGE: return pred_test<PT_RANGE>(p, aux, v);
-    case PK_NE: return pred_test<PT_NE>(p, aux, v);
-    case PK_BITMAP: return pred_test<PT_BITMAP>(p, aux, v);
-    case PK_LIST: return pred_test<PT_LIST>(p, aux, v);
-    case PK_FALSE: return false;
-    default: return true;
+    case PK_RANGE: r = pred_test<PT_RANGE>(p, aux, v); break;
+    case PK_NE: r = pred_test<PT_NE>(p, aux, v); break;
+    case PK_BITMAP: r = pred_test<PT_BITMAP>(p, aux, v); break;
+    case PK_LIST: r = pred_test<PT_LIST>(p, aux, v); break;
+    case PK_FALSE: r = false; break;
+    default: r = true; break;
   }
+  return r != (p.neg != 0);
 }
 
 // key_digit for a key whose raw values are read in 32 bits and whose kmin
@@ -641,13 +644,57 @@ __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
 }
 
 // ------------------------------------------------------------------ tile phases
+// Bit g: item (wbase + g * gstride + lane) passes test p (before any
+// complement).  Segment mode reads only the items still set in `live`.
+template <bool SEG, int GPW>
+__device__ __forceinline__ uint32_t filter_tests(const QueryDesc& q, const TileView& t, const uint16_t* seg,
+                                                 const PredDesc& p, uint32_t wbase, uint32_t gstride, uint32_t live) {
+  const int lane = threadIdx.x & 31;
+  const ColDesc& c = q.cols[p.col];
+  uint32_t m = 0;
+  dispatch_col<SEG>(c.enc, [&](auto et) {
+    dispatch_test(p, [&](auto kt) {
+      constexpr int E = decltype(et)::value;
+      constexpr int K = decltype(kt)::value;
+      if constexpr (SEG) {
+#pragma unroll 2
+        for (int g = 0; g < GPW; ++g) {
+          if (!((live >> g) & 1u)) continue;
+          const uint32_t o = (uint32_t)seg[wbase + g * gstride + lane];
+          bool ok;
+          if constexpr (K >= PT_RANGE32) ok = pred_test32<K>(p, t.aux, col_raw32<E>(c, t, o));
+          else ok = pred_test<K>(p, t.aux, col_raw<E>(c, t, o));
+          m |= (ok ? 1u : 0u) << g;
+        }
+      } else {
+        // rows of a tile are always readable (stale beyond the last row,
+        // masked by `valid`), so every group is evaluated without branches
+        // and the unrolled loads of several groups overlap
+#pragma unroll 4
+        for (int g = 0; g < GPW; ++g) {
+          const uint32_t o = wbase + g * gstride + lane;
+          bool ok;
+          if constexpr (K >= PT_RANGE32) ok = pred_test32<K>(p, t.aux, col_raw32<E>(c, t, o));
+          else ok = pred_test<K>(p, t.aux, col_raw<E>(c, t, o));
+          m |= (ok ? 1u : 0u) << g;
+        }
+      }
+    });
+  });
+  return m;
+}
+
 // Filter: bit g of the result says item (wbase + g * gstride + lane) passes
-// every predicate.  Callers deal 32-item groups to warps round-robin
-// (wbase = 32 * warp, gstride = 32 * warps), so that the clustered passing
-// rows of sorted data spread evenly over the warps.  Items are rows (row mode) or aligned segments (segment mode,
-// item -> first row through seg[]).  Predicates are evaluated one at a time
-// over all of the warp's items, with the column / test dispatch hoisted out of
-// the item loop.
+// the filter, a conjunction of clauses (Section 5: AND, OR, NOT).  Callers
+// deal 32-item groups to warps round-robin (wbase = 32 * warp, gstride = 32 *
+// warps), so that the clustered passing rows of sorted data spread evenly
+// over the warps.  Items are rows (row mode) or aligned segments (segment
+// mode, item -> first row through seg[]).  Predicates are evaluated one at a
+// time over all of the warp's items, with the column / test dispatch hoisted
+// out of the item loop: bit g of `m` is the item's result (complemented for a
+// negated predicate; a pass bitmap already holds the complement), AND-ed into
+// the mask for a predicate alone in its clause, else OR-ed into `acc`, which
+// the clause's last member ANDs in.
 template <bool SEG, int GPW>
 __device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileView& t, const uint16_t* seg,
                                                  uint32_t wbase, uint32_t gstride, uint32_t n_items) {
@@ -655,56 +702,31 @@ __device__ __forceinline__ uint32_t phase_filter(const QueryDesc& q, const TileV
   uint32_t valid = 0;
 #pragma unroll
   for (int g = 0; g < GPW; ++g) valid |= (wbase + g * gstride + lane < n_items ? 1u : 0u) << g;
-  uint32_t pm = valid;
-  int first = 0;
-  if constexpr (!SEG) {
-    // the first n_pbm predicates were evaluated once per run by the helper
-    // warp: one bit per row
-    for (; first < q.n_pbm; ++first) {
-      const uint32_t* PB = t.pbm + (size_t)q.preds[first].pbm * t.nwords;
-#pragma unroll 4
-      for (int g = 0; g < GPW; ++g)
-        if (!((PB[(wbase + g * gstride) >> 5] >> lane) & 1u)) pm &= ~(1u << g);
-    }
-  }
-  for (int oi = first; oi < q.n_preds; ++oi) {
+  uint32_t pm = valid, acc = 0;
+  for (int oi = 0; oi < q.n_preds; ++oi) {
     if (!__any_sync(0xFFFFFFFFu, pm != 0)) break;
     const PredDesc& p = q.preds[oi];
-    if (p.kind == PK_TRUE) continue;
-    if (p.kind == PK_FALSE) {
-      pm = 0;
-      continue;
-    }
-    const ColDesc& c = q.cols[p.col];
-    dispatch_col<SEG>(c.enc, [&](auto et) {
-      dispatch_test(p, [&](auto kt) {
-        constexpr int E = decltype(et)::value;
-        constexpr int K = decltype(kt)::value;
-        if constexpr (SEG) {
-#pragma unroll 2
-          for (int g = 0; g < GPW; ++g) {
-            if (!((pm >> g) & 1u)) continue;
-            const uint32_t o = (uint32_t)seg[wbase + g * gstride + lane];
-            bool ok;
-            if constexpr (K >= PT_RANGE32) ok = pred_test32<K>(p, t.aux, col_raw32<E>(c, t, o));
-            else ok = pred_test<K>(p, t.aux, col_raw<E>(c, t, o));
-            if (!ok) pm &= ~(1u << g);
-          }
-        } else {
-          // rows of a tile are always readable (stale beyond the last row,
-          // masked by `valid`), so every group is evaluated without branches
-          // and the unrolled loads of several groups overlap
+    uint32_t m = 0;
+    if (!SEG && p.pbm != 0xFF) {
+      // evaluated once per run by the helper warp: one bit per row
+      const uint32_t* PB = t.pbm + (size_t)p.pbm * t.nwords;
 #pragma unroll 4
-          for (int g = 0; g < GPW; ++g) {
-            const uint32_t o = wbase + g * gstride + lane;
-            bool ok;
-            if constexpr (K >= PT_RANGE32) ok = pred_test32<K>(p, t.aux, col_raw32<E>(c, t, o));
-            else ok = pred_test<K>(p, t.aux, col_raw<E>(c, t, o));
-            pm &= ok ? 0xFFFFFFFFu : ~(1u << g);
-          }
-        }
-      });
-    });
+      for (int g = 0; g < GPW; ++g) m |= ((PB[(wbase + g * gstride) >> 5] >> lane) & 1u) << g;
+    } else if (p.kind == PK_TRUE || p.kind == PK_FALSE) {
+      m = p.kind == PK_TRUE ? ~0u : 0u;
+    } else {
+      m = filter_tests<SEG, GPW>(q, t, seg, p, wbase, gstride, pm);
+      if (p.neg) m = ~m;
+    }
+    if (p.clause == PC_ALONE) {
+      pm &= m;
+    } else {
+      acc |= m;
+      if (p.clause == PC_LAST) {
+        pm &= acc;
+        acc = 0;
+      }
+    }
   }
   return pm & valid;
 }

@@ -177,8 +177,21 @@ __device__ inline void build_segments(const QueryDesc& q, const Smem& sm, uint32
 template <class Value, class Listed>
 __device__ inline void segment_update(const QueryDesc& q, const Smem& sm, const uint32_t* aux, unsigned long long s,
                                       unsigned long long L, Value value, Listed listed) {
-  for (int i = 0; i < q.n_preds; ++i)
-    if (!pred_eval(q.preds[i], aux, value(q.preds[i].col))) return;
+  // the filter's clauses: a predicate alone must hold, a clause needs one
+  // member that holds (pred_eval complements negated predicates)
+  bool acc = false;
+  for (int i = 0; i < q.n_preds; ++i) {
+    const PredDesc& p = q.preds[i];
+    if (p.clause == PC_ALONE) {
+      if (!pred_eval(p, aux, value(p.col))) return;
+    } else {
+      acc = acc || pred_eval(p, aux, value(p.col));
+      if (p.clause == PC_LAST) {
+        if (!acc) return;
+        acc = false;
+      }
+    }
+  }
   unsigned long long gid = 0;
   for (int ki = 0; ki < q.n_keys; ++ki) {
     const KeyDesc& k = q.keys[ki];

@@ -494,6 +494,7 @@ struct PlanCopy {
   std::vector<std::vector<uint32_t>> str_lens;
   std::vector<uint32_t> group_by;
   std::vector<cq_aggregate> aggs;
+  std::vector<cq_filter_node> filter;
   cq_plan plan;
 
   explicit PlanCopy(const cq_plan& p) {
@@ -527,6 +528,9 @@ struct PlanCopy {
     plan.n_group_by = (uint32_t)group_by.size();
     plan.aggs = aggs.empty() ? nullptr : aggs.data();
     plan.n_aggs = (uint32_t)aggs.size();
+    filter.assign(p.filter, p.filter + (p.filter ? p.n_filter : 0));
+    plan.filter = filter.empty() ? nullptr : filter.data();
+    plan.n_filter = p.n_filter;
   }
 };
 
@@ -682,7 +686,8 @@ static void serve(cq_server* srv) {
     // wait for one another.  Waiting small queries go first, as one batch, when
     // nothing runs, the batch is full or the oldest has waited max_wait_us;
     // otherwise the oldest large query runs alone.  With one lane
-    // (n_streams == 1) every query is batched.
+    // (n_streams == 1) every query is batched, but for those a batch cannot
+    // take, which run alone when nothing else waits.
     int sidx = -1;
     std::vector<std::shared_ptr<Request>> b;
     const bool two_lanes = srv->opt.n_streams >= 2;
@@ -696,12 +701,13 @@ static void serve(cq_server* srv) {
         else if (srv->pending.empty() && !srv->pending_large.empty()) b = take_batch(srv, srv->pending_large, 1);
         if (!b.empty()) sidx = 0;
       }
-    } else if (srv->stream_busy[0] == 0 && !srv->pending.empty()) {
-      if (srv->inflight.empty() || srv->pending.size() >= srv->opt.max_batch || srv->stop ||
-          Clock::now() - srv->pending.front()->submitted >= max_wait) {
+    } else if (srv->stream_busy[0] == 0) {
+      if (!srv->pending.empty() && (srv->inflight.empty() || srv->pending.size() >= srv->opt.max_batch ||
+                                    srv->stop || Clock::now() - srv->pending.front()->submitted >= max_wait))
         b = take_batch(srv, srv->pending, srv->opt.max_batch);
-        if (!b.empty()) sidx = 0;
-      }
+      else if (srv->pending.empty() && !srv->pending_large.empty())
+        b = take_batch(srv, srv->pending_large, 1);
+      if (!b.empty()) sidx = 0;
     }
     if (!b.empty()) {
       {
@@ -826,8 +832,15 @@ extern "C" int cq_server_submit(cq_server* srv, cq_table* table, const cq_plan* 
   r->large = srv->opt.n_streams >= 2 && table->n_rows > srv->large_rows;
   {
     PlanCopy pc(*plan);   // literals resolved at planning; the copy lives until then
-    const int rc = r->large ? plan_solo_query(table, &pc.plan, &r->planned)
-                            : plan_batch_query(table, &pc.plan, 0, srv->ctx->batch_smem, &r->planned);
+    int rc = r->large ? plan_solo_query(table, &pc.plan, &r->planned)
+                      : plan_batch_query(table, &pc.plan, 0, srv->ctx->batch_smem, &r->planned);
+    if (rc == CQ_ERR_UNSUPPORTED && !r->large) {
+      // what a batch cannot take (a key domain in the global hash table, a
+      // table above 2^31 rows) runs alone, in the large lane
+      clear_error();
+      rc = plan_solo_query(table, &pc.plan, &r->planned);
+      r->large = rc == CQ_OK;
+    }
     if (rc != CQ_OK) return rc;
   }
   {
