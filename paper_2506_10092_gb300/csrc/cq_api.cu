@@ -1503,6 +1503,9 @@ static int report_status(cq_result* r) {
   if (err == CQ_ERR_INVALID_ARG && what == 2)
     return set_error(err, "bitmap column %llu: boundary %llu lies before tile row %llu (corrupt cursor)", idx,
                      st[3], st[2]);
+  if (err == CQ_ERR_INVALID_ARG && what == 4)
+    return set_error(err, "shared group-table slot %llu was counted without a valid key (%llu); its updates were "
+                     "dropped", st[2], st[3]);
   return set_error(err, "device status %d", err);
 }
 

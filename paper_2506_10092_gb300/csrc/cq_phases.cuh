@@ -593,7 +593,16 @@ __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
       }
       continue;
     }
-    const long long g = q.table_dense ? (long long)s : (q.ghash ? gindex(q, sm.tkeys64[s]) : (long long)sm.tkeys[s]);
+    // a counted slot always holds its key; one that does not (or a key
+    // outside the domain) is reported and dropped, never used as an index
+    const unsigned long long key = q.table_dense ? s : (q.ghash ? sm.tkeys64[s] : (unsigned long long)sm.tkeys[s]);
+    const bool bad = q.ghash ? key == kEmptyGroup : key >= q.n_groups;
+    if (bad) {
+      report(q, CQ_ERR_INVALID_ARG, 4ull, s, key);
+      reset_slot(q, sm, s);
+      continue;
+    }
+    const long long g = q.ghash ? gindex(q, key) : (long long)key;
     if (g < 0) {   // global hash table full: the query fails, the host retries larger
       reset_slot(q, sm, s);
       continue;
