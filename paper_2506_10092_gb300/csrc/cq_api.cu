@@ -1034,6 +1034,12 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       else { rlo = pc.stats.min_val; rhi = pc.stats.max_val; }
       // a warp reduces up to 128 values (4 per lane) in 32 bits
       d.red32 = (!idx && !d.wide && rlo > -((i128)1 << 24) && rhi < ((i128)1 << 24)) ? 1 : 0;
+      d.ubits = 0;
+      if (d.red32 && rlo >= 0) {
+        uint8_t b = 1;
+        while (((i128)1 << b) <= rhi) ++b;
+        d.ubits = b;
+      }
       d.n32 = (d.red32 && narrow_col(cd, pc)) ? 1 : 0;
       {
         const i128 b = std::max<i128>(rhi < 0 ? -rhi : rhi, rlo < 0 ? -rlo : rlo) + 1;
@@ -1121,6 +1127,32 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   P->grid_ctas = opts ? opts->grid_ctas : 0u;
   P->generic = opts && opts->kernel == 1;
   P->row_fn = nullptr;
+  // ---- run lines (grouping on runs, Section 7): when key 0 is an RLE column
+  // whose runs are long next to the table, the specialised row kernel gives
+  // every run of it a line of the shared table (slot = line * width + the
+  // other keys' digits) instead of hashing the group id
+  q.line_mode = 0;
+  if (!batch && !q.seg_mode && !q.ghash && !q.table_dense && q.n_keys >= 1 && !P->generic && jit_enabled() &&
+      q.cols[q.keys[0].col].enc == ENC_RLE) {
+    const ColDesc& kc = q.cols[q.keys[0].col];
+    const uint64_t inner = q.keys[0].stride;
+    // (the lines' key digits live in the table's unused key words: 8 bytes a
+    // line within 4 bytes a slot, so at most table_slots / 2 lines)
+    uint32_t lg = 0;
+    while (lg < 16 && (2ull << lg) * inner <= q.table_slots && (2ull << lg) * 2 <= q.table_slots) ++lg;
+    const uint64_t lines = 1ull << lg;
+    // runs a tile holds on average, plus the one it starts in
+    const double per_tile = (double)tile * (double)kc.n / (double)(n_rows ? n_rows : 1) + 1.0;
+    if (lines * inner <= q.table_slots && (double)lines >= 2.0 * per_tile) {
+      q.line_mode = 1;
+      q.line_log2 = (uint8_t)lg;
+      q.line_slot = kc.bslot;
+      q.line_inner = (uint32_t)inner;
+      uint32_t p2 = 1;
+      while (p2 < 32 && inner % (2 * p2) == 0) p2 *= 2;
+      q.line_swz = p2 - 1;
+    }
+  }
   // ---- outputs
   q.n_out = plan->n_group_by + plan->n_aggs;
   P->out_kind.clear();

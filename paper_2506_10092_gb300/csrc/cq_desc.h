@@ -109,6 +109,8 @@ struct AggDesc {
   uint8_t op;        // cq_agg_op (for finalize)
   uint8_t out_kind;  // 0 int64, 1 uint64, 2 double
   uint8_t red32;     // SUM: |raw| < 2^24 -> a warp batch (<= 128 values) is reduced in 32 bits
+  uint8_t ubits;     // SUM with red32 and raw values in [0, 2^ubits): a warp's prefix sums fit
+                     // ubits + 5 bits, so several SUMs share one 32-bit scan (0: not known)
   uint8_t w32;       // MIN/MAX: raw values fit int32 -> 32-bit shared accumulator, warp-reduced
   uint8_t n32;       // values read in 32 bits (narrow column and red32 / w32)
   uint8_t s32;       // SUM: shared accumulator is one 32-bit word (sw32): 1 unsigned, 2 signed;
@@ -135,6 +137,15 @@ struct QueryDesc {
   uint32_t stage_bytes;    // bytes of one stage (all row-level columns)
   uint32_t table_slots;    // shared-memory group-table slots (power of two)
   uint8_t table_dense;     // 1: slot = gid (gid domain fits the table)
+  uint8_t line_mode;       // row mode, key 0 on an RLE column (grouping on runs, Section 7): the
+                           // shared table is 2^line_log2 lines of line_inner slots, one line per
+                           // run of that column (line = run ordinal mod lines), slot = line *
+                           // line_inner + the other keys' packed digits; no hashing or probing
+  uint8_t line_log2;
+  uint8_t line_slot;       // bitmap slot of key 0's column
+  uint32_t line_inner;     // slots per line = keys[0].stride
+  uint32_t line_swz;       // a line's slot for inner digits x is x ^ (line & line_swz): the
+                           // largest power of two (at most 32) dividing line_inner, minus one
   uint8_t n_sw;            // 64-bit shared accumulator words per slot
   uint8_t n_sw32;          // 32-bit shared accumulator words per slot (word 0 = COUNT)
   uint8_t n_gw;            // global accumulator words per group (word 0 = COUNT)

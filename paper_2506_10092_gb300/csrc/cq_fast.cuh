@@ -16,14 +16,15 @@
 //
 // S provides (all constexpr): tile_rows, n_cols, n_bitmaps, n_row_cols,
 // stage_bytes, n_preds, n_pbm, n_keys, n_aggs, one_group, table_dense, ghash
-// (groups in the global hash table, 64-bit packed keys); per
+// (groups in the global hash table, 64-bit packed keys), line_mode (the
+// shared table holds one line per run of key 0's RLE column); per
 // column c: enc, v64, e64, bw, bslot, raw_off, stage_off; bcol(j), the
 // column of bitmap slot j; row_col(i), the i-th staged column; per predicate
 // i (evaluation order): pcol, pkind, pn32, ppbm, pneg (complemented), pcl
 // (PC_ALONE / PC_MEMBER / PC_LAST: its place in its clause);
 // per key k: kcol, kremap, kn32; per aggregate i: akind, acol, asw, awide,
 // asw32, agw, ared32, aw32, an32, as32, asrc (the first aggregate reading the
-// same column value, whose read is reused).
+// same column value, whose read is reused), aub (SUM inputs in [0, 2^aub)).
 #pragma once
 
 #include "cq_rowpath.cuh"
@@ -351,12 +352,54 @@ __device__ constexpr bool seg_reducible() {
   return true;
 }
 
+// Packed prefix sums for runs of equal groups: each SUM aggregate whose
+// inputs lie in [0, 2^aub) takes a field of aub + 5 bits (a sum of 32 inputs
+// fits) in one of two 32-bit words, in aggregate order.  pk_place gives the
+// word (word = true) or the bit offset of aggregate `want`, -1 when the SUMs
+// do not all fit.
+template <class S>
+__device__ constexpr int pk_place(int want, bool word) {
+  int w = 0, off = 0;
+  for (int i = 0; i < S::n_aggs; ++i) {
+    if (S::akind(i) != AK_SUM) continue;
+    const int b = S::aub(i);
+    if (b == 0) return -1;
+    if (off + b + 5 > 32) {
+      ++w;
+      off = 0;
+    }
+    if (w > 1) return -1;
+    if (i == want) return word ? w : off;
+    off += b + 5;
+  }
+  return -1;
+}
+
+template <class S>
+__device__ constexpr bool pk_ok() {
+  bool any = false;
+  for (int i = 0; i < S::n_aggs; ++i)
+    if (S::akind(i) == AK_SUM) {
+      if (pk_place<S>(i, true) < 0) return false;
+      any = true;
+    }
+  return any;
+}
+
 // Aggregate the n_pass compacted rows of this warp, 32 at a time (one per
 // lane): group id from the key digits, a shared-table slot, COUNT and every
 // aggregate.  A single-group query reduces across the warp first.
+//
+// Line mode (S::line_mode, tiles with line_ok): key 0 is an RLE column and
+// the shared table holds one line per run of it, so "gid" is the slot itself:
+// line (run ordinal line_cur + rank, modulo the line count) times the line
+// width plus the other keys' packed digits; the flush recovers the group.  A
+// tile with more runs than lines (line_ok false) updates the global
+// accumulators of the true group directly.
 template <class S>
 __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& sm, const TileView& t,
-                                               const uint16_t* list, uint32_t n_pass, unsigned long long row0) {
+                                               const uint16_t* list, uint32_t n_pass, unsigned long long row0,
+                                               bool line_ok, unsigned long long line_cur) {
   const int lane = threadIdx.x & 31;
   for (uint32_t j0 = 0; j0 < n_pass; j0 += 32) {
     const uint32_t j = j0 + lane;
@@ -364,8 +407,18 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
     const uint32_t o = list[act ? j : j0];
     // the packed key: 64-bit for a hash domain, else the 32-bit dense gid
     typename Pick<S::ghash, unsigned long long, uint32_t>::type gid = 0;
+    uint32_t line = 0;
     static_for<S::n_keys>([&](auto K) {
       constexpr int k = decltype(K)::value;
+      if constexpr (S::line_mode && k == 0) {
+        if (line_ok) {
+          constexpr int jl = S::bslot(S::kcol(0));
+          constexpr uint32_t nw = S::tile_rows / 32;
+          const uint32_t r = rank_incl(t.bm + jl * nw, t.pre + jl * (nw + 1), o);
+          line = (uint32_t)(line_cur + r) & ((1u << q.line_log2) - 1u);
+          return;
+        }
+      }
       unsigned long long d = 0;
       long long raw = 0;
       if (!fast_digit<S, k>(q, t, o, &d, &raw)) {
@@ -378,6 +431,11 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
       if constexpr (S::ghash) gid += d * q.keys[k].stride;
       else gid += (uint32_t)d * (uint32_t)q.keys[k].stride;
     });
+    // a line's slots are its inner digits with the low bits XOR-ed by the
+    // line, so that rows of equal inner digits in different runs fall in
+    // different shared-memory banks
+    if constexpr (S::line_mode)
+      if (line_ok) gid = line * q.line_inner + (gid ^ (line & q.line_swz));
     long long val[S::n_aggs + 1];
     static_for<S::n_aggs>([&](auto A) {
       constexpr int i = decltype(A)::value;
@@ -434,10 +492,51 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
           const int seg0 = 31 - __clz(heads & upto);   // first lane of my run (act lanes)
           const bool tail = act && (lane == 31 || !((actm >> (lane + 1)) & 1u) || ((heads >> (lane + 1)) & 1u));
           int red[S::n_aggs + 1];
+          constexpr bool packed = pk_ok<S>();
+          if constexpr (packed) {
+            // every SUM at once: an inclusive prefix scan of the packed
+            // fields, a run's sum the difference at its ends (fields never
+            // carry into each other)
+            uint32_t pw0 = 0, pw1 = 0;
+            static_for<S::n_aggs>([&](auto A) {
+              constexpr int i = decltype(A)::value;
+              if constexpr (S::akind(i) == AK_SUM) {
+                const uint32_t x = act ? ((uint32_t)val[i] << pk_place<S>(i, false)) : 0u;
+                if constexpr (pk_place<S>(i, true) == 0) pw0 += x;
+                else pw1 += x;
+              }
+            });
+            constexpr bool two = [] {
+              for (int i = 0; i < S::n_aggs; ++i)
+                if (S::akind(i) == AK_SUM && pk_place<S>(i, true) == 1) return true;
+              return false;
+            }();
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+              const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, pw0, d);
+              if (lane >= d) pw0 += y0;
+              if constexpr (two) {
+                const uint32_t y1 = __shfl_up_sync(0xFFFFFFFFu, pw1, d);
+                if (lane >= d) pw1 += y1;
+              }
+            }
+            const int src = seg0 > 0 ? seg0 - 1 : 0;
+            uint32_t b0 = __shfl_sync(0xFFFFFFFFu, pw0, src), b1 = 0;
+            if constexpr (two) b1 = __shfl_sync(0xFFFFFFFFu, pw1, src);
+            if (seg0 == 0) b0 = b1 = 0;
+            static_for<S::n_aggs>([&](auto A) {
+              constexpr int i = decltype(A)::value;
+              if constexpr (S::akind(i) == AK_SUM) {
+                constexpr int off = pk_place<S>(i, false), width = S::aub(i) + 5;
+                const uint32_t dw = pk_place<S>(i, true) == 0 ? pw0 - b0 : pw1 - b1;
+                red[i] = (int)((dw >> off) & (width >= 32 ? 0xFFFFFFFFu : ((1u << width) - 1u)));
+              }
+            });
+          }
           static_for<S::n_aggs>([&](auto A) {
             constexpr int i = decltype(A)::value;
             constexpr int kind = S::akind(i);
-            if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+            if constexpr ((kind == AK_SUM && !packed) || kind == AK_MIN || kind == AK_MAX) {
               constexpr bool mn = kind == AK_MIN;
               int x = act ? (int)val[i] : (kind == AK_SUM ? 0 : (mn ? INT_MAX : INT_MIN));
 #pragma unroll
@@ -454,6 +553,7 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
             bool ok = true;
             const unsigned cnt = (unsigned)(lane - seg0 + 1);
             if constexpr (S::table_dense) slot = (int)gid;
+            else if constexpr (S::line_mode) slot = line_ok ? (int)gid : -1;
             else slot = table_slot_t<S::ghash>(q, sm, gid);
             if (slot >= 0) {
               atomicAdd(scount(q, sm, slot), cnt);
@@ -478,6 +578,7 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
       uint32_t gi = 0;   // global accumulator index, used when the shared table has no slot
       if (act) {
         if constexpr (S::table_dense) slot = (int)gid;
+        else if constexpr (S::line_mode) slot = line_ok ? (int)gid : -1;
         else slot = table_slot_t<S::ghash>(q, sm, gid);
         if (slot >= 0) {
           atomicAdd(scount(q, sm, slot), 1u);
@@ -523,6 +624,91 @@ __device__ __forceinline__ bool fast_pred_value(const QueryDesc& q, const uint32
   return r != S::pneg(I);
 }
 
+// Line mode: the flush of one shared slot with the shape's aggregates known
+// at compile time (the generic flush_slot and reset_slot read them from the
+// descriptor): add slot s (cnt rows) into group gid's global accumulators,
+// then clear it.
+template <class S>
+__device__ __forceinline__ void fast_flush_slot(const QueryDesc& q, const Smem& sm, uint32_t s, unsigned cnt,
+                                                uint32_t gid) {
+  atomicAdd(gword(q, 0, gid), (unsigned long long)cnt);
+  *scount(q, sm, s) = 0;
+  static_for<S::n_aggs>([&](auto A) {
+    constexpr int i = decltype(A)::value;
+    constexpr int kind = S::akind(i);
+    if constexpr (kind == AK_SUM || kind == AK_ISUM) {
+      I128 x;
+      if constexpr (S::as32(i) == 1) {
+        x = sext((long long)(unsigned)*sword32(q, sm, S::asw32(i), s));
+        *sword32(q, sm, S::asw32(i), s) = 0;
+      } else if constexpr (S::as32(i) == 2) {
+        x = sext((long long)*sword32(q, sm, S::asw32(i), s));
+        *sword32(q, sm, S::asw32(i), s) = 0;
+      } else if constexpr (S::awide(i)) {
+        x.lo = *sword(q, sm, S::asw(i), s);
+        x.hi = (long long)*sword(q, sm, S::asw(i) + 1, s);
+        *sword(q, sm, S::asw(i), s) = 0;
+        *sword(q, sm, S::asw(i) + 1, s) = 0;
+      } else {
+        x = sext((long long)*sword(q, sm, S::asw(i), s));
+        *sword(q, sm, S::asw(i), s) = 0;
+      }
+      global_add_limbs(gword(q, S::agw(i), gid), gword(q, S::agw(i) + 1, gid), gword(q, S::agw(i) + 2, gid), x);
+    } else if constexpr (kind == AK_MIN || kind == AK_MAX || kind == AK_IMIN || kind == AK_IMAX) {
+      constexpr bool mn = kind == AK_MIN || kind == AK_IMIN;
+      long long v;
+      if constexpr (S::aw32(i)) {
+        v = *sword32(q, sm, S::asw32(i), s);
+        *sword32(q, sm, S::asw32(i), s) = mn ? INT_MAX : INT_MIN;
+        if (v != (mn ? (long long)INT_MAX : (long long)INT_MIN)) {
+          if (mn) atomicMin(reinterpret_cast<long long*>(gword(q, S::agw(i), gid)), v);
+          else atomicMax(reinterpret_cast<long long*>(gword(q, S::agw(i), gid)), v);
+        }
+      } else {
+        v = (long long)*sword(q, sm, S::asw(i), s);
+        *sword(q, sm, S::asw(i), s) = mn ? (unsigned long long)LLONG_MAX : (unsigned long long)LLONG_MIN;
+        if (v != (mn ? LLONG_MAX : LLONG_MIN)) {
+          if (mn) atomicMin(reinterpret_cast<long long*>(gword(q, S::agw(i), gid)), v);
+          else atomicMax(reinterpret_cast<long long*>(gword(q, S::agw(i), gid)), v);
+        }
+      }
+      if constexpr (kind == AK_IMIN || kind == AK_IMAX) {
+        unsigned* lc = reinterpret_cast<unsigned*>(sword32(q, sm, S::asw32(i) + (S::aw32(i) ? 1 : 0), s));
+        if (*lc) atomicAdd(gword(q, S::agw(i) + 1, gid), (unsigned long long)*lc);
+        *lc = 0;
+      }
+    }
+  });
+}
+
+// Line mode: flush the lines of runs [ord_lo, ord_hi), which have all ended,
+// while the other warps still aggregate; the lines' slots are dealt to the
+// compute threads (thread `me` of `threads`).  No run being aggregated
+// shares a line with these (the tile walk's full-flush rule).
+template <class S>
+__device__ __forceinline__ void fast_flush_lines(const QueryDesc& q, const Smem& sm, unsigned long long ord_lo,
+                                                 unsigned long long ord_hi, uint32_t me, uint32_t threads) {
+  const uint32_t lines = 1u << q.line_log2;
+  const uint32_t inner = q.line_inner;
+  const uint32_t n = (uint32_t)(ord_hi - ord_lo) * inner;   // at most lines * inner slots
+  for (uint32_t f = me; f < n; f += threads) {
+    const uint32_t xi = f / inner;
+    const uint32_t j = f - xi * inner;
+    const uint32_t line = (uint32_t)(ord_lo + xi) & (lines - 1u);
+    const uint32_t s = line * inner + j;
+    const unsigned cnt = *scount(q, sm, s);
+    if (cnt == 0) continue;
+    const unsigned long long d = sm.tkeys64[line];
+    const unsigned long long gid = d * q.keys[0].stride + (j ^ (line & q.line_swz));
+    if (d == ~0ull || gid >= q.n_groups) {
+      report(q, CQ_ERR_INVALID_ARG, 4ull, s, gid);
+      reset_slot(q, sm, s);
+      continue;
+    }
+    fast_flush_slot<S>(q, sm, s, cnt, (uint32_t)gid);
+  }
+}
+
 template <class S>
 struct FastBody {
   template <int NCW, int GPW>
@@ -531,7 +717,21 @@ struct FastBody {
     constexpr uint32_t GS = NCW * 32;
     const uint32_t pm = fast_filter<S, GS, GPW>(q, tv, wbase, rows);
     const uint32_t n_pass = compact<GPW>(pm, wbase, GS, list);
-    fast_aggregate<S>(q, sm, tv, list, n_pass, row0);
+    bool line_ok = false;
+    unsigned long long line_cur = 0;
+    if constexpr (S::line_mode) {
+      // the tile's runs of key 0's column: ordinals line_cur .. line_cur + nset
+      constexpr int jl = S::bslot(S::kcol(0));
+      constexpr uint32_t nw = S::tile_rows / 32;
+      line_cur = tv.cur[jl];
+      const uint32_t nset = tv.pre[jl * (nw + 1) + nw];
+      line_ok = nset < (1u << q.line_log2);
+      if (line_ok && wbase == 0) line_digits(q, sm, tv, line_cur, nset);
+    }
+    fast_aggregate<S>(q, sm, tv, list, n_pass, row0, line_ok, line_cur);
+    // the lines of the runs that ended before this tile
+    if constexpr (S::line_mode)
+      fast_flush_lines<S>(q, sm, tv.line_base, line_cur, threadIdx.x, NCW * 32);
   }
 
   // Bulk copies of tile u's row-level columns into stage st (a full tile's

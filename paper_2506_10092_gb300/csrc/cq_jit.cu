@@ -78,15 +78,16 @@ int jit_helpers(const QueryDesc& q) { return q.n_bitmaps >= 2 ? 2 : 1; }
 // warps, gpw 32-row groups per warp and minb CTAs per SM.
 static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) {
   std::string s;
-  char buf[256];
+  char buf[512];
   s += "#include \"cq_fast.cuh\"\nnamespace cq {\nstruct JitShape {\n";
-  snprintf(buf, sizeof(buf),
+  const int n = snprintf(buf, sizeof(buf),
            "  static constexpr int tile_rows = %u, n_preds = %u, n_pbm = %u, n_keys = %u, n_aggs = %u;\n"
            "  static constexpr int n_cols = %u, n_bitmaps = %u, n_row_cols = %u, stage_bytes = %u;\n"
-           "  static constexpr bool one_group = %s, table_dense = %s, ghash = %s;\n",
+           "  static constexpr bool one_group = %s, table_dense = %s, ghash = %s, line_mode = %s;\n",
            q.tile_rows, q.n_preds, q.n_pbm, q.n_keys, q.n_aggs, q.n_cols, q.n_bitmaps, q.n_row_cols, q.stage_bytes,
            (q.n_groups == 1 && !q.ghash) ? "true" : "false", q.table_dense ? "true" : "false",
-           q.ghash ? "true" : "false");
+           q.ghash ? "true" : "false", q.line_mode ? "true" : "false");
+  if (n < 0 || n >= (int)sizeof(buf)) return std::string();   // (never: the text is bounded)
   s += buf;
   std::vector<long long> enc, v64, e64, bw, bslot, roff, soff, bcol(q.n_bitmaps, 0), rcol;
   for (int c = 0; c < q.n_cols; ++c) {
@@ -134,7 +135,7 @@ static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) 
   emit_fn(s, "kcol", kcol);
   emit_fn(s, "kremap", kremap);
   emit_fn(s, "kn32", kn32);
-  std::vector<long long> akind, acol, asw, awide, asw32, agw, ared32, aw32, an32, as32, asrc;
+  std::vector<long long> akind, acol, asw, awide, asw32, agw, ared32, aw32, an32, as32, asrc, aub;
   for (int i = 0; i < q.n_aggs; ++i) {
     const AggDesc& a = q.aggs[i];
     akind.push_back(a.kind);
@@ -144,6 +145,7 @@ static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) 
     asw32.push_back(a.sw32);
     agw.push_back(a.gw);
     ared32.push_back(a.red32);
+    aub.push_back(a.ubits);
     aw32.push_back(a.w32);
     an32.push_back(a.n32);
     as32.push_back(a.s32);
@@ -170,6 +172,7 @@ static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) 
   emit_fn(s, "an32", an32);
   emit_fn(s, "as32", as32);
   emit_fn(s, "asrc", asrc);
+  emit_fn(s, "aub", aub);
   s += "};\n}  // namespace cq\n";
   const int nh = jit_helpers(q);
   snprintf(buf, sizeof(buf),
@@ -199,6 +202,7 @@ static double g_jit_total_s = 0;
 static uint64_t g_jit_compiles = 0;
 
 static int compile(const std::string& src, JitKernel* k, bool load = true) {
+  if (src.empty()) return set_error(CQ_ERR_CUDA, "the specialised kernel's source could not be formed");
   std::vector<const char*> names, texts;
   for (int i = 0; i < kNumJitHeaders; ++i) {
     names.push_back(kJitHeaders[i].name);
@@ -294,6 +298,17 @@ namespace cq {
 // global hash table, single group) of the specialised body, with and without
 // the warp pre-reduction of sorted keys; only compiled.
 static void check_shape(uint32_t variant, QueryDesc* q) {
+  // variants 4 and 5: variants 0 and 3 with the run-line table (key 0 on
+  // the RLE column 0)
+  if (variant == 4 || variant == 5) {
+    check_shape(variant == 4 ? 0 : 3, q);
+    q->line_mode = 1;
+    q->line_log2 = 4;
+    q->line_slot = 0;
+    q->line_inner = 64;
+    q->line_swz = 31;
+    return;
+  }
   memset(q, 0, sizeof(*q));
   q->tile_rows = 8192;
   q->n_groups = 1000;
@@ -332,7 +347,10 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
     agg(2, AK_MIN, 4, 2, 0, 2, 7, 0, 1, 1, 0);
     agg(3, AK_MAX, 4, 2, 0, 3, 8, 0, 1, 1, 0);
     agg(4, AK_COUNT, 0, 0, 0, 0, 0, 0, 0, 0, 0);
-    if (variant == 3) agg(0, AK_COUNT, 0, 0, 0, 0, 0, 0, 0, 0, 0);   // reducible across a warp
+    if (variant == 3) {
+      agg(0, AK_COUNT, 0, 0, 0, 0, 0, 0, 0, 0, 0);   // reducible across a warp
+      q->aggs[1].ubits = 20;                         // packed prefix sums
+    }
   } else {
     q->n_cols = 5; q->n_preds = 6; q->n_keys = 1; q->n_aggs = 7; q->n_bitmaps = 2; q->n_pbm = 1;
     if (variant == 1) {
@@ -374,11 +392,12 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
 // run-time compilation that needs no GPU.  *seconds receives the compile time.
 extern "C" int cq_jit_check(uint32_t variant, double* seconds) {
   cq::clear_error();
-  if (variant > 3) return cq::set_error(CQ_ERR_INVALID_ARG, "variant must be 0 .. 3");
+  if (variant > 5) return cq::set_error(CQ_ERR_INVALID_ARG, "variant must be 0 .. 5");
   cq::QueryDesc q;
   cq::check_shape(variant, &q);
   cq::JitKernel k;
-  const int rc = cq::compile(cq::shape_source(q, (variant == 0 || variant == 3) ? 28 : 16, (variant == 0 || variant == 3) ? 8 : 16, 1), &k, false);
+  const bool wide = variant == 0 || variant == 3 || variant == 4 || variant == 5;
+  const int rc = cq::compile(cq::shape_source(q, wide ? 28 : 16, wide ? 8 : 16, 1), &k, false);
   if (seconds) *seconds = k.compile_s;
   return rc;
 }

@@ -146,6 +146,7 @@ struct TileView {
   const uint8_t* stage;              // staged row-level columns of this tile
   const uint32_t* aux;               // predicate / key tables (shared or global memory)
   uint32_t nwords;
+  unsigned long long line_base;      // line mode: first run whose line is not flushed yet
 };
 
 // ------------------------------------------------------------------ dispatch
@@ -575,19 +576,78 @@ __device__ __forceinline__ void reset_slot(const QueryDesc& q, const Smem& sm, u
         break;
     }
   }
-  if (!q.table_dense) {
+  if (!q.table_dense && !q.line_mode) {   // (line mode keeps line digits there)
     if (q.ghash) sm.tkeys64[s] = kEmptyGroup;
     else sm.tkeys[s] = kEmptyKey;
   }
 }
 
-// Add every occupied slot into the global accumulators and clear the table.
+// Add shared slot s (cnt rows counted) into the global accumulators of group
+// index gid and clear the slot.
+__device__ inline void flush_slot(const QueryDesc& q, const Smem& sm, uint32_t s, unsigned cnt, uint32_t gid) {
+  atomicAdd(gword(q, 0, gid), (unsigned long long)cnt);
+  for (int i = 0; i < q.n_aggs; ++i) {
+    const AggDesc& a = q.aggs[i];
+    switch (a.kind) {
+      case AK_SUM:
+      case AK_ISUM: {
+        I128 x;
+        if (a.s32 == 1) {
+          x = sext((long long)(unsigned)*sword32(q, sm, a.sw32, s));
+        } else if (a.s32 == 2) {
+          x = sext((long long)*sword32(q, sm, a.sw32, s));
+        } else if (a.wide) {
+          x.lo = *sword(q, sm, a.sw, s);
+          x.hi = (long long)*sword(q, sm, a.sw + 1, s);
+        } else {
+          x = sext((long long)*sword(q, sm, a.sw, s));
+        }
+        global_add_limbs(gword(q, a.gw, gid), gword(q, a.gw + 1, gid), gword(q, a.gw + 2, gid), x);
+        break;
+      }
+      case AK_MIN:
+      case AK_IMIN: {
+        const long long v = a.w32 ? (long long)*sword32(q, sm, a.sw32, s) : (long long)*sword(q, sm, a.sw, s);
+        if (v != (a.w32 ? (long long)INT_MAX : LLONG_MAX)) atomicMin(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
+        break;
+      }
+      case AK_MAX:
+      case AK_IMAX: {
+        const long long v = a.w32 ? (long long)*sword32(q, sm, a.sw32, s) : (long long)*sword(q, sm, a.sw, s);
+        if (v != (a.w32 ? (long long)INT_MIN : LLONG_MIN)) atomicMax(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
+        break;
+      }
+      default:
+        break;
+    }
+    if (a.kind == AK_IMIN || a.kind == AK_IMAX) {
+      const unsigned lc = *slisted(q, sm, a, s);
+      if (lc) atomicAdd(gword(q, a.gw + 1, gid), (unsigned long long)lc);
+    }
+  }
+  reset_slot(q, sm, s);
+}
+
+// Group id of run-line slot s (line mode): key 0's digit of the line's run
+// (recorded in the line's digit word when the run's tile was aggregated, see
+// line_digits), times its stride, plus the slot's inner digits (the slot's
+// place in the line, un-swizzled).
+__device__ __forceinline__ bool line_group(const QueryDesc& q, const Smem& sm, uint32_t s, unsigned long long* gid) {
+  const uint32_t line = s / q.line_inner, inner = (s - line * q.line_inner) ^ (line & q.line_swz);
+  if (line >= (1u << q.line_log2)) return false;
+  const unsigned long long d = sm.tkeys64[line];
+  if (d == ~0ull) return false;
+  *gid = d * q.keys[0].stride + inner;
+  return true;
+}
+
+// Flush the shared table into the global accumulators and clear it.
 __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
   const uint32_t S = q.table_slots;
   for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
     const unsigned cnt = *scount(q, sm, s);
     if (cnt == 0) {
-      if (!q.table_dense) {
+      if (!q.table_dense && !q.line_mode) {
         if (q.ghash) sm.tkeys64[s] = kEmptyGroup;
         else sm.tkeys[s] = kEmptyKey;
       }
@@ -595,8 +655,15 @@ __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
     }
     // a counted slot always holds its key; one that does not (or a key
     // outside the domain) is reported and dropped, never used as an index
-    const unsigned long long key = q.table_dense ? s : (q.ghash ? sm.tkeys64[s] : (unsigned long long)sm.tkeys[s]);
-    const bool bad = q.ghash ? key == kEmptyGroup : key >= q.n_groups;
+    unsigned long long key = 0;
+    bool bad;
+    if (q.line_mode) {
+      bad = !line_group(q, sm, s, &key);
+      bad = bad || key >= q.n_groups;
+    } else {
+      key = q.table_dense ? s : (q.ghash ? sm.tkeys64[s] : (unsigned long long)sm.tkeys[s]);
+      bad = q.ghash ? key == kEmptyGroup : key >= q.n_groups;
+    }
     if (bad) {
       report(q, CQ_ERR_INVALID_ARG, 4ull, s, key);
       reset_slot(q, sm, s);
@@ -607,48 +674,21 @@ __device__ inline void flush_table(const QueryDesc& q, const Smem& sm) {
       reset_slot(q, sm, s);
       continue;
     }
-    const uint32_t gid = (uint32_t)g;
-    atomicAdd(gword(q, 0, gid), (unsigned long long)cnt);
-    for (int i = 0; i < q.n_aggs; ++i) {
-      const AggDesc& a = q.aggs[i];
-      switch (a.kind) {
-        case AK_SUM:
-        case AK_ISUM: {
-          I128 x;
-          if (a.s32 == 1) {
-            x = sext((long long)(unsigned)*sword32(q, sm, a.sw32, s));
-          } else if (a.s32 == 2) {
-            x = sext((long long)*sword32(q, sm, a.sw32, s));
-          } else if (a.wide) {
-            x.lo = *sword(q, sm, a.sw, s);
-            x.hi = (long long)*sword(q, sm, a.sw + 1, s);
-          } else {
-            x = sext((long long)*sword(q, sm, a.sw, s));
-          }
-          global_add_limbs(gword(q, a.gw, gid), gword(q, a.gw + 1, gid), gword(q, a.gw + 2, gid), x);
-          break;
-        }
-        case AK_MIN:
-        case AK_IMIN: {
-          const long long v = a.w32 ? (long long)*sword32(q, sm, a.sw32, s) : (long long)*sword(q, sm, a.sw, s);
-          if (v != (a.w32 ? (long long)INT_MAX : LLONG_MAX)) atomicMin(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
-          break;
-        }
-        case AK_MAX:
-        case AK_IMAX: {
-          const long long v = a.w32 ? (long long)*sword32(q, sm, a.sw32, s) : (long long)*sword(q, sm, a.sw, s);
-          if (v != (a.w32 ? (long long)INT_MIN : LLONG_MIN)) atomicMax(reinterpret_cast<long long*>(gword(q, a.gw, gid)), v);
-          break;
-        }
-        default:
-          break;
-      }
-      if (a.kind == AK_IMIN || a.kind == AK_IMAX) {
-        const unsigned lc = *slisted(q, sm, a, s);
-        if (lc) atomicAdd(gword(q, a.gw + 1, gid), (unsigned long long)lc);
-      }
-    }
-    reset_slot(q, sm, s);
+    flush_slot(q, sm, s, cnt, (uint32_t)g);
+  }
+}
+
+// Line mode: record key 0's digit for the lines of a tile's runs, ordinals
+// cur .. cur + nset (warp 0 of the compute warps; ~0 when a value lies outside
+// the key's domain, which the flush then reports).
+__device__ inline void line_digits(const QueryDesc& q, const Smem& sm, const TileView& t, unsigned long long cur,
+                                   uint32_t nset) {
+  const uint32_t lines = 1u << q.line_log2;
+  const KeyDesc& k = q.keys[0];
+  for (uint32_t r = threadIdx.x & 31; r <= nset; r += 32) {
+    unsigned long long d;
+    if (!key_digit(k, t.aux, win_value(q.cols[k.col], t, r), &d)) d = ~0ull;
+    sm.tkeys64[(uint32_t)(cur + r) & (lines - 1u)] = d;
   }
 }
 

@@ -321,6 +321,12 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
   __syncthreads();
 
   uint32_t rows_since_flush = 0;
+  // line mode: the first run ordinal of key 0's column whose line has not
+  // been flushed (every thread tracks it).  While tile t is aggregated, the
+  // compute warps flush the lines of the runs that ended before it,
+  // [line_base, first run of t), so after its barrier line_base is tile t's
+  // first run; a full flush moves it to the next tile's first run.
+  unsigned long long line_base = q.line_mode ? sm.tcur[q.line_slot] : 0ull;
   uint16_t* mylist = sm.clist + (helper ? 0 : warp) * (GPW * 32);
   const uint32_t wbase = warp * 32;
   uint32_t st = 0, ph = 0;   // stage of tile t and the parity of its barrier phase
@@ -344,6 +350,7 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
       tv.stage = sm.stage + (size_t)st * q.stage_bytes;
       tv.aux = aux_smem ? sm.aux : q.aux;
       tv.nwords = nwords;
+      tv.line_base = line_base;
       Body::template tile<NCW, GPW>(q, sm, tv, wbase, rows, mylist, s);
     } else if (nb && t + 1 < t_end) {
       const int wb1 = (int)(wbi + 1 == kWinBufs ? 0 : wbi + 1);
@@ -356,16 +363,33 @@ __device__ __forceinline__ void row_range(const QueryDesc& q, const Smem& sm, un
     // the global accumulators)
     rows_since_flush += rows;
     const bool last = t + 1 == t_end;
-    const int need = __syncthreads_or(threadIdx.x == 0 &&
-                                      (last || (!q.table_dense && sm.misc[0] * 2 > (int)q.table_slots) ||
-                                       rows_since_flush + T > q.flush_rows));
+    // line mode: the helper that built tile t + 1's bitmaps of key 0's column
+    // asks for a full flush when that tile's last run would share a line with
+    // a run not flushed by then (tile t's first run or later: ordinal
+    // difference >= lines)
+    bool lines_full = false;
+    // tile t's first run: read before the barrier (the helper rebuilds this
+    // buffer for tile t + 2 once past it)
+    const unsigned long long first_run_t = q.line_mode ? sm.tcur[buf * kMaxBitmapCols + q.line_slot] : 0ull;
+    if (q.line_mode && helper && lane == 0 && hw == (int)q.line_slot % NH && !last) {
+      const int b1 = buf ^ 1;
+      const unsigned long long last_ord =
+          sm.tcur[b1 * kMaxBitmapCols + q.line_slot] + sm.pre[((size_t)b1 * nb + q.line_slot) * (nwords + 1) + nwords];
+      lines_full = last_ord - first_run_t >= (1ull << q.line_log2);
+    }
+    const int need = __syncthreads_or(lines_full ||
+                                      (threadIdx.x == 0 &&
+                                       (last || (!q.table_dense && !q.line_mode && sm.misc[0] * 2 > (int)q.table_slots) ||
+                                        rows_since_flush + T > q.flush_rows)));
     // tile t's stage is free: refill it with tile t + stages
     if (helper && hw == 0 && lane == 0 && t + q.stages < t_end) Body::issue(q, sm, t + q.stages, st);
+    if (q.line_mode) line_base = first_run_t;
     if (need) {
       flush_table(q, sm);
       if (threadIdx.x == 0) sm.misc[0] = 0;
       __syncthreads();
       rows_since_flush = 0;
+      if (q.line_mode && !last) line_base = sm.tcur[(buf ^ 1) * kMaxBitmapCols + q.line_slot];
     }
     if (++st == q.stages) {
       st = 0;
