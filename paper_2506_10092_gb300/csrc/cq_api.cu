@@ -1045,10 +1045,15 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
         const i128 b = std::max<i128>(rhi < 0 ? -rhi : rhi, rlo < 0 ? -rlo : rlo) + 1;
         const i128 limit = rlo >= 0 ? ((i128)1 << 32) : ((i128)1 << 31);
         d.s32 = (!idx && b * (i128)q.flush_rows < limit) ? (rlo >= 0 ? 1 : 2) : 0;
+        // else, row mode, inputs in [0, 2^24): two 32-bit limb words, the low
+        // kSplitBits bits and the rest, each updated without a returned value;
+        // a flush period of at most 2^20 rows keeps both below 2^32
+        if (!d.s32 && !idx && !q.seg_mode && rlo >= 0 && rhi < ((i128)1 << 24) && q.flush_rows <= (1u << 20))
+          d.s32 = 3;
       }
       if (d.s32) {
         d.sw32 = (uint8_t)sw32;
-        sw32 += 1;
+        sw32 += d.s32 == 3 ? 2 : 1;
       } else {
         d.sw = (uint8_t)sw;
         sw += d.wide ? 2 : 1;

@@ -13,6 +13,7 @@ namespace cq {
 // ---------------------------------------------------------------- limits
 constexpr int kMaxCols = 16;      // referenced columns per query
 constexpr int kMaxPreds = 16;
+constexpr int kSplitBits = 12;      // low limb of a split SUM accumulator (s32 == 3)
 constexpr int kMaxKeys = 8;
 constexpr int kMaxAggs = 16;
 constexpr int kMaxBitmapCols = 8; // RLE / index columns per query
@@ -114,7 +115,9 @@ struct AggDesc {
   uint8_t w32;       // MIN/MAX: raw values fit int32 -> 32-bit shared accumulator, warp-reduced
   uint8_t n32;       // values read in 32 bits (narrow column and red32 / w32)
   uint8_t s32;       // SUM: shared accumulator is one 32-bit word (sw32): 1 unsigned, 2 signed;
-                     // the flush period keeps it from wrapping
+                     // the flush period keeps it from wrapping; 3: two 32-bit limb words
+                     // (sw32: the inputs' low kSplitBits bits, sw32 + 1: the rest), inputs
+                     // in [0, 2^24), flush period <= 2^20 rows
   int64_t base;      // value added back at finalize (packed base or index default)
 };
 

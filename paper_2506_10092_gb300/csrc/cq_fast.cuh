@@ -288,7 +288,9 @@ __device__ __forceinline__ void fast_update(const QueryDesc& q, const Smem& sm, 
   const uint32_t slots = q.table_slots;
   if constexpr (kind == AK_SUM) {
     if (slot >= 0) {
-      if constexpr (S::as32(I)) atomicAdd(&sm.tacc32[(size_t)S::asw32(I) * slots + slot], (unsigned)v);
+      if constexpr (S::as32(I) == 3)
+        split_add(sword32(q, sm, S::asw32(I), slot), sword32(q, sm, S::asw32(I) + 1, slot), (unsigned)v);
+      else if constexpr (S::as32(I)) atomicAdd(&sm.tacc32[(size_t)S::asw32(I) * slots + slot], (unsigned)v);
       else if constexpr (!S::awide(I)) smem_add64(&sm.tacc[(size_t)S::asw(I) * slots + slot], v);
       else atomic_add_i128(&sm.tacc[(size_t)S::asw(I) * slots + slot], &sm.tacc[(size_t)(S::asw(I) + 1) * slots + slot],
                            sext(v));
@@ -458,7 +460,9 @@ __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& s
         if constexpr (kind == AK_SUM && S::ared32(i)) {
           const int r = __reduce_add_sync(0xFFFFFFFFu, act ? (int)val[i] : 0);
           if (lane == 0) {
-            if constexpr (S::as32(i)) atomicAdd(&sm.tacc32[(size_t)S::asw32(i) * q.table_slots], (unsigned)r);
+            if constexpr (S::as32(i) == 3)
+              split_add(sword32(q, sm, S::asw32(i), 0), sword32(q, sm, S::asw32(i) + 1, 0), (unsigned)r);
+            else if constexpr (S::as32(i)) atomicAdd(&sm.tacc32[(size_t)S::asw32(i) * q.table_slots], (unsigned)r);
             else smem_add64(&sm.tacc[(size_t)S::asw(i) * q.table_slots], (long long)r);
           }
         } else if constexpr ((kind == AK_MIN || kind == AK_MAX) && S::aw32(i)) {
@@ -638,7 +642,11 @@ __device__ __forceinline__ void fast_flush_slot(const QueryDesc& q, const Smem& 
     constexpr int kind = S::akind(i);
     if constexpr (kind == AK_SUM || kind == AK_ISUM) {
       I128 x;
-      if constexpr (S::as32(i) == 1) {
+      if constexpr (S::as32(i) == 3) {
+        x = sext(split_value(sword32(q, sm, S::asw32(i), s), sword32(q, sm, S::asw32(i) + 1, s)));
+        *sword32(q, sm, S::asw32(i), s) = 0;
+        *sword32(q, sm, S::asw32(i) + 1, s) = 0;
+      } else if constexpr (S::as32(i) == 1) {
         x = sext((long long)(unsigned)*sword32(q, sm, S::asw32(i), s));
         *sword32(q, sm, S::asw32(i), s) = 0;
       } else if constexpr (S::as32(i) == 2) {

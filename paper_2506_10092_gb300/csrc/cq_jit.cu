@@ -307,6 +307,7 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
     q->line_slot = 0;
     q->line_inner = 64;
     q->line_swz = 31;
+    if (variant == 4) q->aggs[1].s32 = 3;   // split limb words
     return;
   }
   memset(q, 0, sizeof(*q));

@@ -509,12 +509,26 @@ __device__ __forceinline__ void smem_add64(unsigned long long* w, long long x) {
   if (h) atomicAdd(p + 1, h);
 }
 
+// Split SUM accumulator (s32 == 3): x < 2^31 goes to two 32-bit limb words,
+// its low kSplitBits bits and the rest, with atomics whose result is unused.
+// lo and hi are the accumulator's two words (word sw32 and sw32 + 1 of the slot).
+__device__ __forceinline__ void split_add(int* lo, int* hi, unsigned x) {
+  atomicAdd(reinterpret_cast<unsigned*>(lo), x & ((1u << kSplitBits) - 1u));
+  if (x >> kSplitBits) atomicAdd(reinterpret_cast<unsigned*>(hi), x >> kSplitBits);
+}
+
+// Value of a split SUM accumulator.
+__device__ __forceinline__ long long split_value(const int* lo, const int* hi) {
+  return (long long)(unsigned)*lo + ((long long)(unsigned)*hi << kSplitBits);
+}
+
 // Add a 128-bit contribution to a SUM accumulator in shared memory (slot >= 0)
 // or straight into the global limbs of global index gi (see gindex).
 __device__ __forceinline__ void sum_add(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot, uint32_t gi,
                                         I128 x) {
   if (slot >= 0) {
-    if (a.s32) atomicAdd(reinterpret_cast<unsigned*>(sword32(q, sm, a.sw32, slot)), (unsigned)x.lo);
+    if (a.s32 == 3) split_add(sword32(q, sm, a.sw32, slot), sword32(q, sm, a.sw32 + 1, slot), (unsigned)x.lo);
+    else if (a.s32) atomicAdd(reinterpret_cast<unsigned*>(sword32(q, sm, a.sw32, slot)), (unsigned)x.lo);
     else if (!a.wide) smem_add64(sword(q, sm, a.sw, slot), (long long)x.lo);
     else atomic_add_i128(sword(q, sm, a.sw, slot), sword(q, sm, a.sw + 1, slot), x);
   } else {
@@ -557,6 +571,7 @@ __device__ __forceinline__ void reset_slot(const QueryDesc& q, const Smem& sm, u
       case AK_ISUM:
         if (a.s32) {
           *sword32(q, sm, a.sw32, s) = 0;
+          if (a.s32 == 3) *sword32(q, sm, a.sw32 + 1, s) = 0;
         } else {
           *sword(q, sm, a.sw, s) = 0;
           if (a.wide) *sword(q, sm, a.sw + 1, s) = 0;
@@ -592,7 +607,9 @@ __device__ inline void flush_slot(const QueryDesc& q, const Smem& sm, uint32_t s
       case AK_SUM:
       case AK_ISUM: {
         I128 x;
-        if (a.s32 == 1) {
+        if (a.s32 == 3) {
+          x = sext(split_value(sword32(q, sm, a.sw32, s), sword32(q, sm, a.sw32 + 1, s)));
+        } else if (a.s32 == 1) {
           x = sext((long long)(unsigned)*sword32(q, sm, a.sw32, s));
         } else if (a.s32 == 2) {
           x = sext((long long)*sword32(q, sm, a.sw32, s));
@@ -950,7 +967,8 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
           for (int m = 0; m < MI; ++m) x += act[m] ? (int)val[m] : 0;
           r = __reduce_add_sync(0xFFFFFFFFu, x);
           if (lane == 0) {
-            if (a.s32) atomicAdd(reinterpret_cast<unsigned*>(sword32(q, sm, a.sw32, 0)), (unsigned)r);
+            if (a.s32 == 3) split_add(sword32(q, sm, a.sw32, 0), sword32(q, sm, a.sw32 + 1, 0), (unsigned)r);
+            else if (a.s32) atomicAdd(reinterpret_cast<unsigned*>(sword32(q, sm, a.sw32, 0)), (unsigned)r);
             else smem_add64(sword(q, sm, a.sw, 0), (long long)r);
           }
         } else {
