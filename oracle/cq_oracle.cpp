@@ -20,6 +20,7 @@
 #include "cq_oracle.h"
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -30,9 +31,126 @@ namespace {
 
 typedef __int128 i128;
 
+// Unsigned 256-bit integer (two 128-bit limbs) for the exact sums of squares
+// and the variance numerator.
+typedef unsigned __int128 u128;
+struct U256 {
+  u128 lo = 0, hi = 0;
+};
+
+U256 add256(U256 a, U256 b) {
+  U256 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1 : 0);
+  return r;
+}
+
+U256 sub256(U256 a, U256 b) {   // a >= b
+  U256 r;
+  r.lo = a.lo - b.lo;
+  r.hi = a.hi - b.hi - (a.lo < b.lo ? 1 : 0);
+  return r;
+}
+
+// full product of two 128-bit values, schoolbook on 64-bit halves
+U256 mul128(u128 a, u128 b) {
+  const u128 m = ~(u128)0 >> 64;
+  const u128 a0 = a & m, a1 = a >> 64, b0 = b & m, b1 = b >> 64;
+  const u128 p00 = a0 * b0, p01 = a0 * b1, p10 = a1 * b0, p11 = a1 * b1;
+  const u128 mid = (p00 >> 64) + (p01 & m) + (p10 & m);
+  U256 r;
+  r.lo = (p00 & m) | (mid << 64);
+  r.hi = p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);
+  return r;
+}
+
+int bitlen256(U256 a) {
+  int n = 0;
+  if (a.hi) {
+    n = 128;
+    for (u128 x = a.hi; x; x >>= 1) ++n;
+  } else {
+    for (u128 x = a.lo; x; x >>= 1) ++n;
+  }
+  return n;
+}
+
+bool bit256(U256 a, int i) { return i < 128 ? ((a.lo >> i) & 1) : ((a.hi >> (i - 128)) & 1); }
+
+bool ge256(U256 a, U256 b) { return a.hi != b.hi ? a.hi > b.hi : a.lo >= b.lo; }
+
+U256 shl1(U256 a) {
+  U256 r;
+  r.hi = (a.hi << 1) | (a.lo >> 127);
+  r.lo = a.lo << 1;
+  return r;
+}
+
+// n / d rounded once to the nearest double (ties to even), d > 0: the
+// quotient's bits are produced by long division until 64 significant bits
+// are known; every further bit and the remainder fold into a sticky bit.
+double div_round(U256 n, u128 d) {
+  if (n.lo == 0 && n.hi == 0) return 0.0;
+  U256 dd;
+  dd.lo = d;
+  U256 rem;
+  uint64_t top = 0;     // leading quotient bits
+  int got = 0;          // significant quotient bits in top
+  int exp2 = 0;         // value = top * 2^exp2 (before rounding)
+  bool sticky = false;
+  // integer part: bits of n from the most significant down
+  for (int i = bitlen256(n) - 1; i >= 0; --i) {
+    rem = shl1(rem);
+    if (bit256(n, i)) rem.lo |= 1;
+    const bool q = ge256(rem, dd);
+    if (q) rem = sub256(rem, dd);
+    if (got < 64) {
+      if (got || q) {
+        top = (top << 1) | (q ? 1u : 0u);
+        ++got;
+      }
+    } else {
+      sticky = sticky || q;
+      ++exp2;
+    }
+  }
+  // fraction bits until 64 significant bits are known
+  while (got < 64) {
+    rem = shl1(rem);
+    const bool q = ge256(rem, dd);
+    if (q) rem = sub256(rem, dd);
+    if (got || q) {
+      top = (top << 1) | (q ? 1u : 0u);
+      ++got;
+    }
+    --exp2;
+  }
+  sticky = sticky || rem.lo != 0 || rem.hi != 0;
+  // top has 64 bits and the sticky lies below a double's rounding position
+  return std::ldexp((double)(top | (sticky ? 1u : 0u)), exp2);
+}
+
+// Variance from n, the exact SUM s1 and sum of squares s2 (Section 7):
+// (n * s2 - s1^2) / (n * n) for the population, / (n * (n - 1)) for a sample.
+double variance(uint64_t n, i128 s1, U256 s2, bool sample) {
+  const uint64_t den1 = sample ? n - 1 : n;
+  if (n == 0 || den1 == 0) return 0.0;
+  const u128 a1 = s1 < 0 ? (u128)(-s1) : (u128)s1;
+  const U256 sq = mul128(a1, a1);
+  const U256 ns2 = add256(mul128(s2.lo, (u128)n), [&] {
+    U256 h = mul128(s2.hi, (u128)n);   // s2.hi * n * 2^128: its low limb shifts up
+    U256 r;
+    r.hi = h.lo;
+    return r;
+  }());
+  const U256 num = sub256(ns2, sq);   // >= 0 (Cauchy-Schwarz)
+  return div_round(num, (u128)n * (u128)den1);
+}
+
 struct Acc {
   uint64_t count = 0;
   std::vector<i128> sum;
+  std::vector<U256> sq;     // sums of squares (VAR / STD)
   std::vector<int64_t> mn, mx;
   std::vector<bool> seen;
 };
@@ -255,6 +373,7 @@ typedef std::map<std::vector<int64_t>, Acc> GroupMap;
 
 void update(const Query& q, Acc& a, const std::vector<int64_t>& row) {
   if (a.sum.empty()) {
+    a.sq.assign(q.n_aggs, U256());
     a.sum.assign(q.n_aggs, 0);
     a.mn.assign(q.n_aggs, 0);
     a.mx.assign(q.n_aggs, 0);
@@ -266,7 +385,11 @@ void update(const Query& q, Acc& a, const std::vector<int64_t>& row) {
     if (g.op == ORC_COUNT) continue;
     int64_t v = row[q.slot[g.col]];
     const orc_column& c = q.cols[g.col];
-    if (g.op == ORC_SUM || g.op == ORC_AVG) a.sum[i] += (i128)v;
+    if (g.op == ORC_SUM || g.op == ORC_AVG || g.op >= ORC_VAR_POP) a.sum[i] += (i128)v;
+    if (g.op >= ORC_VAR_POP) {
+      const u128 m = v < 0 ? (u128)(-(i128)v) : (u128)v;
+      a.sq[i] = add256(a.sq[i], mul128(m, m));
+    }
     if (g.op == ORC_MIN || g.op == ORC_MAX) {
       if (!a.seen[i]) {
         a.mn[i] = a.mx[i] = v;
@@ -296,6 +419,7 @@ void merge_into(const Query& q, GroupMap& dst, const GroupMap& src) {
     for (uint32_t i = 0; i < q.n_aggs; ++i) {
       const orc_agg& g = q.aggs[i];
       a.sum[i] += b.sum[i];
+      a.sq[i] = add256(a.sq[i], b.sq[i]);
       if (!b.seen[i]) continue;
       if (!a.seen[i]) { a.mn[i] = b.mn[i]; a.mx[i] = b.mx[i]; a.seen[i] = true; continue; }
       const orc_column& c = q.cols[g.col];
@@ -379,10 +503,10 @@ extern "C" int orc_query(const orc_column* cols, uint32_t n_cols, uint64_t n_row
   for (uint32_t i = 0; i < n_preds; ++i) if (!use(preds[i].col)) return ORC_ERR_ARG;
   for (uint32_t i = 0; i < n_group_by; ++i) if (!use(group_by[i])) return ORC_ERR_ARG;
   for (uint32_t i = 0; i < n_aggs; ++i) {
-    if (aggs[i].op < ORC_SUM || aggs[i].op > ORC_AVG) return ORC_ERR_ARG;
+    if (aggs[i].op < ORC_SUM || aggs[i].op > ORC_STD_SAMP) return ORC_ERR_ARG;
     if (aggs[i].op == ORC_COUNT) continue;
     if (!use(aggs[i].col)) return ORC_ERR_ARG;
-    if (cols[aggs[i].col].enc == ORC_DICT && (aggs[i].op == ORC_SUM || aggs[i].op == ORC_AVG))
+    if (cols[aggs[i].col].enc == ORC_DICT && aggs[i].op != ORC_MIN && aggs[i].op != ORC_MAX)
       return ORC_ERR_ARG;
   }
   for (uint32_t c : q.used) if (validate(cols[c], n_rows) != ORC_OK) return ORC_ERR_ARG;
@@ -446,6 +570,7 @@ extern "C" int orc_query(const orc_column* cols, uint32_t n_cols, uint64_t n_row
   if (n_group_by == 0 && all.empty()) {          // no GROUP BY: one row even if nothing passes
     Acc a;
     a.sum.assign(n_aggs, 0); a.mn.assign(n_aggs, 0); a.mx.assign(n_aggs, 0); a.seen.assign(n_aggs, false);
+    a.sq.assign(n_aggs, U256());
     all[std::vector<int64_t>()] = a;
   }
   orc_result* r = new orc_result;
@@ -454,7 +579,7 @@ extern "C" int orc_query(const orc_column* cols, uint32_t n_cols, uint64_t n_row
   for (uint32_t i = 0; i < n_aggs; ++i) r->ops.push_back(aggs[i].op);
   for (auto& kv : all) {
     Acc& a = kv.second;
-    if (a.sum.empty()) { a.sum.assign(n_aggs, 0); a.mn.assign(n_aggs, 0); a.mx.assign(n_aggs, 0); a.seen.assign(n_aggs, false); }
+    if (a.sum.empty()) { a.sum.assign(n_aggs, 0); a.mn.assign(n_aggs, 0); a.mx.assign(n_aggs, 0); a.seen.assign(n_aggs, false); a.sq.assign(n_aggs, U256()); }
     for (uint32_t i = 0; i < n_aggs; ++i) {
       if (aggs[i].op == ORC_SUM) {
         i128 s = a.sum[i];
@@ -488,6 +613,14 @@ extern "C" void orc_result_agg(const orc_result* r, uint32_t a, void* out) {
         // the compiler's __int128 -> double conversion rounds to nearest even
         ((double*)out)[g] = x.count ? (double)x.sum[a] / (double)x.count : 0.0;
         break;
+      case ORC_VAR_POP:
+      case ORC_VAR_SAMP:
+        ((double*)out)[g] = variance(x.count, x.sum[a], x.sq[a], op == ORC_VAR_SAMP);
+        break;
+      case ORC_STD_POP:
+      case ORC_STD_SAMP:
+        ((double*)out)[g] = std::sqrt(variance(x.count, x.sum[a], x.sq[a], op == ORC_STD_SAMP));
+        break;
     }
   }
 }
@@ -501,6 +634,14 @@ extern "C" void orc_result_sum128(const orc_result* r, uint32_t a, uint64_t* lo,
 }
 
 extern "C" void orc_result_free(orc_result* r) { delete r; }
+
+extern "C" double orc_div_round(const uint64_t* n4, const uint64_t* d2) {
+  U256 n;
+  n.lo = ((u128)n4[1] << 64) | n4[0];
+  n.hi = ((u128)n4[3] << 64) | n4[2];
+  const u128 d = ((u128)d2[1] << 64) | d2[0];
+  return d ? div_round(n, d) : 0.0;
+}
 
 extern "C" int orc_align(uint32_t k, const int64_t* const* run_ends, const uint64_t* n_runs,
                          uint64_t n_rows, uint64_t* n_segments, int64_t* seg_ends, int64_t* ridx) {

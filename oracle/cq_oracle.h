@@ -29,7 +29,12 @@ extern "C" {
 
 enum { ORC_RLE = 1, ORC_DICT = 2, ORC_INDEX = 3, ORC_PACKED = 4, ORC_PLAIN = 5 };
 enum { ORC_LT = 0, ORC_LE, ORC_GT, ORC_GE, ORC_EQ, ORC_NE, ORC_BETWEEN, ORC_IN };
-enum { ORC_SUM = 0, ORC_COUNT, ORC_MIN, ORC_MAX, ORC_AVG };
+enum { ORC_SUM = 0, ORC_COUNT, ORC_MIN, ORC_MAX, ORC_AVG,
+       /* Section 7: STD and VAR from COUNT, SUM and the sum of squares; the
+          exact rational value rounded once to double (STD: the square root of
+          that double); population (n) or sample (n - 1) denominator, 0 when
+          the denominator is 0 */
+       ORC_VAR_POP, ORC_VAR_SAMP, ORC_STD_POP, ORC_STD_SAMP };
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_OVERFLOW = -6 };
 
 typedef struct {
@@ -111,11 +116,16 @@ int orc_result_status(const orc_result* r);
 uint64_t orc_result_num_groups(const orc_result* r);
 /* key column k of every group, groups in ascending lexicographic key order */
 void orc_result_keys(const orc_result* r, uint32_t k, int64_t* out);
-/* aggregate a: SUM/MIN/MAX as int64, COUNT as uint64 bits, AVG as double */
+/* aggregate a: SUM/MIN/MAX as int64, COUNT as uint64 bits, AVG / VAR / STD as double */
 void orc_result_agg(const orc_result* r, uint32_t a, void* out);
 /* exact 128-bit SUM of aggregate a (lo, hi words) for every group */
 void orc_result_sum128(const orc_result* r, uint32_t a, uint64_t* lo, int64_t* hi);
 void orc_result_free(orc_result* r);
+
+/* n / d rounded once to the nearest double (ties to even), n given as four
+ * 64-bit limbs (least significant first), d as two; the rounding step of
+ * VAR / STD, exported for its own tests.  0 when d is 0. */
+double orc_div_round(const uint64_t* n4, const uint64_t* d2);
 
 /* Common refinement of k RLE columns' run boundaries (Section 6 Alignment):
  * the sorted distinct union of all exclusive run ends, and for each segment

@@ -19,7 +19,9 @@ from . import build as _build
 
 ORC_RLE, ORC_DICT, ORC_INDEX, ORC_PACKED, ORC_PLAIN = 1, 2, 3, 4, 5
 _OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7}
-_AGGS = {"sum": 0, "count": 1, "min": 2, "max": 3, "avg": 4}
+_AGGS = {"sum": 0, "count": 1, "min": 2, "max": 3, "avg": 4, "var_pop": 5, "var_samp": 6, "std_pop": 7,
+         "std_samp": 8}
+_FLOAT_AGGS = ("avg", "var_pop", "var_samp", "std_pop", "std_samp")
 ORC_ERR_OVERFLOW = -6
 
 
@@ -75,6 +77,8 @@ def lib():
             L.orc_result_agg.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p]
             L.orc_result_sum128.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]
             L.orc_result_free.argtypes = [C.c_void_p]
+            L.orc_div_round.argtypes = [C.c_void_p, C.c_void_p]
+            L.orc_div_round.restype = C.c_double
             L.orc_align.argtypes = [C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint64,
                                     C.POINTER(C.c_uint64), C.c_void_p, C.c_void_p]
             _lib = L
@@ -142,7 +146,7 @@ class _Marshal:
 class OracleResult:
     status: int
     keys: List[np.ndarray]           # one int64 array per group-by column
-    aggs: List[np.ndarray]           # int64 (SUM/MIN/MAX), uint64 (COUNT), float64 (AVG)
+    aggs: List[np.ndarray]           # int64 (SUM/MIN/MAX), uint64 (COUNT), float64 (AVG/VAR/STD)
     sum128: TDict[int, tuple]        # agg index -> (lo uint64[], hi int64[]) for SUM/AVG
 
     @property
@@ -181,7 +185,7 @@ def query(table, plan, row_ranges=None, n_threads: int = 1) -> OracleResult:
         res_aggs = []
         s128 = {}
         for i, a in enumerate(plan.aggs):
-            dt = {"count": np.uint64, "avg": np.float64}.get(a.op, np.int64)
+            dt = np.uint64 if a.op == "count" else (np.float64 if a.op in _FLOAT_AGGS else np.int64)
             x = np.empty(g, dtype=dt)
             L.orc_result_agg(out, i, x.ctypes.data)
             res_aggs.append(x)
@@ -232,3 +236,11 @@ def cores() -> int:
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+def div_round(n: int, d: int) -> float:
+    """The oracle's correctly rounded n / d (0 <= n < 2^256, 0 < d < 2^128)."""
+    L = lib()
+    nn = np.array([(n >> (64 * i)) & (2**64 - 1) for i in range(4)], dtype=np.uint64)
+    dd = np.array([(d >> (64 * i)) & (2**64 - 1) for i in range(2)], dtype=np.uint64)
+    return float(L.orc_div_round(nn.ctypes.data, dd.ctypes.data))

@@ -399,210 +399,219 @@ __device__ constexpr bool pk_ok() {
 // tile with more runs than lines (line_ok false) updates the global
 // accumulators of the true group directly.
 template <class S>
+__device__ __forceinline__ void fast_agg_step(const QueryDesc& q, const Smem& sm, const TileView& t, uint32_t o,
+                                              bool act, unsigned long long row0, bool line_ok,
+                                              unsigned long long line_cur) {
+  const int lane = threadIdx.x & 31;
+  // the packed key: 64-bit for a hash domain, else the 32-bit dense gid
+  typename Pick<S::ghash, unsigned long long, uint32_t>::type gid = 0;
+  uint32_t line = 0;
+  static_for<S::n_keys>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    if constexpr (S::line_mode && k == 0) {
+      if (line_ok) {
+        constexpr int jl = S::bslot(S::kcol(0));
+        constexpr uint32_t nw = S::tile_rows / 32;
+        const uint32_t r = rank_incl(t.bm + jl * nw, t.pre + jl * (nw + 1), o);
+        line = (uint32_t)(line_cur + r) & ((1u << q.line_log2) - 1u);
+        return;
+      }
+    }
+    unsigned long long d = 0;
+    long long raw = 0;
+    if (!fast_digit<S, k>(q, t, o, &d, &raw)) {
+      if (act) {
+        act = false;
+        report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)k << 8), row0 + o, (unsigned long long)raw);
+      }
+      d = 0;
+    }
+    if constexpr (S::ghash) gid += d * q.keys[k].stride;
+    else gid += (uint32_t)d * (uint32_t)q.keys[k].stride;
+  });
+  // a line's slots are its inner digits with the low bits XOR-ed by the
+  // line, so that rows of equal inner digits in different runs fall in
+  // different shared-memory banks
+  if constexpr (S::line_mode)
+    if (line_ok) gid = line * q.line_inner + (gid ^ (line & q.line_swz));
+  long long val[S::n_aggs + 1];
+  static_for<S::n_aggs>([&](auto A) {
+    constexpr int i = decltype(A)::value;
+    constexpr int kind = S::akind(i);
+    if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+      if constexpr (S::asrc(i) == i) {
+        if constexpr (S::an32(i)) val[i] = (long long)fast_raw32<S, S::acol(i)>(q, t, o);
+        else val[i] = fast_raw<S, S::acol(i)>(q, t, o);
+      } else {
+        val[i] = val[S::asrc(i)];
+      }
+    }
+  });
+  if constexpr (S::one_group) {
+    const uint32_t n = __popc(__ballot_sync(0xFFFFFFFFu, act));
+    if (lane == 0) atomicAdd(scount(q, sm, 0), n);
+    static_for<S::n_aggs>([&](auto A) {
+      constexpr int i = decltype(A)::value;
+      constexpr int kind = S::akind(i);
+      if constexpr (kind == AK_SUM && S::ared32(i)) {
+        const int r = __reduce_add_sync(0xFFFFFFFFu, act ? (int)val[i] : 0);
+        if (lane == 0) {
+          if constexpr (S::as32(i) == 3)
+            split_add(sword32(q, sm, S::asw32(i), 0), sword32(q, sm, S::asw32(i) + 1, 0), (unsigned)r);
+          else if constexpr (S::as32(i)) atomicAdd(&sm.tacc32[(size_t)S::asw32(i) * q.table_slots], (unsigned)r);
+          else smem_add64(&sm.tacc[(size_t)S::asw(i) * q.table_slots], (long long)r);
+        }
+      } else if constexpr ((kind == AK_MIN || kind == AK_MAX) && S::aw32(i)) {
+        constexpr bool mn = kind == AK_MIN;
+        const int x = act ? (int)val[i] : (mn ? INT_MAX : INT_MIN);
+        const int r = mn ? __reduce_min_sync(0xFFFFFFFFu, x) : __reduce_max_sync(0xFFFFFFFFu, x);
+        if (lane == 0) {
+          int* p = reinterpret_cast<int*>(&sm.tacc32[(size_t)S::asw32(i) * q.table_slots]);
+          if (mn) atomicMin(p, r);
+          else atomicMax(p, r);
+        }
+      } else if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+        if (act) fast_update<S, i>(q, sm, 0, 0, val[i]);
+      } else if constexpr (kind != AK_COUNT) {
+        if (act) fast_index_update<S, i>(q, sm, t, 0, 0, o);
+      }
+    });
+  } else {
+    if constexpr (seg_reducible<S>()) {
+      // Sorted keys (runs of equal groups among consecutive passing rows):
+      // reduce each run of equal gids across the warp first and let its
+      // last lane update the table once -- COUNT = run length, SUM and
+      // MIN / MAX by a segmented shuffle scan.  Taken when the runs average
+      // two or more rows; otherwise every lane updates (below).
+      const auto prev = __shfl_up_sync(0xFFFFFFFFu, gid, 1);
+      const uint32_t actm = __ballot_sync(0xFFFFFFFFu, act);
+      // (a head also follows a lane without a row: in-place groups have holes)
+      const bool head = act && (lane == 0 || prev != gid || !((actm >> (lane - 1)) & 1u));
+      const uint32_t heads = __ballot_sync(0xFFFFFFFFu, head);
+      if (2 * __popc(heads) <= __popc(actm)) {
+        const uint32_t upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+        const int seg0 = 31 - __clz(heads & upto);   // first lane of my run (act lanes)
+        const bool tail = act && (lane == 31 || !((actm >> (lane + 1)) & 1u) || ((heads >> (lane + 1)) & 1u));
+        int red[S::n_aggs + 1];
+        constexpr bool packed = pk_ok<S>();
+        if constexpr (packed) {
+          // every SUM at once: an inclusive prefix scan of the packed
+          // fields, a run's sum the difference at its ends (fields never
+          // carry into each other)
+          uint32_t pw0 = 0, pw1 = 0;
+          static_for<S::n_aggs>([&](auto A) {
+            constexpr int i = decltype(A)::value;
+            if constexpr (S::akind(i) == AK_SUM) {
+              const uint32_t x = act ? ((uint32_t)val[i] << pk_place<S>(i, false)) : 0u;
+              if constexpr (pk_place<S>(i, true) == 0) pw0 += x;
+              else pw1 += x;
+            }
+          });
+          constexpr bool two = [] {
+            for (int i = 0; i < S::n_aggs; ++i)
+              if (S::akind(i) == AK_SUM && pk_place<S>(i, true) == 1) return true;
+            return false;
+          }();
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, pw0, d);
+            if (lane >= d) pw0 += y0;
+            if constexpr (two) {
+              const uint32_t y1 = __shfl_up_sync(0xFFFFFFFFu, pw1, d);
+              if (lane >= d) pw1 += y1;
+            }
+          }
+          const int src = seg0 > 0 ? seg0 - 1 : 0;
+          uint32_t b0 = __shfl_sync(0xFFFFFFFFu, pw0, src), b1 = 0;
+          if constexpr (two) b1 = __shfl_sync(0xFFFFFFFFu, pw1, src);
+          if (seg0 == 0) b0 = b1 = 0;
+          static_for<S::n_aggs>([&](auto A) {
+            constexpr int i = decltype(A)::value;
+            if constexpr (S::akind(i) == AK_SUM) {
+              constexpr int off = pk_place<S>(i, false), width = S::aub(i) + 5;
+              const uint32_t dw = pk_place<S>(i, true) == 0 ? pw0 - b0 : pw1 - b1;
+              red[i] = (int)((dw >> off) & (width >= 32 ? 0xFFFFFFFFu : ((1u << width) - 1u)));
+            }
+          });
+        }
+        static_for<S::n_aggs>([&](auto A) {
+          constexpr int i = decltype(A)::value;
+          constexpr int kind = S::akind(i);
+          if constexpr ((kind == AK_SUM && !packed) || kind == AK_MIN || kind == AK_MAX) {
+            constexpr bool mn = kind == AK_MIN;
+            int x = act ? (int)val[i] : (kind == AK_SUM ? 0 : (mn ? INT_MAX : INT_MIN));
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+              const int y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+              if (lane - d >= seg0) x = kind == AK_SUM ? x + y : (mn ? min(x, y) : max(x, y));
+            }
+            red[i] = x;
+          }
+        });
+        if (tail) {
+          int slot = -1;
+          uint32_t gi = 0;
+          bool ok = true;
+          const unsigned cnt = (unsigned)(lane - seg0 + 1);
+          if constexpr (S::table_dense) slot = (int)gid;
+          else if constexpr (S::line_mode) slot = line_ok ? (int)gid : -1;
+          else slot = table_slot_t<S::ghash>(q, sm, gid);
+          if (slot >= 0) {
+            atomicAdd(scount(q, sm, slot), cnt);
+          } else {
+            const long long g = gindex_t<S::ghash>(q, gid);
+            ok = g >= 0;
+            gi = (uint32_t)g;
+            if (ok) atomicAdd(gword(q, 0, gi), (unsigned long long)cnt);
+          }
+          static_for<S::n_aggs>([&](auto A) {
+            constexpr int i = decltype(A)::value;
+            constexpr int kind = S::akind(i);
+            if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+              if (ok) fast_update<S, i>(q, sm, slot, gi, (long long)red[i]);
+            }
+          });
+        }
+        return;
+      }
+    }
+    int slot = -1;
+    uint32_t gi = 0;   // global accumulator index, used when the shared table has no slot
+    if (act) {
+      if constexpr (S::table_dense) slot = (int)gid;
+      else if constexpr (S::line_mode) slot = line_ok ? (int)gid : -1;
+      else slot = table_slot_t<S::ghash>(q, sm, gid);
+      if (slot >= 0) {
+        atomicAdd(scount(q, sm, slot), 1u);
+      } else {
+        const long long g = gindex_t<S::ghash>(q, gid);
+        if (g < 0) act = false;   // global hash table full: the host retries larger
+        gi = (uint32_t)g;
+        if (act) atomicAdd(gword(q, 0, gi), 1ull);
+      }
+    }
+    static_for<S::n_aggs>([&](auto A) {
+      constexpr int i = decltype(A)::value;
+      constexpr int kind = S::akind(i);
+      if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+        if (act) fast_update<S, i>(q, sm, slot, gi, val[i]);
+      } else if constexpr (kind != AK_COUNT) {
+        if (act) fast_index_update<S, i>(q, sm, t, slot, gi, o);
+      }
+    });
+  }
+}
+
+// The compacted rows list[0 .. n_pass), 32 at a time.
+template <class S>
 __device__ __forceinline__ void fast_aggregate(const QueryDesc& q, const Smem& sm, const TileView& t,
                                                const uint16_t* list, uint32_t n_pass, unsigned long long row0,
                                                bool line_ok, unsigned long long line_cur) {
   const int lane = threadIdx.x & 31;
   for (uint32_t j0 = 0; j0 < n_pass; j0 += 32) {
     const uint32_t j = j0 + lane;
-    bool act = j < n_pass;
-    const uint32_t o = list[act ? j : j0];
-    // the packed key: 64-bit for a hash domain, else the 32-bit dense gid
-    typename Pick<S::ghash, unsigned long long, uint32_t>::type gid = 0;
-    uint32_t line = 0;
-    static_for<S::n_keys>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      if constexpr (S::line_mode && k == 0) {
-        if (line_ok) {
-          constexpr int jl = S::bslot(S::kcol(0));
-          constexpr uint32_t nw = S::tile_rows / 32;
-          const uint32_t r = rank_incl(t.bm + jl * nw, t.pre + jl * (nw + 1), o);
-          line = (uint32_t)(line_cur + r) & ((1u << q.line_log2) - 1u);
-          return;
-        }
-      }
-      unsigned long long d = 0;
-      long long raw = 0;
-      if (!fast_digit<S, k>(q, t, o, &d, &raw)) {
-        if (act) {
-          act = false;
-          report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)k << 8), row0 + o, (unsigned long long)raw);
-        }
-        d = 0;
-      }
-      if constexpr (S::ghash) gid += d * q.keys[k].stride;
-      else gid += (uint32_t)d * (uint32_t)q.keys[k].stride;
-    });
-    // a line's slots are its inner digits with the low bits XOR-ed by the
-    // line, so that rows of equal inner digits in different runs fall in
-    // different shared-memory banks
-    if constexpr (S::line_mode)
-      if (line_ok) gid = line * q.line_inner + (gid ^ (line & q.line_swz));
-    long long val[S::n_aggs + 1];
-    static_for<S::n_aggs>([&](auto A) {
-      constexpr int i = decltype(A)::value;
-      constexpr int kind = S::akind(i);
-      if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
-        if constexpr (S::asrc(i) == i) {
-          if constexpr (S::an32(i)) val[i] = (long long)fast_raw32<S, S::acol(i)>(q, t, o);
-          else val[i] = fast_raw<S, S::acol(i)>(q, t, o);
-        } else {
-          val[i] = val[S::asrc(i)];
-        }
-      }
-    });
-    if constexpr (S::one_group) {
-      const uint32_t n = __popc(__ballot_sync(0xFFFFFFFFu, act));
-      if (lane == 0) atomicAdd(scount(q, sm, 0), n);
-      static_for<S::n_aggs>([&](auto A) {
-        constexpr int i = decltype(A)::value;
-        constexpr int kind = S::akind(i);
-        if constexpr (kind == AK_SUM && S::ared32(i)) {
-          const int r = __reduce_add_sync(0xFFFFFFFFu, act ? (int)val[i] : 0);
-          if (lane == 0) {
-            if constexpr (S::as32(i) == 3)
-              split_add(sword32(q, sm, S::asw32(i), 0), sword32(q, sm, S::asw32(i) + 1, 0), (unsigned)r);
-            else if constexpr (S::as32(i)) atomicAdd(&sm.tacc32[(size_t)S::asw32(i) * q.table_slots], (unsigned)r);
-            else smem_add64(&sm.tacc[(size_t)S::asw(i) * q.table_slots], (long long)r);
-          }
-        } else if constexpr ((kind == AK_MIN || kind == AK_MAX) && S::aw32(i)) {
-          constexpr bool mn = kind == AK_MIN;
-          const int x = act ? (int)val[i] : (mn ? INT_MAX : INT_MIN);
-          const int r = mn ? __reduce_min_sync(0xFFFFFFFFu, x) : __reduce_max_sync(0xFFFFFFFFu, x);
-          if (lane == 0) {
-            int* p = reinterpret_cast<int*>(&sm.tacc32[(size_t)S::asw32(i) * q.table_slots]);
-            if (mn) atomicMin(p, r);
-            else atomicMax(p, r);
-          }
-        } else if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
-          if (act) fast_update<S, i>(q, sm, 0, 0, val[i]);
-        } else if constexpr (kind != AK_COUNT) {
-          if (act) fast_index_update<S, i>(q, sm, t, 0, 0, o);
-        }
-      });
-    } else {
-      if constexpr (seg_reducible<S>()) {
-        // Sorted keys (runs of equal groups among consecutive passing rows):
-        // reduce each run of equal gids across the warp first and let its
-        // last lane update the table once -- COUNT = run length, SUM and
-        // MIN / MAX by a segmented shuffle scan.  Taken when the runs average
-        // two or more rows; otherwise every lane updates (below).
-        const auto prev = __shfl_up_sync(0xFFFFFFFFu, gid, 1);
-        const uint32_t actm = __ballot_sync(0xFFFFFFFFu, act);
-        const bool head = act && (lane == 0 || prev != gid);
-        const uint32_t heads = __ballot_sync(0xFFFFFFFFu, head);
-        if (2 * __popc(heads) <= __popc(actm)) {
-          const uint32_t upto = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
-          const int seg0 = 31 - __clz(heads & upto);   // first lane of my run (act lanes)
-          const bool tail = act && (lane == 31 || !((actm >> (lane + 1)) & 1u) || ((heads >> (lane + 1)) & 1u));
-          int red[S::n_aggs + 1];
-          constexpr bool packed = pk_ok<S>();
-          if constexpr (packed) {
-            // every SUM at once: an inclusive prefix scan of the packed
-            // fields, a run's sum the difference at its ends (fields never
-            // carry into each other)
-            uint32_t pw0 = 0, pw1 = 0;
-            static_for<S::n_aggs>([&](auto A) {
-              constexpr int i = decltype(A)::value;
-              if constexpr (S::akind(i) == AK_SUM) {
-                const uint32_t x = act ? ((uint32_t)val[i] << pk_place<S>(i, false)) : 0u;
-                if constexpr (pk_place<S>(i, true) == 0) pw0 += x;
-                else pw1 += x;
-              }
-            });
-            constexpr bool two = [] {
-              for (int i = 0; i < S::n_aggs; ++i)
-                if (S::akind(i) == AK_SUM && pk_place<S>(i, true) == 1) return true;
-              return false;
-            }();
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-              const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, pw0, d);
-              if (lane >= d) pw0 += y0;
-              if constexpr (two) {
-                const uint32_t y1 = __shfl_up_sync(0xFFFFFFFFu, pw1, d);
-                if (lane >= d) pw1 += y1;
-              }
-            }
-            const int src = seg0 > 0 ? seg0 - 1 : 0;
-            uint32_t b0 = __shfl_sync(0xFFFFFFFFu, pw0, src), b1 = 0;
-            if constexpr (two) b1 = __shfl_sync(0xFFFFFFFFu, pw1, src);
-            if (seg0 == 0) b0 = b1 = 0;
-            static_for<S::n_aggs>([&](auto A) {
-              constexpr int i = decltype(A)::value;
-              if constexpr (S::akind(i) == AK_SUM) {
-                constexpr int off = pk_place<S>(i, false), width = S::aub(i) + 5;
-                const uint32_t dw = pk_place<S>(i, true) == 0 ? pw0 - b0 : pw1 - b1;
-                red[i] = (int)((dw >> off) & (width >= 32 ? 0xFFFFFFFFu : ((1u << width) - 1u)));
-              }
-            });
-          }
-          static_for<S::n_aggs>([&](auto A) {
-            constexpr int i = decltype(A)::value;
-            constexpr int kind = S::akind(i);
-            if constexpr ((kind == AK_SUM && !packed) || kind == AK_MIN || kind == AK_MAX) {
-              constexpr bool mn = kind == AK_MIN;
-              int x = act ? (int)val[i] : (kind == AK_SUM ? 0 : (mn ? INT_MAX : INT_MIN));
-#pragma unroll
-              for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-                if (lane - d >= seg0) x = kind == AK_SUM ? x + y : (mn ? min(x, y) : max(x, y));
-              }
-              red[i] = x;
-            }
-          });
-          if (tail) {
-            int slot = -1;
-            uint32_t gi = 0;
-            bool ok = true;
-            const unsigned cnt = (unsigned)(lane - seg0 + 1);
-            if constexpr (S::table_dense) slot = (int)gid;
-            else if constexpr (S::line_mode) slot = line_ok ? (int)gid : -1;
-            else slot = table_slot_t<S::ghash>(q, sm, gid);
-            if (slot >= 0) {
-              atomicAdd(scount(q, sm, slot), cnt);
-            } else {
-              const long long g = gindex_t<S::ghash>(q, gid);
-              ok = g >= 0;
-              gi = (uint32_t)g;
-              if (ok) atomicAdd(gword(q, 0, gi), (unsigned long long)cnt);
-            }
-            static_for<S::n_aggs>([&](auto A) {
-              constexpr int i = decltype(A)::value;
-              constexpr int kind = S::akind(i);
-              if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
-                if (ok) fast_update<S, i>(q, sm, slot, gi, (long long)red[i]);
-              }
-            });
-          }
-          continue;
-        }
-      }
-      int slot = -1;
-      uint32_t gi = 0;   // global accumulator index, used when the shared table has no slot
-      if (act) {
-        if constexpr (S::table_dense) slot = (int)gid;
-        else if constexpr (S::line_mode) slot = line_ok ? (int)gid : -1;
-        else slot = table_slot_t<S::ghash>(q, sm, gid);
-        if (slot >= 0) {
-          atomicAdd(scount(q, sm, slot), 1u);
-        } else {
-          const long long g = gindex_t<S::ghash>(q, gid);
-          if (g < 0) act = false;   // global hash table full: the host retries larger
-          gi = (uint32_t)g;
-          if (act) atomicAdd(gword(q, 0, gi), 1ull);
-        }
-      }
-      static_for<S::n_aggs>([&](auto A) {
-        constexpr int i = decltype(A)::value;
-        constexpr int kind = S::akind(i);
-        if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
-          if (act) fast_update<S, i>(q, sm, slot, gi, val[i]);
-        } else if constexpr (kind != AK_COUNT) {
-          if (act) fast_index_update<S, i>(q, sm, t, slot, gi, o);
-        }
-      });
-    }
+    const bool act = j < n_pass;
+    fast_agg_step<S>(q, sm, t, list[act ? j : j0], act, row0, line_ok, line_cur);
   }
 }
 
@@ -724,7 +733,6 @@ struct FastBody {
                                               uint32_t rows, uint16_t* list, unsigned long long row0) {
     constexpr uint32_t GS = NCW * 32;
     const uint32_t pm = fast_filter<S, GS, GPW>(q, tv, wbase, rows);
-    const uint32_t n_pass = compact<GPW>(pm, wbase, GS, list);
     bool line_ok = false;
     unsigned long long line_cur = 0;
     if constexpr (S::line_mode) {
@@ -736,7 +744,32 @@ struct FastBody {
       line_ok = nset < (1u << q.line_log2);
       if (line_ok && wbase == 0) line_digits(q, sm, tv, line_cur, nset);
     }
-    fast_aggregate<S>(q, sm, tv, list, n_pass, row0, line_ok, line_cur);
+    bool in_place = false;
+    if constexpr (seg_reducible<S>() && !S::one_group) {
+      // passing rows in long stretches (sorted data): when at least half of
+      // the warp's non-empty 32-row groups pass whole, aggregate the groups
+      // in place (lane = row), without compaction
+      uint32_t full = 0, busy = 0;
+#pragma unroll
+      for (int g = 0; g < GPW; ++g) {
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (pm >> g) & 1u);
+        full += bal == 0xFFFFFFFFu ? 1u : 0u;
+        busy += bal != 0u ? 1u : 0u;
+      }
+      in_place = busy != 0 && 2 * full >= busy;
+      if (in_place) {
+        const int lane = threadIdx.x & 31;
+        for (int g = 0; g < GPW; ++g) {
+          const bool ok = (pm >> g) & 1u;
+          if (__ballot_sync(0xFFFFFFFFu, ok))
+            fast_agg_step<S>(q, sm, tv, wbase + g * GS + lane, ok, row0, line_ok, line_cur);
+        }
+      }
+    }
+    if (!in_place) {
+      const uint32_t n_pass = compact<GPW>(pm, wbase, GS, list);
+      fast_aggregate<S>(q, sm, tv, list, n_pass, row0, line_ok, line_cur);
+    }
     // the lines of the runs that ended before this tile
     if constexpr (S::line_mode)
       fast_flush_lines<S>(q, sm, tv.line_base, line_cur, threadIdx.x, NCW * 32);

@@ -117,7 +117,7 @@ class Pred:
 
 @dataclasses.dataclass
 class Agg:
-    op: str                         # sum count min max avg
+    op: str                         # sum count min max avg var_pop var_samp std_pop std_samp
     col: int = 0                    # ignored for count
 
 

@@ -11,6 +11,9 @@ definition of an LSB-first stream.  Small inputs only.
 """
 from __future__ import annotations
 
+import math
+from fractions import Fraction
+
 import numpy as np
 
 
@@ -127,6 +130,21 @@ def query(table, plan):
             continue
         v = flat[a.col][rows]
         col = table.columns[a.col]
+        if a.op in ("var_pop", "var_samp", "std_pop", "std_samp"):
+            # Section 7: from COUNT, SUM and the sum of squares; the exact
+            # rational rounded once (Fraction -> float), STD its square root
+            s1, s2, cnt = [0] * G, [0] * G, [0] * G
+            for g, x in zip(inv.tolist(), v.tolist()):
+                s1[g] += int(x)
+                s2[g] += int(x) * int(x)
+                cnt[g] += 1
+            out = []
+            for g in range(G):
+                n_, d = cnt[g], cnt[g] - (1 if a.op.endswith("samp") else 0)
+                var = float(Fraction(n_ * s2[g] - s1[g] * s1[g], n_ * d)) if n_ and d else 0.0
+                out.append(math.sqrt(var) if a.op.startswith("std") else var)
+            aggs.append(np.array(out, dtype=np.float64))
+            continue
         if a.op in ("sum", "avg"):
             s = [0] * G
             for g, x in zip(inv.tolist(), v.tolist()):        # scatter(reduce=sum)

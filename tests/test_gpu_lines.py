@@ -133,3 +133,26 @@ def test_short_runs_keep_the_hash_table(cq, ctx, oracle_mod):
     table = dg.Table([a, b, v, v], n)
     plan = dg.Plan([], [0, 1], AGGS)
     check(run(cq, ctx, table, plan), oracle_mod.query(table, plan, n_threads=4), "short runs")
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_in_place_groups_with_holes(cq, ctx, oracle_mod, seed):
+    """Sorted keys and a filter that passes rows in stretches: most 32-row
+    groups pass whole and are aggregated in place; the stretches' edges leave
+    groups with holes, where a run of equal keys must not span a failing row."""
+    rng = np.random.default_rng(300 + seed)
+    n = 700_001
+    key = dg.Plain((np.arange(n) // int(rng.integers(3, 40))).astype(np.int32) % 4000)
+    sel = dg.make_rle(rng, n, float(rng.choice([20.0, 70.0, 300.0])), 0, 9, np.int32, np.int32)
+    v = dg.make_packed(rng.integers(0, 1 << 10, size=n).astype(np.uint64), 10, 5)
+    w = dg.Plain(rng.integers(-500, 500, size=n).astype(np.int32))
+    table = dg.Table([key, sel, v, w], n)
+    aggs = [dg.Agg("count"), dg.Agg("sum", 2), dg.Agg("sum", 3), dg.Agg("min", 3), dg.Agg("max", 2)]
+    for preds in ([dg.Pred(1, "lt", 6)], [dg.Pred(1, "ne", 3), dg.Pred(3, "gt", -450)]):
+        plan = dg.Plan(preds, [0], aggs)
+        check(run(cq, ctx, table, plan), oracle_mod.query(table, plan, n_threads=4), f"seed {seed} {preds}")
+        plan = dg.Plan(preds, [1, 0], aggs)
+        check(run(cq, ctx, table, plan), oracle_mod.query(table, plan, n_threads=4), f"seed {seed} {preds} rle key")
+        # SUMs of non-negative inputs only: the packed prefix sums
+        plan = dg.Plan(preds, [0], [dg.Agg("count"), dg.Agg("sum", 2), dg.Agg("avg", 2)])
+        check(run(cq, ctx, table, plan), oracle_mod.query(table, plan, n_threads=4), f"seed {seed} {preds} packed")
