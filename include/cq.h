@@ -209,10 +209,21 @@ typedef struct {
   uint32_t arg;                 /* PRED: predicate index; AND / OR: operand count; NOT: unused */
 } cq_filter_node;
 
-typedef enum { CQ_SUM = 0, CQ_COUNT = 1, CQ_MIN = 2, CQ_MAX = 3, CQ_AVG = 4 } cq_agg_op;
+/* STD and VAR follow Section 7 (computed from COUNT, SUM and the sum of the
+ * squared values): the exact rational (n * sum(x^2) - sum(x)^2) / (n * n)
+ * (population) or / (n * (n - 1)) (sample) rounded once to double, 0 when
+ * the denominator is 0; STD is the square root of that double.  Their input
+ * values must lie within +-2^31 of the column's packed base (index columns:
+ * of its default), else planning fails with CQ_ERR_UNSUPPORTED.  Each takes
+ * a hidden SUM of the same values, so a plan holds at most 16 aggregates
+ * counting those. */
+typedef enum {
+  CQ_SUM = 0, CQ_COUNT = 1, CQ_MIN = 2, CQ_MAX = 3, CQ_AVG = 4,
+  CQ_VAR_POP = 5, CQ_VAR_SAMP = 6, CQ_STD_POP = 7, CQ_STD_SAMP = 8
+} cq_agg_op;
 
 typedef struct {
-  int32_t op;                   /* cq_agg_op; SUM / AVG are rejected on dictionary columns */
+  int32_t op;                   /* cq_agg_op; only MIN / MAX / COUNT take dictionary columns */
   uint32_t col;                 /* ignored for COUNT(*) */
 } cq_aggregate;
 

@@ -30,7 +30,8 @@ CQ_I32, CQ_I64 = 1, 2
 CQ_MEM_HOST_COPY, CQ_MEM_DEVICE_BORROW = 0, 1
 CQ_EXEC_FUSED, CQ_EXEC_DECOMPRESS_THEN_SCAN = 0, 1
 OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7}
-AGGS = {"sum": 0, "count": 1, "min": 2, "max": 3, "avg": 4}
+AGGS = {"sum": 0, "count": 1, "min": 2, "max": 3, "avg": 4, "var_pop": 5, "var_samp": 6, "std_pop": 7,
+        "std_samp": 8}
 
 
 class CQError(RuntimeError):

@@ -624,11 +624,11 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     if (use(plan->group_by[i]) < 0) return set_error(CQ_ERR_INVALID_ARG, "group-by %u: bad column %u", i, plan->group_by[i]);
   for (uint32_t i = 0; i < plan->n_aggs; ++i) {
     const cq_aggregate& a = plan->aggs[i];
-    if (a.op < CQ_SUM || a.op > CQ_AVG) return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: bad op %d", i, a.op);
+    if (a.op < CQ_SUM || a.op > CQ_STD_SAMP) return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: bad op %d", i, a.op);
     if (a.op == CQ_COUNT) continue;
     if (use(a.col) < 0) return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: bad column %u", i, a.col);
-    if ((a.op == CQ_SUM || a.op == CQ_AVG) && is_dict(tcols[a.col]))
-      return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: SUM/AVG of a dictionary column", i);
+    if (a.op != CQ_MIN && a.op != CQ_MAX && is_dict(tcols[a.col]))
+      return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: SUM/AVG/VAR/STD of a dictionary column", i);
   }
   // ---- tile / pipeline shape
   q.tile_rows = tile;
@@ -996,14 +996,62 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   }
   if (q.flush_rows < tile) q.flush_rows = tile;
   // ---- aggregates
-  q.n_aggs = (uint8_t)plan->n_aggs;
+  uint32_t n_all = plan->n_aggs;       // user aggregates, then hidden SUM companions of VAR / STD
   uint32_t sw = 0, sw32 = 1, gw = 1;   // 32-bit word 0 is COUNT
   q.has_index_agg = 0;
+  // SUM / AVG (and the hidden SUM of a VAR / STD): accumulator layout
+  auto plan_sum = [&](AggDesc& d, const PlanCol& pc, const ColDesc& cd, bool idx) {
+    d.kind = idx ? AK_ISUM : AK_SUM;
+    i128 bound;
+    if (idx) {
+      bound = (i128)pc.stats.max_abs_val + (pc.base < 0 ? -(i128)pc.base : (i128)pc.base);
+      d.base = pc.base;
+    } else if (cd.raw_is_offset && pc.enc == ENC_PACKED) {
+      bound = (i128)std::max<int64_t>(pc.stats.max_raw, 0);
+      d.base = pc.base;
+    } else {
+      bound = pc.stats.max_abs_val;
+      d.base = 0;
+    }
+    d.wide = bound * (i128)q.flush_rows >= ((i128)1 << 62) ? 1 : 0;
+    // raw values small enough to be summed across a warp batch in 32 bits
+    i128 rlo, rhi;
+    if (cd.raw_is_offset) { rlo = pc.stats.min_raw; rhi = pc.stats.max_raw; }
+    else { rlo = pc.stats.min_val; rhi = pc.stats.max_val; }
+    // a warp reduces up to 128 values (4 per lane) in 32 bits
+    d.red32 = (!idx && !d.wide && rlo > -((i128)1 << 24) && rhi < ((i128)1 << 24)) ? 1 : 0;
+    d.ubits = 0;
+    if (d.red32 && rlo >= 0) {
+      uint8_t b = 1;
+      while (((i128)1 << b) <= rhi) ++b;
+      d.ubits = b;
+    }
+    d.n32 = (d.red32 && narrow_col(cd, pc)) ? 1 : 0;
+    {
+      const i128 b = std::max<i128>(rhi < 0 ? -rhi : rhi, rlo < 0 ? -rlo : rlo) + 1;
+      const i128 limit = rlo >= 0 ? ((i128)1 << 32) : ((i128)1 << 31);
+      d.s32 = (!idx && b * (i128)q.flush_rows < limit) ? (rlo >= 0 ? 1 : 2) : 0;
+      // else, row mode, inputs in [0, 2^24): two 32-bit limb words, the low
+      // kSplitBits bits and the rest, each updated without a returned value;
+      // a flush period of at most 2^20 rows keeps both below 2^32
+      if (!d.s32 && !idx && !q.seg_mode && rlo >= 0 && rhi < ((i128)1 << 24) && q.flush_rows <= (1u << 20))
+        d.s32 = 3;
+    }
+    if (d.s32) {
+      d.sw32 = (uint8_t)sw32;
+      sw32 += d.s32 == 3 ? 2 : 1;
+    } else {
+      d.sw = (uint8_t)sw;
+      sw += d.wide ? 2 : 1;
+    }
+    d.gw = gw;
+    gw += 3;
+  };
   for (uint32_t i = 0; i < plan->n_aggs; ++i) {
     const cq_aggregate& a = plan->aggs[i];
     AggDesc& d = q.aggs[i];
     d.op = (uint8_t)a.op;
-    d.out_kind = a.op == CQ_COUNT ? 1 : (a.op == CQ_AVG ? 2 : 0);
+    d.out_kind = a.op == CQ_COUNT ? 1 : ((a.op == CQ_AVG || a.op >= CQ_VAR_POP) ? 2 : 0);
     if (a.op == CQ_COUNT) {
       d.kind = AK_COUNT;
       continue;
@@ -1014,52 +1062,36 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     d.col = (uint8_t)ci;
     const bool idx = pc.enc == ENC_INDEX;
     if (idx) q.has_index_agg = 1;
-    if (a.op == CQ_SUM || a.op == CQ_AVG) {
-      d.kind = idx ? AK_ISUM : AK_SUM;
+    if (a.op >= CQ_VAR_POP) {
+      // VAR / STD (Section 7): the sum of squares of shifted values r (raw
+      // offsets of a packed column, value - default of an index column), a
+      // hidden SUM of the same r, and COUNT; a shift leaves a variance as is
       i128 bound;
-      if (idx) {
-        bound = (i128)pc.stats.max_abs_val + (pc.base < 0 ? -(i128)pc.base : (i128)pc.base);
-        d.base = pc.base;
-      } else if (cd.raw_is_offset && pc.enc == ENC_PACKED) {
-        bound = (i128)std::max<int64_t>(pc.stats.max_raw, 0);
-        d.base = pc.base;
-      } else {
-        bound = pc.stats.max_abs_val;
-        d.base = 0;
-      }
-      d.wide = bound * (i128)q.flush_rows >= ((i128)1 << 62) ? 1 : 0;
-      // raw values small enough to be summed across a warp batch in 32 bits
-      i128 rlo, rhi;
-      if (cd.raw_is_offset) { rlo = pc.stats.min_raw; rhi = pc.stats.max_raw; }
-      else { rlo = pc.stats.min_val; rhi = pc.stats.max_val; }
-      // a warp reduces up to 128 values (4 per lane) in 32 bits
-      d.red32 = (!idx && !d.wide && rlo > -((i128)1 << 24) && rhi < ((i128)1 << 24)) ? 1 : 0;
-      d.ubits = 0;
-      if (d.red32 && rlo >= 0) {
-        uint8_t b = 1;
-        while (((i128)1 << b) <= rhi) ++b;
-        d.ubits = b;
-      }
-      d.n32 = (d.red32 && narrow_col(cd, pc)) ? 1 : 0;
-      {
-        const i128 b = std::max<i128>(rhi < 0 ? -rhi : rhi, rlo < 0 ? -rlo : rlo) + 1;
-        const i128 limit = rlo >= 0 ? ((i128)1 << 32) : ((i128)1 << 31);
-        d.s32 = (!idx && b * (i128)q.flush_rows < limit) ? (rlo >= 0 ? 1 : 2) : 0;
-        // else, row mode, inputs in [0, 2^24): two 32-bit limb words, the low
-        // kSplitBits bits and the rest, each updated without a returned value;
-        // a flush period of at most 2^20 rows keeps both below 2^32
-        if (!d.s32 && !idx && !q.seg_mode && rlo >= 0 && rhi < ((i128)1 << 24) && q.flush_rows <= (1u << 20))
-          d.s32 = 3;
-      }
-      if (d.s32) {
-        d.sw32 = (uint8_t)sw32;
-        sw32 += d.s32 == 3 ? 2 : 1;
-      } else {
-        d.sw = (uint8_t)sw;
-        sw += d.wide ? 2 : 1;
-      }
+      if (idx) bound = std::max<i128>((i128)pc.stats.max_val - pc.base, (i128)pc.base - pc.stats.min_val);
+      else if (cd.raw_is_offset) bound = std::max<i128>(pc.stats.max_raw, -(i128)pc.stats.min_raw);
+      else bound = std::max<i128>(pc.stats.max_val, -(i128)pc.stats.min_val);
+      if (bound >= ((i128)1 << 31))
+        return set_error(CQ_ERR_UNSUPPORTED, "aggregate %u: VAR/STD take values within +-2^31 of the column's base", i);
+      if (n_all >= (uint32_t)kMaxAggs)
+        return set_error(CQ_ERR_INVALID_ARG, "plan exceeds 16 aggregates counting those VAR/STD add");
+      d.kind = idx ? AK_ISUM2 : AK_SUM2;
+      d.base = idx ? pc.base : 0;
+      d.wide = bound * bound * (i128)q.flush_rows >= ((i128)1 << 62) ? 1 : 0;
+      d.red32 = d.ubits = d.n32 = d.s32 = d.w32 = 0;
+      d.sw = (uint8_t)sw;
+      sw += d.wide ? 2 : 1;
       d.gw = gw;
       gw += 3;
+      d.pair = (uint8_t)n_all;
+      AggDesc& c = q.aggs[n_all++];
+      memset(&c, 0, sizeof(c));
+      c.op = CQ_SUM;
+      c.col = (uint8_t)ci;
+      plan_sum(c, pc, cd, idx);
+      continue;
+    }
+    if (a.op == CQ_SUM || a.op == CQ_AVG) {
+      plan_sum(d, pc, cd, idx);
     } else {  // MIN / MAX
       i128 rlo, rhi;
       if (idx || cd.raw_is_offset) { rlo = pc.stats.min_raw; rhi = pc.stats.max_raw; }
@@ -1085,6 +1117,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
       }
     }
   }
+  q.n_aggs = (uint8_t)n_all;
   q.n_sw = (uint8_t)sw;
   q.n_sw32 = (uint8_t)sw32;
   q.n_gw = (uint8_t)gw;

@@ -47,6 +47,9 @@ enum AggKind : uint8_t {
   AK_ISUM = 4,      // index column: sum of (value - default) over listed passing rows
   AK_IMIN = 5,      // index column: min over listed passing rows + listed count
   AK_IMAX = 6,
+  AK_SUM2 = 7,      // VAR / STD: sum of squared raw values (shifted by the packed base, which
+                    // leaves a variance unchanged); its SUM companion is aggregate `pair`
+  AK_ISUM2 = 8,     // index column: sum of (value - default)^2 over listed passing rows
 };
 
 // Device view of one referenced column.
@@ -119,6 +122,7 @@ struct AggDesc {
                      // (sw32: the inputs' low kSplitBits bits, sw32 + 1: the rest), inputs
                      // in [0, 2^24), flush period <= 2^20 rows
   int64_t base;      // value added back at finalize (packed base or index default)
+  uint8_t pair;      // AK_SUM2 / AK_ISUM2: the hidden SUM of the same values
 };
 
 struct QueryDesc {

@@ -297,6 +297,15 @@ __device__ __forceinline__ void fast_update(const QueryDesc& q, const Smem& sm, 
     } else {
       global_add_limbs(gword(q, S::agw(I), gid), gword(q, S::agw(I) + 1, gid), gword(q, S::agw(I) + 2, gid), sext(v));
     }
+  } else if constexpr (kind == AK_SUM2) {
+    const long long v2 = v * v;   // |v| < 2^31 (planner)
+    if (slot >= 0) {
+      if constexpr (!S::awide(I)) smem_add64(&sm.tacc[(size_t)S::asw(I) * slots + slot], v2);
+      else atomic_add_i128(&sm.tacc[(size_t)S::asw(I) * slots + slot], &sm.tacc[(size_t)(S::asw(I) + 1) * slots + slot],
+                           sext(v2));
+    } else {
+      global_add_limbs(gword(q, S::agw(I), gid), gword(q, S::agw(I) + 1, gid), gword(q, S::agw(I) + 2, gid), sext(v2));
+    }
   } else if constexpr (kind == AK_MIN || kind == AK_MAX) {
     constexpr bool mn = kind == AK_MIN;
     if (slot >= 0) {
@@ -333,6 +342,9 @@ __device__ __forceinline__ void fast_index_update(const QueryDesc& q, const Smem
   if (!index_lookup(q.cols[S::acol(I)], t, o, &v)) return;
   if constexpr (kind == AK_ISUM) {
     sum_add(q, sm, a, slot, gid, index_delta(v, a.base));
+  } else if constexpr (kind == AK_ISUM2) {
+    const long long dv = v - a.base;   // |v - default| < 2^31 (planner)
+    sum_add(q, sm, a, slot, gid, sext(dv * dv));
   } else {
     minmax_add(q, sm, a, slot, gid, v, kind == AK_IMIN);
     if (slot >= 0) atomicAdd(slisted(q, sm, a, slot), 1u);
@@ -349,7 +361,7 @@ __device__ constexpr bool seg_reducible() {
     const int k = S::akind(i);
     if (k == AK_SUM && !S::ared32(i)) return false;
     if ((k == AK_MIN || k == AK_MAX) && !S::aw32(i)) return false;
-    if (k == AK_ISUM || k == AK_IMIN || k == AK_IMAX) return false;
+    if (k == AK_ISUM || k == AK_IMIN || k == AK_IMAX || k == AK_SUM2 || k == AK_ISUM2) return false;
   }
   return true;
 }
@@ -438,7 +450,7 @@ __device__ __forceinline__ void fast_agg_step(const QueryDesc& q, const Smem& sm
   static_for<S::n_aggs>([&](auto A) {
     constexpr int i = decltype(A)::value;
     constexpr int kind = S::akind(i);
-    if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+    if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX || kind == AK_SUM2) {
       if constexpr (S::asrc(i) == i) {
         if constexpr (S::an32(i)) val[i] = (long long)fast_raw32<S, S::acol(i)>(q, t, o);
         else val[i] = fast_raw<S, S::acol(i)>(q, t, o);
@@ -470,7 +482,7 @@ __device__ __forceinline__ void fast_agg_step(const QueryDesc& q, const Smem& sm
           if (mn) atomicMin(p, r);
           else atomicMax(p, r);
         }
-      } else if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+      } else if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX || kind == AK_SUM2) {
         if (act) fast_update<S, i>(q, sm, 0, 0, val[i]);
       } else if constexpr (kind != AK_COUNT) {
         if (act) fast_index_update<S, i>(q, sm, t, 0, 0, o);
@@ -593,7 +605,7 @@ __device__ __forceinline__ void fast_agg_step(const QueryDesc& q, const Smem& sm
     static_for<S::n_aggs>([&](auto A) {
       constexpr int i = decltype(A)::value;
       constexpr int kind = S::akind(i);
-      if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+      if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX || kind == AK_SUM2) {
         if (act) fast_update<S, i>(q, sm, slot, gi, val[i]);
       } else if constexpr (kind != AK_COUNT) {
         if (act) fast_index_update<S, i>(q, sm, t, slot, gi, o);
@@ -649,7 +661,7 @@ __device__ __forceinline__ void fast_flush_slot(const QueryDesc& q, const Smem& 
   static_for<S::n_aggs>([&](auto A) {
     constexpr int i = decltype(A)::value;
     constexpr int kind = S::akind(i);
-    if constexpr (kind == AK_SUM || kind == AK_ISUM) {
+    if constexpr (kind == AK_SUM || kind == AK_ISUM || kind == AK_SUM2 || kind == AK_ISUM2) {
       I128 x;
       if constexpr (S::as32(i) == 3) {
         x = sext(split_value(sword32(q, sm, S::asw32(i), s), sword32(q, sm, S::asw32(i) + 1, s)));

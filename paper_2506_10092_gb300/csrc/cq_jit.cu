@@ -151,10 +151,13 @@ static std::string shape_source(const QueryDesc& q, int ncw, int gpw, int minb) 
     as32.push_back(a.s32);
     // the value read of an earlier aggregate on the same column is reused
     int src = i;
-    const bool plain_kind = a.kind == AK_SUM || a.kind == AK_MIN || a.kind == AK_MAX;
+    auto plain = [](const AggDesc& x) {
+      return x.kind == AK_SUM || x.kind == AK_MIN || x.kind == AK_MAX || x.kind == AK_SUM2;
+    };
+    const bool plain_kind = plain(a);
     for (int j = 0; j < i && plain_kind; ++j) {
       const AggDesc& b = q.aggs[j];
-      if ((b.kind == AK_SUM || b.kind == AK_MIN || b.kind == AK_MAX) && b.col == a.col && b.n32 == a.n32) {
+      if (plain(b) && b.col == a.col && b.n32 == a.n32) {
         src = j;
         break;
       }
@@ -385,6 +388,12 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
     agg(4, AK_IMAX, 1, 5, 0, 2, 8, 0, 0, 0, 0);
     agg(5, AK_SUM, 0, 6, 0, 0, 10, 0, 0, 0, 0);
     agg(6, AK_SUM, 4, 7, 0, 0, 13, 1, 0, 0, 0);
+    if (variant == 2) {   // sums of squares (VAR / STD) of a plain and of an index column
+      q->aggs[5].kind = AK_SUM2;
+      q->aggs[5].pair = 6;
+      q->aggs[3].kind = AK_ISUM2;
+      q->aggs[3].pair = 0;
+    }
   }
 }
 }  // namespace cq

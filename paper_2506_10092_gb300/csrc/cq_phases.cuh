@@ -569,6 +569,8 @@ __device__ __forceinline__ void reset_slot(const QueryDesc& q, const Smem& sm, u
     switch (a.kind) {
       case AK_SUM:
       case AK_ISUM:
+      case AK_SUM2:
+      case AK_ISUM2:
         if (a.s32) {
           *sword32(q, sm, a.sw32, s) = 0;
           if (a.s32 == 3) *sword32(q, sm, a.sw32 + 1, s) = 0;
@@ -605,7 +607,9 @@ __device__ inline void flush_slot(const QueryDesc& q, const Smem& sm, uint32_t s
     const AggDesc& a = q.aggs[i];
     switch (a.kind) {
       case AK_SUM:
-      case AK_ISUM: {
+      case AK_ISUM:
+      case AK_SUM2:
+      case AK_ISUM2: {
         I128 x;
         if (a.s32 == 3) {
           x = sext(split_value(sword32(q, sm, a.sw32, s), sword32(q, sm, a.sw32 + 1, s)));
@@ -820,6 +824,7 @@ template <bool SEG>
 __device__ __forceinline__ void agg_item(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot,
                                          uint32_t gi, long long v, uint32_t len) {
   if (a.kind == AK_SUM) sum_add(q, sm, a, slot, gi, SEG ? mul_s64(v, (long long)len) : sext(v));
+  else if (a.kind == AK_SUM2) sum_add(q, sm, a, slot, gi, SEG ? mul_s64(v * v, (long long)len) : sext(v * v));
   else minmax_add(q, sm, a, slot, gi, v, a.kind == AK_MIN);
 }
 
@@ -927,7 +932,7 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
       const AggDesc& a = q.aggs[ai];
       if (a.kind == AK_COUNT) continue;
       const ColDesc& c = q.cols[a.col];
-      if (a.kind == AK_ISUM || a.kind == AK_IMIN || a.kind == AK_IMAX) {
+      if (a.kind == AK_ISUM || a.kind == AK_ISUM2 || a.kind == AK_IMIN || a.kind == AK_IMAX) {
         // index column: only listed rows differ from the default, which the
         // finalize step adds back from COUNT
 #pragma unroll
@@ -936,6 +941,9 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
           if (act[m] && index_lookup(c, t, o[m], &v)) {
             if (a.kind == AK_ISUM) {
               sum_add(q, sm, a, slot[m], gi[m], index_delta(v, a.base));
+            } else if (a.kind == AK_ISUM2) {
+              const long long dv = v - a.base;   // |v - default| < 2^31 (planner)
+              sum_add(q, sm, a, slot[m], gi[m], sext(dv * dv));
             } else {
               minmax_add(q, sm, a, slot[m], gi[m], v, a.kind == AK_IMIN);
               if (slot[m] >= 0) atomicAdd(slisted(q, sm, a, slot[m]), 1u);

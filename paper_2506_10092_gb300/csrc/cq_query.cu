@@ -65,6 +65,8 @@ __device__ __forceinline__ void init_group(const QueryDesc& q, size_t i) {
     switch (a.kind) {
       case AK_SUM:
       case AK_ISUM:
+      case AK_SUM2:
+      case AK_ISUM2:
         q.gacc[(size_t)a.gw * G + i] = 0;
         q.gacc[(size_t)(a.gw + 1) * G + i] = 0;
         q.gacc[(size_t)(a.gw + 2) * G + i] = 0;
@@ -94,7 +96,7 @@ __global__ void fold_sums_kernel(const __grid_constant__ QueryDesc q) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < G; i += (size_t)gridDim.x * blockDim.x) {
     for (int ai = 0; ai < q.n_aggs; ++ai) {
       const AggDesc& a = q.aggs[ai];
-      if (a.kind != AK_SUM && a.kind != AK_ISUM) continue;
+      if (a.kind != AK_SUM && a.kind != AK_ISUM && a.kind != AK_SUM2 && a.kind != AK_ISUM2) continue;
       unsigned long long* w0 = &q.gacc[(size_t)a.gw * G + i];
       unsigned long long* w1 = &q.gacc[(size_t)(a.gw + 1) * G + i];
       unsigned long long* w2 = &q.gacc[(size_t)(a.gw + 2) * G + i];
@@ -201,6 +203,113 @@ __device__ __forceinline__ I128 add128(I128 a, I128 b) {
   return r;
 }
 
+// ------------------------------------------------------------------ VAR / STD
+// n / d rounded once to the nearest double (ties to even) for a 256-bit n
+// (limbs n[0] least significant) and a 128-bit d = (d1, d0) > 0: restoring
+// long division, one quotient bit per step, until 64 significant quotient
+// bits are known; later quotient bits and the remainder make a sticky bit
+// below the double's rounding position.
+__device__ double div_rn_256(const unsigned long long n[4], unsigned long long d0, unsigned long long d1) {
+  int top_bit = 255;
+  while (top_bit >= 0 && !((n[top_bit >> 6] >> (top_bit & 63)) & 1ull)) --top_bit;
+  if (top_bit < 0) return 0.0;
+  unsigned long long r0 = 0, r1 = 0, r2 = 0;   // remainder, below 2 d < 2^129
+  auto step = [&](unsigned long long in) -> bool {
+    r2 = (r2 << 1) | (r1 >> 63);
+    r1 = (r1 << 1) | (r0 >> 63);
+    r0 = (r0 << 1) | in;
+    const bool ge = r2 != 0 || r1 > d1 || (r1 == d1 && r0 >= d0);
+    if (ge) {
+      const unsigned long long b = r0 < d0 ? 1ull : 0ull;
+      r0 -= d0;
+      r1 = r1 - d1 - b;
+      r2 = 0;
+    }
+    return ge;
+  };
+  unsigned long long top = 0;
+  int got = 0, e = 0;
+  bool sticky = false;
+  for (int i = top_bit; i >= 0; --i) {
+    const bool qb = step((n[i >> 6] >> (i & 63)) & 1ull);
+    if (got < 64) {
+      if (got || qb) {
+        top = (top << 1) | (qb ? 1ull : 0ull);
+        ++got;
+      }
+    } else {
+      sticky = sticky || qb;
+      ++e;
+    }
+  }
+  while (got < 64) {
+    const bool qb = step(0);
+    if (got || qb) {
+      top = (top << 1) | (qb ? 1ull : 0ull);
+      ++got;
+    }
+    --e;
+  }
+  sticky = sticky || (r0 | r1 | r2) != 0;
+  return scalbn(__ull2double_rn(top | (sticky ? 1ull : 0ull)), e);
+}
+
+// Variance of a group (Section 7: from COUNT, SUM and the sum of squares):
+// (n * s2 - s1^2) / (n * (n or n - 1)), exact up to the final rounding; 0
+// when the denominator is 0.  s2 >= 0 below 2^126, |s1| below 2^127.
+__device__ double variance(unsigned long long n, I128 s1, I128 s2, bool sample) {
+  const unsigned long long den1 = sample ? n - 1 : n;
+  if (n == 0 || den1 == 0) return 0.0;
+  // |s1|
+  unsigned long long a0 = s1.lo, a1 = (unsigned long long)s1.hi;
+  if (s1.hi < 0) {
+    a0 = ~a0 + 1ull;
+    a1 = ~a1 + (a0 == 0 ? 1ull : 0ull);
+  }
+  // s1^2 (256 bits): a0^2 + 2 a0 a1 2^64 + a1^2 2^128
+  unsigned long long sq[4];
+  {
+    const unsigned long long p00l = a0 * a0, p00h = __umul64hi(a0, a0);
+    const unsigned long long p01l = a0 * a1, p01h = __umul64hi(a0, a1);
+    const unsigned long long p11l = a1 * a1, p11h = __umul64hi(a1, a1);
+    // cross term doubled: (p01h:p01l) * 2 -> 129 bits
+    const unsigned long long c2 = p01h >> 63, x1 = (p01h << 1) | (p01l >> 63), x0 = p01l << 1;
+    sq[0] = p00l;
+    unsigned long long t = p00h + x0;
+    unsigned long long c = t < p00h ? 1ull : 0ull;
+    sq[1] = t;
+    t = p11l + x1;
+    unsigned long long cc = t < p11l ? 1ull : 0ull;
+    const unsigned long long t2 = t + c;
+    cc += t2 < t ? 1ull : 0ull;
+    sq[2] = t2;
+    sq[3] = p11h + c2 + cc;
+  }
+  // n * s2 (s2 < 2^126: at most 190 bits)
+  unsigned long long ns[4];
+  {
+    const unsigned long long s0 = s2.lo, s1w = (unsigned long long)s2.hi;
+    const unsigned long long l0 = n * s0, h0 = __umul64hi(n, s0);
+    const unsigned long long l1 = n * s1w, h1 = __umul64hi(n, s1w);
+    ns[0] = l0;
+    ns[1] = h0 + l1;
+    ns[2] = h1 + (ns[1] < h0 ? 1ull : 0ull);
+    ns[3] = 0;
+  }
+  // numerator = n s2 - s1^2 >= 0
+  unsigned long long num[4];
+  unsigned long long borrow = 0;
+  for (int i = 0; i < 4; ++i) {
+    const unsigned long long x = ns[i], y = sq[i];
+    const unsigned long long d = x - y - borrow;
+    borrow = (x < y || (x == y && borrow)) ? 1ull : 0ull;
+    num[i] = d;
+  }
+  // denominator n * den1 (128 bits)
+  const unsigned long long d0 = n * den1, d1 = __umul64hi(n, den1);
+  return div_rn_256(num, d0, d1);
+}
+
 // Result row `row` of the group with packed key `key` whose accumulators sit
 // at index g (dense domains: key == g).
 __device__ __forceinline__ void write_group(const QueryDesc& q, size_t row, unsigned long long key, size_t g) {
@@ -237,6 +346,16 @@ __device__ __forceinline__ void write_group(const QueryDesc& q, size_t row, unsi
           if (!fits) report(q, CQ_ERR_OVERFLOW, 3ull + ((unsigned long long)idx << 8), g, x.lo);
           reinterpret_cast<long long*>(q.out[oc])[row] = (long long)x.lo;
         }
+        break;
+      }
+      case AK_SUM2:
+      case AK_ISUM2: {
+        // VAR / STD of the shifted values (raw offsets, or value - default):
+        // a variance does not change under a shift
+        const I128 s1 = read_sum(q, q.aggs[a.pair].gw, g), s2 = read_sum(q, a.gw, g);
+        const bool sample = a.op == CQ_VAR_SAMP || a.op == CQ_STD_SAMP;
+        const double v = variance(cnt, s1, s2, sample);
+        reinterpret_cast<double*>(q.out[oc])[row] = (a.op == CQ_STD_POP || a.op == CQ_STD_SAMP) ? sqrt(v) : v;
         break;
       }
       case AK_MIN:

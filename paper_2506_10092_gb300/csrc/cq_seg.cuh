@@ -217,6 +217,9 @@ __device__ inline void segment_update(const QueryDesc& q, const Smem& sm, const 
     const AggDesc& a = q.aggs[ai];
     if (a.kind == AK_SUM) {
       sum_add(q, sm, a, slot, gi, mul_s64(value(a.col), (long long)L));
+    } else if (a.kind == AK_SUM2) {
+      const long long v = value(a.col);   // |v| < 2^31 (planner)
+      sum_add(q, sm, a, slot, gi, mul_s64(v * v, (long long)L));
     } else if (a.kind == AK_MIN || a.kind == AK_MAX) {
       minmax_add(q, sm, a, slot, gi, value(a.col), a.kind == AK_MIN);
     } else if (a.kind != AK_COUNT) {
@@ -224,6 +227,9 @@ __device__ inline void segment_update(const QueryDesc& q, const Smem& sm, const 
       if (!listed(a.col, &v)) continue;
       if (a.kind == AK_ISUM) {
         sum_add(q, sm, a, slot, gi, index_delta(v, a.base));
+      } else if (a.kind == AK_ISUM2) {
+        const long long dv = v - a.base;
+        sum_add(q, sm, a, slot, gi, sext(dv * dv));
       } else {
         minmax_add(q, sm, a, slot, gi, v, a.kind == AK_IMIN);
         if (slot >= 0) atomicAdd(slisted(q, sm, a, slot), 1u);
