@@ -432,10 +432,11 @@ int cq_selftest_bounded_wait(cq_ctx* ctx, uint32_t limit_us, int32_t* device_sta
  * took (either may be NULL).  No counterpart in the paper.  Always CQ_OK. */
 int cq_jit_stats(uint64_t* compiles, double* seconds);
 
-/* Compile, without loading, one of six built-in shapes (variant 0 .. 5)
+/* Compile, without loading, one of eight built-in shapes (variant 0 .. 7)
  * that between them exercise every encoding, predicate kind, clause form,
  * key mapping, aggregate layout and group table of the specialised row
- * kernel (4 and 5: the run-line table): a check
+ * kernel (4 and 5: the run-line table; 6 and 7: the serial walk of sorted
+ * data): a check
  * of the run-time compiler that needs no GPU.  *seconds (may be NULL)
  * receives the compile time.  CQ_ERR_INVALID_ARG for another variant,
  * CQ_ERR_CUDA (with the compiler's log in cq_last_error) when compilation

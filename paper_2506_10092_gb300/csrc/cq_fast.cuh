@@ -738,13 +738,263 @@ __device__ __forceinline__ void fast_flush_lines(const QueryDesc& q, const Smem&
   }
 }
 
+// ------------------------------------------------------------------ serial segments
+// Sorted data (Section 7: an aggregate over a run of equal groups is one
+// update).  Every lane walks R consecutive rows of its own from registers,
+// keeps the open stretch's group, COUNT and partial aggregates, and updates
+// the group table once per stretch of passing rows with one group: no
+// compaction, no shuffles, no per-row table access.  Taken when the filter
+// is decided by pass bitmaps alone, every key but the run-line key and every
+// aggregated value is a field of at most 32 bits of a staged column, and
+// every aggregate reduces in 32 bits.
+
+template <class S>
+__device__ constexpr int col_bits_of(int c) {
+  return S::enc(c) == ENC_PLAIN ? (S::v64(c) ? 64 : 32) : S::bw(c);
+}
+
+template <class S>
+__device__ constexpr bool staged32(int c) {
+  return ((S::enc(c) == ENC_PLAIN && !S::v64(c)) || S::enc(c) == ENC_PACKED || S::enc(c) == ENC_DICT) &&
+         col_bits_of<S>(c) <= 32;
+}
+
+// Index of column c among the staged columns (-1: not staged).
+template <class S>
+__device__ constexpr int ser_rc(int c) {
+  for (int i = 0; i < S::n_row_cols; ++i)
+    if (S::row_col(i) == c) return i;
+  return -1;
+}
+
+// Rows a lane walks: the smallest of 8, 16, 32 at which every staged
+// column's fields end on a 32-bit word boundary.
+template <class S>
+__device__ constexpr int ser_rows() {
+  int r = 8;
+  for (int i = 0; i < S::n_row_cols; ++i)
+    while ((r * col_bits_of<S>(S::row_col(i))) % 32 != 0) r *= 2;
+  return r;
+}
+
+template <class S>
+__device__ constexpr bool ser_ok() {
+  if (!seg_reducible<S>() || S::one_group || S::ghash) return false;
+  for (int i = 0; i < S::n_preds; ++i)
+    if (S::ppbm(i) == 0xFF && S::pkind(i) != PK_TRUE && S::pkind(i) != PK_FALSE) return false;
+  for (int k = 0; k < S::n_keys; ++k) {
+    if (S::line_mode && k == 0) continue;
+    if (!staged32<S>(S::kcol(k)) || ser_rc<S>(S::kcol(k)) < 0 || !S::kn32(k)) return false;
+  }
+  for (int i = 0; i < S::n_aggs; ++i) {
+    const int kind = S::akind(i);
+    if (kind == AK_COUNT) continue;
+    if (kind != AK_SUM && kind != AK_MIN && kind != AK_MAX) return false;
+    if (!staged32<S>(S::acol(i)) || ser_rc<S>(S::acol(i)) < 0 || !S::an32(i)) return false;
+  }
+  for (int i = 0; i < S::n_row_cols; ++i)
+    if (col_bits_of<S>(S::row_col(i)) > 32) return false;
+  return true;
+}
+
+// Field r (a constant) of B-bit fields held in registers, LSB first.
+template <int B, int r, int N>
+__device__ __forceinline__ uint32_t ser_field(const uint32_t (&w)[N]) {
+  constexpr int bit = r * B, wi = bit >> 5, sh = bit & 31;
+  if constexpr (B == 32) return w[wi];
+  else if constexpr (sh + B <= 32) return (w[wi] >> sh) & ((1u << B) - 1u);
+  else return __funnelshift_r(w[wi], w[wi + 1], sh) & ((1u << B) - 1u);
+}
+
+// Digit of key K from its 32-bit raw value (as fast_digit).
+template <class S, int K>
+__device__ __forceinline__ bool ser_digit(const QueryDesc& q, const TileView& t, int v, uint32_t* d) {
+  const KeyDesc& k = q.keys[K];
+  const uint32_t x = (uint32_t)v - (uint32_t)(int)k.kmin;
+  if constexpr (!S::kremap(K)) {
+    *d = x;
+    return x < k.card;
+  } else {
+    if (x >= 32u * k.aux_len) return false;
+    const uint32_t w = t.aux[k.aux_off + (x >> 5)];
+    if (!((w >> (x & 31)) & 1u)) return false;
+    *d = t.aux[k.prefix_off + (x >> 5)] + __popc(w & ((1u << (x & 31)) - 1u));
+    return true;
+  }
+}
+
+// One stretch's update: cnt rows of group gid, partial aggregates acc.
+template <class S>
+__device__ __forceinline__ void ser_flush(const QueryDesc& q, const Smem& sm, uint32_t gid, uint32_t cnt,
+                                          const int* acc) {
+  int slot;
+  uint32_t gi = 0;
+  bool ok = true;
+  if constexpr (S::table_dense || S::line_mode) slot = (int)gid;
+  else slot = table_slot_t<false>(q, sm, gid);
+  if (slot >= 0) {
+    atomicAdd(scount(q, sm, slot), cnt);
+  } else {
+    const long long g = gindex_t<false>(q, gid);
+    ok = g >= 0;
+    gi = (uint32_t)g;
+    if (ok) atomicAdd(gword(q, 0, gi), (unsigned long long)cnt);
+  }
+  static_for<S::n_aggs>([&](auto A) {
+    constexpr int i = decltype(A)::value;
+    constexpr int kind = S::akind(i);
+    if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX)
+      if (ok) fast_update<S, i>(q, sm, slot, gi, (long long)acc[i]);
+  });
+}
+
+// Rows o0 .. o0 + R - 1 of one lane: `pass` their filter bits, `starts` the
+// run-start bits of key 0's column from row o0 on (VARY: a run starts
+// inside, so the line advances), `line` the line at row o0.
+template <class S, int R, bool VARY>
+__device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, const TileView& t, uint32_t o0,
+                                         uint32_t pass, uint32_t starts, uint32_t line, unsigned long long row0) {
+  constexpr int NRC = S::n_row_cols > 0 ? S::n_row_cols : 1;
+  uint32_t w[NRC][R];
+  static_for<S::n_row_cols>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int NW = R * col_bits_of<S>(S::row_col(i)) / 32;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(t.stage + S::stage_off(S::row_col(i))) + (o0 / R) * NW;
+    if constexpr (NW % 4 == 0) {
+#pragma unroll
+      for (int j = 0; j < NW / 4; ++j) {
+        const uint4 v = reinterpret_cast<const uint4*>(src)[j];
+        w[i][4 * j] = v.x;
+        w[i][4 * j + 1] = v.y;
+        w[i][4 * j + 2] = v.z;
+        w[i][4 * j + 3] = v.w;
+      }
+    } else if constexpr (NW % 2 == 0) {
+#pragma unroll
+      for (int j = 0; j < NW / 2; ++j) {
+        const uint2 v = reinterpret_cast<const uint2*>(src)[j];
+        w[i][2 * j] = v.x;
+        w[i][2 * j + 1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NW; ++j) w[i][j] = src[j];
+    }
+  });
+  uint32_t lmask = 0;
+  if constexpr (S::line_mode) lmask = (1u << q.line_log2) - 1u;
+  uint32_t cur = 0, cnt = 0;
+  int acc[S::n_aggs + 1];
+#pragma unroll
+  for (int i = 0; i <= S::n_aggs; ++i) acc[i] = 0;
+  bool open = false;
+  static_for<R>([&](auto RI) {
+    constexpr int r = decltype(RI)::value;
+    if constexpr (VARY && r > 0) line = (line + ((starts >> r) & 1u)) & lmask;
+    bool p = (pass >> r) & 1u;
+    uint32_t g = 0;
+    static_for<S::n_keys>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      if constexpr (!(S::line_mode && k == 0)) {
+        constexpr int c = S::kcol(k);
+        const int v = (int)ser_field<col_bits_of<S>(c), r>(w[ser_rc<S>(c)]);
+        uint32_t d;
+        if (!ser_digit<S, k>(q, t, v, &d)) {
+          if (p) {
+            report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)k << 8), row0 + o0 + r,
+                   (unsigned long long)(long long)v);
+            p = false;
+          }
+          d = 0;
+        }
+        g += d * (uint32_t)q.keys[k].stride;
+      }
+    });
+    if constexpr (S::line_mode) g = line * q.line_inner + (g ^ (line & q.line_swz));
+    // the open stretch ends before this row: flush it
+    if (open && (!p || g != cur)) ser_flush<S>(q, sm, cur, cnt, acc);
+    const bool st = p && (!open || g != cur);   // a stretch starts here
+    static_for<S::n_aggs>([&](auto A) {
+      constexpr int i = decltype(A)::value;
+      constexpr int kind = S::akind(i);
+      if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
+        constexpr int c = S::acol(i);
+        const int v = (int)ser_field<col_bits_of<S>(c), r>(w[ser_rc<S>(c)]);
+        const int m = kind == AK_SUM ? acc[i] + v : (kind == AK_MIN ? min(acc[i], v) : max(acc[i], v));
+        acc[i] = st ? v : m;
+      }
+    });
+    cnt = st ? 1u : cnt + 1u;
+    cur = st ? g : cur;
+    open = p;   // (a failing row's updates above are never flushed)
+  });
+  if (open) ser_flush<S>(q, sm, cur, cnt, acc);
+}
+
+// The compute warps' serial pass over a tile: warp w takes the tile's rows
+// [w * 32 * GPW, (w + 1) * 32 * GPW), its lanes R consecutive rows each, so
+// that the lanes' staged words are consecutive in shared memory.
+template <class S, int NCW, int GPW>
+__device__ __forceinline__ void fast_serial(const QueryDesc& q, const Smem& sm, const TileView& t, uint32_t wbase,
+                                            uint32_t rows, unsigned long long row0, unsigned long long line_cur) {
+  constexpr int R = ser_rows<S>();
+  constexpr uint32_t span = GPW * 32;
+  constexpr uint32_t nw = S::tile_rows / 32;
+  constexpr uint32_t inner_bits = R == 32 ? 0xFFFFFFFEu : ((1u << R) - 2u);
+  const int lane = threadIdx.x & 31;
+  const uint32_t first = (wbase >> 5) * span;
+  for (uint32_t b = first; b < first + span; b += 32u * R) {
+    const uint32_t o0 = b + (uint32_t)lane * R;
+    uint32_t pass = 0;
+    if (o0 < first + span && o0 < rows) {
+      uint32_t valid = R == 32 ? 0xFFFFFFFFu : ((1u << R) - 1u);
+      if (rows - o0 < (uint32_t)R) valid &= (1u << (rows - o0)) - 1u;
+      // the filter's clauses over the pass-bitmap words of these rows
+      uint32_t pm = valid, acc = 0;
+      static_for<S::n_preds>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int kind = S::pkind(i);
+        constexpr int cl = S::pcl(i);
+        if constexpr (S::ppbm(i) != 0xFF) {
+          const uint32_t x = t.pbm[(size_t)S::ppbm(i) * nw + (o0 >> 5)] >> (o0 & 31);
+          if constexpr (cl == PC_ALONE) pm &= x;
+          else acc |= x;
+        } else if constexpr (kind == PK_FALSE) {
+          if constexpr (cl == PC_ALONE) pm = 0;
+        } else if constexpr (kind == PK_TRUE) {
+          if constexpr (cl != PC_ALONE) acc = ~0u;
+        }
+        if constexpr (cl == PC_LAST) {
+          pm &= acc;
+          acc = 0;
+        }
+      });
+      pass = pm & valid;
+    }
+    if (!__any_sync(0xFFFFFFFFu, pass != 0)) continue;
+    uint32_t line = 0, starts = 0;
+    bool vary = false;
+    if constexpr (S::line_mode) {
+      constexpr int jl = S::bslot(S::kcol(0));
+      const uint32_t* B = t.bm + jl * nw;
+      const uint32_t oo = o0 < rows ? o0 : 0u;
+      line = (uint32_t)(line_cur + rank_incl(B, t.pre + jl * (nw + 1), oo)) & ((1u << q.line_log2) - 1u);
+      starts = B[oo >> 5] >> (oo & 31);
+      vary = __any_sync(0xFFFFFFFFu, pass != 0 && (starts & inner_bits) != 0);
+    }
+    if (pass != 0) {
+      if (vary) ser_walk<S, R, true>(q, sm, t, o0, pass, starts, line, row0);
+      else ser_walk<S, R, false>(q, sm, t, o0, pass, starts, line, row0);
+    }
+  }
+}
+
 template <class S>
 struct FastBody {
   template <int NCW, int GPW>
   __device__ static __forceinline__ void tile(const QueryDesc& q, const Smem& sm, const TileView& tv, uint32_t wbase,
                                               uint32_t rows, uint16_t* list, unsigned long long row0) {
     constexpr uint32_t GS = NCW * 32;
-    const uint32_t pm = fast_filter<S, GS, GPW>(q, tv, wbase, rows);
     bool line_ok = false;
     unsigned long long line_cur = 0;
     if constexpr (S::line_mode) {
@@ -756,6 +1006,16 @@ struct FastBody {
       line_ok = nset < (1u << q.line_log2);
       if (line_ok && wbase == 0) line_digits(q, sm, tv, line_cur, nset);
     }
+    if constexpr (ser_ok<S>()) {
+      // (the same choice in every warp: line_ok is the tile's)
+      if (!S::line_mode || line_ok) {
+        fast_serial<S, NCW, GPW>(q, sm, tv, wbase, rows, row0, line_cur);
+        if constexpr (S::line_mode)
+          fast_flush_lines<S>(q, sm, tv.line_base, line_cur, threadIdx.x, NCW * 32);
+        return;
+      }
+    }
+    const uint32_t pm = fast_filter<S, GS, GPW>(q, tv, wbase, rows);
     bool in_place = false;
     if constexpr (seg_reducible<S>() && !S::one_group) {
       // passing rows in long stretches (sorted data): when at least half of

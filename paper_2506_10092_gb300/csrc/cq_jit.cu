@@ -277,6 +277,10 @@ int jit_row_kernel(const QueryDesc& q, int ncw, int gpw, int minb, int device, s
     k = nk;
     g_jit_total_s += nk->compile_s;
     g_jit_compiles++;
+    const char* log_env = getenv("CQ_JIT_LOG");
+    if (log_env && log_env[0] == '1')
+      fprintf(stderr, "[cq jit] shape: %d compute warps, %d groups per warp, %d CTAs per SM, %u-row tiles, %u B "
+                      "shared, line mode %d\n", ncw, gpw, minb, q.tile_rows, q.smem_bytes, (int)q.line_mode);
   }
   if (device < 64 && !((k->smem_set_mask >> device) & 1ull)) {
     cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k->kernel),
@@ -296,11 +300,53 @@ cudaError_t launch_row_jit(const void* fn, const QueryDesc& q, unsigned grid, in
 }  // namespace cq
 
 namespace cq {
-// Four synthetic shapes that between them use every encoding, predicate
+// Eight synthetic shapes that between them use every encoding, predicate
 // kind, key mapping, aggregate layout and group domain (shared hash table,
-// global hash table, single group) of the specialised body, with and without
-// the warp pre-reduction of sorted keys; only compiled.
+// run lines, global hash table, single group, dense table) of the
+// specialised body, with and without the warp pre-reduction and the serial
+// walk of sorted keys; only compiled.
 static void check_shape(uint32_t variant, QueryDesc* q) {
+  // variants 6 and 7: sorted-data shapes taking the serial walk -- a filter
+  // of pass bitmaps only, staged 32-bit keys and values, 32-bit reducible
+  // aggregates; 6 with the run-line table and 8-row lanes, 7 with a dense
+  // table and 16-row lanes (a 14-bit column)
+  if (variant == 6 || variant == 7) {
+    memset(q, 0, sizeof(*q));
+    q->tile_rows = 8192;
+    q->n_cols = 5; q->n_preds = 1; q->n_keys = 2; q->n_aggs = 5; q->n_bitmaps = 2; q->n_pbm = 1;
+    q->n_row_cols = 3; q->row_cols[0] = 2; q->row_cols[1] = 3; q->row_cols[2] = 4;
+    const uint8_t kbw = variant == 6 ? 4 : 14;
+    q->stage_bytes = 8192u * (kbw + 8 + 12) / 8;
+    auto col = [&](int i, uint8_t enc, uint8_t bw, uint8_t bslot, uint32_t soff) {
+      ColDesc& c = q->cols[i];
+      c.enc = enc; c.bw = bw; c.bslot = bslot; c.raw_is_offset = enc == ENC_RLE ? 0 : 1; c.stage_off = soff;
+    };
+    col(0, ENC_RLE, 0, 0, 0);
+    col(1, ENC_RLE, 0, 1, 0);
+    col(2, ENC_DICT, kbw, 0xFF, 0);
+    col(3, ENC_PACKED, 8, 0xFF, 8192u * kbw / 8);
+    col(4, ENC_PACKED, 12, 0xFF, 8192u * (kbw + 8) / 8);
+    q->preds[0].col = 1; q->preds[0].kind = PK_RANGE; q->preds[0].n32 = 1; q->preds[0].pbm = 0;
+    q->keys[0].col = variant == 6 ? 0 : 2; q->keys[0].n32 = 1;
+    q->keys[1].col = variant == 6 ? 2 : 3; q->keys[1].n32 = 1;
+    auto agg = [&](int i, uint8_t kind, uint8_t c, uint8_t sw32, uint8_t s32, uint8_t w32) {
+      AggDesc& a = q->aggs[i];
+      a.kind = kind; a.col = c; a.sw32 = sw32; a.s32 = s32; a.w32 = w32; a.red32 = kind == AK_SUM;
+      a.n32 = kind != AK_COUNT; a.gw = (uint32_t)(1 + 3 * i);
+    };
+    agg(0, AK_SUM, 3, 1, 1, 0);
+    agg(1, AK_SUM, 4, 2, 3, 0);
+    agg(2, AK_MIN, 4, 4, 0, 1);
+    agg(3, AK_MAX, 3, 5, 0, 1);
+    agg(4, AK_COUNT, 0, 0, 0, 0);
+    if (variant == 6) {
+      q->n_groups = 160000; q->table_slots = 1024;
+      q->line_mode = 1; q->line_log2 = 5; q->line_inner = 16; q->line_swz = 15;
+    } else {
+      q->n_groups = 1000; q->table_slots = 1024; q->table_dense = 1;
+    }
+    return;
+  }
   // variants 4 and 5: variants 0 and 3 with the run-line table (key 0 on
   // the RLE column 0)
   if (variant == 4 || variant == 5) {
@@ -402,12 +448,14 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
 // run-time compilation that needs no GPU.  *seconds receives the compile time.
 extern "C" int cq_jit_check(uint32_t variant, double* seconds) {
   cq::clear_error();
-  if (variant > 5) return cq::set_error(CQ_ERR_INVALID_ARG, "variant must be 0 .. 5");
+  if (variant > 7) return cq::set_error(CQ_ERR_INVALID_ARG, "variant must be 0 .. 7");
   cq::QueryDesc q;
   cq::check_shape(variant, &q);
   cq::JitKernel k;
-  const bool wide = variant == 0 || variant == 3 || variant == 4 || variant == 5;
-  const int rc = cq::compile(cq::shape_source(q, wide ? 28 : 16, wide ? 8 : 16, 1), &k, false);
+  // (28 compute warps for the heterogeneous-like shapes, 16 for the others;
+  // variant 6 as the two-CTA shape, whose register budget is the tightest)
+  const bool wide = variant == 0 || variant == 3 || variant == 4 || variant == 5 || variant == 7;
+  const int rc = cq::compile(cq::shape_source(q, wide ? 28 : 16, wide ? 8 : 16, variant == 6 ? 2 : 1), &k, false);
   if (seconds) *seconds = k.compile_s;
   return rc;
 }

@@ -89,14 +89,15 @@ def test_generator_library_exports_its_header(libpath):
 
 def test_specialised_row_kernel_compiles_without_a_gpu(libpath):
     """The run-time compiler builds the shape-specialised row kernel from the
-    library's embedded device headers: six check shapes that between them use
-    every encoding, predicate kind, clause form, key mapping, aggregate layout
-    and group table (shared hash table, run lines, global hash table, single
-    group), with and without the warp pre-reduction."""
+    library's embedded device headers: eight check shapes that between them
+    use every encoding, predicate kind, clause form, key mapping, aggregate
+    layout and group table (shared hash table, run lines, global hash table,
+    single group, dense table), with and without the warp pre-reduction and
+    the serial walk of sorted data."""
     from paper_2506_10092_gb300 import cq
-    for variant in range(6):
+    for variant in range(8):
         secs = cq.cq_jit_check(variant)
         assert 0 < secs < 120
     with pytest.raises(cq.CQError) as e:
-        cq.cq_jit_check(6)
+        cq.cq_jit_check(8)
     assert e.value.status == cq.CQ_ERR_INVALID_ARG
