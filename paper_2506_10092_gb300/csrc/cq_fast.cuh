@@ -883,11 +883,13 @@ __device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, con
   });
   uint32_t lmask = 0;
   if constexpr (S::line_mode) lmask = (1u << q.line_log2) - 1u;
-  uint32_t cur = 0, cnt = 0;
+  // A failing row's group is kNone, so a stretch ends exactly where the
+  // group changes; a failing stretch accumulates too but is never flushed.
+  constexpr uint32_t kNone = 0xFFFFFFFFu;   // above every group id (< 2^32 - 1)
+  uint32_t cur = kNone, cnt = 0;
   int acc[S::n_aggs + 1];
 #pragma unroll
   for (int i = 0; i <= S::n_aggs; ++i) acc[i] = 0;
-  bool open = false;
   static_for<R>([&](auto RI) {
     constexpr int r = decltype(RI)::value;
     if constexpr (VARY && r > 0) line = (line + ((starts >> r) & 1u)) & lmask;
@@ -911,42 +913,64 @@ __device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, con
       }
     });
     if constexpr (S::line_mode) g = line * q.line_inner + (g ^ (line & q.line_swz));
-    // the open stretch ends before this row: flush it
-    if (open && (!p || g != cur)) ser_flush<S>(q, sm, cur, cnt, acc);
-    const bool st = p && (!open || g != cur);   // a stretch starts here
+    g = p ? g : kNone;
+    if constexpr (r == 0) {
+      cur = g;
+      cnt = 0;
+      static_for<S::n_aggs>([&](auto A) {
+        constexpr int i = decltype(A)::value;
+        constexpr int kind = S::akind(i);
+        if constexpr (kind == AK_MIN || kind == AK_MAX) acc[i] = kind == AK_MIN ? INT_MAX : INT_MIN;
+      });
+    } else if (g != cur) {
+      // the stretch before this row ends
+      if (cur != kNone) ser_flush<S>(q, sm, cur, cnt, acc);
+      cur = g;
+      cnt = 0;
+      static_for<S::n_aggs>([&](auto A) {
+        constexpr int i = decltype(A)::value;
+        constexpr int kind = S::akind(i);
+        if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX)
+          acc[i] = kind == AK_SUM ? 0 : (kind == AK_MIN ? INT_MAX : INT_MIN);
+      });
+    }
+    cnt += 1u;
     static_for<S::n_aggs>([&](auto A) {
       constexpr int i = decltype(A)::value;
       constexpr int kind = S::akind(i);
       if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX) {
         constexpr int c = S::acol(i);
         const int v = (int)ser_field<col_bits_of<S>(c), r>(w[ser_rc<S>(c)]);
-        const int m = kind == AK_SUM ? acc[i] + v : (kind == AK_MIN ? min(acc[i], v) : max(acc[i], v));
-        acc[i] = st ? v : m;
+        acc[i] = kind == AK_SUM ? acc[i] + v : (kind == AK_MIN ? min(acc[i], v) : max(acc[i], v));
       }
     });
-    cnt = st ? 1u : cnt + 1u;
-    cur = st ? g : cur;
-    open = p;   // (a failing row's updates above are never flushed)
   });
-  if (open) ser_flush<S>(q, sm, cur, cnt, acc);
+  if (cur != kNone) ser_flush<S>(q, sm, cur, cnt, acc);
 }
 
-// The compute warps' serial pass over a tile: warp w takes the tile's rows
-// [w * 32 * GPW, (w + 1) * 32 * GPW), its lanes R consecutive rows each, so
-// that the lanes' staged words are consecutive in shared memory.
+// The compute warps' serial pass over a tile: the tile's passes of 32 * R
+// consecutive rows (lane l takes rows l * R .. l * R + R - 1 of a pass, so
+// that the lanes' staged words are consecutive in shared memory) are dealt
+// to the warps from a shared counter, one per tile parity, so that warps
+// whose rows pass more take fewer passes.  Thread 0 clears the next tile's
+// counter (misc[4 + parity]) at the start of every tile.
 template <class S, int NCW, int GPW>
-__device__ __forceinline__ void fast_serial(const QueryDesc& q, const Smem& sm, const TileView& t, uint32_t wbase,
-                                            uint32_t rows, unsigned long long row0, unsigned long long line_cur) {
+__device__ __forceinline__ void fast_serial(const QueryDesc& q, const Smem& sm, const TileView& t, uint32_t rows,
+                                            unsigned long long row0, unsigned long long line_cur) {
   constexpr int R = ser_rows<S>();
-  constexpr uint32_t span = GPW * 32;
+  constexpr uint32_t passes = S::tile_rows / (32u * R);
   constexpr uint32_t nw = S::tile_rows / 32;
   constexpr uint32_t inner_bits = R == 32 ? 0xFFFFFFFEu : ((1u << R) - 2u);
   const int lane = threadIdx.x & 31;
-  const uint32_t first = (wbase >> 5) * span;
-  for (uint32_t b = first; b < first + span; b += 32u * R) {
-    const uint32_t o0 = b + (uint32_t)lane * R;
+  int* ctr = sm.misc + 4 + ((uint32_t)(row0 / S::tile_rows) & 1u);
+  for (;;) {
+    uint32_t j = 0;
+    if (lane == 0) j = (uint32_t)atomicAdd(ctr, 1);
+    j = __shfl_sync(0xFFFFFFFFu, j, 0);
+    if (j >= passes) break;
+    const uint32_t o0 = j * 32u * R + (uint32_t)lane * R;
     uint32_t pass = 0;
-    if (o0 < first + span && o0 < rows) {
+    if (o0 < rows) {
       uint32_t valid = R == 32 ? 0xFFFFFFFFu : ((1u << R) - 1u);
       if (rows - o0 < (uint32_t)R) valid &= (1u << (rows - o0)) - 1u;
       // the filter's clauses over the pass-bitmap words of these rows
@@ -995,6 +1019,9 @@ struct FastBody {
   __device__ static __forceinline__ void tile(const QueryDesc& q, const Smem& sm, const TileView& tv, uint32_t wbase,
                                               uint32_t rows, uint16_t* list, unsigned long long row0) {
     constexpr uint32_t GS = NCW * 32;
+    // the serial walk's pass counter of the next tile (see fast_serial)
+    if constexpr (ser_ok<S>())
+      if (threadIdx.x == 0) sm.misc[4 + (((uint32_t)(row0 / S::tile_rows) & 1u) ^ 1u)] = 0;
     bool line_ok = false;
     unsigned long long line_cur = 0;
     if constexpr (S::line_mode) {
@@ -1009,7 +1036,7 @@ struct FastBody {
     if constexpr (ser_ok<S>()) {
       // (the same choice in every warp: line_ok is the tile's)
       if (!S::line_mode || line_ok) {
-        fast_serial<S, NCW, GPW>(q, sm, tv, wbase, rows, row0, line_cur);
+        fast_serial<S, NCW, GPW>(q, sm, tv, rows, row0, line_cur);
         if constexpr (S::line_mode)
           fast_flush_lines<S>(q, sm, tv.line_base, line_cur, threadIdx.x, NCW * 32);
         return;
