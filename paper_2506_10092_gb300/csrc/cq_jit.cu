@@ -388,6 +388,8 @@ static void check_shape(uint32_t variant, QueryDesc* q) {
     col(2, ENC_INDEX, 1, 0, 1, 0, 0);
     col(3, ENC_PLAIN, 0, 0, 0xFF, 0, 14352);
     col(4, ENC_PACKED, 1, 20, 0xFF, 1, 47136);
+    q->n_row_cols = 3; q->row_cols[0] = 1; q->row_cols[1] = 3; q->row_cols[2] = 4;
+    q->stage_bytes = 47136 + 8192 * 20 / 8;
     pred(0, 1, PK_BITMAP, 1, 0xFF);
     pred(1, 3, PK_RANGE, 1, 0xFF);
     key(0, 0, 0, 1);
