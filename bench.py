@@ -117,22 +117,29 @@ def kernel_source_hash(read=None) -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic(workload_name: str):
-    """dram bytes per launch of the fused kernel from the committed ncu summary,
-    when it was taken on the current kernel sources; else None."""
-    p = os.path.join(ROOT, "profiles", "row_query_kernel_heterogeneous.json")
-    if not os.path.exists(p):
-        return None
-    try:
-        with open(p) as f:
-            d = json.load(f)
-        if d.get("kernel_sources_sha256_16") != kernel_source_hash():
-            return None
-        if d.get("workload") != workload_name:
-            return None
-        return float(d["dram_bytes_per_launch"])
-    except Exception:
-        return None
+def profile_traffic(workload_name: str, n_rows: int = 0):
+    """dram bytes per launch of the fused kernel from a committed ncu summary
+    (profiles/*.json) taken on the current kernel sources, else None.  A
+    summary names its workload (bytes per launch as captured and scaled) or a
+    workload family whose traffic grows with the rows (bytes scaled from the
+    captured rows to n_rows)."""
+    import glob
+    h = kernel_source_hash()
+    for p in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.json"))):
+        try:
+            with open(p) as f:
+                d = json.load(f)
+            if d.get("kernel_sources_sha256_16") != h:
+                continue
+            if d.get("workload") == workload_name:
+                return float(d["dram_bytes_per_launch"])
+            fam = d.get("family")
+            if fam and workload_name.startswith(fam) and n_rows and d.get("capture_rows"):
+                cap = float(d["dram_bytes_read_capture"]) + float(d["dram_bytes_write_capture"])
+                return cap * n_rows / float(d["capture_rows"])
+        except Exception:
+            continue
+    return None
 
 
 class Clocks:
@@ -348,7 +355,7 @@ def run_cq(args):
     k_us = statistics.mean(kernel_us)
     peak, peak_src = measured_peak()
     achieved = alg_bytes / (k_us * 1e-6) / 1e9
-    traffic = profile_traffic(name)
+    traffic = profile_traffic(name, n_rows)
 
     # end to end through the public API: pinned host buffers -> columns ->
     # query -> result read back, every step
@@ -517,7 +524,10 @@ def run_nested_secondary(cq, ctx, stream, args, torch, peak, steps: int = 3):
                 "rows_per_s": n_rows / (ms / 1000.0), "compressed_bytes": alg, "groups": groups,
                 "kernel_us": k_us, "achieved_gbs": alg / (k_us * 1e-6) / 1e9,
                 "frac_of_measured_hbm": alg / (k_us * 1e-6) / 1e9 / peak, "steps": steps,
-                "table_build_s": t_gen, "launches_per_query": launches_per_query(n_rows)}
+                "table_build_s": t_gen, "launches_per_query": launches_per_query(n_rows),
+                # DRAM bytes of the whole query (all launches), scaled from the
+                # committed ncu summary of the same kernel, or None
+                "traffic_per_query": profile_traffic(f"nested-lean-{n_rows}", n_rows)}
     except Exception as e:   # the main line stands without it
         return {"workload": "nested-lean-20000000000", "error": str(e)[:300]}
 

@@ -850,8 +850,10 @@ __device__ __forceinline__ void ser_flush(const QueryDesc& q, const Smem& sm, ui
 
 // Rows o0 .. o0 + R - 1 of one lane: `pass` their filter bits, `starts` the
 // run-start bits of key 0's column from row o0 on (VARY: a run starts
-// inside, so the line advances), `line` the line at row o0.
-template <class S, int R, bool VARY>
+// inside, so the line advances), `line` the line at row o0.  Without CHECK
+// every field of every staged key is a valid digit (ser_keys_total), so the
+// digits are not tested.
+template <class S, int R, bool VARY, bool CHECK>
 __device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, const TileView& t, uint32_t o0,
                                          uint32_t pass, uint32_t starts, uint32_t line, unsigned long long row0) {
   constexpr int NRC = S::n_row_cols > 0 ? S::n_row_cols : 1;
@@ -886,7 +888,7 @@ __device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, con
   // A failing row's group is kNone, so a stretch ends exactly where the
   // group changes; a failing stretch accumulates too but is never flushed.
   constexpr uint32_t kNone = 0xFFFFFFFFu;   // above every group id (< 2^32 - 1)
-  uint32_t cur = kNone, cnt = 0;
+  uint32_t cur = kNone, s0 = 0;   // the open stretch's group and first row
   int acc[S::n_aggs + 1];
 #pragma unroll
   for (int i = 0; i <= S::n_aggs; ++i) acc[i] = 0;
@@ -901,13 +903,17 @@ __device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, con
         constexpr int c = S::kcol(k);
         const int v = (int)ser_field<col_bits_of<S>(c), r>(w[ser_rc<S>(c)]);
         uint32_t d;
-        if (!ser_digit<S, k>(q, t, v, &d)) {
-          if (p) {
-            report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)k << 8), row0 + o0 + r,
-                   (unsigned long long)(long long)v);
-            p = false;
+        if constexpr (CHECK) {
+          if (!ser_digit<S, k>(q, t, v, &d)) {
+            if (p) {
+              report(q, CQ_ERR_INVALID_ARG, 1ull + ((unsigned long long)k << 8), row0 + o0 + r,
+                     (unsigned long long)(long long)v);
+              p = false;
+            }
+            d = 0;
           }
-          d = 0;
+        } else {
+          d = (uint32_t)v;   // (digit = field: the key's minimum is 0)
         }
         g += d * (uint32_t)q.keys[k].stride;
       }
@@ -916,7 +922,6 @@ __device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, con
     g = p ? g : kNone;
     if constexpr (r == 0) {
       cur = g;
-      cnt = 0;
       static_for<S::n_aggs>([&](auto A) {
         constexpr int i = decltype(A)::value;
         constexpr int kind = S::akind(i);
@@ -924,9 +929,9 @@ __device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, con
       });
     } else if (g != cur) {
       // the stretch before this row ends
-      if (cur != kNone) ser_flush<S>(q, sm, cur, cnt, acc);
+      if (cur != kNone) ser_flush<S>(q, sm, cur, (uint32_t)r - s0, acc);
       cur = g;
-      cnt = 0;
+      s0 = r;
       static_for<S::n_aggs>([&](auto A) {
         constexpr int i = decltype(A)::value;
         constexpr int kind = S::akind(i);
@@ -934,7 +939,6 @@ __device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, con
           acc[i] = kind == AK_SUM ? 0 : (kind == AK_MIN ? INT_MAX : INT_MIN);
       });
     }
-    cnt += 1u;
     static_for<S::n_aggs>([&](auto A) {
       constexpr int i = decltype(A)::value;
       constexpr int kind = S::akind(i);
@@ -945,7 +949,23 @@ __device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, con
       }
     });
   });
-  if (cur != kNone) ser_flush<S>(q, sm, cur, cnt, acc);
+  if (cur != kNone) ser_flush<S>(q, sm, cur, (uint32_t)R - s0, acc);
+}
+
+// Whether every field of every staged key is a valid digit: no remap, key
+// minimum 0 and at least 2^B digit values for B-bit fields.
+template <class S>
+__device__ __forceinline__ bool ser_keys_total(const QueryDesc& q) {
+  bool all = true;
+  static_for<S::n_keys>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    if constexpr (!(S::line_mode && k == 0)) {
+      constexpr int B = col_bits_of<S>(S::kcol(k));
+      if constexpr (S::kremap(k) || B >= 32) all = false;
+      else all = all && q.keys[k].kmin == 0 && q.keys[k].card >= (1ull << B);
+    }
+  });
+  return all;
 }
 
 // The compute warps' serial pass over a tile: the tile's passes of 32 * R
@@ -1007,8 +1027,13 @@ __device__ __forceinline__ void fast_serial(const QueryDesc& q, const Smem& sm, 
       vary = __any_sync(0xFFFFFFFFu, pass != 0 && (starts & inner_bits) != 0);
     }
     if (pass != 0) {
-      if (vary) ser_walk<S, R, true>(q, sm, t, o0, pass, starts, line, row0);
-      else ser_walk<S, R, false>(q, sm, t, o0, pass, starts, line, row0);
+      if (ser_keys_total<S>(q)) {
+        if (vary) ser_walk<S, R, true, false>(q, sm, t, o0, pass, starts, line, row0);
+        else ser_walk<S, R, false, false>(q, sm, t, o0, pass, starts, line, row0);
+      } else {
+        if (vary) ser_walk<S, R, true, true>(q, sm, t, o0, pass, starts, line, row0);
+        else ser_walk<S, R, false, true>(q, sm, t, o0, pass, starts, line, row0);
+      }
     }
   }
 }
