@@ -848,6 +848,62 @@ __device__ __forceinline__ void ser_flush(const QueryDesc& q, const Smem& sm, ui
   });
 }
 
+// Shared-memory reductions issued under a predicate (no branch): the walk
+// issues its stretch update on every row, live only where a stretch ends.
+__device__ __forceinline__ void red_add_if(bool p, const void* a, unsigned v) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q red.shared.add.u32 [%0], %1;\n}"
+               ::"r"(smem_addr(a)), "r"(v), "r"((unsigned)p) : "memory");
+}
+__device__ __forceinline__ void red_min_if(bool p, const void* a, int v) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q red.shared.min.s32 [%0], %1;\n}"
+               ::"r"(smem_addr(a)), "r"(v), "r"((unsigned)p) : "memory");
+}
+__device__ __forceinline__ void red_max_if(bool p, const void* a, int v) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q red.shared.max.s32 [%0], %1;\n}"
+               ::"r"(smem_addr(a)), "r"(v), "r"((unsigned)p) : "memory");
+}
+
+// Whether the stretch update can be issued that way: slots are group ids
+// (run lines or a dense table) and every accumulator is a 32-bit word
+// updated without its old value (COUNT, 32-bit or split-limb SUMs, 32-bit
+// MIN / MAX).
+template <class S>
+__device__ constexpr bool ser_pred_ok() {
+  if (!(S::line_mode || S::table_dense)) return false;
+  for (int i = 0; i < S::n_aggs; ++i) {
+    const int kind = S::akind(i);
+    if (kind == AK_SUM && S::as32(i) == 0) return false;
+    if ((kind == AK_MIN || kind == AK_MAX) && !S::aw32(i)) return false;
+  }
+  return true;
+}
+
+// ser_flush under predicate f (slot = gid; gid need not be a slot when f is
+// false: no address is touched then).
+template <class S>
+__device__ __forceinline__ void ser_flush_if(const QueryDesc& q, const Smem& sm, bool f, uint32_t gid,
+                                             uint32_t cnt, const int* acc) {
+  const int slot = (int)gid;
+  red_add_if(f, scount(q, sm, slot), cnt);
+  static_for<S::n_aggs>([&](auto A) {
+    constexpr int i = decltype(A)::value;
+    constexpr int kind = S::akind(i);
+    if constexpr (kind == AK_SUM) {
+      if constexpr (S::as32(i) == 3) {
+        const unsigned x = (unsigned)acc[i];
+        red_add_if(f, sword32(q, sm, S::asw32(i), slot), x & ((1u << kSplitBits) - 1u));
+        red_add_if(f && (x >> kSplitBits) != 0u, sword32(q, sm, S::asw32(i) + 1, slot), x >> kSplitBits);
+      } else {
+        red_add_if(f, sword32(q, sm, S::asw32(i), slot), (unsigned)acc[i]);
+      }
+    } else if constexpr (kind == AK_MIN) {
+      red_min_if(f, sword32(q, sm, S::asw32(i), slot), acc[i]);
+    } else if constexpr (kind == AK_MAX) {
+      red_max_if(f, sword32(q, sm, S::asw32(i), slot), acc[i]);
+    }
+  });
+}
+
 // Rows o0 .. o0 + R - 1 of one lane: `pass` their filter bits, `starts` the
 // run-start bits of key 0's column from row o0 on (VARY: a run starts
 // inside, so the line advances), `line` the line at row o0.  Without CHECK
@@ -926,6 +982,19 @@ __device__ __forceinline__ void ser_walk(const QueryDesc& q, const Smem& sm, con
         constexpr int i = decltype(A)::value;
         constexpr int kind = S::akind(i);
         if constexpr (kind == AK_MIN || kind == AK_MAX) acc[i] = kind == AK_MIN ? INT_MAX : INT_MIN;
+      });
+    } else if constexpr (ser_pred_ok<S>()) {
+      // the stretch before this row ends where the group changes: its update
+      // is issued on every row, live only there
+      const bool brk = g != cur;
+      ser_flush_if<S>(q, sm, brk && cur != kNone, cur, (uint32_t)r - s0, acc);
+      cur = g;
+      s0 = brk ? (uint32_t)r : s0;
+      static_for<S::n_aggs>([&](auto A) {
+        constexpr int i = decltype(A)::value;
+        constexpr int kind = S::akind(i);
+        if constexpr (kind == AK_SUM || kind == AK_MIN || kind == AK_MAX)
+          acc[i] = brk ? (kind == AK_SUM ? 0 : (kind == AK_MIN ? INT_MAX : INT_MIN)) : acc[i];
       });
     } else if (g != cur) {
       // the stretch before this row ends
