@@ -371,7 +371,22 @@ bool row_passes(const Query& q, const std::vector<int64_t>& row, std::vector<uin
 
 typedef std::map<std::vector<int64_t>, Acc> GroupMap;
 
-void update(const Query& q, Acc& a, const std::vector<int64_t>& row) {
+// The input value of aggregate g at this row: the column's value, or the
+// exact result of the expression (false when it leaves the int64 range).
+bool agg_value(const Query& q, const orc_agg& g, const std::vector<int64_t>& row, int64_t* v) {
+  const int64_t x = row[q.slot[g.col]];
+  if (g.expr == ORC_EXPR_NONE) {
+    *v = x;
+    return true;
+  }
+  const i128 a = x, b = row[q.slot[g.col2]];
+  const i128 r = g.expr == ORC_EXPR_ADD ? a + b : (g.expr == ORC_EXPR_SUB ? a - b : a * b);
+  if (r > (i128)INT64_MAX || r < (i128)INT64_MIN) return false;
+  *v = (int64_t)r;
+  return true;
+}
+
+bool update(const Query& q, Acc& a, const std::vector<int64_t>& row) {
   if (a.sum.empty()) {
     a.sq.assign(q.n_aggs, U256());
     a.sum.assign(q.n_aggs, 0);
@@ -383,7 +398,8 @@ void update(const Query& q, Acc& a, const std::vector<int64_t>& row) {
   for (uint32_t i = 0; i < q.n_aggs; ++i) {
     const orc_agg& g = q.aggs[i];
     if (g.op == ORC_COUNT) continue;
-    int64_t v = row[q.slot[g.col]];
+    int64_t v;
+    if (!agg_value(q, g, row, &v)) return false;
     const orc_column& c = q.cols[g.col];
     if (g.op == ORC_SUM || g.op == ORC_AVG || g.op >= ORC_VAR_POP) a.sum[i] += (i128)v;
     if (g.op >= ORC_VAR_POP) {
@@ -407,6 +423,7 @@ void update(const Query& q, Acc& a, const std::vector<int64_t>& row) {
       }
     }
   }
+  return true;
 }
 
 void merge_into(const Query& q, GroupMap& dst, const GroupMap& src) {
@@ -452,7 +469,7 @@ int scan_chunk(const Query& q, uint64_t rb, uint64_t re, GroupMap& groups) {
     for (size_t u = 0; u < q.used.size(); ++u) row[u] = flat[u][r];
     if (!row_passes(q, row, stack)) continue;
     for (uint32_t k = 0; k < q.n_gb; ++k) key[k] = row[q.slot[q.gb[k]]];
-    update(q, groups[key], row);
+    if (!update(q, groups[key], row)) return ORC_ERR_OVERFLOW;
   }
   return ORC_OK;
 }
@@ -508,6 +525,13 @@ extern "C" int orc_query(const orc_column* cols, uint32_t n_cols, uint64_t n_row
     if (!use(aggs[i].col)) return ORC_ERR_ARG;
     if (cols[aggs[i].col].enc == ORC_DICT && aggs[i].op != ORC_MIN && aggs[i].op != ORC_MAX)
       return ORC_ERR_ARG;
+    if (aggs[i].expr < ORC_EXPR_NONE || aggs[i].expr > ORC_EXPR_MUL) return ORC_ERR_ARG;
+    if (aggs[i].expr != ORC_EXPR_NONE) {
+      const int32_t op = aggs[i].op;
+      if (op != ORC_SUM && op != ORC_MIN && op != ORC_MAX && op != ORC_AVG) return ORC_ERR_ARG;
+      if (!use(aggs[i].col2)) return ORC_ERR_ARG;
+      if (cols[aggs[i].col].enc == ORC_DICT || cols[aggs[i].col2].enc == ORC_DICT) return ORC_ERR_ARG;
+    }
   }
   for (uint32_t c : q.used) if (validate(cols[c], n_rows) != ORC_OK) return ORC_ERR_ARG;
   // A predicate on a dictionary column is a function of the row's string;

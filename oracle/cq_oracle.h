@@ -87,9 +87,18 @@ typedef struct {
   uint32_t arg;
 } orc_node;
 
+/* An aggregate's input is column `col`, or, with an expression, the
+ * position-wise result `col` (expr) `col2` of two columns (Section 6:
+ * arithmetic on aligned columns, e.g. c1 + c2 after alignment): computed
+ * exactly per row; a row whose result leaves the int64 range makes the
+ * query fail with ORC_ERR_OVERFLOW.  Expressions take SUM, MIN, MAX and
+ * AVG over non-dictionary columns. */
+enum { ORC_EXPR_NONE = 0, ORC_EXPR_ADD = 1, ORC_EXPR_SUB = 2, ORC_EXPR_MUL = 3 };
 typedef struct {
   int32_t op;
   uint32_t col;                   /* ignored for COUNT(*) */
+  int32_t expr;                   /* ORC_EXPR_* */
+  uint32_t col2;                  /* second operand of an expression */
 } orc_agg;
 
 typedef struct orc_result orc_result;

@@ -53,7 +53,10 @@ _NODES = {"pred": 0, "and": 1, "or": 2, "not": 3}
 
 
 class _Agg(C.Structure):
-    _fields_ = [("op", C.c_int32), ("col", C.c_uint32)]
+    _fields_ = [("op", C.c_int32), ("col", C.c_uint32), ("expr", C.c_int32), ("col2", C.c_uint32)]
+
+
+_EXPRS = {None: 0, "add": 1, "sub": 2, "mul": 3}
 
 
 _lib = None
@@ -159,7 +162,8 @@ def query(table, plan, row_ranges=None, n_threads: int = 1) -> OracleResult:
     m = _Marshal()
     cols = (_Col * len(table.columns))(*[m.column(c) for c in table.columns])
     preds = (_Pred * max(1, len(plan.preds)))(*[m.pred(p) for p in plan.preds])
-    aggs = (_Agg * max(1, len(plan.aggs)))(*[_Agg(_AGGS[a.op], int(a.col)) for a in plan.aggs])
+    aggs = (_Agg * max(1, len(plan.aggs)))(*[_Agg(_AGGS[a.op], int(a.col), _EXPRS[getattr(a, "expr", None)],
+                                                   int(getattr(a, "col2", 0))) for a in plan.aggs])
     prog = list(getattr(plan, "filter", None) or [])
     nodes = (_Node * max(1, len(prog)))(*[_Node(_NODES[k], int(a)) for k, a in prog])
     gb = m.k(np.array(list(plan.group_by) or [0], dtype=np.uint32))

@@ -119,6 +119,8 @@ class Pred:
 class Agg:
     op: str                         # sum count min max avg var_pop var_samp std_pop std_samp
     col: int = 0                    # ignored for count
+    expr: Optional[str] = None      # "add" / "sub" / "mul": the input is col (expr) col2, row by row
+    col2: int = 0
 
 
 @dataclasses.dataclass

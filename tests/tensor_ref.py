@@ -105,7 +105,8 @@ def query(table, plan):
     """Returns (keys: list of int arrays, aggs: list of arrays, overflow: bool)."""
     n = table.n_rows
     flat = {}
-    for i in set([p.col for p in plan.preds] + list(plan.group_by) + [a.col for a in plan.aggs if a.op != "count"]):
+    for i in set([p.col for p in plan.preds] + list(plan.group_by) + [a.col for a in plan.aggs if a.op != "count"]
+                 + [a.col2 for a in plan.aggs if getattr(a, "expr", None)]):
         flat[i] = decode(table.columns[i])
     mask = filter_mask(plan, [_pred_mask(table.columns[p.col], flat[p.col], p) for p in plan.preds], n)
     rows = np.flatnonzero(mask)
@@ -129,6 +130,13 @@ def query(table, plan):
             aggs.append(count)
             continue
         v = flat[a.col][rows]
+        if getattr(a, "expr", None):
+            # position-wise arithmetic on the (aligned) rows, exact Python ints
+            w = flat[a.col2][rows]
+            f = {"add": lambda x, y: x + y, "sub": lambda x, y: x - y, "mul": lambda x, y: x * y}[a.expr]
+            v = np.array([f(int(x), int(y)) for x, y in zip(v.tolist(), w.tolist())], dtype=object)
+            if any(x > 2**63 - 1 or x < -2**63 for x in v.tolist()):
+                raise ValueError("expression value outside int64")
         col = table.columns[a.col]
         if a.op in ("var_pop", "var_samp", "std_pop", "std_samp"):
             # Section 7: from COUNT, SUM and the sum of squares; the exact
