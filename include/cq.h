@@ -222,9 +222,21 @@ typedef enum {
   CQ_VAR_POP = 5, CQ_VAR_SAMP = 6, CQ_STD_POP = 7, CQ_STD_SAMP = 8
 } cq_agg_op;
 
+/* An aggregate's input is column `col`, or, with an expression, the
+ * position-wise result `col` (expr) `col2` of two columns (Section 6:
+ * arithmetic on aligned columns, e.g. c1 + c2 after alignment), evaluated
+ * once per aligned segment in segment mode and once per row otherwise.
+ * Expressions take SUM, MIN, MAX and AVG over non-dictionary columns
+ * (CQ_ERR_INVALID_ARG otherwise); the columns' value ranges must keep every
+ * result within int64, else planning fails with CQ_ERR_UNSUPPORTED.  Row-mode
+ * plans with an expression run the generic row kernel. */
+typedef enum { CQ_EXPR_NONE = 0, CQ_EXPR_ADD = 1, CQ_EXPR_SUB = 2, CQ_EXPR_MUL = 3 } cq_expr;
+
 typedef struct {
   int32_t op;                   /* cq_agg_op; only MIN / MAX / COUNT take dictionary columns */
   uint32_t col;                 /* ignored for COUNT(*) */
+  int32_t expr;                 /* cq_expr; CQ_EXPR_NONE: the column itself */
+  uint32_t col2;                /* second operand of an expression */
 } cq_aggregate;
 
 typedef struct {

@@ -56,7 +56,10 @@ NODES = {"pred": CQ_NODE_PRED, "and": CQ_NODE_AND, "or": CQ_NODE_OR, "not": CQ_N
 
 
 class cq_aggregate(C.Structure):
-    _fields_ = [("op", C.c_int32), ("col", C.c_uint32)]
+    _fields_ = [("op", C.c_int32), ("col", C.c_uint32), ("expr", C.c_int32), ("col2", C.c_uint32)]
+
+
+EXPRS = {None: 0, "add": 1, "sub": 2, "mul": 3}   # cq_expr
 
 
 class cq_plan(C.Structure):
@@ -315,7 +318,10 @@ class PlanStruct:
                 self.keep += [bufs, ptrs, lens]
                 s.strs, s.str_lens, s.n_strs = C.addressof(ptrs), lens.ctypes.data, len(bufs)
         gb = np.array(list(plan.group_by) or [0], dtype=np.uint32)
-        aggs = (cq_aggregate * max(1, len(plan.aggs)))(*[cq_aggregate(AGGS[a.op], int(a.col)) for a in plan.aggs])
+        aggs = (cq_aggregate * max(1, len(plan.aggs)))(*[cq_aggregate(AGGS[a.op], int(a.col),
+                                                                      EXPRS[getattr(a, "expr", None)],
+                                                                      int(getattr(a, "col2", 0)))
+                                                         for a in plan.aggs])
         prog = list(getattr(plan, "filter", None) or [])
         nodes = (cq_filter_node * max(1, len(prog)))(*[cq_filter_node(NODES[k], int(a)) for k, a in prog])
         self.keep += [preds, gb, aggs, nodes]

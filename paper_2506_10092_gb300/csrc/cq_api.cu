@@ -629,6 +629,15 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     if (use(a.col) < 0) return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: bad column %u", i, a.col);
     if (a.op != CQ_MIN && a.op != CQ_MAX && is_dict(tcols[a.col]))
       return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: SUM/AVG/VAR/STD of a dictionary column", i);
+    if (a.expr < CQ_EXPR_NONE || a.expr > CQ_EXPR_MUL)
+      return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: bad expression %d", i, a.expr);
+    if (a.expr != CQ_EXPR_NONE) {
+      if (a.op != CQ_SUM && a.op != CQ_MIN && a.op != CQ_MAX && a.op != CQ_AVG)
+        return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: expressions take SUM, MIN, MAX and AVG", i);
+      if (use(a.col2) < 0) return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: bad column %u", i, a.col2);
+      if (is_dict(tcols[a.col]) || is_dict(tcols[a.col2]))
+        return set_error(CQ_ERR_INVALID_ARG, "aggregate %u: expression over a dictionary column", i);
+    }
   }
   // ---- tile / pipeline shape
   q.tile_rows = tile;
@@ -981,7 +990,7 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   // flush period of at least 2^18 rows shortens the period to fit it
   for (uint32_t i = 0; i < plan->n_aggs && !q.run_walk; ++i) {
     const cq_aggregate& a = plan->aggs[i];
-    if (a.op != CQ_SUM && a.op != CQ_AVG) continue;
+    if ((a.op != CQ_SUM && a.op != CQ_AVG) || a.expr != CQ_EXPR_NONE) continue;
     const PlanCol& pc = tcols[a.col];
     if (pc.enc == ENC_INDEX) continue;
     const ColDesc& cd = q.cols[slot[a.col]];
@@ -1060,6 +1069,45 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
     const PlanCol& pc = tcols[a.col];
     const ColDesc& cd = q.cols[ci];
     d.col = (uint8_t)ci;
+    if (a.expr != CQ_EXPR_NONE) {
+      // position-wise arithmetic on two columns (Section 6): the range of
+      // the result by interval arithmetic on the columns' value ranges; it
+      // must stay within int64, accumulated in 64-bit (or 128-bit) words
+      const PlanCol& pc2 = tcols[a.col2];
+      const i128 l1 = pc.stats.min_val, h1 = pc.stats.max_val, l2 = pc2.stats.min_val, h2 = pc2.stats.max_val;
+      i128 lo, hi;
+      if (a.expr == CQ_EXPR_ADD) {
+        lo = l1 + l2;
+        hi = h1 + h2;
+      } else if (a.expr == CQ_EXPR_SUB) {
+        lo = l1 - h2;
+        hi = h1 - l2;
+      } else {
+        const i128 p[4] = {l1 * l2, l1 * h2, h1 * l2, h1 * h2};
+        lo = std::min(std::min(p[0], p[1]), std::min(p[2], p[3]));
+        hi = std::max(std::max(p[0], p[1]), std::max(p[2], p[3]));
+      }
+      if (lo < (i128)LLONG_MIN || hi > (i128)LLONG_MAX)
+        return set_error(CQ_ERR_UNSUPPORTED, "aggregate %u: the expression's values may leave the int64 range", i);
+      d.expr = (uint8_t)a.expr;
+      d.col2 = (uint8_t)slot[a.col2];
+      d.base = 0;
+      d.red32 = d.ubits = d.n32 = d.s32 = d.w32 = 0;
+      d.sw = (uint8_t)sw;
+      d.gw = gw;
+      if (a.op == CQ_SUM || a.op == CQ_AVG) {
+        const i128 bound = std::max<i128>(hi, -lo);
+        d.kind = AK_SUM;
+        d.wide = bound * (i128)q.flush_rows >= ((i128)1 << 62) ? 1 : 0;
+        sw += d.wide ? 2 : 1;
+        gw += 3;
+      } else {
+        d.kind = a.op == CQ_MIN ? AK_MIN : AK_MAX;
+        sw += 1;
+        gw += 1;
+      }
+      continue;
+    }
     const bool idx = pc.enc == ENC_INDEX;
     if (idx) q.has_index_agg = 1;
     if (a.op >= CQ_VAR_POP) {
@@ -1163,7 +1211,10 @@ static int plan_query_tile(const std::vector<PlanCol>& tcols, uint64_t n_rows, c
   P->ctas_per_sm = (!q.seg_mode && ncw == 8) ? 2 : 1;
   if (q.seg_mode && smem_limit <= ctx->smem_two) P->ctas_per_sm = smem_limit <= ctx->smem_three ? 3 : 2;
   P->grid_ctas = opts ? opts->grid_ctas : 0u;
-  P->generic = opts && opts->kernel == 1;
+  // (aggregates over expressions run the generic row kernel in row mode)
+  bool has_expr = false;
+  for (uint32_t i = 0; i < plan->n_aggs; ++i) has_expr = has_expr || plan->aggs[i].expr != CQ_EXPR_NONE;
+  P->generic = (opts && opts->kernel == 1) || has_expr;
   P->row_fn = nullptr;
   // ---- run lines (grouping on runs, Section 7): when key 0 is an RLE column
   // whose runs are long next to the table, the specialised row kernel gives
@@ -1239,8 +1290,10 @@ static int plan_query(const std::vector<PlanCol>& tcols, uint64_t n_rows, const 
   };
   for (uint32_t i = 0; i < plan->n_preds && plan->preds; ++i) look(plan->preds[i].col);
   for (uint32_t i = 0; i < plan->n_group_by && plan->group_by; ++i) look(plan->group_by[i]);
-  for (uint32_t i = 0; i < plan->n_aggs && plan->aggs; ++i)
+  for (uint32_t i = 0; i < plan->n_aggs && plan->aggs; ++i) {
     if (plan->aggs[i].op != CQ_COUNT) look(plan->aggs[i].col);
+    if (plan->aggs[i].op != CQ_COUNT && plan->aggs[i].expr != CQ_EXPR_NONE) look(plan->aggs[i].col2);
+  }
   struct Shape { int ncw; uint32_t tile; size_t limit; };
   std::vector<Shape> shapes;
   auto add = [&](int ncw, uint32_t first, size_t limit) {
@@ -1505,8 +1558,11 @@ extern "C" int cq_query_run_ex(cq_table* table, const cq_plan* plan, const cq_ex
     if (plan) {
       for (uint32_t i = 0; i < plan->n_preds && plan->preds; ++i) if (plan->preds[i].col < cols.size()) used[plan->preds[i].col] = true;
       for (uint32_t i = 0; i < plan->n_group_by && plan->group_by; ++i) if (plan->group_by[i] < cols.size()) used[plan->group_by[i]] = true;
-      for (uint32_t i = 0; i < plan->n_aggs && plan->aggs; ++i)
-        if (plan->aggs[i].op != CQ_COUNT && plan->aggs[i].col < cols.size()) used[plan->aggs[i].col] = true;
+      for (uint32_t i = 0; i < plan->n_aggs && plan->aggs; ++i) {
+        const cq_aggregate& a = plan->aggs[i];
+        if (a.op != CQ_COUNT && a.col < cols.size()) used[a.col] = true;
+        if (a.op != CQ_COUNT && a.expr != CQ_EXPR_NONE && a.col2 < cols.size()) used[a.col2] = true;
+      }
     }
     for (size_t i = 0; i < cols.size(); ++i) {
       if (!used[i]) continue;

@@ -123,7 +123,11 @@ struct AggDesc {
                      // in [0, 2^24), flush period <= 2^20 rows
   int64_t base;      // value added back at finalize (packed base or index default)
   uint8_t pair;      // AK_SUM2 / AK_ISUM2: the hidden SUM of the same values
+  uint8_t expr;      // EXPR_*: the input is col (expr) col2 in actual values (base 0, 64-bit words)
+  uint8_t col2;      // second operand's index into QueryDesc::cols
 };
+
+enum { EXPR_NONE = 0, EXPR_ADD = 1, EXPR_SUB = 2, EXPR_MUL = 3 };
 
 struct QueryDesc {
   uint64_t n_rows;

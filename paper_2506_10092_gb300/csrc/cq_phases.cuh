@@ -820,6 +820,13 @@ __device__ __forceinline__ uint32_t compact(uint32_t pm, uint32_t wbase, uint32_
 
 // One aggregate's update for one item (slot >= 0: shared table; else global).
 // Row mode items are single rows (len 1); segment items weigh by length.
+// col (expr) col2 of two actual values; the planner keeps the result within
+// int64 (unsigned arithmetic: no undefined overflow).
+__device__ __forceinline__ long long expr_apply(uint8_t e, long long x, long long y) {
+  const unsigned long long a = (unsigned long long)x, b = (unsigned long long)y;
+  return (long long)(e == EXPR_ADD ? a + b : (e == EXPR_SUB ? a - b : a * b));
+}
+
 template <bool SEG>
 __device__ __forceinline__ void agg_item(const QueryDesc& q, const Smem& sm, const AggDesc& a, int slot,
                                          uint32_t gi, long long v, uint32_t len) {
@@ -953,7 +960,22 @@ __device__ __forceinline__ void phase_aggregate(const QueryDesc& q, const Smem& 
         }
         continue;
       }
-      if (a.col != last_col) {
+      if (a.expr != EXPR_NONE) {
+        // position-wise arithmetic on two columns (Section 6), in actual values
+        long long y[MI];
+        auto read = [&](const ColDesc& cc, long long* out) {
+          dispatch_col<SEG>(cc.enc, [&](auto et) {
+            constexpr int E = decltype(et)::value;
+#pragma unroll
+            for (int m = 0; m < MI; ++m) out[m] = col_raw<E>(cc, t, o[m]) + (cc.raw_is_offset ? cc.base : 0);
+          });
+        };
+        read(c, val);
+        read(q.cols[a.col2], y);
+#pragma unroll
+        for (int m = 0; m < MI; ++m) val[m] = expr_apply(a.expr, val[m], y[m]);
+        last_col = -1;
+      } else if (a.col != last_col) {
         dispatch_col<SEG>(c.enc, [&](auto et) {
           constexpr int E = decltype(et)::value;
           if (a.n32) {

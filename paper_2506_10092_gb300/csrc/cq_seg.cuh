@@ -213,15 +213,21 @@ __device__ inline void segment_update(const QueryDesc& q, const Smem& sm, const 
     gi = (uint32_t)g;
     atomicAdd(gword(q, 0, gi), L);
   }
+  // an aggregate's value on the segment: the column's, or the expression
+  // of two columns' values (Section 6: arithmetic on aligned columns)
+  auto aval = [&](const AggDesc& a) -> long long {
+    const long long x = value(a.col);
+    return a.expr == EXPR_NONE ? x : expr_apply(a.expr, x, value(a.col2));
+  };
   for (int ai = 0; ai < q.n_aggs; ++ai) {
     const AggDesc& a = q.aggs[ai];
     if (a.kind == AK_SUM) {
-      sum_add(q, sm, a, slot, gi, mul_s64(value(a.col), (long long)L));
+      sum_add(q, sm, a, slot, gi, mul_s64(aval(a), (long long)L));
     } else if (a.kind == AK_SUM2) {
       const long long v = value(a.col);   // |v| < 2^31 (planner)
       sum_add(q, sm, a, slot, gi, mul_s64(v * v, (long long)L));
     } else if (a.kind == AK_MIN || a.kind == AK_MAX) {
-      minmax_add(q, sm, a, slot, gi, value(a.col), a.kind == AK_MIN);
+      minmax_add(q, sm, a, slot, gi, aval(a), a.kind == AK_MIN);
     } else if (a.kind != AK_COUNT) {
       long long v;
       if (!listed(a.col, &v)) continue;

@@ -174,8 +174,10 @@ static bool plan_is_segment(const cq_table* t, const cq_plan* p) {
     if (!ok(p->preds[i].col)) return false;
   for (uint32_t i = 0; i < p->n_group_by && p->group_by; ++i)
     if (!ok(p->group_by[i])) return false;
-  for (uint32_t i = 0; i < p->n_aggs && p->aggs; ++i)
+  for (uint32_t i = 0; i < p->n_aggs && p->aggs; ++i) {
     if (p->aggs[i].op != CQ_COUNT && !ok(p->aggs[i].col)) return false;
+    if (p->aggs[i].op != CQ_COUNT && p->aggs[i].expr != CQ_EXPR_NONE && !ok(p->aggs[i].col2)) return false;
+  }
   return true;
 }
 
