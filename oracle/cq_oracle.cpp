@@ -218,6 +218,22 @@ int validate(const orc_column& c, uint64_t n_rows) {
     }
     case ORC_PLAIN:
       return ORC_OK;
+    case ORC_RLE_INDEX: {
+      // walk rows in order: each next row must start a run or be listed
+      uint64_t cursor = 0, i = 0, k = 0;
+      while (i < c.n_runs || k < c.nnz) {
+        if (i < c.n_runs && c.run_starts[i] == (int64_t)cursor) {
+          if (c.run_ends[i] <= c.run_starts[i]) return ORC_ERR_ARG;
+          cursor = (uint64_t)c.run_ends[i++];
+        } else if (k < c.nnz && c.positions[k] == (int64_t)cursor) {
+          ++cursor;
+          ++k;
+        } else {
+          return ORC_ERR_ARG;   // a gap, an overlap or an unsorted entry
+        }
+      }
+      return cursor == n_rows ? ORC_OK : ORC_ERR_ARG;
+    }
   }
   return ORC_ERR_ARG;
 }
@@ -256,6 +272,22 @@ extern "C" int orc_decode(const orc_column* cp, uint64_t rb, uint64_t re, int64_
     }
     case ORC_PLAIN:
       for (uint64_t r = rb; r < re; ++r) out[r - rb] = c.values[r];
+      return ORC_OK;
+    case ORC_RLE_INDEX:
+      // row r: the listed value, else the value of the run starting at or
+      // before r (validate() has checked that one of them covers r)
+      for (uint64_t r = rb; r < re; ++r) {
+        const int64_t* p = std::lower_bound(c.positions, c.positions + c.nnz, (int64_t)r);
+        if (p != c.positions + c.nnz && *p == (int64_t)r) {
+          out[r - rb] = c.idx_values[p - c.positions];
+          continue;
+        }
+        const int64_t* s = std::upper_bound(c.run_starts, c.run_starts + c.n_runs, (int64_t)r);
+        if (s == c.run_starts) return ORC_ERR_ARG;
+        const uint64_t i = (uint64_t)(s - c.run_starts) - 1;
+        if ((int64_t)r >= c.run_ends[i]) return ORC_ERR_ARG;
+        out[r - rb] = c.run_values[i];
+      }
       return ORC_OK;
   }
   return ORC_ERR_ARG;

@@ -27,7 +27,11 @@
 extern "C" {
 #endif
 
-enum { ORC_RLE = 1, ORC_DICT = 2, ORC_INDEX = 3, ORC_PACKED = 4, ORC_PLAIN = 5 };
+/* ORC_RLE_INDEX: the RLE + Index composite (Section 3.2): runs
+ * [run_starts[i], run_ends[i]) hold run_values[i] (starts and exclusive
+ * ends, sorted, disjoint), rows positions[k] hold idx_values[k]; runs and
+ * positions together cover every row exactly once. */
+enum { ORC_RLE = 1, ORC_DICT = 2, ORC_INDEX = 3, ORC_PACKED = 4, ORC_PLAIN = 5, ORC_RLE_INDEX = 6 };
 enum { ORC_LT = 0, ORC_LE, ORC_GT, ORC_GE, ORC_EQ, ORC_NE, ORC_BETWEEN, ORC_IN };
 enum { ORC_SUM = 0, ORC_COUNT, ORC_MIN, ORC_MAX, ORC_AVG,
        /* Section 7: STD and VAR from COUNT, SUM and the sum of squares; the
@@ -60,6 +64,9 @@ typedef struct {
   const uint8_t* dict_bytes;
   const uint64_t* dict_offsets;
   uint32_t n_entries;
+  /* RLE_INDEX: run starts (with run_values, run_ends, n_runs and the INDEX
+     fields idx_values, positions, nnz) */
+  const int64_t* run_starts;
 } orc_column;
 
 typedef struct {

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-ORC_RLE, ORC_DICT, ORC_INDEX, ORC_PACKED, ORC_PLAIN = 1, 2, 3, 4, 5
+ORC_RLE, ORC_DICT, ORC_INDEX, ORC_PACKED, ORC_PLAIN, ORC_RLE_INDEX = 1, 2, 3, 4, 5, 6
 _OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7}
 _AGGS = {"sum": 0, "count": 1, "min": 2, "max": 3, "avg": 4, "var_pop": 5, "var_samp": 6, "std_pop": 7,
          "std_samp": 8}
@@ -33,6 +33,7 @@ class _Col(C.Structure):
         ("idx_values", C.c_void_p), ("positions", C.c_void_p), ("nnz", C.c_uint64), ("default_value", C.c_int64),
         ("values", C.c_void_p),
         ("dict_bytes", C.c_void_p), ("dict_offsets", C.c_void_p), ("n_entries", C.c_uint32),
+        ("run_starts", C.c_void_p),
     ]
 
 
@@ -108,7 +109,8 @@ class _Marshal:
 
     def column(self, c) -> _Col:
         s = _Col()
-        s.enc = {"rle": ORC_RLE, "dict": ORC_DICT, "index": ORC_INDEX, "packed": ORC_PACKED, "plain": ORC_PLAIN}[c.enc]
+        s.enc = {"rle": ORC_RLE, "dict": ORC_DICT, "index": ORC_INDEX, "packed": ORC_PACKED, "plain": ORC_PLAIN,
+                 "rle_index": ORC_RLE_INDEX}[c.enc]
         s.n_rows = int(c.n_rows)
         if c.enc == "rle":
             v, e = self.k(_i64(c.run_values)), self.k(_i64(c.run_ends))
@@ -128,6 +130,11 @@ class _Marshal:
         elif c.enc == "plain":
             v = self.k(_i64(c.values))
             s.values = _p(v)
+        elif c.enc == "rle_index":
+            rv, rs, re_ = self.k(_i64(c.run_values)), self.k(_i64(c.run_starts)), self.k(_i64(c.run_ends))
+            s.run_values, s.run_starts, s.run_ends, s.n_runs = _p(rv), _p(rs), _p(re_), int(rs.shape[0])
+            v, p = self.k(_i64(c.values)), self.k(_i64(c.positions))
+            s.idx_values, s.positions, s.nnz = _p(v), _p(p), int(p.shape[0])
         return s
 
     def pred(self, p) -> _Pred:

@@ -54,6 +54,20 @@ class Index:
 
 
 @dataclasses.dataclass
+class RLEIndex:
+    """RLE + Index composite (Section 3.2): runs [run_starts[i], run_ends[i])
+    hold run_values[i]; rows positions[k] hold values[k]; together they cover
+    every row exactly once."""
+    run_values: np.ndarray          # [R]
+    run_starts: np.ndarray          # [R], sorted
+    run_ends: np.ndarray            # [R], exclusive
+    values: np.ndarray              # [nnz]
+    positions: np.ndarray           # [nnz], sorted unique
+    n_rows: int
+    enc: str = "rle_index"
+
+
+@dataclasses.dataclass
 class Dict:
     strings: List[bytes]            # sorted bytewise, unique
     words: np.ndarray               # uint32 packed codes
@@ -263,6 +277,23 @@ def zipf_ranks(rng: np.random.Generator, n: int, n_ranks: int, s: float, chunk: 
 # --------------------------------------------------------------------------
 # column builders
 # --------------------------------------------------------------------------
+def rle_index_encode(values: np.ndarray, min_run: int) -> RLEIndex:
+    """RLE + Index of a value sequence: runs of equal values at least
+    min_run long are RLE runs, the rows of shorter runs are index entries."""
+    v = np.asarray(values, dtype=np.int64)
+    n = int(v.shape[0])
+    if n == 0:
+        z = np.zeros(0, np.int64)
+        return RLEIndex(z, z, z, z, z, 0)
+    brk = np.flatnonzero(v[1:] != v[:-1]) + 1
+    starts = np.concatenate([[0], brk]).astype(np.int64)
+    ends = np.concatenate([brk, [n]]).astype(np.int64)
+    long_ = (ends - starts) >= min_run
+    pos = np.concatenate([np.arange(s, e, dtype=np.int64) for s, e in zip(starts[~long_], ends[~long_])]) \
+        if (~long_).any() else np.zeros(0, np.int64)
+    return RLEIndex(v[starts[long_]], starts[long_], ends[long_], v[pos], pos, n)
+
+
 def make_rle(rng, n_rows, mean_run, lo, hi, val_dtype=np.int32, end_dtype=None) -> RLE:
     ends = geometric_ends(rng, n_rows, mean_run, end_dtype)
     vals = rng.integers(lo, hi + 1, size=ends.shape[0], dtype=np.int64).astype(val_dtype)
