@@ -98,6 +98,25 @@ int cq_column_create_rle(cq_ctx* ctx, cq_dtype val_t, const void* run_values,
                          cq_dtype end_t, const void* run_ends, uint64_t n_runs,
                          uint64_t n_rows, uint32_t mem_flags, cq_column** out);
 
+/* RLE + Index composite (Section 3.2 Composite Encodings): RLE runs for the
+ * column's pure stretches, Index entries for its scattered rows.  Run i holds
+ * run_values[i] on rows [run_starts[i], run_ends[i]) (exclusive ends); row
+ * positions[k] holds values[k].  Runs are sorted and disjoint, positions
+ * sorted and unique, and runs and positions together cover rows 0 ..
+ * n_rows - 1 exactly once.  All buffers are HOST memory (copied); val_t for
+ * run_values and values, pos_t for starts, ends and positions (CQ_I32 /
+ * CQ_I64).  The library merges the two parts in row order into one RLE
+ * column whose unit runs are the listed rows (cq_column_encoding reports 1,
+ * RLE): an RLE run here is a value and an end, a listed row a value
+ * and a position, so the merged column is as large as the composite.
+ * Errors: CQ_ERR_SIZE_MISMATCH (a row neither started by the next run nor
+ * the next listed row -- a gap, an overlap or unsorted input -- or coverage
+ * other than n_rows), CQ_ERR_UNSORTED (an empty run), CQ_ERR_INVALID_ARG. */
+int cq_column_create_rle_index(cq_ctx* ctx, cq_dtype val_t, cq_dtype pos_t, const void* run_values,
+                               const void* run_starts, const void* run_ends, uint64_t n_runs,
+                               const void* values, const void* positions, uint64_t nnz, uint64_t n_rows,
+                               cq_column** out);
+
 /* Dictionary-encoded strings (Section 2.1: strings are value- and
  * dictionary-encoded to numeric codes).  The dictionary -- always HOST memory
  * -- holds n_entries strings, entry i being dict_bytes[dict_offsets[i] ..

@@ -88,6 +88,8 @@ _SIGS = {
     "cq_ctx_num_sms": [_VP, C.POINTER(C.c_uint32)],
     "cq_last_error": [],
     "cq_column_create_rle": [_VP, C.c_int, _VP, C.c_int, _VP, C.c_uint64, C.c_uint64, C.c_uint32, C.POINTER(_VP)],
+    "cq_column_create_rle_index": [_VP, C.c_int, C.c_int, _VP, _VP, _VP, C.c_uint64, _VP, _VP, C.c_uint64,
+                                   C.c_uint64, C.POINTER(_VP)],
     "cq_column_create_dict": [_VP, _VP, _VP, C.c_uint32, _VP, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32,
                               C.POINTER(_VP)],
     "cq_column_create_index": [_VP, C.c_int, _VP, C.c_int, _VP, C.c_uint64, C.c_int64, C.c_uint64, C.c_uint32,
@@ -246,6 +248,19 @@ def cq_column_create_rle(ctx, run_values, run_ends, n_rows: int) -> Handle:
     return Handle(out.value, lib.cq_column_destroy, [ctx] + ([v, e] if _is_dev(v) else []))
 
 
+def cq_column_create_rle_index(ctx, run_values, run_starts, run_ends, values, positions, n_rows: int) -> Handle:
+    """Host arrays; values share one dtype, starts / ends / positions another."""
+    rv = np.ascontiguousarray(run_values)
+    vv = np.ascontiguousarray(values, dtype=rv.dtype)
+    rs = np.ascontiguousarray(run_starts)
+    re_ = np.ascontiguousarray(run_ends, dtype=rs.dtype)
+    ps = np.ascontiguousarray(positions, dtype=rs.dtype)
+    out = C.c_void_p()
+    _check(lib.cq_column_create_rle_index(ctx.ptr, _dt(rv), _dt(rs), _ptr(rv), _ptr(rs), _ptr(re_), int(rs.shape[0]),
+                                          _ptr(vv), _ptr(ps), int(ps.shape[0]), int(n_rows), C.byref(out)))
+    return Handle(out.value, lib.cq_column_destroy, [ctx])
+
+
 def cq_column_create_dict(ctx, strings: Sequence[bytes], packed_codes, bit_width: int, n_rows: int) -> Handle:
     w = _contig(packed_codes)
     blob = b"".join(strings)
@@ -281,6 +296,12 @@ def cq_column_create_plain(ctx, values) -> Handle:
     out = C.c_void_p()
     _check(lib.cq_column_create_plain(ctx.ptr, _dt(v), _ptr(v), int(v.shape[0]), _mem(v), C.byref(out)))
     return Handle(out.value, lib.cq_column_destroy, [ctx] + ([v] if _is_dev(v) else []))
+
+
+def cq_column_encoding(col) -> int:
+    e = C.c_uint32()
+    _check(lib.cq_column_encoding(col.ptr, C.byref(e)))
+    return e.value
 
 
 def cq_column_device_bytes(col) -> int:
@@ -569,6 +590,9 @@ def column_from(ctx, col, device: bool = False) -> Handle:
                                           CQ_I64 if col.logical == "i64" else CQ_I32)
     if col.enc == "plain":
         return cq_column_create_plain(ctx, t(col.values))
+    if col.enc == "rle_index":   # host arrays only (the library merges them on the host)
+        return cq_column_create_rle_index(ctx, col.run_values, col.run_starts, col.run_ends, col.values,
+                                          col.positions, col.n_rows)
     raise ValueError(col.enc)
 
 

@@ -284,6 +284,68 @@ extern "C" int cq_column_create_rle(cq_ctx* ctx, cq_dtype val_t, const void* run
   return finish_or_release(c, out);
 }
 
+// RLE + Index composite (Section 3.2).  The runs and the listed rows are
+// merged in row order into one RLE column whose unit runs are the listed
+// rows: here a run costs a value and an end, as a listed row costs a value
+// and a position, so the merged column is as large as the composite.
+extern "C" int cq_column_create_rle_index(cq_ctx* ctx, cq_dtype val_t, cq_dtype pos_t, const void* run_values,
+                                          const void* run_starts, const void* run_ends, uint64_t n_runs,
+                                          const void* values, const void* positions, uint64_t nnz, uint64_t n_rows,
+                                          cq_column** out) {
+  clear_error();
+  if (!ctx || !out) return set_error(CQ_ERR_INVALID_ARG, "NULL context or output");
+  if (!dtype_ok(val_t) || !dtype_ok(pos_t)) return set_error(CQ_ERR_INVALID_ARG, "bad dtype");
+  if ((n_runs && (!run_values || !run_starts || !run_ends)) || (nnz && (!values || !positions)))
+    return set_error(CQ_ERR_INVALID_ARG, "NULL buffer");
+  auto rd = [](const void* p, cq_dtype t, uint64_t i) -> int64_t {
+    return t == CQ_I32 ? (int64_t) static_cast<const int32_t*>(p)[i] : static_cast<const int64_t*>(p)[i];
+  };
+  std::vector<int64_t> mv, me;
+  mv.reserve(n_runs + nnz);
+  me.reserve(n_runs + nnz);
+  // rows in order: the next row must start a run or be listed
+  uint64_t cursor = 0, i = 0, k = 0;
+  while (i < n_runs || k < nnz) {
+    if (i < n_runs && rd(run_starts, pos_t, i) == (int64_t)cursor) {
+      const int64_t e = rd(run_ends, pos_t, i);
+      if (e <= (int64_t)cursor)
+        return set_error(CQ_ERR_UNSORTED, "run %llu is empty or ends before it starts", (unsigned long long)i);
+      mv.push_back(rd(run_values, val_t, i));
+      me.push_back(e);
+      cursor = (uint64_t)e;
+      ++i;
+    } else if (k < nnz && rd(positions, pos_t, k) == (int64_t)cursor) {
+      mv.push_back(rd(values, val_t, k));
+      me.push_back((int64_t)cursor + 1);
+      ++cursor;
+      ++k;
+    } else {
+      return set_error(CQ_ERR_SIZE_MISMATCH,
+                       "row %llu is neither the start of the next run nor the next listed row (a gap, an overlap "
+                       "or unsorted input)", (unsigned long long)cursor);
+    }
+    if (cursor > n_rows)
+      return set_error(CQ_ERR_SIZE_MISMATCH, "runs and listed rows reach past n_rows %llu", (unsigned long long)n_rows);
+  }
+  if (cursor != n_rows)
+    return set_error(CQ_ERR_SIZE_MISMATCH, "runs and listed rows cover %llu of %llu rows", (unsigned long long)cursor,
+                     (unsigned long long)n_rows);
+  // the RLE column keeps the value type; ends in 32 bits when they fit
+  std::vector<int32_t> v32, e32;
+  const void* vp = mv.data();
+  const void* ep = me.data();
+  if (val_t == CQ_I32) {
+    v32.assign(mv.begin(), mv.end());
+    vp = v32.data();
+  }
+  const cq_dtype end_t = n_rows <= (uint64_t)INT_MAX ? CQ_I32 : CQ_I64;
+  if (end_t == CQ_I32) {
+    e32.assign(me.begin(), me.end());
+    ep = e32.data();
+  }
+  return cq_column_create_rle(ctx, val_t, vp, end_t, ep, mv.size(), n_rows, CQ_MEM_HOST_COPY, out);
+}
+
 extern "C" int cq_column_create_dict(cq_ctx* ctx, const char* dict_bytes, const uint64_t* dict_offsets,
                                      uint32_t n_entries, const uint32_t* packed_codes, uint64_t n_words,
                                      uint32_t bit_width, uint64_t n_rows, uint32_t mem_flags, cq_column** out) {
