@@ -218,6 +218,15 @@ int validate(const orc_column& c, uint64_t n_rows) {
     }
     case ORC_PLAIN:
       return ORC_OK;
+    case ORC_PACKED_INDEX: {
+      if (c.bit_width < 1 || c.bit_width > 64) return ORC_ERR_ARG;
+      if (c.n_words < (n_rows * c.bit_width + 31) / 32) return ORC_ERR_ARG;
+      for (uint64_t i = 0; i < c.nnz; ++i) {
+        if (c.positions[i] < 0 || (uint64_t)c.positions[i] >= n_rows) return ORC_ERR_ARG;
+        if (i && c.positions[i] <= c.positions[i - 1]) return ORC_ERR_ARG;
+      }
+      return ORC_OK;
+    }
     case ORC_RLE_INDEX: {
       // walk rows in order: each next row must start a run or be listed
       uint64_t cursor = 0, i = 0, k = 0;
@@ -273,6 +282,14 @@ extern "C" int orc_decode(const orc_column* cp, uint64_t rb, uint64_t re, int64_
     case ORC_PLAIN:
       for (uint64_t r = rb; r < re; ++r) out[r - rb] = c.values[r];
       return ORC_OK;
+    case ORC_PACKED_INDEX: {
+      // the packed field, replaced by the listed value on listed rows
+      for (uint64_t r = rb; r < re; ++r)
+        out[r - rb] = (int64_t)((uint64_t)c.base + read_field(c.words, c.n_words, r, c.bit_width));
+      uint64_t k = std::lower_bound(c.positions, c.positions + c.nnz, (int64_t)rb) - c.positions;
+      for (; k < c.nnz && (uint64_t)c.positions[k] < re; ++k) out[c.positions[k] - rb] = c.idx_values[k];
+      return ORC_OK;
+    }
     case ORC_RLE_INDEX:
       // row r: the listed value, else the value of the run starting at or
       // before r (validate() has checked that one of them covers r)

@@ -31,7 +31,12 @@ extern "C" {
  * [run_starts[i], run_ends[i]) hold run_values[i] (starts and exclusive
  * ends, sorted, disjoint), rows positions[k] hold idx_values[k]; runs and
  * positions together cover every row exactly once. */
-enum { ORC_RLE = 1, ORC_DICT = 2, ORC_INDEX = 3, ORC_PACKED = 4, ORC_PLAIN = 5, ORC_RLE_INDEX = 6 };
+/* ORC_PACKED_INDEX: the Plain + Index composite (Section 3.2, outlier
+ * patching): a narrow bit-packed part (the PACKED fields: words, bit_width,
+ * base) holds one field per row, and the rows positions[k] (sorted, unique)
+ * hold idx_values[k] instead; the packed fields at those rows are never read. */
+enum { ORC_RLE = 1, ORC_DICT = 2, ORC_INDEX = 3, ORC_PACKED = 4, ORC_PLAIN = 5, ORC_RLE_INDEX = 6,
+       ORC_PACKED_INDEX = 7 };
 enum { ORC_LT = 0, ORC_LE, ORC_GT, ORC_GE, ORC_EQ, ORC_NE, ORC_BETWEEN, ORC_IN };
 enum { ORC_SUM = 0, ORC_COUNT, ORC_MIN, ORC_MAX, ORC_AVG,
        /* Section 7: STD and VAR from COUNT, SUM and the sum of squares; the

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-ORC_RLE, ORC_DICT, ORC_INDEX, ORC_PACKED, ORC_PLAIN, ORC_RLE_INDEX = 1, 2, 3, 4, 5, 6
+ORC_RLE, ORC_DICT, ORC_INDEX, ORC_PACKED, ORC_PLAIN, ORC_RLE_INDEX, ORC_PACKED_INDEX = 1, 2, 3, 4, 5, 6, 7
 _OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7}
 _AGGS = {"sum": 0, "count": 1, "min": 2, "max": 3, "avg": 4, "var_pop": 5, "var_samp": 6, "std_pop": 7,
          "std_samp": 8}
@@ -110,7 +110,7 @@ class _Marshal:
     def column(self, c) -> _Col:
         s = _Col()
         s.enc = {"rle": ORC_RLE, "dict": ORC_DICT, "index": ORC_INDEX, "packed": ORC_PACKED, "plain": ORC_PLAIN,
-                 "rle_index": ORC_RLE_INDEX}[c.enc]
+                 "rle_index": ORC_RLE_INDEX, "packed_index": ORC_PACKED_INDEX}[c.enc]
         s.n_rows = int(c.n_rows)
         if c.enc == "rle":
             v, e = self.k(_i64(c.run_values)), self.k(_i64(c.run_ends))
@@ -130,6 +130,11 @@ class _Marshal:
         elif c.enc == "plain":
             v = self.k(_i64(c.values))
             s.values = _p(v)
+        elif c.enc == "packed_index":
+            w = self.k(np.ascontiguousarray(c.words, dtype=np.uint32))
+            s.words, s.n_words, s.bit_width, s.base = _p(w), int(w.shape[0]), int(c.bit_width), int(c.base)
+            v, p = self.k(_i64(c.values)), self.k(_i64(c.positions))
+            s.idx_values, s.positions, s.nnz = _p(v), _p(p), int(p.shape[0])
         elif c.enc == "rle_index":
             rv, rs, re_ = self.k(_i64(c.run_values)), self.k(_i64(c.run_starts)), self.k(_i64(c.run_ends))
             s.run_values, s.run_starts, s.run_ends, s.n_runs = _p(rv), _p(rs), _p(re_), int(rs.shape[0])

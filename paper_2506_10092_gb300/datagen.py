@@ -68,6 +68,20 @@ class RLEIndex:
 
 
 @dataclasses.dataclass
+class PackedIndex:
+    """Plain + Index composite (Section 3.2, outlier patching): a narrow
+    bit-packed field per row (base + field) and the outliers listed by
+    position; the fields at listed rows hold anything and are never read."""
+    words: np.ndarray               # uint32 packed fields
+    bit_width: int
+    base: int
+    values: np.ndarray              # [nnz] outliers
+    positions: np.ndarray           # [nnz], sorted unique
+    n_rows: int
+    enc: str = "packed_index"
+
+
+@dataclasses.dataclass
 class Dict:
     strings: List[bytes]            # sorted bytewise, unique
     words: np.ndarray               # uint32 packed codes
@@ -292,6 +306,22 @@ def rle_index_encode(values: np.ndarray, min_run: int) -> RLEIndex:
     pos = np.concatenate([np.arange(s, e, dtype=np.int64) for s, e in zip(starts[~long_], ends[~long_])]) \
         if (~long_).any() else np.zeros(0, np.int64)
     return RLEIndex(v[starts[long_]], starts[long_], ends[long_], v[pos], pos, n)
+
+
+def packed_index_encode(values: np.ndarray, bit_width: int, fill: Optional[np.ndarray] = None) -> PackedIndex:
+    """Plain + Index of a value sequence: the values in [base, base +
+    2^bit_width) around the median (centering) are packed, the rest listed;
+    the packed fields at listed rows take `fill` (default 0)."""
+    v = np.asarray(values, dtype=np.int64)
+    n = int(v.shape[0])
+    base = int(np.median(v)) - (1 << (bit_width - 1)) if n else 0
+    off = v.astype(object) - base
+    inl = np.array([0 <= int(x) < (1 << bit_width) for x in off], dtype=bool)
+    pos = np.flatnonzero(~inl).astype(np.int64)
+    fields = np.where(inl, off, 0).astype(np.uint64) if n else np.zeros(0, np.uint64)
+    if fill is not None and pos.size:
+        fields[pos] = np.asarray(fill, dtype=np.uint64)[:pos.size] & np.uint64((1 << bit_width) - 1)
+    return PackedIndex(pack_bits(fields, bit_width), bit_width, base, v[pos], pos, n)
 
 
 def make_rle(rng, n_rows, mean_run, lo, hi, val_dtype=np.int32, end_dtype=None) -> RLE:

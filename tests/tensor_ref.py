@@ -41,6 +41,11 @@ def decode(col) -> np.ndarray:
         return decode_bits(col.words, col.bit_width, col.n_rows)
     if col.enc == "plain":
         return np.asarray(col.values, dtype=np.int64).astype(object)
+    if col.enc == "packed_index":
+        out = decode_bits(col.words, col.bit_width, col.n_rows) + int(col.base)
+        for v, p in zip(np.asarray(col.values).tolist(), np.asarray(col.positions).tolist()):
+            out[p] = int(v)
+        return out
     if col.enc == "rle_index":
         out = np.empty(col.n_rows, dtype=object)
         for v, s, e in zip(np.asarray(col.run_values).tolist(), np.asarray(col.run_starts).tolist(),

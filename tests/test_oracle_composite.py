@@ -1,8 +1,12 @@
-"""Pins of the oracle's RLE + Index composite (Section 3.2 Composite
-Encodings: runs for the pure stretches, Index for the scattered rows, the two
-disjoint).  The pins: the paper's [A,A,A,A,B,C,D] example, decoding against
-the plain sequence, queries on the composite against the same queries on the
-plain column, and the rejection of gaps and overlaps."""
+"""Pins of the oracle's composite encodings (Section 3.2 Composite
+Encodings).  RLE + Index (runs for the pure stretches, Index for the
+scattered rows, the two disjoint): the paper's [A,A,A,A,B,C,D] example,
+decoding against the plain sequence, queries on the composite against the
+same queries on the plain column, the rejection of gaps and overlaps.
+Plain + Index (a narrow packed part, outliers listed): the paper's
+[1, 2, 3, 10^10, 10^10] example with garbage in the ignored packed slots,
+random columns with outliers decoded and queried against the plain column,
+unsorted positions rejected."""
 import json
 import os
 
@@ -80,3 +84,47 @@ def test_gaps_and_overlaps_are_rejected(oracle_mod):
     for c in bad:
         with pytest.raises(ValueError, match="status -1"):
             oracle_mod.query(dg.Table([c], c.n_rows), dg.Plan([], [], [dg.Agg("sum", 0)]))
+
+
+# ---------------------------------------------------------------- Plain + Index
+def test_plain_index_paper_example(oracle_mod):
+    """[1, 2, 3, 10^10, 10^10]: the regular values in a narrow packed part,
+    the outliers at 3 and 4 listed; the packed fields at the listed rows hold
+    garbage that decoding never reads."""
+    g = json.load(open(os.path.join(GOLDEN, "plain_index_example.json")))
+    n = len(g["column"])
+    fields = np.array(g["plain"] + [7, 5], dtype=np.uint64)        # 7, 5: the ignored slots
+    col = dg.PackedIndex(dg.pack_bits(fields, 3), 3, 0, np.array(g["index"]["v"], np.int64),
+                         np.array(g["index"]["p"], np.int64), n)
+    assert oracle_mod.decode(col).tolist() == g["column"]
+    enc = dg.packed_index_encode(np.array(g["column"]), 3)
+    assert enc.positions.tolist() == g["index"]["p"] and enc.values.tolist() == g["index"]["v"]
+    assert oracle_mod.decode(enc).tolist() == g["column"]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_plain_index_queries_match_the_plain_column(oracle_mod, seed):
+    rng = np.random.default_rng(950 + seed)
+    n = int(rng.integers(1, 3000))
+    seqs = []
+    for _ in range(3):
+        v = rng.integers(-100, 100, size=n).astype(np.int64)
+        out = rng.random(n) < float(rng.choice([0.0, 0.01, 0.2]))
+        v[out] = rng.integers(-(1 << 40), 1 << 40, size=int(out.sum()))
+        seqs.append(v)
+    w = int(rng.integers(8, 12))
+    comp = dg.Table([dg.packed_index_encode(s, w, fill=rng.integers(0, 1 << w, size=n)) for s in seqs], n)
+    plain = dg.Table([dg.Plain(s) for s in seqs], n)
+    for c, s in zip(comp.columns, seqs):
+        assert oracle_mod.decode(c).tolist() == s.tolist()
+    plan = random_plan(rng, plain)
+    a, b = oracle_mod.query(comp, plan), oracle_mod.query(plain, plan)
+    assert [x.tolist() for x in a.keys] == [x.tolist() for x in b.keys]
+    assert [x.tolist() for x in a.aggs] == [x.tolist() for x in b.aggs]
+    assert_same(a, tensor_ref.query(comp, plan))
+
+
+def test_plain_index_unsorted_positions_are_rejected(oracle_mod):
+    col = dg.PackedIndex(dg.pack_bits(np.zeros(5, np.uint64), 2), 2, 0, np.array([9, 8]), np.array([3, 1]), 5)
+    with pytest.raises(ValueError, match="status -1"):
+        oracle_mod.query(dg.Table([col], 5), dg.Plan([], [], [dg.Agg("sum", 0)]))
