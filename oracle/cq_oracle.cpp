@@ -739,3 +739,41 @@ extern "C" int orc_align(uint32_t k, const int64_t* const* run_ends, const uint6
         ridx[j * all.size() + s] = std::lower_bound(run_ends[j], run_ends[j] + n_runs[j], all[s]) - run_ends[j];
   return ORC_OK;
 }
+
+// Get Join Index: the definition written out -- for each left row in order,
+// the right rows holding the same value, in order.
+extern "C" int orc_join_index(const orc_column* left, const orc_column* right, uint64_t* n_pairs,
+                              int64_t* left_rows, int64_t* right_rows) {
+  if (!left || !right || !n_pairs) return ORC_ERR_ARG;
+  if (validate(*left, left->n_rows) != ORC_OK || validate(*right, right->n_rows) != ORC_OK) return ORC_ERR_ARG;
+  std::vector<int64_t> lv(left->n_rows), rv(right->n_rows);
+  if (orc_decode(left, 0, left->n_rows, lv.data()) != ORC_OK) return ORC_ERR_ARG;
+  if (orc_decode(right, 0, right->n_rows, rv.data()) != ORC_OK) return ORC_ERR_ARG;
+  std::map<int64_t, std::vector<int64_t>> rows_of;   // right value -> its rows, ascending
+  for (uint64_t j = 0; j < rv.size(); ++j) rows_of[rv[j]].push_back((int64_t)j);
+  uint64_t n = 0;
+  for (uint64_t i = 0; i < lv.size(); ++i) {
+    auto it = rows_of.find(lv[i]);
+    if (it == rows_of.end()) continue;
+    for (int64_t j : it->second) {
+      if (left_rows) left_rows[n] = (int64_t)i;
+      if (right_rows) right_rows[n] = j;
+      ++n;
+    }
+  }
+  *n_pairs = n;
+  return ORC_OK;
+}
+
+// Apply Join Index: gather the column's values at the given rows.
+extern "C" int orc_apply_join_index(const orc_column* c, const int64_t* rows, uint64_t n, int64_t* out) {
+  if (!c || (n && (!rows || !out))) return ORC_ERR_ARG;
+  if (validate(*c, c->n_rows) != ORC_OK) return ORC_ERR_ARG;
+  std::vector<int64_t> v(c->n_rows);
+  if (orc_decode(c, 0, c->n_rows, v.data()) != ORC_OK) return ORC_ERR_ARG;
+  for (uint64_t k = 0; k < n; ++k) {
+    if (rows[k] < 0 || (uint64_t)rows[k] >= c->n_rows) return ORC_ERR_ARG;
+    out[k] = v[rows[k]];
+  }
+  return ORC_OK;
+}

@@ -156,6 +156,19 @@ double orc_div_round(const uint64_t* n4, const uint64_t* d2);
 int orc_align(uint32_t k, const int64_t* const* run_ends, const uint64_t* n_runs,
               uint64_t n_rows, uint64_t* n_segments, int64_t* seg_ends, int64_t* ridx);
 
+/* Get Join Index (the paper's Join Operations section): every pair (i, j) of
+ * rows with left[i] == right[j] (values as decoded; dictionary columns by
+ * code), in ascending (i, j) order.  The paper's Join Index tensors hold the
+ * same pairs in whatever order the hash join yields them.  Call once with
+ * left_rows and right_rows NULL to get the count, then with buffers of that
+ * size. */
+int orc_join_index(const orc_column* left, const orc_column* right, uint64_t* n_pairs, int64_t* left_rows,
+                   int64_t* right_rows);
+
+/* Apply Join Index: out[k] = the value of column c at row rows[k] (rows in
+ * any order, with repeats). */
+int orc_apply_join_index(const orc_column* c, const int64_t* rows, uint64_t n, int64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

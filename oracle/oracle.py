@@ -85,6 +85,9 @@ def lib():
             L.orc_div_round.restype = C.c_double
             L.orc_align.argtypes = [C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint64,
                                     C.POINTER(C.c_uint64), C.c_void_p, C.c_void_p]
+            L.orc_join_index.argtypes = [C.POINTER(_Col), C.POINTER(_Col), C.POINTER(C.c_uint64), C.c_void_p,
+                                         C.c_void_p]
+            L.orc_apply_join_index.argtypes = [C.POINTER(_Col), C.c_void_p, C.c_uint64, C.c_void_p]
             _lib = L
     return _lib
 
@@ -260,3 +263,32 @@ def div_round(n: int, d: int) -> float:
     nn = np.array([(n >> (64 * i)) & (2**64 - 1) for i in range(4)], dtype=np.uint64)
     dd = np.array([(d >> (64 * i)) & (2**64 - 1) for i in range(2)], dtype=np.uint64)
     return float(L.orc_div_round(nn.ctypes.data, dd.ctypes.data))
+
+
+def join_index(left, right):
+    """(left rows, right rows) of every pair with equal values, ascending."""
+    L = lib()
+    m = _Marshal()
+    a, b = m.column(left), m.column(right)
+    n = C.c_uint64()
+    rc = L.orc_join_index(C.byref(a), C.byref(b), C.byref(n), None, None)
+    if rc != 0:
+        raise ValueError(f"oracle rejected the join (status {rc})")
+    li = np.empty(int(n.value), dtype=np.int64)
+    ri = np.empty(int(n.value), dtype=np.int64)
+    if n.value:
+        L.orc_join_index(C.byref(a), C.byref(b), C.byref(n), li.ctypes.data, ri.ctypes.data)
+    return li, ri
+
+
+def apply_join_index(col, rows):
+    L = lib()
+    m = _Marshal()
+    s = m.column(col)
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty(r.shape[0], dtype=np.int64)
+    rc = L.orc_apply_join_index(C.byref(s), r.ctypes.data if r.size else None, int(r.shape[0]),
+                                out.ctypes.data if out.size else None)
+    if rc != 0:
+        raise ValueError(f"oracle rejected the rows (status {rc})")
+    return out
